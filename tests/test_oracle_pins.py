@@ -1,0 +1,536 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+Nothing here re-types the oracle's own loops.  Each check compares the oracle
+with an independent statement of the same result:
+
+* eq. 6 and its printed roots (Section 2), and the mode shapes of eq. 4;
+* the normal-mode solution (eq. 7) of eq. 3 and its exact value at t = 10 s;
+* the exact discrete map of classical RK4 on a linear system: per normal mode
+  the state is multiplied by R(i theta) = 1 + z + z^2/2 + z^3/6 + z^4/24 at
+  z = i theta each step, so after n steps it is a closed form in R^n;
+* brute force on tiny systems: y_n = P(hA)^n y_0 with P the RK4 polynomial and
+  A the first-order system matrix assembled from a different description of
+  the springs (extension map) than the oracle uses (force per mass);
+* the uniform fixed-free chain's closed-form spectrum at s = 1024;
+* energy laws: the modal energy decays as |R|^(2n), so the drift scales as h^5;
+* invariances: linearity, time/stiffness scaling, instance permutation;
+* planted mistakes: mutant builds of the oracle must fail these pins.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_02207_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+# --------------------------------------------------------------------------
+# Independent closed forms (test side)
+# --------------------------------------------------------------------------
+
+def rk4_amplification(theta):
+    """R(i theta): the classical RK4 stability polynomial on the imaginary axis."""
+    z = 1j * np.asarray(theta, dtype=np.float64)
+    return 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def rk4_log_modulus(theta):
+    """log |R(i theta)|, from |R|^2 = 1 - theta^6/72 + theta^8/576 (expand re^2 + im^2).
+
+    Taking log(abs(R)) directly loses everything at small theta, where
+    1 - |R| ~ theta^6/144 is below the FP64 spacing near 1.
+    """
+    t = np.asarray(theta, dtype=np.float64)
+    return 0.5 * np.log1p(-t ** 6 / 72 + t ** 8 / 576)
+
+
+def rk4_power(theta, n):
+    """R(i theta)^n via polar form (|R|^n, n arg R)."""
+    R = rk4_amplification(theta)
+    mag = np.exp(n * rk4_log_modulus(theta))
+    ang = n * np.angle(R)
+    return mag * np.cos(ang), mag * np.sin(ang)
+
+
+def test_rk4_modulus_expansion():
+    theta = np.array([0.05, 0.3, 1.0, 2.0, 2.8])
+    R = rk4_amplification(theta)
+    assert np.allclose(np.exp(rk4_log_modulus(theta)), np.abs(R), rtol=1e-14)
+
+
+def modal_solution(Phi, omega, x0, h, n):
+    """Exact discrete RK4 state after n steps from (x0, 0) for x'' = -B x.
+
+    Phi: columns are M-orthonormal mode shapes, omega the natural frequencies,
+    x0 = Phi a.  Returns x_n, v_n.
+    """
+    a = np.linalg.solve(Phi, x0)
+    re, im = rk4_power(omega * h, n)
+    x = Phi @ (a * re)
+    v = Phi @ (-a * omega * im)
+    return x, v
+
+
+def extension_matrix(s):
+    """Spring extensions e = D x of a fixed-free chain: e_0 = x_0, e_i = x_i - x_{i-1}."""
+    D = np.eye(s)
+    D[np.arange(1, s), np.arange(0, s - 1)] = -1.0
+    return D
+
+
+def chain_K_from_energy(springs):
+    """K = D^T diag(C) D, the Hessian of the spring energy 1/2 sum C_i e_i^2."""
+    C = np.asarray(springs, dtype=np.float64).ravel()
+    D = extension_matrix(C.size)
+    return D.T @ np.diag(C) @ D
+
+
+def rk4_matrix(A, h):
+    """P(hA) = I + hA + (hA)^2/2 + (hA)^3/6 + (hA)^4/24."""
+    Z = h * A
+    I = np.eye(A.shape[0])
+    Z2 = Z @ Z
+    Z3 = Z2 @ Z
+    Z4 = Z3 @ Z
+    return I + Z + Z2 / 2 + Z3 / 6 + Z4 / 24
+
+
+def first_order_matrix(M, K):
+    s = M.shape[0]
+    A = np.zeros((2 * s, 2 * s))
+    A[:s, s:] = np.eye(s)
+    A[s:, :s] = -np.linalg.solve(M, K)
+    return A
+
+
+def relmax(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# --------------------------------------------------------------------------
+# Eq. 6: characteristic equation and printed roots
+# --------------------------------------------------------------------------
+
+def eq3_modes(m=2.0, C=2025.0):
+    """Closed form of eqs. 4-6 for eq. 3: omega^2 = (C/m)(3 -+ sqrt 5)/2, mode shapes B/A."""
+    w_hi = math.sqrt(C / m * (3 + math.sqrt(5)) / 2)
+    w_lo = math.sqrt(C / m * (3 - math.sqrt(5)) / 2)
+    # eq. 4 with lambda^2 = -omega^2:  B/A = 2 - m omega^2 / C
+    r_hi = 2 - m * w_hi ** 2 / C
+    r_lo = 2 - m * w_lo ** 2 / C
+    return w_hi, w_lo, r_hi, r_lo
+
+
+def test_eq6_closed_form_solves_characteristic_polynomial():
+    g = read_golden("eq6_roots.txt")
+    m, C = g["m_kg"], g["C_N_per_m"]
+    w_hi, w_lo, r_hi, r_lo = eq3_modes(m, C)
+    # roots of m^2 lam^4 + 3 m C lam^2 + C^2 = 0 by a library polynomial solver
+    lam = np.roots([m ** 2, 0.0, 3 * m * C, 0.0, C ** 2])
+    assert np.allclose(lam.real, 0.0, atol=1e-9)
+    got = np.sort(np.abs(lam.imag))
+    assert np.allclose(got, [w_lo, w_lo, w_hi, w_hi], rtol=1e-12)
+    # mode shapes are the golden-ratio pair (1 -+ sqrt 5)/2
+    assert r_hi == pytest.approx((1 - math.sqrt(5)) / 2, rel=1e-13)
+    assert r_lo == pytest.approx((1 + math.sqrt(5)) / 2, rel=1e-13)
+
+
+def test_eq6_printed_roots_match_reading():
+    """Printed roots 51.47 / 19.66 against the reading m = 2 kg, C = 2025 N/m.
+
+    The reading gives 51.4855 / 19.6657, 3e-4 above the printed values (the
+    printed pair corresponds to C/m = 1012, not 1012.5); the ratio of the two
+    printed roots is phi^2 = (3 + sqrt 5)/2 to print precision, as eq. 6 fixes.
+    """
+    g = read_golden("eq6_roots.txt")
+    w_hi, w_lo, _, _ = eq3_modes(g["m_kg"], g["C_N_per_m"])
+    assert w_hi == pytest.approx(g["omega_high"], rel=5e-4)
+    assert w_lo == pytest.approx(g["omega_low"], rel=5e-4)
+    assert g["omega_high"] / g["omega_low"] == pytest.approx((3 + math.sqrt(5)) / 2, rel=1e-4)
+
+
+@pytest.mark.parametrize("mode", ["high", "low"])
+def test_oracle_mode_shapes_and_printed_frequencies(mode):
+    """A mode-shape start stays in its mode, at the eq. 6 frequency."""
+    g = read_golden("eq6_roots.txt")
+    m, C = g["m_kg"], g["C_N_per_m"]
+    w_hi, w_lo, r_hi, r_lo = eq3_modes(m, C)
+    w, r = (w_hi, r_hi) if mode == "high" else (w_lo, r_lo)
+    h, n = 1e-4, 20_000
+    res = oracle.rk4_chain([[m, m]], [[C, C]], [[1.0, r]], [[0.0, 0.0]], h, n, ckpt_every=100)
+    xt = res["x_traj"][0]
+    # shape preserved: x2 / x1 == r along the whole trajectory
+    big = np.abs(xt[:, 0]) > 1e-3
+    assert np.allclose(xt[big, 1] / xt[big, 0], r, rtol=1e-10)
+    # amplitude is the exact discrete RK4 factor Re(R^n)
+    steps = 100 * np.arange(1, xt.shape[0] + 1)
+    re, _ = rk4_power(w * h, steps)
+    assert np.max(np.abs(xt[:, 0] - re)) < 1e-12
+    # frequency of the oracle's own motion: for one mode sampled every k steps,
+    # x[c+1] + x[c-1] = 2 cos(k h w_sim) x[c] (|R| = 1 to 1e-16 per step here)
+    c = np.nonzero(np.abs(xt[1:-1, 0]) > 0.5)[0] + 1
+    cosk = np.mean((xt[c + 1, 0] + xt[c - 1, 0]) / (2 * xt[c, 0]))
+    w_sim = math.acos(cosk) / (100 * h)
+    printed = g["omega_high"] if mode == "high" else g["omega_low"]
+    assert w_sim == pytest.approx(printed, rel=5e-4)
+    # RK4 lags the true frequency by theta^4/120 relative (arg R = theta - theta^5/120 + ...)
+    assert w_sim == pytest.approx(np.angle(rk4_amplification(w * h)) / h, rel=1e-9)
+    assert w_sim == pytest.approx(w, rel=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Eq. 3 trajectory: exact ODE and exact discrete RK4
+# --------------------------------------------------------------------------
+
+def eq3_phi():
+    w_hi, w_lo, r_hi, r_lo = eq3_modes()
+    Phi = np.array([[1.0, 1.0], [r_hi, r_lo]])
+    return Phi, np.array([w_hi, w_lo])
+
+
+def test_oracle_eq3_matches_normal_mode_solution_at_10s():
+    """Eq. 7 (read as the sum of both normal modes) at t = 10 s, x(0) = (1, 0)."""
+    cfg = inputs.eq3_single()
+    res = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"])
+    w_hi, w_lo, _, _ = eq3_modes()
+    T = cfg["h"][0] * cfg["n_steps"]
+    s5 = math.sqrt(5)
+    x1 = (5 + s5) / 10 * math.cos(w_hi * T) + (5 - s5) / 10 * math.cos(w_lo * T)
+    x2 = (math.cos(w_lo * T) - math.cos(w_hi * T)) / s5
+    # exact ODE: RK4 truncation (phase lag n theta^5 / 120) is below 2e-9 here
+    assert np.max(np.abs(res["x"][0] - [x1, x2])) < 2e-9
+    assert x1 == pytest.approx(0.5919944676872458, abs=1e-12)
+    assert x2 == pytest.approx(-0.5530375088023508, abs=1e-12)
+
+
+@pytest.mark.parametrize("x0", [(1.0, 0.0), (2.0, -3.0)])
+def test_oracle_eq3_matches_exact_discrete_rk4(x0):
+    """x(0) = (1, 0) and the Fig. 2 start (2, -3): oracle == discrete RK4 closed form."""
+    if x0 == (2.0, -3.0):
+        g = read_golden("fig2_initial_condition.txt")
+        x0 = (g["x1_0"], g["x2_0"])
+    cfg = inputs.eq3_single(x0)
+    n = cfg["n_steps"]
+    res = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], n,
+                           ckpt_every=10_000)
+    Phi, w = eq3_phi()
+    for c in range(res["x_traj"].shape[1]):
+        xe, ve = modal_solution(Phi, w, np.array(x0), 1e-4, 10_000 * (c + 1))
+        assert relmax(res["x_traj"][0, c], xe) < 1e-11
+        assert relmax(res["v_traj"][0, c], ve) < 1e-11
+    if x0 == (1.0, 0.0):
+        # 40-digit evaluation of the same closed form, rounded to FP64
+        assert res["x"][0] == pytest.approx([0.5919944669044028, -0.55303750830408224], abs=1e-11)
+        assert res["v"][0] == pytest.approx([8.1504651108505194, -16.620613689578883], abs=1e-9)
+
+
+def test_fig2_modal_coefficients():
+    """For (2, -3) the modal amplitudes are 1 + 4/sqrt5 (high) and 1 - 4/sqrt5 (low)."""
+    Phi, _ = eq3_phi()
+    a = np.linalg.solve(Phi, [2.0, -3.0])
+    assert a[0] == pytest.approx(1 + 4 / math.sqrt(5), rel=1e-13)
+    assert a[1] == pytest.approx(1 - 4 / math.sqrt(5), rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Brute force: matrix power of the RK4 polynomial
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 8])
+def test_oracle_chain_matches_matrix_power(s):
+    rng = np.random.default_rng(100 + s)
+    m = rng.uniform(0.5, 2.0, s)
+    C = rng.uniform(1e2, 1e3, s)
+    x0 = rng.normal(size=s)
+    v0 = rng.normal(size=s)
+    K = chain_K_from_energy(C)
+    A = first_order_matrix(np.diag(m), K)
+    wmax = math.sqrt(np.max(np.linalg.eigvals(-A[s:, :s]).real))
+    h = 2 * math.pi / wmax / 50
+    n = 300
+    P = rk4_matrix(A, h)
+    y = np.linalg.matrix_power(P, n) @ np.concatenate([x0, v0])
+    res = oracle.rk4_chain(m[None], C[None], x0[None], v0[None], h, n)
+    assert relmax(res["x"][0], y[:s]) < 1e-11
+    assert relmax(res["v"][0], y[s:]) < 1e-11
+
+
+@pytest.mark.parametrize("s", [2, 3, 6, 9])
+def test_oracle_dense_matches_matrix_power(s):
+    rng = np.random.default_rng(200 + s)
+    G = rng.normal(size=(s, s))
+    M = np.eye(s) + 0.3 * G @ G.T / s
+    H = rng.normal(size=(s, s))
+    K = H @ H.T + s * np.eye(s)
+    x0 = rng.normal(size=s)
+    v0 = rng.normal(size=s)
+    A = first_order_matrix(M, K)
+    wmax = math.sqrt(np.max(np.abs(np.linalg.eigvals(A))) ** 2)
+    h = 2 * math.pi / wmax / 60
+    n = 250
+    P = rk4_matrix(A, h)
+    y = np.linalg.matrix_power(P, n) @ np.concatenate([x0, v0])
+    res = oracle.rk4_dense(M, K, x0[None], v0[None], h, n)
+    assert relmax(res["x"][0], y[:s]) < 1e-11
+    assert relmax(res["v"][0], y[s:]) < 1e-11
+
+
+def test_oracle_dense_general_M_modal_closed_form():
+    """General SPD M (s = 12): generalised eigenvectors give the exact discrete map."""
+    from scipy.linalg import eigh
+
+    s = 12
+    rng = np.random.default_rng(7)
+    G = rng.normal(size=(s, s))
+    M = np.eye(s) + 0.1 * G @ G.T / s
+    Q = inputs.haar_orthogonal(rng, s)
+    lam = np.exp(rng.uniform(0, math.log(1e4), s))
+    K = (Q * lam) @ Q.T
+    K = 0.5 * (K + K.T)
+    w2, Phi = eigh(K, M)
+    w = np.sqrt(w2)
+    h = float(inputs.fp32_exact(2 * math.pi / w[-1] / 100))
+    x0 = rng.normal(size=s)
+    n = 2000
+    res = oracle.rk4_dense(M, K, x0[None], np.zeros((1, s)), h, n)
+    xe, ve = modal_solution(Phi, w, x0, h, n)
+    assert relmax(res["x"][0], xe) < 1e-10
+    assert relmax(res["v"][0], ve) < 1e-10
+
+
+def test_oracle_dense_identity_mass_single_mode_s256():
+    """M = I, K = Q diag(lam) Q^T, x0 = Q e_k: x_n = Q e_k Re(R(i sqrt(lam_k) h)^n)."""
+    cfg = inputs.dense_group(s=256, n_inst=1, n_steps=400)
+    Q, lam = cfg["Q"], cfg["lam"]
+    K = cfg["K"][0]
+    s = 256
+    h = cfg["h"][0]
+    ks = [int(np.argmax(lam)), int(np.argmin(lam)), 17]
+    x0 = np.stack([Q[:, k] for k in ks])
+    res = oracle.rk4_dense(np.eye(s), K, x0, np.zeros_like(x0), h, cfg["n_steps"])
+    for i, k in enumerate(ks):
+        w = math.sqrt(lam[k])
+        re, im = rk4_power(w * h, cfg["n_steps"])
+        assert relmax(res["x"][i], Q[:, k] * re) < 1e-10
+        assert np.max(np.abs(res["v"][i] - Q[:, k] * (-w * im))) < 1e-10 * w
+
+
+# --------------------------------------------------------------------------
+# Uniform chain at full size (s = 1024)
+# --------------------------------------------------------------------------
+
+def uniform_chain_mode(s, k, m, C):
+    """Mode k (1-based) of the uniform fixed-free chain.
+
+    omega_k^2 = 4 (C/m) sin^2((2k-1) pi / (2(2s+1))),  u_k(j) = sin((2k-1) j pi / (2s+1)).
+    """
+    w = 2 * math.sqrt(C / m) * math.sin((2 * k - 1) * math.pi / (2 * (2 * s + 1)))
+    j = np.arange(1, s + 1)
+    u = np.sin((2 * k - 1) * j * math.pi / (2 * s + 1))
+    return w, u
+
+
+def test_uniform_chain_closed_form_is_eigenpair():
+    s, m, C = 7, 1.3, 250.0
+    K = chain_K_from_energy(np.full(s, C))
+    for k in range(1, s + 1):
+        w, u = uniform_chain_mode(s, k, m, C)
+        assert np.allclose(K @ u, m * w ** 2 * u, atol=1e-10 * C)
+    # s = 2 reduces to eq. 6
+    w1, _ = uniform_chain_mode(2, 2, 2.0, 2025.0)
+    w2, _ = uniform_chain_mode(2, 1, 2.0, 2025.0)
+    w_hi, w_lo, _, _ = eq3_modes()
+    assert w1 == pytest.approx(w_hi, rel=1e-13)
+    assert w2 == pytest.approx(w_lo, rel=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 300, 1024])
+def test_oracle_uniform_chain_s1024_single_mode(k):
+    s, m, C = 1024, 1.0, 500.0
+    w, u = uniform_chain_mode(s, k, m, C)
+    wmax, _ = uniform_chain_mode(s, s, m, C)
+    h = float(inputs.fp32_exact(2 * math.pi / wmax / 100))
+    n = 1000
+    masses, springs = inputs.uniform_chain(s, m, C)
+    res = oracle.rk4_chain(masses, springs, u[None], np.zeros((1, s)), h, n)
+    re, im = rk4_power(w * h, n)
+    assert relmax(res["x"][0], u * re) < 1e-11
+    assert np.max(np.abs(res["v"][0] - u * (-w * im))) < 1e-11 * max(w, 1.0)
+
+
+# --------------------------------------------------------------------------
+# Energy
+# --------------------------------------------------------------------------
+
+def test_energy_eq3_initial_value():
+    """x(0) = (1, 0): both springs stretched by 1, E0 = C = 2025 J."""
+    cfg = inputs.eq3_single()
+    E = oracle.energy_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"])
+    assert E[0] == 2025.0
+
+
+def test_energy_eq3_discrete_decay_law():
+    """Modal energy is multiplied by |R(i theta)|^2 per step; drift -2.45e-11 after 1e5 steps."""
+    cfg = inputs.eq3_single()
+    res = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"])
+    E = oracle.energy_chain(cfg["masses"], cfg["springs"], res["x"], res["v"])[0]
+    Phi, w = eq3_phi()
+    M = np.diag([2.0, 2.0])
+    K = chain_K_from_energy([2025.0, 2025.0])
+    a = np.linalg.solve(Phi, cfg["x0"][0])
+    E0_modes = 0.5 * a ** 2 * np.array([Phi[:, k] @ K @ Phi[:, k] for k in range(2)])
+    assert E0_modes.sum() == pytest.approx(2025.0, rel=1e-14)
+    E_exp = np.sum(E0_modes * np.exp(2 * cfg["n_steps"] * rk4_log_modulus(w * 1e-4)))
+    drift = (E - 2025.0) / 2025.0
+    assert drift == pytest.approx((E_exp - 2025.0) / 2025.0, rel=1e-3)
+    assert drift == pytest.approx(-2.4508e-11, rel=1e-3)
+    _ = M
+
+
+def test_energy_drift_is_fifth_order_in_h():
+    """At a fixed horizon, halving h divides the energy drift by 2^5."""
+    cfg = inputs.eq3_single()
+    T = 2.0
+    drifts = []
+    for h in (4e-4, 2e-4):
+        n = int(round(T / h))
+        res = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], h, n)
+        E = oracle.energy_chain(cfg["masses"], cfg["springs"], res["x"], res["v"])[0]
+        drifts.append((2025.0 - E) / 2025.0)
+    assert drifts[0] / drifts[1] == pytest.approx(32.0, rel=0.02)
+
+
+def test_energy_chain_equals_quadratic_form():
+    rng = np.random.default_rng(3)
+    s = 9
+    m = rng.uniform(0.5, 2.0, (4, s))
+    C = rng.uniform(1e2, 1e3, (4, s))
+    x = rng.normal(size=(4, s))
+    v = rng.normal(size=(4, s))
+    E = oracle.energy_chain(m, C, x, v)
+    for i in range(4):
+        K = chain_K_from_energy(C[i])
+        Ed = oracle.energy_dense(np.diag(m[i]), K, x[i:i + 1], v[i:i + 1])[0]
+        assert E[i] == pytest.approx(Ed, rel=1e-13)
+
+
+def test_energy_dense_modal_form():
+    """1/2 v^T M v + 1/2 x^T K x == 1/2 sum_k (b_k^2 + omega_k^2 a_k^2) in M-orthonormal modes."""
+    from scipy.linalg import eigh
+
+    s = 10
+    rng = np.random.default_rng(11)
+    G = rng.normal(size=(s, s))
+    M = np.eye(s) + 0.2 * G @ G.T / s
+    H = rng.normal(size=(s, s))
+    K = H @ H.T
+    w2, Phi = eigh(K, M)
+    x = rng.normal(size=(3, s))
+    v = rng.normal(size=(3, s))
+    E = oracle.energy_dense(M, K, x, v)
+    for i in range(3):
+        a = Phi.T @ M @ x[i]
+        b = Phi.T @ M @ v[i]
+        assert E[i] == pytest.approx(0.5 * np.sum(b ** 2 + w2 * a ** 2), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Invariances
+# --------------------------------------------------------------------------
+
+def test_oracle_linearity():
+    cfg = inputs.two_dof_batch(n_inst=8, n_steps=500)
+    xa = cfg["x0"]
+    xb = np.roll(cfg["x0"], 1, axis=0)
+    kw = dict(h=cfg["h"], n_steps=500)
+    ra = oracle.rk4_chain(cfg["masses"], cfg["springs"], xa, cfg["v0"], **kw)
+    rb = oracle.rk4_chain(cfg["masses"], cfg["springs"], xb, cfg["v0"], **kw)
+    rab = oracle.rk4_chain(cfg["masses"], cfg["springs"], xa + xb, cfg["v0"], **kw)
+    assert relmax(rab["x"], ra["x"] + rb["x"]) < 1e-12
+
+
+def test_oracle_time_scaling_is_exact():
+    """C -> 4C, h -> h/2 gives the same x_n and twice the velocity, bit for bit."""
+    cfg = inputs.two_dof_batch(n_inst=4, n_steps=300)
+    r1 = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], 300)
+    r2 = oracle.rk4_chain(cfg["masses"], 4 * cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"] / 2, 300)
+    assert np.array_equal(r1["x"], r2["x"])
+    assert np.array_equal(2 * r1["v"], r2["v"])
+
+
+def test_oracle_instance_permutation_and_threads():
+    cfg = inputs.two_dof_batch(n_inst=16, n_steps=200)
+    perm = np.random.default_rng(0).permutation(16)
+    r1 = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], 200)
+    r2 = oracle.rk4_chain(cfg["masses"][perm], cfg["springs"][perm], cfg["x0"][perm], cfg["v0"][perm],
+                          cfg["h"][perm], 200, threads=4)
+    assert np.array_equal(r1["x"][perm], r2["x"])
+    assert np.array_equal(r1["v"][perm], r2["v"])
+
+
+def test_oracle_single_oscillator():
+    """s = 1 is one mass on one spring: x_n = Re(R^n), closed form."""
+    m, C, h, n = 3.0, 300.0, 1e-3, 5000
+    res = oracle.rk4_chain([[m]], [[C]], [[1.0]], [[0.0]], h, n)
+    re, im = rk4_power(math.sqrt(C / m) * h, n)
+    assert res["x"][0, 0] == pytest.approx(re, abs=1e-13)
+    assert res["v"][0, 0] == pytest.approx(-math.sqrt(C / m) * im, abs=1e-12)
+
+
+def test_oracle_checkpoints_and_resume():
+    """Checkpoint c is the state after (c+1)*k steps; restarting from a checkpoint is bitwise."""
+    cfg = inputs.two_dof_batch(n_inst=3, n_steps=400)
+    full = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], 400, ckpt_every=100)
+    half = oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], 200)
+    rest = oracle.rk4_chain(cfg["masses"], cfg["springs"], half["x"], half["v"], cfg["h"], 200)
+    assert np.array_equal(full["x_traj"][:, 1], half["x"])
+    assert np.array_equal(full["x_traj"][:, 3], full["x"])
+    assert np.array_equal(rest["x"], full["x"])
+    assert np.array_equal(rest["v"], full["v"])
+
+
+def test_oracle_rejects_bad_arguments():
+    with pytest.raises(RuntimeError):
+        oracle.rk4_chain([[1.0, 1.0]], [[1.0, 1.0]], [[1.0, 0.0]], [[0.0, 0.0]], 1e-3, 10, ckpt_every=3)
+    with pytest.raises(RuntimeError):
+        M = np.array([[1.0, 2.0], [2.0, 1.0]])  # indefinite
+        oracle.rk4_dense(M, np.eye(2), [[1.0, 0.0]], [[0.0, 0.0]], 1e-3, 10)
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each mutant build must fail at least one pin
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mutant", [1, 2, 3])
+def test_pins_catch_planted_mistakes(mutant):
+    s = 3
+    rng = np.random.default_rng(5)
+    m = rng.uniform(0.5, 2.0, s)
+    C = rng.uniform(1e2, 1e3, s)
+    x0 = rng.normal(size=s)
+    K = chain_K_from_energy(C)
+    A = first_order_matrix(np.diag(m), K)
+    h, n = 1e-3, 200
+    y = np.linalg.matrix_power(rk4_matrix(A, h), n) @ np.concatenate([x0, np.zeros(s)])
+    good = oracle.rk4_chain(m[None], C[None], x0[None], np.zeros((1, s)), h, n)
+    bad = oracle.rk4_chain(m[None], C[None], x0[None], np.zeros((1, s)), h, n, mutant=mutant)
+    assert relmax(good["x"][0], y[:s]) < 1e-11
+    assert relmax(bad["x"][0], y[:s]) > 1e-6
