@@ -1,0 +1,342 @@
+"""Benchmark: DOF-steps/s of batched classical RK4 on coupled linear oscillators.
+
+Workload (one "step" of this benchmark): 65,536 independent 2-DOF spring systems
+of eq. 2 (masses log-uniform [0.1, 10] kg, spring rates log-uniform [1e2, 1e4]
+N/m, x(0) ~ U(-1, 1), v(0) = 0, h = T_min/200 per instance), each integrated for
+1e4 RK4 steps in one call of cho_integrate_batch.  DOF-steps per step:
+65,536 * 2 * 1e4 = 1.31e9.  Headline arithmetic: FP32 with Kahan-compensated
+state; the FP64 mode is reported beside it.  The error against the FP64 oracle
+on sampled instances is measured in the same run.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank integrates its own 65,536 systems (weak scaling,
+no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-steps/s at stated error vs FP64 oracle"
+UNIT = "DOF-steps/s"
+N_INST = 65_536
+N_STEPS = 10_000
+S = 2
+DOF_STEPS = N_INST * S * N_STEPS
+# Algorithmic work of one RK4 step of an s-DOF system with dense B: 4 s^2 FMA for
+# the four B x products, 6 s for the stage states, 6 s for the weighted sums,
+# 2 s for the update: (4 s^2 + 14 s) FMA = 2 (4 s^2 + 14 s) flops per instance-step.
+FLOPS_PER_INSTANCE_STEP = 2 * (4 * S * S + 14 * S)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_alu_peak_tflops(sm_count, mhz):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample_rate(cfg, n_sample, threads=1):
+    """Time the FP64 oracle on the first n_sample instances; DOF-steps/s and seconds."""
+    import oracle
+
+    sl = slice(0, n_sample)
+    t0 = time.perf_counter()
+    oracle.rk4_chain(cfg["masses"][sl], cfg["springs"][sl], cfg["x0"][sl], cfg["v0"][sl], cfg["h"][sl],
+                     cfg["n_steps"], 0, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_sample * cfg["s"] * cfg["n_steps"] / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on this host's cores, a bounded sample per step."""
+    rank, _, world = dist_env()
+    if world > 1 and rank != 0:
+        return
+    from paper_1702_02207_gb300 import inputs
+
+    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS)
+    oracle_sample_rate(cfg, 16)  # build the oracle
+    _, t_cal = oracle_sample_rate(cfg, 64)
+    # per-step sample sized so that warm-up plus timed steps take about two minutes
+    per_step_s = 120.0 / max(1, args.steps + args.warmup)
+    n_sample = int(max(16, min(N_INST, per_step_s / (t_cal / 64))))
+    for _ in range(args.warmup):
+        oracle_sample_rate(cfg, n_sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample_rate(cfg, n_sample)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * n_sample * S * N_STEPS / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "two_dof_eq2_batch", "n_inst": N_INST, "s": S, "n_steps": N_STEPS,
+                   "sample_per_step": n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n_sample} of the {N_INST} systems, {N_STEPS} steps, per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = dist_env()
+    import torch
+
+    from paper_1702_02207_gb300 import cho, inputs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---- set-up (off the timed region): inputs, system, device arrays ----
+    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS, seed=inputs.SEED_BASE + 1 + 1000 * rank)
+    ctx = cho.cho_init(local_rank)
+    sys_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
+    x0 = torch.as_tensor(cfg["x0"], device=dev)
+    v0 = torch.as_tensor(cfg["v0"], device=dev)
+    h = torch.as_tensor(cfg["h"], device=dev)
+    out = {"x": torch.empty_like(x0), "v": torch.empty_like(v0)}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step(prec):
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, N_STEPS, prec, out=out, stream=stream)
+
+    def timed(prec, k, w):
+        for _ in range(w):
+            step(prec)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(float(i))          # L2 flush between timed iterations (outside the events)
+            ev[i][0].record(stream)
+            step(prec)
+            ev[i][1].record(stream)
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms
+
+    # ---- headline: FP32 + Kahan ----
+    sampler = ClockSampler(local_rank)
+    for _ in range(args.warmup):
+        step("fp32_kahan")
+    sampler.start()
+    ms = timed("fp32_kahan", args.steps, 0)
+    clocks = sampler.stop()
+    t_rank = sum(ms) / 1e3
+    if pg is not None:
+        t = torch.tensor([t_rank], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_rank
+    value = world * args.steps * DOF_STEPS / t_max
+    avg_kernel_s = t_rank / args.steps
+
+    # ---- accuracy of the headline mode against the oracle (sampled, untimed) ----
+    def sampled_error(prec, n_sample=64):
+        import oracle
+
+        idx = np.unique(np.concatenate([[0, N_INST - 1], np.random.default_rng(3).choice(N_INST, n_sample - 2, False)]))
+        sel = {k: torch.as_tensor(cfg[k][idx], device=dev) for k in ("x0", "v0", "h")}
+        ms_, sp_ = cfg["masses"][idx], cfg["springs"][idx]
+        s2 = cho.cho_create_system(ctx, "two_dof", masses=ms_, springs=sp_)
+        r = cho.cho_integrate_batch(ctx, s2, sel["x0"], sel["v0"], sel["h"], N_STEPS, prec, 100, trajectory=True)
+        torch.cuda.synchronize()
+        cho.cho_destroy_system(s2)
+        ref = oracle.rk4_chain(ms_, sp_, cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx], N_STEPS, 100,
+                               threads=min(16, os.cpu_count() or 1))
+        e = []
+        for k in ("x_traj", "v_traj"):
+            g = r[k].cpu().numpy()
+            num = np.max(np.abs(g - ref[k]), axis=(1, 2))
+            den = np.max(np.abs(ref[k]), axis=(1, 2))
+            e.append(num / den)
+        e = np.maximum(e[0], e[1])
+        return {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)), "instances": int(len(idx))}
+
+    line = {}
+    if rank == 0:
+        err32 = sampled_error("fp32_kahan")
+        # ---- e2e: the same call with pinned host buffers (copies inside the timed region) ----
+        hx0 = torch.as_tensor(cfg["x0"]).pin_memory()
+        hv0 = torch.as_tensor(cfg["v0"]).pin_memory()
+        hh = torch.as_tensor(cfg["h"]).pin_memory()
+        hout = {"x": torch.empty_like(hx0).pin_memory(), "v": torch.empty_like(hv0).pin_memory()}
+        k_e2e = max(3, min(args.steps, 50))
+        for _ in range(3):
+            cho.cho_integrate_batch(ctx, sys_, hx0, hv0, hh, N_STEPS, "fp32_kahan", out=hout, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            cho.cho_integrate_batch(ctx, sys_, hx0, hv0, hh, N_STEPS, "fp32_kahan", out=hout, stream=stream)
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        h2d = (hx0.numel() + hv0.numel() + hh.numel()) * 8
+        d2h = (hout["x"].numel() + hout["v"].numel()) * 8
+
+        peaks = measured_peaks()
+        max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+        achieved = N_INST * N_STEPS * FLOPS_PER_INSTANCE_STEP / avg_kernel_s / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "two_dof_eq2_batch", "n_inst_per_gpu": N_INST, "s": S, "n_steps": N_STEPS,
+                       "prec": "fp32_kahan", "l2": "flushed between timed iterations (512 MiB write)",
+                       "parallelism": f"instances sharded over {world} GPU(s)"},
+            "error_vs_oracle": err32,
+            "roofline": {"bound": "alu", "kernel": "rk4_small<S=2,FP32+Kahan>", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
+            "clocks": clocks,
+            "e2e": {"value": DOF_STEPS / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e},
+            "gpu_launches": args.steps,
+        }
+        if not args.no_extras:
+            # FP64 mode of the same workload (fewer steps: FP64 runs far below FP32 on this part)
+            ms64 = timed("fp64", 3, 1)
+            t64 = sum(ms64) / 1e3 / 3
+            line["modes"] = {
+                "fp32_kahan": {"value": value / world, "ms_per_step": 1e3 * t_rank / args.steps, "error": err32},
+                "fp64": {"value": DOF_STEPS / t64, "ms_per_step": 1e3 * t64, "error": sampled_error("fp64", 32)},
+            }
+            # plain form (one launch per stage, one system at a time), sampled and extrapolated
+            n_plain, n_plain_steps = 2, 2000
+            sl = slice(0, n_plain)
+            sp = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"][sl], springs=cfg["springs"][sl])
+            cho.cho_integrate_plain(ctx, sp, x0[sl].contiguous(), v0[sl].contiguous(), h[sl].contiguous(), 20, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cho.cho_integrate_plain(ctx, sp, x0[sl].contiguous(), v0[sl].contiguous(), h[sl].contiguous(),
+                                    n_plain_steps, stream=stream)
+            torch.cuda.synchronize()
+            tp = time.perf_counter() - t0
+            cho.cho_destroy_system(sp)
+            plain_rate = n_plain * S * n_plain_steps / tp
+            line["plain_form"] = {"value": plain_rate, "unit": UNIT,
+                                  "sample": f"{n_plain} systems x {n_plain_steps} steps, FP64, 5 launches per step",
+                                  "batched_over_plain": value / world / plain_rate}
+        if not args.no_cpu_baseline:
+            n_cpu = 16384
+            rate, dt = oracle_sample_rate(cfg, n_cpu)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"first {n_cpu} of the {N_INST} systems x {N_STEPS} steps, "
+                                              f"single-threaded FP64 C oracle ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    cho.cho_destroy_system(sys_)
+    cho.cho_shutdown(ctx)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * cho.h -- C ABI of the batched coupled-harmonic-oscillator integrator.
+ *
+ * The library integrates many independent instances of eq. 1 of "Parallel
+ * Implementation of the Coupled Harmonic Oscillator" (arXiv 1702.02207),
+ *
+ *     sum_j (m_ij x_j'' + k_ij x_j) = 0,   i.e.  M x'' + K x = 0,        (eq. 1)
+ *
+ * with fixed-step classical fourth-order Runge-Kutta on the first-order form
+ * y = (x, v), v = x' (Section 3: x3 = x1', x4 = x2', right-hand side D(1)..D(4)).
+ * Each RK4 step evaluates the acceleration a = -M^{-1} K x four times (the
+ * D(3), D(4) rows of Section 3), forms the stage states, and adds the weighted
+ * sum h/6 (k1 + 2 k2 + 2 k3 + k4) to the state.
+ *
+ * Three kinds of system are accepted:
+ *   CHO_TWO_DOF  the spring system of eq. 2 (Section 2, Figure 1): mass 1 on a
+ *                wall spring C1, spring C2 between masses 1 and 2, mass 2 free.
+ *                Eq. 3 is the case m1 = m2, C1 = C2.
+ *   CHO_CHAIN    eq. 2 generalised to s masses: spring i joins mass i-1 and i,
+ *                spring 0 joins mass 0 to the wall, the last mass is free.
+ *                K is tridiagonal with K_ii = C_i + C_{i+1}, K_{i,i+1} = -C_{i+1}.
+ *   CHO_DENSE    eq. 1 with full symmetric positive definite M and symmetric K.
+ *
+ * Conventions for every call:
+ *   - every function returns a cho_status and never aborts the process;
+ *   - on error, output parameters are left untouched and cho_last_error()
+ *     returns a message for the calling thread;
+ *   - handles are opaque and owned by the library;
+ *   - arrays passed in are owned by the caller; the library copies what it keeps;
+ *   - all floating-point inputs and outputs are IEEE binary64, row-major;
+ *   - device pointers must be CUDA device memory of the context's device (or
+ *     managed memory); "stream" is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef CHO_H
+#define CHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cho_status {
+    CHO_OK = 0,
+    CHO_PENDING = 1,        /* cho_poll: the request has not finished yet            */
+    CHO_EINVAL = -1,        /* bad argument (null pointer, size, kind, precision)    */
+    CHO_ENOMEM = -2,        /* device or host allocation failed                       */
+    CHO_EBUDGET = -3,       /* a request can never fit in the serving memory budget  */
+    CHO_EUNSTABLE = -4,     /* omega_max * h exceeds the RK4 stability limit 2*sqrt 2 */
+    CHO_ENOTSPD = -5,       /* M is not symmetric positive definite                   */
+    CHO_ETIMEOUT = -6,      /* a bounded wait gave up                                 */
+    CHO_ENONFINITE = -7,    /* a non-finite input or state                            */
+    CHO_ECANCELLED = -8,    /* the request was cancelled                              */
+    CHO_ECUDA = -9,         /* a CUDA runtime call failed                             */
+    CHO_EINTERNAL = -10,    /* an internal consistency check failed                   */
+    CHO_ENOTFOUND = -11     /* unknown ticket                                         */
+} cho_status;
+
+typedef enum cho_kind {
+    CHO_TWO_DOF = 0,
+    CHO_CHAIN = 1,
+    CHO_DENSE = 2
+} cho_kind;
+
+/* Arithmetic of the integration (the state is always returned in FP64).
+ *   CHO_FP64             FP64 state and stages.
+ *   CHO_FP32_KAHAN       FP32 state and stages, Kahan-compensated state update,
+ *                        M^{-1}K and h/6 carried as unevaluated FP32 pairs (hi + lo).
+ *   CHO_DENSE_FP32_SIMT  dense systems: like CHO_FP32_KAHAN (the same kernel family).
+ *   CHO_DENSE_BF16X3/X5/X6  dense systems with a shared (M, K): the product
+ *                        M^{-1}K X on tensor cores with M^{-1}K and X split into
+ *                        BF16 pieces (3, 5 or 6 partial products), FP32 accumulation,
+ *                        FP32 + Kahan state.                                        */
+typedef enum cho_prec {
+    CHO_FP64 = 0,
+    CHO_FP32_KAHAN = 1,
+    CHO_DENSE_BF16X3 = 2,
+    CHO_DENSE_BF16X5 = 3,
+    CHO_DENSE_BF16X6 = 4,
+    CHO_DENSE_FP32_SIMT = 5
+} cho_prec;
+
+/* Where the state arrays of a batch live. */
+typedef enum cho_mem {
+    CHO_MEM_DEVICE = 0,     /* device pointers; the call is asynchronous on the stream  */
+    CHO_MEM_HOST = 1        /* host pointers; the library stages them through device
+                               memory and returns after the results are in host memory */
+} cho_mem;
+
+typedef struct cho_ctx cho_ctx;
+typedef struct cho_system_impl* cho_system;
+
+/* Optional context settings (pass NULL for defaults).  Zero fields take defaults. */
+typedef struct cho_config {
+    int64_t budget_bytes;   /* serving: device bytes for resident request state (default 40 GiB) */
+    int32_t chunk_steps;    /* serving: RK4 steps per chunk between scheduling points (default 1000) */
+    int32_t max_slots;      /* serving: maximum resident requests (default 1 << 20)       */
+    int32_t reserved[4];
+} cho_config;
+
+/* Description of one system kind and size, with n_sys parameter sets.
+ * TWO_DOF / CHAIN: masses (n_sys, s) in kg and springs (n_sys, s) in N/m, springs[.,0]
+ *   is the wall spring; every value must be finite and > 0.  TWO_DOF requires s == 2.
+ * DENSE: M and K (n_sys, s, s), row-major; M symmetric positive definite, K symmetric
+ *   (relative asymmetry <= 1e-12), all finite.
+ * All pointers are host memory; the library copies them. */
+typedef struct cho_system_desc {
+    int32_t kind;           /* cho_kind */
+    int32_t s;              /* degrees of freedom, >= 1 */
+    int64_t n_sys;          /* parameter sets, >= 1 */
+    const double* masses;
+    const double* springs;
+    const double* M;
+    const double* K;
+} cho_system_desc;
+
+/* One batch of independent instances of one system.
+ * Instance i uses parameter set i when the system has n_inst sets, or set 0 when it
+ * has one.  Layouts (row-major, FP64):
+ *   x0, v0, x_out, v_out      (n_inst, s)
+ *   h                         (n_inst) when h_per_inst != 0, else (1)
+ *   x_traj, v_traj (optional) (n_inst, n_steps / ckpt_every, s): checkpoint c holds the
+ *                             state after (c + 1) * ckpt_every steps
+ *   energy (optional)         (n_inst, n_steps / ckpt_every): energy of each checkpoint,
+ *                             1/2 v^T M v + 1/2 x^T K x in FP64; needs x_traj and v_traj
+ * x_out/v_out may alias x0/v0.  ckpt_every must divide n_steps when it is non-zero. */
+typedef struct cho_batch_desc {
+    cho_system system;
+    int64_t n_inst;
+    int32_t prec;           /* cho_prec */
+    int32_t mem;            /* cho_mem: where x0, v0, h and all outputs live */
+    const double* x0;
+    const double* v0;
+    const double* h;
+    int32_t h_per_inst;
+    int32_t reserved0;
+    int64_t n_steps;
+    int64_t ckpt_every;
+    double* x_out;
+    double* v_out;
+    double* x_traj;
+    double* v_traj;
+    double* energy;
+} cho_batch_desc;
+
+/* One serving request: a single instance of one parameter set of a system. */
+typedef struct cho_request {
+    cho_system system;
+    int64_t sys_index;      /* which parameter set of the system */
+    const double* x0;       /* host, (s) */
+    const double* v0;       /* host, (s) */
+    double h;
+    int64_t n_steps;
+    int32_t prec;           /* CHO_FP64 or CHO_FP32_KAHAN */
+    int32_t priority;       /* 0 (highest), 1, 2 */
+} cho_request;
+
+typedef struct cho_result {
+    double* x;              /* caller-owned host buffer of s values, filled on CHO_OK */
+    double* v;              /* caller-owned host buffer of s values, filled on CHO_OK */
+    double t_submit;        /* seconds on the library's monotonic clock */
+    double t_admit;
+    double t_done;
+} cho_result;
+
+/* ---- context -------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  Errors: CHO_EINVAL (bad device),
+ * CHO_ECUDA.  The context owns its device buffers and its serving thread. */
+cho_status cho_init(cho_ctx** out, int device, const cho_config* cfg);
+
+/* Stop serving (pending requests finish as CHO_ECANCELLED), free everything.
+ * Systems created on the context must be destroyed first or are freed here. */
+void cho_shutdown(cho_ctx* ctx);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* cho_last_error(void);
+
+/* ---- systems (step a0: set-up, off the integration loop) -------------------------- */
+
+/* Validate a system description and build the iteration matrix B = M^{-1} K of every
+ * parameter set (eqs. 1-3; for TWO_DOF/CHAIN from the spring rates per mass, for DENSE
+ * by a Cholesky solve), its largest natural frequency omega_max (the square root of the
+ * largest eigenvalue of the pencil (K, M)), and the FP32/BF16 splittings the kernels
+ * use; upload them to the device.  Errors: CHO_EINVAL, CHO_ENOTSPD, CHO_ENOMEM, CHO_ECUDA. */
+cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* desc, cho_system* out);
+
+/* omega_max: the largest natural frequency over all parameter sets (rad/s). */
+cho_status cho_system_info(cho_system sys, double* omega_max, int32_t* s, int64_t* n_sys);
+
+/* Largest natural frequency of each parameter set, omega (n_sys), host memory. */
+cho_status cho_system_omegas(cho_system sys, double* omega);
+
+void cho_destroy_system(cho_system sys);
+
+/* ---- batched integration (steps a1-a5) -------------------------------------------- */
+
+/* Integrate every instance of the batch for n_steps classical RK4 steps (Section 3's
+ * first-order form, eq. 1 right-hand side), writing the final state, optional
+ * checkpoints and optional FP64 energies.  Kernel choice: s <= 32 any kind -> rk4_small;
+ * CHAIN/TWO_DOF s > 32 -> rk4_chain; DENSE s > 32 with one shared parameter set ->
+ * rk4_dense.  Errors: CHO_EINVAL, CHO_EUNSTABLE (omega_max * h > 2 sqrt 2 for some
+ * instance; checked on host values only, i.e. for CHO_MEM_HOST or h_per_inst == 0),
+ * CHO_ECUDA, CHO_ENOMEM.  CHO_MEM_DEVICE: asynchronous on `stream`. */
+cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
+
+/* The same integration in the plain form: one system at a time, one kernel launch per
+ * RK stage and one per update, FP64 state kept in device memory between launches.
+ * This is the un-batched baseline the batched kernels are measured against.  Only
+ * prec == CHO_FP64; checkpoints and energy are not supported (pass NULL / 0).
+ * Uses a device work buffer of 10 s doubles held by the context. */
+cho_status cho_integrate_plain(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
+
+/* FP64 energy 1/2 v^T M v + 1/2 x^T K x of states x, v (n_inst, n_per, s); state (i, c)
+ * uses parameter set i (or 0 when the system has one set).  E is (n_inst, n_per).
+ * mem selects host or device pointers as in cho_batch_desc.  Errors: CHO_EINVAL, CHO_ECUDA. */
+cho_status cho_energy(cho_ctx* ctx, cho_system sys, const double* x, const double* v,
+                      int64_t n_inst, int64_t n_per, int32_t mem, double* E, void* stream);
+
+/* ---- serving: continuous batching of single-instance requests --------------------- */
+
+/* Queue one request.  Inputs are copied; returns at once with a ticket.
+ * Errors: CHO_EINVAL, CHO_EUNSTABLE, CHO_EBUDGET (the request alone exceeds the budget). */
+cho_status cho_submit(cho_ctx* ctx, const cho_request* req, uint64_t* ticket);
+
+/* CHO_PENDING while queued or running; CHO_OK with out->x, out->v filled once done
+ * (the ticket is then released); or the request's error (CHO_ECANCELLED,
+ * CHO_ENONFINITE, CHO_ECUDA).  CHO_ENOTFOUND for an unknown or released ticket. */
+cho_status cho_poll(cho_ctx* ctx, uint64_t ticket, cho_result* out);
+
+/* Cancel a queued or running request (it stops at its next chunk boundary). */
+cho_status cho_cancel(cho_ctx* ctx, uint64_t ticket);
+
+/* Serving counters: queued, resident, completed requests and resident device bytes. */
+cho_status cho_serve_stats(cho_ctx* ctx, int64_t* queued, int64_t* resident, int64_t* completed,
+                           int64_t* resident_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHO_H */

@@ -1,0 +1,132 @@
+// cho_internal.h -- declarations shared by the library's translation units.
+// Not part of the public ABI (include/cho.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cho {
+
+// Kernel family chosen for a (kind, s, n_sys) system.
+enum Path : int32_t {
+    PATH_SMALL = 0,   // s <= 32, any kind, any number of parameter sets
+    PATH_CHAIN = 1,   // CHAIN / TWO_DOF with s > 32
+    PATH_DENSE = 2,   // DENSE with s > 32 and one shared parameter set
+};
+
+constexpr int kSmallThreads = 64;    // threads per CTA of rk4_small (small CTAs balance the SMs)
+constexpr int kChainMaxThreads = 1024;
+
+// Host-side split of an FP64 value into an unevaluated FP32 pair hi + lo.
+inline void split_pair(double d, float& hi, float& lo)
+{
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+}
+
+// Padded size of the rk4_small family for s <= 32.
+inline int small_S(int s) { return s <= 2 ? 2 : s <= 4 ? 4 : s <= 8 ? 8 : s <= 16 ? 16 : 32; }
+
+// ----------------------------------------------------------------------------
+// Where a kernel's instances get their state, step size and step count.
+//
+// Batch form: x0/v0 (n_inst, s) FP64 in, x_out/v_out FP64 out, optional
+// checkpoint trajectories.  Slot form (serving): instance q is slot
+// slot_ids[q]; its resident state block and step count come from the slot
+// table, and the block is read and written back in the kernel's own precision
+// so that a run split into chunks is bitwise equal to an unsplit run.
+// ----------------------------------------------------------------------------
+struct BatchIO {
+    int64_t n_inst;
+    const double* x0;
+    const double* v0;
+    const double* h;
+    int32_t h_per_inst;
+    int64_t n_steps;
+    int64_t ckpt_every;     // 0: no checkpoints
+    int64_t n_ck;
+    double* x_out;
+    double* v_out;
+    double* x_traj;
+    double* v_traj;
+};
+
+// One resident request in the serving slot table (device memory).
+struct SlotDesc {
+    const void* coef;       // coefficient block of its parameter set (kernel-family layout)
+    void* state;            // resident state block (kernel-family layout, kernel precision)
+    double h;
+    int64_t steps;          // RK4 steps to run in this chunk
+    int32_t s;
+    int32_t status;         // written by the kernel: 0 ok, CHO_ENONFINITE on a non-finite state
+};
+
+struct SlotIO {
+    int64_t n_inst;         // slots in this launch
+    const int32_t* slot_ids;
+    SlotDesc* slots;
+};
+
+// ---- rk4_small ----------------------------------------------------------------
+// Coefficients per parameter set: FP64 B (S*S), or FP32 hi (S*S) followed by lo (S*S).
+struct SmallSys {
+    int32_t s;
+    int32_t S;
+    int32_t per_inst_sys;   // 1: set = instance index, 0: set 0
+    const double* B64;      // [n_sys][S][S]
+    const float* B32;       // [n_sys][2][S][S] (hi then lo)
+};
+
+cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
+cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st);
+
+// ---- rk4_chain ----------------------------------------------------------------
+// Coefficients per parameter set: three diagonals of B = M^{-1}K, each of length s:
+// FP64 [3][s] (sub, main, super) or FP32 [6][s] (sub, main, super hi; then lo).
+struct ChainSys {
+    int32_t s;
+    int32_t per_inst_sys;
+    const double* C64;      // [n_sys][3][s]
+    const float* C32;       // [n_sys][6][s]
+};
+
+int chain_dofs_per_thread(int s);
+cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
+cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaStream_t st);
+
+// ---- rk4_dense (shared B, s > 32) ------------------------------------------------
+struct DenseSys {
+    int32_t s;
+    int32_t s_pad;          // s rounded up to the tile size
+    const double* B64;      // [s][s]
+    const float* B32;       // [2][s_pad][s_pad] (hi, lo), zero padded
+    const uint16_t* Bbf;    // [3][s_pad][s_pad] bf16 pieces of B, zero padded
+};
+int dense_pad(int s);
+cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
+// tensor-core split-BF16 variant (rk4_dense_tc.cu)
+cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
+
+// ---- energy -------------------------------------------------------------------
+struct EnergySys {
+    int32_t kind;           // cho_kind
+    int32_t s;
+    int32_t per_inst_sys;
+    const double* masses;   // [n_sys][s]  (TWO_DOF / CHAIN)
+    const double* springs;  // [n_sys][s]
+    const double* M;        // [n_sys][s][s] (DENSE)
+    const double* K;
+};
+cudaError_t launch_energy(const EnergySys& sys, const double* x, const double* v, int64_t n_inst,
+                          int64_t n_per, double* E, cudaStream_t st);
+
+// ---- plain form (baseline) -----------------------------------------------------
+// One system at a time; y = (x, v) in device memory; k buffers in `work` (8 s doubles).
+struct PlainSys {
+    int32_t s;
+    int32_t dense;          // 0: tridiagonal coefficients, 1: dense B
+    const double* coef;     // tridiagonal [3][s] or dense [s][s] of this parameter set
+};
+cudaError_t launch_plain_step(const PlainSys& sys, double* y, double* work, double h, cudaStream_t st);
+
+}  // namespace cho

@@ -1,0 +1,91 @@
+// ctx.h -- the library's context and system objects (internal).
+#pragma once
+
+#include "../../include/cho.h"
+#include "cho_internal.h"
+
+#include <cstdint>
+#include <mutex>
+#include <set>
+#include <vector>
+
+namespace cho {
+
+// Sets the thread-local message returned by cho_last_error() and returns st.
+cho_status fail(cho_status st, const char* fmt, ...);
+void clear_error();
+
+// Makes `dev` current for the scope and restores the caller's device after.
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    bool ok() const { return ok_; }
+
+private:
+    int prev_ = -1;
+    bool ok_ = false;
+};
+
+// Grow-only device buffer owned by a context.
+class Workspace {
+public:
+    void* get(size_t bytes, cudaError_t* err);
+    void release();
+
+private:
+    void* ptr_ = nullptr;
+    size_t cap_ = 0;
+};
+
+struct ServeEngine;
+
+}  // namespace cho
+
+struct cho_system_impl {
+    cho_ctx* ctx = nullptr;
+    int32_t kind = 0;
+    int32_t s = 0;
+    int64_t n_sys = 0;
+    int32_t path = 0;
+    int32_t S = 0;          // rk4_small padded size
+    int32_t s_pad = 0;      // rk4_dense padded size
+    double omega_max = 0.0;
+    std::vector<double> omegas;
+    // host copies of the description
+    std::vector<double> h_masses, h_springs, h_M, h_K;
+    // device data (see cho_internal.h for layouts)
+    double* d_B64 = nullptr;
+    float* d_B32 = nullptr;
+    uint16_t* d_Bbf = nullptr;
+    double* d_masses = nullptr;
+    double* d_springs = nullptr;
+    double* d_M = nullptr;
+    double* d_K = nullptr;
+    double* d_plain = nullptr;          // FP64 plain-form coefficients, owned
+    const double* d_plain_shared = nullptr;  // or an alias of d_B64
+};
+
+struct cho_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    cho_config cfg{};
+    std::mutex mu;                      // guards `systems`
+    std::set<cho_system_impl*> systems;
+    std::mutex ws_mu;                   // guards `ws`
+    cho::Workspace ws;                  // host-memory batch staging
+    std::mutex plain_mu;
+    cho::Workspace plain_ws;            // plain-form state and stage buffers
+    cho::ServeEngine* serve = nullptr;
+    std::mutex serve_mu;
+};
+
+namespace cho {
+// Builds the dense-path device data (B in FP64, FP32 pairs and BF16 pieces).
+cudaError_t build_dense_device(cho_system_impl* sys, const double* B);
+// BF16 pieces of B for the tensor-core kernel (rk4_dense_tc.cu).
+cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B);
+// Stops the serving thread of a context, if any.
+void serve_stop(cho_ctx* ctx);
+}  // namespace cho

@@ -1,0 +1,306 @@
+// rk4_chain.cu -- classical RK4 for fixed-free spring chains (eq. 2 generalised).
+//
+// B = M^{-1} K of a chain is tridiagonal: row i couples DOF i only to i-1 and
+// i+1, so each stage's acceleration is a three-point stencil
+//     a_i = -(l_i x_{i-1} + d_i x_i + u_i x_{i+1}),
+//     l_i = -C_i / m_i,  d_i = (C_i + C_{i+1}) / m_i,  u_i = -C_{i+1} / m_i,
+// with x_{-1} = 0 (the wall) and u_{s-1} = 0 (the free end).
+//
+// One CTA integrates one instance for the whole horizon.  Thread t owns P
+// consecutive DOFs [tP, tP + P) with their coefficients and state in
+// registers.  Per stage it needs one value from each neighbouring thread:
+// inside a warp these come by shuffle, across warps through a double-buffered
+// shared-memory edge array, so each stage costs a single __syncthreads.
+// Stage order and the state update are those of rk4_small.cu.
+#include "cho_internal.h"
+#include "rk4_common.cuh"
+#include "../../include/cho.h"
+
+namespace cho {
+namespace {
+
+// Batch form: coefficient set per instance or shared; FP64 in and out.
+template <bool F64>
+struct ChainBatchSrc {
+    ChainSys sys;
+    BatchIO io;
+    using Real = std::conditional_t<F64, double, float>;
+
+    __device__ int s(int64_t) const { return sys.s; }
+    __device__ double h(int64_t q) const { return io.h[io.h_per_inst ? q : 0]; }
+    __device__ int64_t steps(int64_t) const { return io.n_steps; }
+    __device__ int64_t ckpt_every() const { return io.ckpt_every; }
+    __device__ const void* coef(int64_t q) const
+    {
+        const int64_t set = sys.per_inst_sys ? q : 0;
+        if constexpr (F64) return sys.C64 + set * 3 * sys.s;
+        else return sys.C32 + set * 6 * sys.s;
+    }
+    __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const double xd = io.x0[q * sys.s + i];
+        const double vd = io.v0[q * sys.s + i];
+        x = (Real)xd;
+        v = (Real)vd;
+        cx = F64 ? 0.f : (float)((double)x - xd);
+        cv = F64 ? 0.f : (float)((double)v - vd);
+    }
+    __device__ void checkpoint(int64_t q, int64_t ck, int i, Real x, Real v, float cx, float cv) const
+    {
+        if (io.x_traj == nullptr) return;
+        const int64_t o = (q * io.n_ck + ck) * sys.s + i;
+        io.x_traj[o] = (double)x - (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+    }
+    __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
+    {
+        io.x_out[q * sys.s + i] = (double)x - (double)cx;
+        io.v_out[q * sys.s + i] = (double)v - (double)cv;
+    }
+    __device__ void flag_nonfinite(int64_t) const {}
+};
+
+// Slot form: state block [x(s), v(s), cx(s), cv(s)] in kernel precision.
+template <bool F64>
+struct ChainSlotSrc {
+    SlotIO io;
+    using Real = std::conditional_t<F64, double, float>;
+
+    __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
+    __device__ int s(int64_t q) const { return d(q).s; }
+    __device__ double h(int64_t q) const { return d(q).h; }
+    __device__ int64_t steps(int64_t q) const { return d(q).steps; }
+    __device__ int64_t ckpt_every() const { return 0; }
+    __device__ const void* coef(int64_t q) const { return d(q).coef; }
+    __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const int sz = d(q).s;
+        const Real* st = (const Real*)d(q).state;
+        x = st[i];
+        v = st[sz + i];
+        if constexpr (F64) {
+            cx = cv = 0.f;
+        } else {
+            cx = st[2 * sz + i];
+            cv = st[3 * sz + i];
+        }
+    }
+    __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
+    __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
+    {
+        const int sz = d(q).s;
+        Real* st = (Real*)d(q).state;
+        st[i] = x;
+        st[sz + i] = v;
+        if constexpr (!F64) {
+            st[2 * sz + i] = cx;
+            st[3 * sz + i] = cv;
+        }
+    }
+    __device__ void flag_nonfinite(int64_t q) const { io.slots[io.slot_ids[q]].status = CHO_ENONFINITE; }
+};
+
+template <int P, bool F64, int MAXT, class Src>
+__global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
+{
+    using Real = std::conditional_t<F64, double, float>;
+    __shared__ Real edge_last[2][32];   // last DOF of each warp
+    __shared__ Real edge_first[2][32];  // first DOF of each warp
+    __shared__ int any_bad;
+
+    const int64_t q = blockIdx.x;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const int s = src.s(q);
+    const int i0 = t * P;
+    if (t == 0) any_bad = 0;
+    __syncthreads();
+
+    // coefficients of rows i0 .. i0+P-1 (zero beyond s: padded DOFs stay at rest)
+    Real lh[P], dh[P], uh[P];
+    float ll[P], dl[P], ul[P];
+    const void* cb = src.coef(q);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = i0 + p;
+        const bool in = i < s;
+        if constexpr (F64) {
+            const double* c = (const double*)cb;
+            lh[p] = in ? c[i] : 0.0;
+            dh[p] = in ? c[s + i] : 0.0;
+            uh[p] = in ? c[2 * s + i] : 0.0;
+            ll[p] = dl[p] = ul[p] = 0.f;
+        } else {
+            const float* c = (const float*)cb;
+            lh[p] = in ? c[i] : 0.f;
+            dh[p] = in ? c[s + i] : 0.f;
+            uh[p] = in ? c[2 * s + i] : 0.f;
+            ll[p] = in ? c[3 * s + i] : 0.f;
+            dl[p] = in ? c[4 * s + i] : 0.f;
+            ul[p] = in ? c[5 * s + i] : 0.f;
+        }
+    }
+
+    const StepSize<F64> hs(src.h(q));
+    Real x[P], v[P];
+    float cx[P], cv[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = i0 + p;
+        if (i < s) {
+            src.load(q, i, x[p], v[p], cx[p], cv[p]);
+        } else {
+            x[p] = v[p] = 0;
+            cx[p] = cv[p] = 0.f;
+        }
+    }
+
+    int buf = 0;
+    auto accel = [&](const Real (&xs)[P], Real (&acc)[P]) {
+        Real left = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
+        Real right = __shfl_down_sync(0xffffffffu, xs[0], 1);
+        if (lane == 31) edge_last[buf][warp] = xs[P - 1];
+        if (lane == 0) edge_first[buf][warp] = xs[0];
+        __syncthreads();
+        if (lane == 0) left = warp > 0 ? edge_last[buf][warp - 1] : (Real)0;
+        if (lane == 31) right = warp + 1 < nwarp ? edge_first[buf][warp + 1] : (Real)0;
+        buf ^= 1;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const Real xl = p == 0 ? left : xs[p - 1];
+            const Real xr = p == P - 1 ? right : xs[p + 1];
+            Real a;
+            if constexpr (F64) {
+                a = fmar(dh[p], xs[p], fmar(uh[p], xr, lh[p] * xl));
+            } else {
+                float lo = fmaf(ul[p], xr, fmaf(dl[p], xs[p], ll[p] * xl));
+                a = fmaf(dh[p], xs[p], fmaf(uh[p], xr, fmaf(lh[p], xl, lo)));
+            }
+            acc[p] = -a;
+        }
+    };
+
+    const int64_t n = src.steps(q);
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        for (int64_t it = 0; it < every; ++it) {
+            Real a[P], xs[P], kx[P], kv[P], vs[P];
+            accel(x, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = v[p];
+                kv[p] = a[p];
+                xs[p] = x[p] + hs.h2 * v[p];
+                vs[p] = v[p] + hs.h2 * a[p];
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = kx[p] + (Real)2 * vs[p];
+                kv[p] = kv[p] + (Real)2 * a[p];
+                xs[p] = x[p] + hs.h2 * vs[p];
+                vs[p] = v[p] + hs.h2 * a[p];
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = kx[p] + (Real)2 * vs[p];
+                kv[p] = kv[p] + (Real)2 * a[p];
+                xs[p] = x[p] + hs.h * vs[p];
+                vs[p] = v[p] + hs.h * a[p];
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = kx[p] + vs[p];
+                kv[p] = kv[p] + a[p];
+                state_add<F64>(x[p], cx[p], hs.inc(kx[p]));
+                state_add<F64>(v[p], cv[p], hs.inc(kv[p]));
+            }
+        }
+        if (src.ckpt_every() > 0) {
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (i0 + p < s) src.checkpoint(q, ck, i0 + p, x[p], v[p], cx[p], cv[p]);
+            ++ck;
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (i0 + p < s) {
+            src.store(q, i0 + p, x[p], v[p], cx[p], cv[p]);
+            bad |= !(isfinite((double)x[p]) && isfinite((double)v[p]));
+        }
+    }
+    if (bad) any_bad = 1;
+    __syncthreads();
+    if (t == 0 && any_bad) src.flag_nonfinite(q);
+}
+
+template <int P, bool F64, class Src>
+cudaError_t launch_p(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
+{
+    int threads = (s_max + P - 1) / P;
+    threads = ((threads + 31) / 32) * 32;
+    if (threads > kChainMaxThreads) return cudaErrorInvalidValue;
+    if (n_inst <= 0) return cudaSuccess;
+    if (n_inst > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if constexpr (P == 8) {
+        if (threads > 256) {   // s > 2048: wide CTAs, 64 registers per thread
+            rk4_chain_kernel<P, F64, kChainMaxThreads, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+            return cudaGetLastError();
+        }
+    }
+    rk4_chain_kernel<P, F64, 256, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+    return cudaGetLastError();
+}
+
+template <bool F64, class Src>
+cudaError_t launch_any(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
+{
+    switch (chain_dofs_per_thread(s_max)) {
+        case 1: return launch_p<1, F64>(src, n_inst, s_max, st);
+        case 2: return launch_p<2, F64>(src, n_inst, s_max, st);
+        case 4: return launch_p<4, F64>(src, n_inst, s_max, st);
+        case 8: return launch_p<8, F64>(src, n_inst, s_max, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// DOFs per thread: at most 256 threads per CTA up to s = 2048, then 8 DOFs per
+// thread on up to 1024 threads (s <= 8192).
+int chain_dofs_per_thread(int s)
+{
+    if (s <= 256) return 1;
+    if (s <= 512) return 2;
+    if (s <= 1024) return 4;
+    return 8;
+}
+
+cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
+{
+    if (fp64) {
+        ChainBatchSrc<true> s{sys, io};
+        return launch_any<true>(s, io.n_inst, sys.s, st);
+    }
+    ChainBatchSrc<false> s{sys, io};
+    return launch_any<false>(s, io.n_inst, sys.s, st);
+}
+
+cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaStream_t st)
+{
+    if (fp64) {
+        ChainSlotSrc<true> s{io};
+        return launch_any<true>(s, io.n_inst, s_max, st);
+    }
+    ChainSlotSrc<false> s{io};
+    return launch_any<false>(s, io.n_inst, s_max, st);
+}
+
+}  // namespace cho

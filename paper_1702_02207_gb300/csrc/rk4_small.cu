@@ -1,0 +1,300 @@
+// rk4_small.cu -- classical RK4 for systems of s <= 32 degrees of freedom.
+//
+// Each instance is integrated by a group of G = S/R lanes of one warp (S = s
+// padded to a power of two, R rows of B = M^{-1}K per lane).  For S <= 4 a
+// single thread holds the whole instance (G = 1): state, stage values and all
+// of B live in registers and no data is exchanged.  For S >= 8 each lane
+// holds R rows of B and R degrees of freedom; the stage displacement is
+// published to a per-group shared-memory slot once per stage and read back
+// as a broadcast, so that every lane can form its rows of B x.
+//
+// One RK4 step on y = (x, v) (Section 3, first-order form; right-hand side
+// D = (v, -B x) as D(1)..D(4) for eq. 2):
+//   a1 = -B x                    k1 = (v,   a1)
+//   a2 = -B (x + h/2 v)          k2 = (v2,  a2),  v2 = v + h/2 a1
+//   a3 = -B (x + h/2 v2)         k3 = (v3,  a3),  v3 = v + h/2 a2
+//   a4 = -B (x + h v3)           k4 = (v4,  a4),  v4 = v + h a3
+//   x += h/6 (v + 2 v2 + 2 v3 + v4),  v += h/6 (a1 + 2 a2 + 2 a3 + a4)
+// The whole horizon runs with the state in registers; only checkpoints and
+// the final state are written to memory.
+#include "cho_internal.h"
+#include "rk4_common.cuh"
+#include "../../include/cho.h"
+
+namespace cho {
+namespace {
+
+constexpr int rows_per_lane(int S) { return S <= 4 ? S : (S == 8 ? 2 : 1); }
+
+// ---- instance sources ----------------------------------------------------------
+
+// Batch form: FP64 arrays in and out, shared step count, optional checkpoints.
+template <bool F64, int S>
+struct BatchSrc {
+    SmallSys sys;
+    BatchIO io;
+    using Real = std::conditional_t<F64, double, float>;
+
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ int s(int64_t) const { return sys.s; }
+    __device__ double h(int64_t q) const { return io.h[io.h_per_inst ? q : 0]; }
+    __device__ int64_t steps(int64_t) const { return io.n_steps; }
+    __device__ int64_t ckpt_every() const { return io.ckpt_every; }
+
+    __device__ void coef(int64_t q, int row, int j, Real& hi, float& lo) const
+    {
+        const int64_t set = sys.per_inst_sys ? q : 0;
+        if constexpr (F64) {
+            hi = sys.B64[(set * S + row) * S + j];
+            lo = 0.f;
+        } else {
+            const float* b = sys.B32 + set * 2 * S * S;
+            hi = b[row * S + j];
+            lo = b[S * S + row * S + j];
+        }
+    }
+    __device__ void load(int64_t q, int row, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const int sz = sys.s;
+        const double xd = row < sz ? io.x0[q * sz + row] : 0.0;
+        const double vd = row < sz ? io.v0[q * sz + row] : 0.0;
+        x = (Real)xd;
+        v = (Real)vd;
+        // Kahan convention: represented value = x - c
+        cx = F64 ? 0.f : (float)((double)x - xd);
+        cv = F64 ? 0.f : (float)((double)v - vd);
+    }
+    __device__ void checkpoint(int64_t q, int64_t ck, int row, Real x, Real v, float cx, float cv) const
+    {
+        const int sz = sys.s;
+        if (row >= sz || io.x_traj == nullptr) return;
+        const int64_t o = (q * io.n_ck + ck) * sz + row;
+        io.x_traj[o] = (double)x - (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+    }
+    __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool) const
+    {
+        const int sz = sys.s;
+        if (row >= sz) return;
+        io.x_out[q * sz + row] = (double)x - (double)cx;
+        io.v_out[q * sz + row] = (double)v - (double)cv;
+    }
+};
+
+// Slot form (serving): resident state block [x(S), v(S), cx(S), cv(S)] in the
+// kernel's precision, coefficient block in the batch layout of one set.
+template <bool F64, int S>
+struct SlotSrc {
+    SlotIO io;
+    using Real = std::conditional_t<F64, double, float>;
+
+    __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ int s(int64_t q) const { return d(q).s; }
+    __device__ double h(int64_t q) const { return d(q).h; }
+    __device__ int64_t steps(int64_t q) const { return d(q).steps; }
+    __device__ int64_t ckpt_every() const { return 0; }
+
+    __device__ void coef(int64_t q, int row, int j, Real& hi, float& lo) const
+    {
+        if constexpr (F64) {
+            hi = ((const double*)d(q).coef)[row * S + j];
+            lo = 0.f;
+        } else {
+            const float* b = (const float*)d(q).coef;
+            hi = b[row * S + j];
+            lo = b[S * S + row * S + j];
+        }
+    }
+    __device__ void load(int64_t q, int row, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const Real* st = (const Real*)d(q).state;
+        x = st[row];
+        v = st[S + row];
+        if constexpr (F64) {
+            cx = cv = 0.f;
+        } else {
+            cx = st[2 * S + row];
+            cv = st[3 * S + row];
+        }
+    }
+    __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
+    __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool bad) const
+    {
+        SlotDesc& sd = io.slots[io.slot_ids[q]];
+        Real* st = (Real*)sd.state;
+        st[row] = x;
+        st[S + row] = v;
+        if constexpr (!F64) {
+            st[2 * S + row] = cx;
+            st[3 * S + row] = cv;
+        }
+        if (bad) sd.status = CHO_ENONFINITE;
+    }
+};
+
+// ---- the kernel ------------------------------------------------------------------
+
+template <int S, bool F64, class Src>
+__global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
+{
+    using Real = std::conditional_t<F64, double, float>;
+    constexpr int R = rows_per_lane(S);
+    constexpr int G = S / R;                      // lanes per instance
+    constexpr int GPB = kSmallThreads / G;        // groups per block
+    __shared__ Real xch[G > 1 ? 2 : 1][G > 1 ? GPB : 1][G > 1 ? S : 1];
+
+    const int64_t tid = (int64_t)blockIdx.x * kSmallThreads + threadIdx.x;
+    const int64_t q = tid / G;
+    const int g = (int)(tid % G);
+    const int grp = threadIdx.x / G;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+    if (q >= src.count()) return;                 // whole groups leave together
+
+    // rows g*R .. g*R+R-1 of B (hi, lo)
+    Real bh[R][S];
+    float bl[R][S];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < S; ++j) src.coef(q, g * R + r, j, bh[r][j], bl[r][j]);
+
+    const StepSize<F64> hs(src.h(q));
+    Real x[R], v[R];
+    float cx[R], cv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) src.load(q, g * R + r, x[r], v[r], cx[r], cv[r]);
+
+    int buf = 0;
+    // acc[r] = -(B xs)[row g*R + r]
+    auto accel = [&](const Real (&xs)[R], Real (&acc)[R]) {
+        if constexpr (G == 1) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Real t = 0;
+                if constexpr (!F64) {
+#pragma unroll
+                    for (int j = 0; j < S; ++j) t = fmaf(bl[r][j], xs[j], t);
+                }
+#pragma unroll
+                for (int j = 0; j < S; ++j) t = fmar(bh[r][j], xs[j], t);
+                acc[r] = -t;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) xch[buf][grp][g * R + r] = xs[r];
+            __syncwarp(gmask);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Real t = 0;
+                if constexpr (!F64) {
+#pragma unroll
+                    for (int j = 0; j < S; ++j) t = fmaf(bl[r][j], xch[buf][grp][j], t);
+                }
+#pragma unroll
+                for (int j = 0; j < S; ++j) t = fmar(bh[r][j], xch[buf][grp][j], t);
+                acc[r] = -t;
+            }
+            buf ^= 1;
+        }
+    };
+
+    const int64_t n = src.steps(q);
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        for (int64_t it = 0; it < every; ++it) {
+            Real a[R], xs[R], kx[R], kv[R], vs[R];
+            accel(x, a);                                   // stage 1
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                kx[r] = v[r];
+                kv[r] = a[r];
+                xs[r] = x[r] + hs.h2 * v[r];
+                vs[r] = v[r] + hs.h2 * a[r];
+            }
+            accel(xs, a);                                  // stage 2
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                kx[r] = kx[r] + (Real)2 * vs[r];
+                kv[r] = kv[r] + (Real)2 * a[r];
+                xs[r] = x[r] + hs.h2 * vs[r];
+                vs[r] = v[r] + hs.h2 * a[r];
+            }
+            accel(xs, a);                                  // stage 3
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                kx[r] = kx[r] + (Real)2 * vs[r];
+                kv[r] = kv[r] + (Real)2 * a[r];
+                xs[r] = x[r] + hs.h * vs[r];
+                vs[r] = v[r] + hs.h * a[r];
+            }
+            accel(xs, a);                                  // stage 4
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                kx[r] = kx[r] + vs[r];
+                kv[r] = kv[r] + a[r];
+                state_add<F64>(x[r], cx[r], hs.inc(kx[r]));
+                state_add<F64>(v[r], cv[r], hs.inc(kv[r]));
+            }
+        }
+        if (src.ckpt_every() > 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) src.checkpoint(q, ck, g * R + r, x[r], v[r], cx[r], cv[r]);
+            ++ck;
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) bad |= !(isfinite((double)x[r]) && isfinite((double)v[r]));
+#pragma unroll
+    for (int r = 0; r < R; ++r) src.store(q, g * R + r, x[r], v[r], cx[r], cv[r], bad);
+}
+
+template <int S, bool F64, class Src>
+cudaError_t launch_one(const Src& src, int64_t n, cudaStream_t st)
+{
+    constexpr int G = S / rows_per_lane(S);
+    const int64_t threads = n * G;
+    const int64_t blocks = (threads + kSmallThreads - 1) / kSmallThreads;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rk4_small_kernel<S, F64, Src><<<(unsigned)blocks, kSmallThreads, 0, st>>>(src);
+    return cudaGetLastError();
+}
+
+template <template <bool, int> class SrcT, class Init>
+cudaError_t dispatch(int S, bool fp64, int64_t n, cudaStream_t st, const Init& init)
+{
+#define CHO_SMALL_CASE(SV)                                                                 \
+    case SV:                                                                               \
+        if (fp64) { SrcT<true, SV> s; init(s); return launch_one<SV, true>(s, n, st); }    \
+        else { SrcT<false, SV> s; init(s); return launch_one<SV, false>(s, n, st); }
+    switch (S) {
+        CHO_SMALL_CASE(2)
+        CHO_SMALL_CASE(4)
+        CHO_SMALL_CASE(8)
+        CHO_SMALL_CASE(16)
+        CHO_SMALL_CASE(32)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CHO_SMALL_CASE
+}
+
+}  // namespace
+
+cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
+{
+    return dispatch<BatchSrc>(sys.S, fp64, io.n_inst, st, [&](auto& s) {
+        s.sys = sys;
+        s.io = io;
+    });
+}
+
+cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st)
+{
+    return dispatch<SlotSrc>(S, fp64, io.n_inst, st, [&](auto& s) { s.io = io; });
+}
+
+}  // namespace cho

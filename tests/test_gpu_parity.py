@@ -1,0 +1,315 @@
+"""GPU parity: every kernel family against the FP64 oracle on the same seeded inputs.
+
+Error metric (per instance): max over checkpoints of |x_gpu - x_ref|_inf divided by
+max over checkpoints of |x_ref|_inf, and the same for v.  Bars: FP64 mode 1e-10,
+FP32 + Kahan mode 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1702_02207_gb300 import cho, inputs
+from parity_util import TOL_FP32, TOL_FP64, oracle_run, rel_err, sample_indices
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = cho.cho_init(0)
+    yield c
+    cho.cho_shutdown(c)
+
+
+def make_system(ctx, cfg):
+    if cfg["kind"] == "dense":
+        return cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
+    return cho.cho_create_system(ctx, cfg["kind"], masses=cfg["masses"], springs=cfg["springs"])
+
+
+def run_gpu(ctx, cfg, prec, ckpt_every, device=True, n_steps=None):
+    import torch
+
+    n_steps = cfg["n_steps"] if n_steps is None else n_steps
+    sys_ = make_system(ctx, cfg)
+    try:
+        if device:
+            dev = torch.device("cuda:0")
+            x0 = torch.as_tensor(cfg["x0"], device=dev)
+            v0 = torch.as_tensor(cfg["v0"], device=dev)
+            h = torch.as_tensor(cfg["h"], device=dev)
+            out = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, n_steps, prec, ckpt_every,
+                                          trajectory=ckpt_every > 0)
+            torch.cuda.synchronize()
+            out = {k: v.cpu().numpy() for k, v in out.items()}
+        else:
+            out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], n_steps, prec,
+                                          ckpt_every, trajectory=ckpt_every > 0)
+    finally:
+        cho.cho_destroy_system(sys_)
+    return out
+
+
+def check(out, ref, tol, idx=None):
+    sel = slice(None) if idx is None else idx
+    ex = rel_err(out["x_traj"][sel], ref["x_traj"])
+    ev = rel_err(out["v_traj"][sel], ref["v_traj"])
+    assert np.all(np.isfinite(out["x"][sel]))
+    assert ex.max() <= tol, (ex.max(), int(np.argmax(ex)))
+    assert ev.max() <= tol, (ev.max(), int(np.argmax(ev)))
+    return ex.max(), ev.max()
+
+
+# ---- eq. 3 (the paper's 2-DOF example) -----------------------------------------------
+
+def test_eq3_fp64_full_horizon(ctx):
+    cfg = inputs.eq3_single()
+    out = run_gpu(ctx, cfg, "fp64", 1000)
+    ref = oracle_run(cfg, ckpt_every=1000)
+    check(out, ref, TOL_FP64)
+    assert np.allclose(out["x"][0], [0.5919944669044028, -0.55303750830408224], atol=1e-10)
+
+
+@pytest.mark.parametrize("x0", [(2.0, -3.0)])
+def test_eq3_fig2_start_fp32(ctx, x0):
+    cfg = inputs.eq3_single(x0)
+    cfg["n_steps"] = 20_000
+    out = run_gpu(ctx, cfg, "fp32_kahan", 200)
+    ref = oracle_run(cfg, ckpt_every=200)
+    check(out, ref, TOL_FP32)
+
+
+# ---- eq. 2 batches --------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+@pytest.mark.parametrize("n_inst", [1, 7, 1000])
+def test_two_dof_batch_ragged(ctx, prec, tol, n_inst):
+    cfg = inputs.two_dof_batch(n_inst=n_inst, n_steps=10_000)
+    out = run_gpu(ctx, cfg, prec, 100)
+    ref = oracle_run(cfg, ckpt_every=100)
+    check(out, ref, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32_kahan", TOL_FP32), ("fp64", TOL_FP64)])
+def test_two_dof_full_size_sampled(ctx, prec, tol):
+    """65,536 systems x 1e4 steps in one launch (the benchmark's configuration), sampled."""
+    cfg = inputs.two_dof_batch()
+    out = run_gpu(ctx, cfg, prec, 100)
+    idx = sample_indices(cfg["x0"].shape[0], 256)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=100)
+    check(out, ref, tol, idx)
+
+
+def test_host_and_device_memory_agree(ctx):
+    cfg = inputs.two_dof_batch(n_inst=300, n_steps=2000)
+    a = run_gpu(ctx, cfg, "fp32_kahan", 100, device=True)
+    b = run_gpu(ctx, cfg, "fp32_kahan", 100, device=False)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v_traj"], b["v_traj"])
+
+
+# ---- small systems (rk4_small) ----------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 3, 4, 5, 8, 9, 16, 17, 31, 32])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_small_chains(ctx, s, prec, tol):
+    cfg = inputs.chain_batch(n_inst=37, s=s, n_steps=3000, seed=500 + s)
+    out = run_gpu(ctx, cfg, prec, 100)
+    ref = oracle_run(cfg, ckpt_every=100)
+    check(out, ref, tol)
+
+
+def dense_per_instance(s, n_inst, seed, n_steps=2000):
+    rng = np.random.default_rng(seed)
+    Ms, Ks = [], []
+    for i in range(n_inst):
+        M, K, _, _ = inputs.dense_system(s, seed * 1000 + i)
+        Ms.append(M)
+        Ks.append(K)
+    M = np.stack(Ms)
+    K = np.stack(Ks)
+    w = inputs.omega_max_dense(M, K)
+    h = inputs.fp32_exact(2 * math.pi / w / 100)
+    return {"kind": "dense", "s": s, "M": M, "K": K, "x0": rng.normal(size=(n_inst, s)),
+            "v0": np.zeros((n_inst, s)), "h": h, "n_steps": n_steps}
+
+
+@pytest.mark.parametrize("s", [2, 6, 8, 13, 32])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_small_dense_per_instance(ctx, s, prec, tol):
+    cfg = dense_per_instance(s, 21, 40 + s)
+    out = run_gpu(ctx, cfg, prec, 100)
+    ref = oracle_run(cfg, ckpt_every=100)
+    check(out, ref, tol)
+
+
+# ---- chains (rk4_chain) -----------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [33, 64, 255, 256, 257, 1023, 1024, 1025, 2100])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_chains(ctx, s, prec, tol):
+    n_inst = 7 if s < 2000 else 2
+    cfg = inputs.chain_batch(n_inst=n_inst, s=s, n_steps=2000, seed=900 + s)
+    out = run_gpu(ctx, cfg, prec, 100)
+    ref = oracle_run(cfg, ckpt_every=100)
+    check(out, ref, tol)
+
+
+def test_chain_full_size_sampled_fp32(ctx):
+    """4096 chains of 1024 masses x 1e4 steps, FP32 + Kahan, sampled against the oracle."""
+    cfg = inputs.chain_batch()
+    out = run_gpu(ctx, cfg, "fp32_kahan", 500)
+    idx = sample_indices(cfg["x0"].shape[0], 12)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=500)
+    check(out, ref, TOL_FP32, idx)
+
+
+# ---- dense shared systems (rk4_dense, CUDA cores) -----------------------------------------
+
+@pytest.mark.parametrize("s", [33, 64, 100, 128, 256])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_simt", TOL_FP32), ("fp32_kahan", TOL_FP32)])
+def test_dense_shared(ctx, s, prec, tol):
+    cfg = inputs.dense_group(s=s, n_inst=37, n_steps=1000)
+    out = run_gpu(ctx, cfg, prec, 100)
+    ref = oracle_run(cfg, ckpt_every=100)
+    check(out, ref, tol)
+
+
+# ---- energy -----------------------------------------------------------------------------
+
+def test_energy_matches_oracle(ctx):
+    import oracle
+
+    cfg = inputs.two_dof_batch(n_inst=50, n_steps=1000)
+    sys_ = make_system(ctx, cfg)
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 1000, "fp64", 100, energy=True)
+    finally:
+        cho.cho_destroy_system(sys_)
+    n_ck = out["x_traj"].shape[1]
+    E_ref = oracle.energy_chain(np.repeat(cfg["masses"], n_ck, 0), np.repeat(cfg["springs"], n_ck, 0),
+                                out["x_traj"].reshape(-1, 2), out["v_traj"].reshape(-1, 2)).reshape(50, n_ck)
+    assert np.allclose(out["energy"], E_ref, rtol=1e-13)
+
+
+def test_energy_dense_and_chain_api(ctx):
+    import oracle
+
+    cfg = inputs.dense_group(s=64, n_inst=9, n_steps=10)
+    sys_ = make_system(ctx, cfg)
+    try:
+        rng = np.random.default_rng(1)
+        x = rng.normal(size=(9, 64))
+        v = rng.normal(size=(9, 64))
+        E = cho.cho_energy(ctx, sys_, x, v)
+    finally:
+        cho.cho_destroy_system(sys_)
+    assert np.allclose(E, oracle.energy_dense(cfg["M"][0], cfg["K"][0], x, v), rtol=1e-13)
+    cfg = inputs.chain_batch(n_inst=5, s=300)
+    sys_ = make_system(ctx, cfg)
+    try:
+        E = cho.cho_energy(ctx, sys_, cfg["x0"], cfg["x0"])
+    finally:
+        cho.cho_destroy_system(sys_)
+    assert np.allclose(E, oracle.energy_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["x0"]), rtol=1e-13)
+
+
+def test_energy_drift_config1_on_gpu(ctx):
+    """GPU FP64 energy after 1e5 steps of eq. 3 shows RK4's drift -2.4508e-11."""
+    cfg = inputs.eq3_single()
+    sys_ = make_system(ctx, cfg)
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], "fp64",
+                                      cfg["n_steps"], energy=True)
+    finally:
+        cho.cho_destroy_system(sys_)
+    drift = (out["energy"][0, -1] - 2025.0) / 2025.0
+    assert drift == pytest.approx(-2.4508e-11, rel=2e-3)
+
+
+# ---- plain form --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["two_dof", "chain", "dense"])
+def test_plain_form_matches_oracle(ctx, kind):
+    if kind == "two_dof":
+        cfg = inputs.two_dof_batch(n_inst=3, n_steps=300)
+    elif kind == "chain":
+        cfg = inputs.chain_batch(n_inst=2, s=300, n_steps=200)
+    else:
+        cfg = inputs.dense_group(s=40, n_inst=2, n_steps=200)
+    sys_ = make_system(ctx, cfg)
+    try:
+        out = cho.cho_integrate_plain(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"])
+    finally:
+        cho.cho_destroy_system(sys_)
+    ref = oracle_run(cfg)
+    assert rel_err(out["x"][:, None], ref["x"][:, None]).max() < TOL_FP64
+
+
+# ---- edge cases and errors ----------------------------------------------------------------
+
+def test_zero_steps_and_zero_instances(ctx):
+    cfg = inputs.chain_batch(n_inst=4, s=40, n_steps=0)
+    out = run_gpu(ctx, cfg, "fp64", 0, n_steps=0)
+    assert np.array_equal(out["x"], cfg["x0"]) and np.array_equal(out["v"], cfg["v0"])
+    out = run_gpu(ctx, cfg, "fp32_kahan", 0, n_steps=0)
+    assert np.array_equal(out["x"], cfg["x0"])      # Kahan carry makes the round trip exact
+    sys_ = make_system(ctx, inputs.chain_batch(n_inst=1, s=40))
+    try:
+        r = cho.cho_integrate_batch(ctx, sys_, np.zeros((0, 40)), np.zeros((0, 40)), [1e-3], 10)
+        assert r["x"].shape == (0, 40)
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+def test_resume_is_bitwise_in_fp64(ctx):
+    cfg = inputs.chain_batch(n_inst=5, s=50, n_steps=400, seed=77)
+    full = run_gpu(ctx, cfg, "fp64", 0)
+    half = run_gpu(ctx, cfg, "fp64", 0, n_steps=200)
+    cfg2 = dict(cfg, x0=half["x"], v0=half["v"])
+    rest = run_gpu(ctx, cfg2, "fp64", 0, n_steps=200)
+    assert np.array_equal(rest["x"], full["x"]) and np.array_equal(rest["v"], full["v"])
+
+
+def test_errors_are_reported(ctx):
+    with pytest.raises(cho.ChoError) as ei:
+        cho.cho_create_system(ctx, "chain", masses=[[1.0, -1.0]], springs=[[1.0, 1.0]])
+    assert ei.value.status == cho.CHO_EINVAL
+    with pytest.raises(cho.ChoError) as ei:
+        cho.cho_create_system(ctx, "dense", M=[[1.0, 2.0], [2.0, 1.0]], K=np.eye(2))
+    assert ei.value.status == cho.CHO_ENOTSPD
+    with pytest.raises(cho.ChoError) as ei:
+        cho.cho_create_system(ctx, "two_dof", masses=[[1.0, 1.0, 1.0]], springs=[[1.0, 1.0, 1.0]])
+    assert ei.value.status == cho.CHO_EINVAL
+    cfg = inputs.eq3_single()
+    sys_ = make_system(ctx, cfg)
+    try:
+        w, s, n = cho.cho_system_info(sys_)
+        assert (s, n) == (2, 1)
+        assert w == pytest.approx(math.sqrt(1012.5 * (3 + math.sqrt(5)) / 2), rel=1e-12)
+        with pytest.raises(cho.ChoError) as ei:      # |omega h| > 2 sqrt 2
+            cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], [3.0 / w], 10)
+        assert ei.value.status == cho.CHO_EUNSTABLE
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 10, ckpt_every=3)
+        assert ei.value.status == cho.CHO_EINVAL
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 10, prec="bf16x3")
+        assert ei.value.status == cho.CHO_EINVAL
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+def test_omega_max_matches_library_eigensolvers(ctx):
+    cfg = inputs.chain_batch(n_inst=3, s=200)
+    sys_ = make_system(ctx, cfg)
+    try:
+        assert np.allclose(cho.cho_system_omegas(sys_), cfg["omega_max"], rtol=1e-12)
+    finally:
+        cho.cho_destroy_system(sys_)
+    cfg = inputs.dense_group(s=96, n_inst=1)
+    sys_ = make_system(ctx, cfg)
+    try:
+        assert cho.cho_system_info(sys_)[0] == pytest.approx(cfg["omega_max"], rel=1e-10)
+    finally:
+        cho.cho_destroy_system(sys_)
