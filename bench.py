@@ -246,10 +246,10 @@ def main():
         sel = {k: torch.as_tensor(cfg[k][idx], device=dev) for k in ("x0", "v0", "h")}
         ms_, sp_ = cfg["masses"][idx], cfg["springs"][idx]
         s2 = cho.cho_create_system(ctx, "two_dof", masses=ms_, springs=sp_)
-        r = cho.cho_integrate_batch(ctx, s2, sel["x0"], sel["v0"], sel["h"], N_STEPS, prec, 100, trajectory=True)
+        r = cho.cho_integrate_batch(ctx, s2, sel["x0"], sel["v0"], sel["h"], N_STEPS, prec, 125, trajectory=True)
         torch.cuda.synchronize()
         cho.cho_destroy_system(s2)
-        ref = oracle.rk4_chain(ms_, sp_, cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx], N_STEPS, 100,
+        ref = oracle.rk4_chain(ms_, sp_, cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx], N_STEPS, 125,
                                threads=min(16, os.cpu_count() or 1))
         e = []
         for k in ("x_traj", "v_traj"):

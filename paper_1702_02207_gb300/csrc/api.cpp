@@ -316,11 +316,21 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
         e = upload(&sys->d_B64, B64.data(), B64.size());
         if (e == cudaSuccess) e = upload(&sys->d_B32, B32.data(), B32.size());
     } else if (sys->path == PATH_CHAIN) {
-        std::vector<float> C32((size_t)n_sys * 6 * s);
-        for (int64_t p = 0; p < n_sys; ++p)
-            for (int k = 0; k < 3 * s; ++k)
-                split_pair(plain[(size_t)p * 3 * s + k], C32[(size_t)p * 6 * s + k], C32[(size_t)p * 6 * s + 3 * s + k]);
-        e = upload(&sys->d_B64, plain.data(), plain.size());
+        // spring form of eq. 2: g_i = C_i / m_i, u_i = C_{i+1} / m_i
+        std::vector<double> C64((size_t)n_sys * 2 * s);
+        std::vector<float> C32((size_t)n_sys * 4 * s);
+        for (int64_t p = 0; p < n_sys; ++p) {
+            const double* m = d->masses + p * s;
+            const double* C = d->springs + p * s;
+            double* c = &C64[(size_t)p * 2 * s];
+            for (int i = 0; i < s; ++i) {
+                c[i] = C[i] / m[i];
+                c[s + i] = i + 1 < s ? C[i + 1] / m[i] : 0.0;
+            }
+            float* f = &C32[(size_t)p * 4 * s];
+            for (int k = 0; k < 2 * s; ++k) split_pair(c[k], f[k], f[2 * s + k]);
+        }
+        e = upload(&sys->d_B64, C64.data(), C64.size());
         if (e == cudaSuccess) e = upload(&sys->d_B32, C32.data(), C32.size());
     } else {
         e = build_dense_device(sys, plain.data());
@@ -334,13 +344,7 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
             if (e == cudaSuccess) e = upload(&sys->d_K, sys->h_K.data(), sys->h_K.size());
         }
     }
-    if (e == cudaSuccess) {
-        if (sys->path == PATH_CHAIN) {
-            sys->d_plain_shared = sys->d_B64;  // same [n_sys][3][s] FP64 layout
-        } else {
-            e = upload(&sys->d_plain, plain.data(), plain.size());
-        }
-    }
+    if (e == cudaSuccess) e = upload(&sys->d_plain, plain.data(), plain.size());
     if (e != cudaSuccess) {
         free_system_device(sys);
         delete sys;
@@ -558,7 +562,7 @@ static cho_status run_plain_device(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     cho_system_impl* sys = b->system;
     const int s = sys->s;
     const bool dense = sys->kind == CHO_DENSE;
-    const double* coef = sys->d_plain ? sys->d_plain : sys->d_plain_shared;
+    const double* coef = sys->d_plain;
     cudaError_t e;
     std::lock_guard<std::mutex> lk(ctx->plain_mu);
     double* work = (double*)ctx->plain_ws.get(sizeof(double) * 10 * (size_t)s, &e);

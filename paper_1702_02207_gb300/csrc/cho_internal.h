@@ -81,13 +81,13 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st);
 
 // ---- rk4_chain ----------------------------------------------------------------
-// Coefficients per parameter set: three diagonals of B = M^{-1}K, each of length s:
-// FP64 [3][s] (sub, main, super) or FP32 [6][s] (sub, main, super hi; then lo).
+// Coefficients per parameter set, spring form of eq. 2: g_i = C_i/m_i and
+// u_i = C_{i+1}/m_i (u_{s-1} = 0): FP64 [2][s] (g, u) or FP32 [4][s] (g, u hi; then lo).
 struct ChainSys {
     int32_t s;
     int32_t per_inst_sys;
-    const double* C64;      // [n_sys][3][s]
-    const float* C32;       // [n_sys][6][s]
+    const double* C64;      // [n_sys][2][s]
+    const float* C32;       // [n_sys][4][s]
 };
 
 int chain_dofs_per_thread(int s);

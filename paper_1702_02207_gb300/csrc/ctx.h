@@ -62,8 +62,7 @@ struct cho_system_impl {
     double* d_springs = nullptr;
     double* d_M = nullptr;
     double* d_K = nullptr;
-    double* d_plain = nullptr;          // FP64 plain-form coefficients, owned
-    const double* d_plain_shared = nullptr;  // or an alias of d_B64
+    double* d_plain = nullptr;          // FP64 plain-form coefficients: tridiagonal [3][s] or dense [s][s]
 };
 
 struct cho_ctx {

@@ -1,17 +1,20 @@
 // rk4_chain.cu -- classical RK4 for fixed-free spring chains (eq. 2 generalised).
 //
-// B = M^{-1} K of a chain is tridiagonal: row i couples DOF i only to i-1 and
-// i+1, so each stage's acceleration is a three-point stencil
-//     a_i = -(l_i x_{i-1} + d_i x_i + u_i x_{i+1}),
-//     l_i = -C_i / m_i,  d_i = (C_i + C_{i+1}) / m_i,  u_i = -C_{i+1} / m_i,
-// with x_{-1} = 0 (the wall) and u_{s-1} = 0 (the free end).
+// Eq. 2 written per mass gives the acceleration from the spring extensions
+// e_i = x_i - x_{i-1} (e_0 = x_0, the wall spring):
+//     a_i = -g_i e_i + u_i e_{i+1},   g_i = C_i / m_i,  u_i = C_{i+1} / m_i,
+// with u_{s-1} = 0 (the free end).  This is B x for the tridiagonal
+// B = M^{-1} K, evaluated in the factored form M^{-1} D^T diag(C) D x (D the
+// difference operator): neighbouring displacements are subtracted first, which
+// is exact when they are close, so slow modes of stiff chains keep their
+// accuracy in FP32.
 //
 // One CTA integrates one instance for the whole horizon.  Thread t owns P
 // consecutive DOFs [tP, tP + P) with their coefficients and state in
-// registers.  Per stage it needs one value from each neighbouring thread:
-// inside a warp these come by shuffle, across warps through a double-buffered
-// shared-memory edge array, so each stage costs a single __syncthreads.
-// Stage order and the state update are those of rk4_small.cu.
+// registers.  Per stage it needs one displacement from each neighbouring
+// thread: inside a warp these come by shuffle, across warps through a
+// double-buffered shared-memory edge array, so each stage costs a single
+// __syncthreads.  Stage order and the state update are those of rk4_small.cu.
 #include "cho_internal.h"
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
@@ -33,8 +36,8 @@ struct ChainBatchSrc {
     __device__ const void* coef(int64_t q) const
     {
         const int64_t set = sys.per_inst_sys ? q : 0;
-        if constexpr (F64) return sys.C64 + set * 3 * sys.s;
-        else return sys.C32 + set * 6 * sys.s;
+        if constexpr (F64) return sys.C64 + set * 2 * sys.s;
+        else return sys.C32 + set * 4 * sys.s;
     }
     __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
     {
@@ -118,9 +121,9 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     if (t == 0) any_bad = 0;
     __syncthreads();
 
-    // coefficients of rows i0 .. i0+P-1 (zero beyond s: padded DOFs stay at rest)
-    Real lh[P], dh[P], uh[P];
-    float ll[P], dl[P], ul[P];
+    // coefficients of DOFs i0 .. i0+P-1 (zero beyond s: padded DOFs stay at rest)
+    Real gh[P], uh[P];
+    float gl[P], ul[P];
     const void* cb = src.coef(q);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -128,18 +131,15 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
         const bool in = i < s;
         if constexpr (F64) {
             const double* c = (const double*)cb;
-            lh[p] = in ? c[i] : 0.0;
-            dh[p] = in ? c[s + i] : 0.0;
-            uh[p] = in ? c[2 * s + i] : 0.0;
-            ll[p] = dl[p] = ul[p] = 0.f;
+            gh[p] = in ? c[i] : 0.0;
+            uh[p] = in ? c[s + i] : 0.0;
+            gl[p] = ul[p] = 0.f;
         } else {
             const float* c = (const float*)cb;
-            lh[p] = in ? c[i] : 0.f;
-            dh[p] = in ? c[s + i] : 0.f;
-            uh[p] = in ? c[2 * s + i] : 0.f;
-            ll[p] = in ? c[3 * s + i] : 0.f;
-            dl[p] = in ? c[4 * s + i] : 0.f;
-            ul[p] = in ? c[5 * s + i] : 0.f;
+            gh[p] = in ? c[i] : 0.f;
+            uh[p] = in ? c[s + i] : 0.f;
+            gl[p] = in ? c[2 * s + i] : 0.f;
+            ul[p] = in ? c[3 * s + i] : 0.f;
         }
     }
 
@@ -167,18 +167,21 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
         if (lane == 0) left = warp > 0 ? edge_last[buf][warp - 1] : (Real)0;
         if (lane == 31) right = warp + 1 < nwarp ? edge_first[buf][warp + 1] : (Real)0;
         buf ^= 1;
+        Real e[P + 1];                       // spring extensions e_{i0} .. e_{i0+P}
+        e[0] = xs[0] - left;
+#pragma unroll
+        for (int p = 1; p < P; ++p) e[p] = xs[p] - xs[p - 1];
+        e[P] = right - xs[P - 1];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const Real xl = p == 0 ? left : xs[p - 1];
-            const Real xr = p == P - 1 ? right : xs[p + 1];
             Real a;
             if constexpr (F64) {
-                a = fmar(dh[p], xs[p], fmar(uh[p], xr, lh[p] * xl));
+                a = fmar(uh[p], e[p + 1], -gh[p] * e[p]);
             } else {
-                float lo = fmaf(ul[p], xr, fmaf(dl[p], xs[p], ll[p] * xl));
-                a = fmaf(dh[p], xs[p], fmaf(uh[p], xr, fmaf(lh[p], xl, lo)));
+                const float lo = fmaf(ul[p], e[p + 1], -gl[p] * e[p]);
+                a = fmaf(uh[p], e[p + 1], fmaf(-gh[p], e[p], lo));
             }
-            acc[p] = -a;
+            acc[p] = a;
         }
     };
 
