@@ -51,20 +51,24 @@ struct BatchIO {
     double* v_traj;
 };
 
-// One resident request in the serving slot table (device memory).
+// One resident request in the serving slot table (device memory).  Written by
+// the host when the request is admitted; `remaining` is decremented by the
+// kernel that advances the slot.
 struct SlotDesc {
     const void* coef;       // coefficient block of its parameter set (kernel-family layout)
     void* state;            // resident state block (kernel-family layout, kernel precision)
     double h;
-    int64_t steps;          // RK4 steps to run in this chunk
+    int64_t remaining;      // RK4 steps still to run
     int32_t s;
-    int32_t status;         // written by the kernel: 0 ok, CHO_ENONFINITE on a non-finite state
+    int32_t pad;
 };
 
 struct SlotIO {
-    int64_t n_inst;         // slots in this launch
+    int64_t n_inst;         // slots advanced by this launch
     const int32_t* slot_ids;
     SlotDesc* slots;
+    int32_t* status;        // per slot: set to CHO_ENONFINITE on a non-finite state
+    int64_t chunk;          // each slot runs min(chunk, remaining) steps
 };
 
 // ---- rk4_small ----------------------------------------------------------------
@@ -104,6 +108,7 @@ struct DenseSys {
 };
 int dense_pad(int s);
 cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
+cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st);
 // tensor-core split-BF16 variant (rk4_dense_tc.cu)
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
 

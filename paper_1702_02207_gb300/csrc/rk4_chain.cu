@@ -60,7 +60,7 @@ struct ChainBatchSrc {
         io.x_out[q * sys.s + i] = (double)x - (double)cx;
         io.v_out[q * sys.s + i] = (double)v - (double)cv;
     }
-    __device__ void flag_nonfinite(int64_t) const {}
+    __device__ void finish(int64_t, int64_t, bool) const {}
 };
 
 // Slot form: state block [x(s), v(s), cx(s), cv(s)] in kernel precision.
@@ -72,7 +72,7 @@ struct ChainSlotSrc {
     __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
     __device__ int s(int64_t q) const { return d(q).s; }
     __device__ double h(int64_t q) const { return d(q).h; }
-    __device__ int64_t steps(int64_t q) const { return d(q).steps; }
+    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
     __device__ int64_t ckpt_every() const { return 0; }
     __device__ const void* coef(int64_t q) const { return d(q).coef; }
     __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
@@ -100,7 +100,12 @@ struct ChainSlotSrc {
             st[3 * sz + i] = cv;
         }
     }
-    __device__ void flag_nonfinite(int64_t q) const { io.slots[io.slot_ids[q]].status = CHO_ENONFINITE; }
+    __device__ void finish(int64_t q, int64_t ran, bool bad) const
+    {
+        const int32_t slot = io.slot_ids[q];
+        io.slots[slot].remaining -= ran;
+        if (bad) io.status[slot] = CHO_ENONFINITE;
+    }
 };
 
 template <int P, bool F64, int MAXT, class Src>
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     }
     if (bad) any_bad = 1;
     __syncthreads();
-    if (t == 0 && any_bad) src.flag_nonfinite(q);
+    if (t == 0) src.finish(q, n, any_bad != 0);
 }
 
 template <int P, bool F64, class Src>

@@ -24,38 +24,126 @@ namespace {
 
 constexpr int kDenseThreads = 256;
 
-template <int RI, int NT, bool F64>
-__global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys sys, BatchIO io)
+// Batch form: FP64 x0/v0 in, FP64 outputs, shared step count, checkpoints.
+template <bool F64>
+struct DenseBatchSrc {
+    BatchIO io;
+    int s;
+    using Real = std::conditional_t<F64, double, float>;
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ double h(int64_t q) const { return io.h[io.h_per_inst ? q : 0]; }
+    __device__ int64_t steps(int64_t) const { return io.n_steps; }
+    __device__ int64_t ckpt_every() const { return io.ckpt_every; }
+    __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const double xd = io.x0[q * s + i];
+        const double vd = io.v0[q * s + i];
+        x = (Real)xd;
+        v = (Real)vd;
+        cx = F64 ? 0.f : (float)((double)x - xd);
+        cv = F64 ? 0.f : (float)((double)v - vd);
+    }
+    __device__ void checkpoint(int64_t q, int64_t ck, int i, Real x, Real v, float cx, float cv) const
+    {
+        if (io.x_traj == nullptr) return;
+        const int64_t o = (q * io.n_ck + ck) * s + i;
+        io.x_traj[o] = (double)x - (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+    }
+    __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
+    {
+        io.x_out[q * s + i] = (double)x - (double)cx;
+        io.v_out[q * s + i] = (double)v - (double)cv;
+    }
+    __device__ void finish(int64_t, int64_t, bool) const {}
+};
+
+// Slot form (serving): state block [x(s), v(s), cx(s), cv(s)] in kernel precision;
+// each slot runs min(chunk, remaining) steps.
+template <bool F64>
+struct DenseSlotSrc {
+    SlotIO io;
+    int s;
+    using Real = std::conditional_t<F64, double, float>;
+    __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ double h(int64_t q) const { return d(q).h; }
+    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
+    __device__ int64_t ckpt_every() const { return 0; }
+    __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
+    {
+        const Real* st = (const Real*)d(q).state;
+        x = st[i];
+        v = st[s + i];
+        if constexpr (F64) {
+            cx = cv = 0.f;
+        } else {
+            cx = st[2 * s + i];
+            cv = st[3 * s + i];
+        }
+    }
+    __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
+    __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
+    {
+        Real* st = (Real*)d(q).state;
+        st[i] = x;
+        st[s + i] = v;
+        if constexpr (!F64) {
+            st[2 * s + i] = cx;
+            st[3 * s + i] = cv;
+        }
+    }
+    __device__ void finish(int64_t q, int64_t ran, bool bad) const
+    {
+        const int32_t slot = io.slot_ids[q];
+        io.slots[slot].remaining -= ran;
+        if (bad) io.status[slot] = CHO_ENONFINITE;
+    }
+};
+
+template <int RI, int NT, bool F64, class Src>
+__global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys sys, const Src src)
 {
     using Real = std::conditional_t<F64, double, float>;
     constexpr int RG = kDenseThreads / NT;          // row groups
     constexpr int SP = RG * RI;                     // padded size handled by this instantiation
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* xsh = (Real*)smem_raw;                    // [2][SP][NT]
+    __shared__ long long max_steps;
+    __shared__ int any_bad[NT];
 
     const int t = threadIdx.x;
     const int n = t % NT;
     const int r = t / NT;
     const int row0 = r * RI;
     const int64_t q = (int64_t)blockIdx.x * NT + n;
-    const bool live = q < io.n_inst;
+    const bool live = q < src.count();
     const int s = sys.s;
     const int ld = sys.s_pad;                       // leading dimension of the transposed B
     const Real* Bt = F64 ? (const Real*)sys.B64 : (const Real*)sys.B32;   // [SP][SP] = B^T
     const float* Btl = sys.B32 + (size_t)ld * ld;                          // lo part (FP32 only)
 
-    const StepSize<F64> hs(live ? io.h[io.h_per_inst ? q : 0] : 1.0);
+    // every instance of the tile runs its own step count; the tile loops to the largest
+    const int64_t my_steps = live ? src.steps(q) : 0;
+    if (t == 0) max_steps = 0;
+    if (t < NT) any_bad[t] = 0;
+    __syncthreads();
+    if (r == 0) atomicMax(&max_steps, (long long)my_steps);
+    __syncthreads();
+    const int64_t nsteps = max_steps;
+
+    const StepSize<F64> hs(live ? src.h(q) : 1.0);
     Real x[RI], v[RI];
     float cx[RI], cv[RI];
 #pragma unroll
     for (int k = 0; k < RI; ++k) {
         const int i = row0 + k;
-        const double xd = (live && i < s) ? io.x0[q * s + i] : 0.0;
-        const double vd = (live && i < s) ? io.v0[q * s + i] : 0.0;
-        x[k] = (Real)xd;
-        v[k] = (Real)vd;
-        cx[k] = F64 ? 0.f : (float)((double)x[k] - xd);
-        cv[k] = F64 ? 0.f : (float)((double)v[k] - vd);
+        if (live && i < s) {
+            src.load(q, i, x[k], v[k], cx[k], cv[k]);
+        } else {
+            x[k] = v[k] = 0;
+            cx[k] = cv[k] = 0.f;
+        }
     }
 
     int buf = 0;
@@ -67,8 +155,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
         Real t0[RI];
 #pragma unroll
         for (int k = 0; k < RI; ++k) t0[k] = 0;
-        const int jmax = s;                          // columns beyond s are zero
-        for (int j = 0; j < jmax; ++j) {
+        for (int j = 0; j < s; ++j) {                // columns beyond s are zero
             const Real xj = X[j * NT + n];
             const Real* col = Bt + (size_t)j * ld + row0;
             if constexpr (F64) {
@@ -96,11 +183,11 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
         buf ^= 1;
     };
 
-    const int64_t nsteps = io.n_steps;
-    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (nsteps > 0 ? nsteps : 1);
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
     int64_t ck = 0;
+    int64_t step = 0;
     for (int64_t done = 0; done < nsteps; done += every) {
-        for (int64_t it = 0; it < every; ++it) {
+        for (int64_t it = 0; it < every; ++it, ++step) {
             Real a[RI], xs[RI], kx[RI], kv[RI], vs[RI];
             accel(x, a);
 #pragma unroll
@@ -127,55 +214,71 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
                 vs[k] = v[k] + hs.h * a[k];
             }
             accel(xs, a);
-#pragma unroll
-            for (int k = 0; k < RI; ++k) {
-                kx[k] = kx[k] + vs[k];
-                kv[k] = kv[k] + a[k];
-                state_add<F64>(x[k], cx[k], hs.inc(kx[k]));
-                state_add<F64>(v[k], cv[k], hs.inc(kv[k]));
-            }
-        }
-        if (io.ckpt_every > 0) {
-            if (live && io.x_traj) {
+            if (step < my_steps) {                   // instances past their horizon hold still
 #pragma unroll
                 for (int k = 0; k < RI; ++k) {
-                    const int i = row0 + k;
-                    if (i < s) {
-                        const int64_t o = (q * io.n_ck + ck) * s + i;
-                        io.x_traj[o] = (double)x[k] - (double)cx[k];
-                        if (io.v_traj) io.v_traj[o] = (double)v[k] - (double)cv[k];
-                    }
+                    kx[k] = kx[k] + vs[k];
+                    kv[k] = kv[k] + a[k];
+                    state_add<F64>(x[k], cx[k], hs.inc(kx[k]));
+                    state_add<F64>(v[k], cv[k], hs.inc(kv[k]));
                 }
+            }
+        }
+        if (src.ckpt_every() > 0) {
+            if (live) {
+#pragma unroll
+                for (int k = 0; k < RI; ++k)
+                    if (row0 + k < s) src.checkpoint(q, ck, row0 + k, x[k], v[k], cx[k], cv[k]);
             }
             ++ck;
         }
     }
+    bool bad = false;
     if (live) {
 #pragma unroll
         for (int k = 0; k < RI; ++k) {
-            const int i = row0 + k;
-            if (i < s) {
-                io.x_out[q * s + i] = (double)x[k] - (double)cx[k];
-                io.v_out[q * s + i] = (double)v[k] - (double)cv[k];
+            if (row0 + k < s) {
+                src.store(q, row0 + k, x[k], v[k], cx[k], cv[k]);
+                bad |= !(isfinite((double)x[k]) && isfinite((double)v[k]));
             }
         }
     }
+    if (bad) any_bad[n] = 1;
+    __syncthreads();
+    if (live && r == 0) src.finish(q, my_steps, any_bad[n] != 0);
 }
 
-template <int RI, int NT, bool F64>
-cudaError_t launch_simt(const DenseSys& sys, const BatchIO& io, cudaStream_t st)
+template <int RI, int NT, bool F64, class Src>
+cudaError_t launch_simt(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     using Real = std::conditional_t<F64, double, float>;
     constexpr int SP = (kDenseThreads / NT) * RI;
     if (sys.s_pad != SP) return cudaErrorInvalidValue;
     const size_t smem = 2 * sizeof(Real) * SP * NT;
-    auto kern = rk4_dense_simt_kernel<RI, NT, F64>;
+    auto kern = rk4_dense_simt_kernel<RI, NT, F64, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (io.n_inst + NT - 1) / NT;
+    const int64_t blocks = (n_inst + NT - 1) / NT;
     if (blocks <= 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, kDenseThreads, smem, st>>>(sys, io);
+    kern<<<(unsigned)blocks, kDenseThreads, smem, st>>>(sys, src);
     return cudaGetLastError();
+}
+
+template <template <bool> class SrcT, class Init>
+cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaStream_t st, const Init& init)
+{
+#define CHO_DENSE_CASE(SPV, RI64, NT64, RI32, NT32)                                                   \
+    case SPV:                                                                                         \
+        if (fp64) { SrcT<true> src; init(src); return launch_simt<RI64, NT64, true>(sys, src, n_inst, st); } \
+        else { SrcT<false> src; init(src); return launch_simt<RI32, NT32, false>(sys, src, n_inst, st); }
+    switch (sys.s_pad) {
+        CHO_DENSE_CASE(64, 2, 8, 4, 16)
+        CHO_DENSE_CASE(128, 4, 8, 8, 16)
+        CHO_DENSE_CASE(256, 8, 8, 16, 16)
+        CHO_DENSE_CASE(512, 8, 4, 16, 8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CHO_DENSE_CASE
 }
 
 }  // namespace
@@ -193,14 +296,19 @@ cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, c
     if (io.n_inst == 0) return cudaSuccess;
     if (prec == CHO_DENSE_BF16X3 || prec == CHO_DENSE_BF16X5 || prec == CHO_DENSE_BF16X6)
         return launch_rk4_dense_tc(sys, io, prec, st);
-    const bool fp64 = prec == CHO_FP64;
-    switch (sys.s_pad) {
-        case 64: return fp64 ? launch_simt<2, 8, true>(sys, io, st) : launch_simt<4, 16, false>(sys, io, st);
-        case 128: return fp64 ? launch_simt<4, 8, true>(sys, io, st) : launch_simt<8, 16, false>(sys, io, st);
-        case 256: return fp64 ? launch_simt<8, 8, true>(sys, io, st) : launch_simt<16, 16, false>(sys, io, st);
-        case 512: return fp64 ? launch_simt<8, 4, true>(sys, io, st) : launch_simt<16, 8, false>(sys, io, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return dispatch_simt<DenseBatchSrc>(sys, prec == CHO_FP64, io.n_inst, st, [&](auto& src) {
+        src.io = io;
+        src.s = sys.s;
+    });
+}
+
+cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st)
+{
+    if (io.n_inst == 0) return cudaSuccess;
+    return dispatch_simt<DenseSlotSrc>(sys, fp64, io.n_inst, st, [&](auto& src) {
+        src.io = io;
+        src.s = sys.s;
+    });
 }
 
 // Device data of a dense system: B^T padded to s_pad in FP64 and as FP32 pairs

@@ -79,6 +79,7 @@ struct BatchSrc {
         io.x_out[q * sz + row] = (double)x - (double)cx;
         io.v_out[q * sz + row] = (double)v - (double)cv;
     }
+    __device__ void finish(int64_t, int64_t, bool) const {}
 };
 
 // Slot form (serving): resident state block [x(S), v(S), cx(S), cv(S)] in the
@@ -92,7 +93,7 @@ struct SlotSrc {
     __device__ int64_t count() const { return io.n_inst; }
     __device__ int s(int64_t q) const { return d(q).s; }
     __device__ double h(int64_t q) const { return d(q).h; }
-    __device__ int64_t steps(int64_t q) const { return d(q).steps; }
+    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
     __device__ int64_t ckpt_every() const { return 0; }
 
     __device__ void coef(int64_t q, int row, int j, Real& hi, float& lo) const
@@ -119,17 +120,22 @@ struct SlotSrc {
         }
     }
     __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
-    __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool bad) const
+    __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool) const
     {
-        SlotDesc& sd = io.slots[io.slot_ids[q]];
-        Real* st = (Real*)sd.state;
+        Real* st = (Real*)d(q).state;
         st[row] = x;
         st[S + row] = v;
         if constexpr (!F64) {
             st[2 * S + row] = cx;
             st[3 * S + row] = cv;
         }
-        if (bad) sd.status = CHO_ENONFINITE;
+    }
+    // once per instance, after every lane has stored: book the steps run, flag a bad state
+    __device__ void finish(int64_t q, int64_t ran, bool bad) const
+    {
+        const int32_t slot = io.slot_ids[q];
+        io.slots[slot].remaining -= ran;
+        if (bad) io.status[slot] = CHO_ENONFINITE;
     }
 };
 
@@ -250,6 +256,8 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     for (int r = 0; r < R; ++r) bad |= !(isfinite((double)x[r]) && isfinite((double)v[r]));
 #pragma unroll
     for (int r = 0; r < R; ++r) src.store(q, g * R + r, x[r], v[r], cx[r], cv[r], bad);
+    if constexpr (G > 1) bad = __any_sync(gmask, bad);
+    if (g == 0) src.finish(q, n, bad);
 }
 
 template <int S, bool F64, class Src>

@@ -256,7 +256,8 @@ def test_zero_steps_and_zero_instances(ctx):
     out = run_gpu(ctx, cfg, "fp64", 0, n_steps=0)
     assert np.array_equal(out["x"], cfg["x0"]) and np.array_equal(out["v"], cfg["v0"])
     out = run_gpu(ctx, cfg, "fp32_kahan", 0, n_steps=0)
-    assert np.array_equal(out["x"], cfg["x0"])      # Kahan carry makes the round trip exact
+    # FP32 value plus FP32 compensation carry the FP64 input to about 2^-48
+    assert np.allclose(out["x"], cfg["x0"], rtol=2e-14, atol=0)
     sys_ = make_system(ctx, inputs.chain_batch(n_inst=1, s=40))
     try:
         r = cho.cho_integrate_batch(ctx, sys_, np.zeros((0, 40)), np.zeros((0, 40)), [1e-3], 10)
