@@ -1,0 +1,285 @@
+"""Serving: continuous batching through cho_submit / cho_poll.
+
+Checks that a request's result is the same alone and inside a mixed stream,
+the same for any chunk length, equal to the batch API and to the oracle within
+tolerance; that admission follows the fixed priorities and the memory budget;
+and that bad requests get clean status codes (faults are made on the host).
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_1702_02207_gb300 import cho, inputs
+from parity_util import TOL_FP32, TOL_FP64, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def wait_all(ctx, tickets, sizes, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    pending = dict(zip(tickets, sizes))
+    while pending:
+        for t in list(pending):
+            try:
+                st, res = cho.cho_poll(ctx, t, pending[t])
+            except cho.ChoError as e:
+                out[t] = e.status
+                del pending[t]
+                continue
+            if st == cho.CHO_OK:
+                out[t] = res
+                del pending[t]
+        if time.time() - t0 > timeout:
+            raise TimeoutError(f"{len(pending)} requests still pending")
+        time.sleep(0.002)
+    return out
+
+
+class Mix:
+    """A few systems of each kernel family and a seeded list of requests on them."""
+
+    def __init__(self, ctx, seed=0):
+        self.ctx = ctx
+        rng = np.random.default_rng(seed)
+        self.systems = []
+        two = inputs.two_dof_batch(n_inst=64, n_steps=1)
+        self.systems.append(("two_dof", cho.cho_create_system(ctx, "two_dof", masses=two["masses"], springs=two["springs"]),
+                             two, 2))
+        for s in (5, 40, 300):
+            ch = inputs.chain_batch(n_inst=16, s=s, n_steps=1, seed=70 + s)
+            self.systems.append(("chain", cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"]),
+                                 ch, s))
+        for s in (12, 64):
+            dn = inputs.dense_group(s=s, n_inst=1, n_steps=1)
+            self.systems.append(("dense", cho.cho_create_system(ctx, "dense", M=dn["M"], K=dn["K"]), dn, s))
+        self.rng = rng
+
+    def request(self, k, n_steps=None, prec="fp32_kahan"):
+        kind, sys_, cfg, s = self.systems[k % len(self.systems)]
+        n_sys = cfg["masses"].shape[0] if kind != "dense" else 1
+        idx = int(self.rng.integers(n_sys))
+        x0 = self.rng.uniform(-1, 1, s)
+        h = float(cfg["h"][idx if kind != "dense" else 0])
+        n = int(self.rng.integers(500, 4000)) if n_steps is None else n_steps
+        return dict(kind=kind, sys=sys_, cfg=cfg, s=s, idx=idx, x0=x0, v0=np.zeros(s), h=h, n=n, prec=prec)
+
+    def submit(self, r, priority=2):
+        return cho.cho_submit(self.ctx, r["sys"], r["x0"], r["v0"], r["h"], r["n"], r["prec"], priority, r["idx"])
+
+    def close(self):
+        for _, s, _, _ in self.systems:
+            cho.cho_destroy_system(s)
+
+
+def reference(r):
+    """Oracle result of one request."""
+    cfg = r["cfg"]
+    if r["kind"] == "dense":
+        c = dict(kind="dense", M=cfg["M"], K=cfg["K"], x0=r["x0"][None], v0=r["v0"][None], h=np.array([r["h"]]))
+    else:
+        i = r["idx"]
+        c = dict(kind="chain", masses=cfg["masses"][i:i + 1], springs=cfg["springs"][i:i + 1], x0=r["x0"][None],
+                 v0=r["v0"][None], h=np.array([r["h"]]))
+    return oracle_run(c, n_steps=r["n"])
+
+
+def batch_result(ctx, r):
+    """The same instance through cho_integrate_batch (same kernel family and precision)."""
+    cfg = r["cfg"]
+    if r["kind"] == "dense":
+        sys_ = r["sys"]
+        out = cho.cho_integrate_batch(ctx, sys_, r["x0"][None], r["v0"][None], [r["h"]], r["n"], r["prec"])
+        return out
+    i = r["idx"]
+    sys_ = cho.cho_create_system(ctx, r["kind"], masses=cfg["masses"][i:i + 1], springs=cfg["springs"][i:i + 1])
+    try:
+        return cho.cho_integrate_batch(ctx, sys_, r["x0"][None], r["v0"][None], [r["h"]], r["n"], r["prec"])
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32_kahan", TOL_FP32), ("fp64", TOL_FP64)])
+def test_alone_matches_batch_and_oracle(prec, tol):
+    ctx = cho.cho_init(0, chunk_steps=700)
+    mix = Mix(ctx, seed=1)
+    try:
+        for k in range(len(mix.systems)):
+            r = mix.request(k, prec=prec)
+            t = mix.submit(r)
+            res = wait_all(ctx, [t], [r["s"]])[t]
+            b = batch_result(ctx, r)
+            assert np.array_equal(res["x"], b["x"][0]) and np.array_equal(res["v"], b["v"][0]), r["kind"]
+            ref = reference(r)
+            assert relerr(res["x"], ref["x"][0]) < 50 * tol
+            assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+
+
+def test_same_result_alone_and_in_the_mix_and_any_chunk():
+    ctx = cho.cho_init(0, chunk_steps=512)
+    mix = Mix(ctx, seed=2)
+    try:
+        probes = [mix.request(k) for k in range(len(mix.systems))]
+        alone = {}
+        for k, r in enumerate(probes):
+            t = mix.submit(r)
+            alone[k] = wait_all(ctx, [t], [r["s"]])[t]
+        # the same requests inside a stream of 300 others of all kinds and priorities
+        others = [mix.request(k) for k in range(300)]
+        tickets, sizes, which = [], [], []
+        for j, r in enumerate(others):
+            tickets.append(mix.submit(r, priority=j % 3))
+            sizes.append(r["s"])
+            which.append(None)
+            if j % 50 == 25:
+                k = (j // 50) % len(probes)
+                tickets.append(mix.submit(probes[k], priority=(j // 50) % 3))
+                sizes.append(probes[k]["s"])
+                which.append(k)
+        res = wait_all(ctx, tickets, sizes)
+        seen = 0
+        for t, k in zip(tickets, which):
+            if k is not None:
+                assert np.array_equal(res[t]["x"], alone[k]["x"]) and np.array_equal(res[t]["v"], alone[k]["v"])
+                seen += 1
+        assert seen == 6
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+    # chunk length does not change results (state stays in kernel precision between chunks)
+    for chunk in (97, 100000):
+        ctx = cho.cho_init(0, chunk_steps=chunk)
+        mix2 = Mix(ctx, seed=2)
+        try:
+            for k, r in enumerate(probes):
+                r2 = dict(r, sys=mix2.systems[k][1])
+                t = mix2.submit(r2)
+                got = wait_all(ctx, [t], [r["s"]])[t]
+                assert np.array_equal(got["x"], alone[k]["x"]), (chunk, k)
+        finally:
+            mix2.close()
+            cho.cho_shutdown(ctx)
+
+
+def test_mixed_stream_against_oracle():
+    ctx = cho.cho_init(0, chunk_steps=1000)
+    mix = Mix(ctx, seed=3)
+    try:
+        reqs = [mix.request(k) for k in range(120)]
+        tickets = [mix.submit(r, priority=k % 3) for k, r in enumerate(reqs)]
+        res = wait_all(ctx, tickets, [r["s"] for r in reqs])
+        for t, r in zip(tickets, reqs):
+            ref = reference(r)
+            assert relerr(res[t]["x"], ref["x"][0]) < 1e-4, (r["kind"], r["s"])
+        st = cho.cho_serve_stats(ctx)
+        assert st["queued"] == 0 and st["resident"] == 0 and st["completed"] >= 120
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+
+
+def test_fixed_priority_admission_and_budget():
+    # two slots at a time: admission order is decided by priority class, FIFO inside a class
+    ctx = cho.cho_init(0, chunk_steps=200, max_slots=2)
+    mix = Mix(ctx, seed=4)
+    try:
+        low = [mix.request(0, n_steps=2000) for _ in range(8)]
+        high = [mix.request(0, n_steps=2000) for _ in range(8)]
+        tl = [mix.submit(r, priority=2) for r in low]
+        th = [mix.submit(r, priority=0) for r in high]
+        peak = 0
+        t0 = time.time()
+        while time.time() - t0 < 60:
+            st = cho.cho_serve_stats(ctx)
+            peak = max(peak, st["resident"])
+            if st["queued"] == 0 and st["resident"] == 0:
+                break
+            time.sleep(0.001)
+        res = wait_all(ctx, tl + th, [2] * 16)
+        assert peak <= 2
+        adm_low = sorted(res[t]["t_admit"] for t in tl)
+        adm_high = [res[t]["t_admit"] for t in th]
+        # at most the two low-priority requests admitted before the high ones arrived run first
+        assert sum(a < max(adm_high) for a in adm_low) <= 2
+        # FIFO inside the high class
+        assert adm_high == sorted(adm_high)
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+    # a byte budget of one FP32 state block of s = 300 (4.8 KB -> 8 KB class) serialises chain requests
+    ctx = cho.cho_init(0, chunk_steps=300, budget_bytes=8192)
+    mix = Mix(ctx, seed=5)
+    try:
+        reqs = [mix.request(3, n_steps=900) for _ in range(4)]
+        ts = [mix.submit(r) for r in reqs]
+        peak_bytes = 0
+        t0 = time.time()
+        while time.time() - t0 < 60:
+            st = cho.cho_serve_stats(ctx)
+            peak_bytes = max(peak_bytes, st["resident_bytes"])
+            if st["queued"] == 0 and st["resident"] == 0:
+                break
+        wait_all(ctx, ts, [300] * 4)
+        assert 0 < peak_bytes <= 8192
+        # a chain of 2000 masses in FP64 needs a 32 KiB block: it can never fit, so submit refuses it
+        big = inputs.chain_batch(n_inst=1, s=2000, n_steps=1)
+        sb = cho.cho_create_system(ctx, "chain", masses=big["masses"], springs=big["springs"])
+        try:
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_submit(ctx, sb, np.zeros(2000), np.zeros(2000), float(big["h"][0]), 10, "fp64")
+            assert ei.value.status == cho.CHO_EBUDGET
+        finally:
+            cho.cho_destroy_system(sb)
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+
+
+def test_request_errors_and_cancel():
+    ctx = cho.cho_init(0, chunk_steps=100, max_slots=1)
+    mix = Mix(ctx, seed=6)
+    try:
+        r = mix.request(0)
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], 10.0, 10, "fp32_kahan", 0, r["idx"])
+        assert ei.value.status == cho.CHO_EUNSTABLE
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_submit(ctx, r["sys"], [np.nan, 0.0], r["v0"], r["h"], 10, "fp32_kahan", 0, r["idx"])
+        assert ei.value.status == cho.CHO_ENONFINITE
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], 10, "fp32_kahan", 3, r["idx"])
+        assert ei.value.status == cho.CHO_EINVAL
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], 10, "fp32_kahan", 0, 10_000)
+        assert ei.value.status == cho.CHO_EINVAL
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_poll(ctx, 987654321, 2)
+        assert ei.value.status == cho.CHO_ENOTFOUND
+        # cancel a long request while it runs, and one still queued behind it
+        t1 = cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], 10_000_000, "fp32_kahan", 0, r["idx"])
+        t2 = cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], 10_000_000, "fp32_kahan", 2, r["idx"])
+        time.sleep(0.05)
+        cho.cho_cancel(ctx, t1)
+        cho.cho_cancel(ctx, t2)
+        out = wait_all(ctx, [t1, t2], [2, 2], timeout=60)
+        assert out[t1] == cho.CHO_ECANCELLED and out[t2] == cho.CHO_ECANCELLED
+        # a finite start that overflows FP32 in flight is reported at a chunk boundary,
+        # without disturbing a healthy request served beside it
+        ok = mix.request(0, n_steps=300)
+        t3 = cho.cho_submit(ctx, r["sys"], [3e38, -3e38], [3e38, 3e38], r["h"], 500, "fp32_kahan", 0, r["idx"])
+        t4 = mix.submit(ok, priority=0)
+        out = wait_all(ctx, [t3, t4], [2, 2])
+        assert out[t3] == cho.CHO_ENONFINITE
+        assert np.array_equal(out[t4]["x"], batch_result(ctx, ok)["x"][0])
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
