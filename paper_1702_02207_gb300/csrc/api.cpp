@@ -83,13 +83,14 @@ static cudaError_t upload(T** dst, const T* src, size_t n)
 
 static void free_system_device(cho_system_impl* s)
 {
-    void* ptrs[] = {s->d_B64, s->d_B32, s->d_Bbf, s->d_masses, s->d_springs, s->d_M, s->d_K, s->d_plain};
+    void* ptrs[] = {s->d_B64, s->d_B32, s->d_Bbf, s->d_masses, s->d_springs, s->d_M, s->d_K, s->d_plain, s->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     s->d_B64 = nullptr;
     s->d_B32 = nullptr;
     s->d_Bbf = nullptr;
     s->d_masses = s->d_springs = s->d_M = s->d_K = s->d_plain = nullptr;
+    s->d_err = nullptr;
 }
 
 // Tridiagonal B = M^{-1} K of a chain (also eq. 2 at s = 2), FP64 [3][s]: sub, main, super.
@@ -421,8 +422,10 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     } else if (p == CHO_FP64 || p == CHO_FP32_KAHAN) {
     } else if (p == CHO_DENSE_FP32_SIMT || p == CHO_DENSE_BF16X3 || p == CHO_DENSE_BF16X5 || p == CHO_DENSE_BF16X6) {
         if (sys->kind != CHO_DENSE) return fail(CHO_EINVAL, "%s: precision %d is for dense systems", who, p);
-        if ((p != CHO_DENSE_FP32_SIMT) && sys->path != PATH_DENSE)
-            return fail(CHO_EINVAL, "%s: BF16 tensor-core modes need a shared dense system with s > 32", who);
+        if ((p != CHO_DENSE_FP32_SIMT) && (sys->path != PATH_DENSE || sys->s_tc == 0))
+            return fail(CHO_EINVAL, "%s: BF16 tensor-core modes need a shared dense system with 32 < s <= 256", who);
+        if (p == CHO_DENSE_BF16X6 && sys->s_tc > 128)
+            return fail(CHO_EINVAL, "%s: bf16x6 needs s <= 128 (its operands exceed shared memory above)", who);
     } else {
         return fail(CHO_EINVAL, "%s: unknown precision %d", who, p);
     }
@@ -484,7 +487,7 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         e = launch_rk4_chain(cs, io, fp64, st);
     } else {
-        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf};
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
         e = launch_rk4_dense(ds, io, b->prec, st);
     }
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: kernel launch: %s", cudaGetErrorString(e));

@@ -101,10 +101,12 @@ cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaS
 // ---- rk4_dense (shared B, s > 32) ------------------------------------------------
 struct DenseSys {
     int32_t s;
-    int32_t s_pad;          // s rounded up to the tile size
-    const double* B64;      // [s][s]
-    const float* B32;       // [2][s_pad][s_pad] (hi, lo), zero padded
-    const uint16_t* Bbf;    // [3][s_pad][s_pad] bf16 pieces of B, zero padded
+    int32_t s_pad;          // SIMT kernels: next power of two >= max(s, 64), <= 512
+    const double* B64;      // [s_pad][s_pad] = B^T, zero padded
+    const float* B32;       // [2][s_pad][s_pad] (hi, lo) of B^T, zero padded
+    const uint16_t* Bbf;    // tensor-core kernel: shared-memory images of the BF16 pieces of B
+    int32_t s_tc;           // tensor-core padded size: 128 or 256 (0: no tensor-core data)
+    int* err;               // device error word of the tensor-core kernel (bounded waits)
 };
 int dense_pad(int s);
 cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);

@@ -49,7 +49,8 @@ struct cho_system_impl {
     int64_t n_sys = 0;
     int32_t path = 0;
     int32_t S = 0;          // rk4_small padded size
-    int32_t s_pad = 0;      // rk4_dense padded size
+    int32_t s_pad = 0;      // rk4_dense padded size (CUDA cores)
+    int32_t s_tc = 0;       // rk4_dense padded size (tensor cores)
     double omega_max = 0.0;
     std::vector<double> omegas;
     // host copies of the description
@@ -62,6 +63,7 @@ struct cho_system_impl {
     double* d_springs = nullptr;
     double* d_M = nullptr;
     double* d_K = nullptr;
+    int* d_err = nullptr;               // tensor-core kernel error word
     double* d_plain = nullptr;          // FP64 plain-form coefficients: tridiagonal [3][s] or dense [s][s]
 };
 

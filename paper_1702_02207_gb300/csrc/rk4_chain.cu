@@ -45,20 +45,20 @@ struct ChainBatchSrc {
         const double vd = io.v0[q * sys.s + i];
         x = (Real)xd;
         v = (Real)vd;
-        cx = F64 ? 0.f : (float)((double)x - xd);
-        cv = F64 ? 0.f : (float)((double)v - vd);
+        cx = F64 ? 0.f : (float)(xd - (double)x);
+        cv = F64 ? 0.f : (float)(vd - (double)v);
     }
     __device__ void checkpoint(int64_t q, int64_t ck, int i, Real x, Real v, float cx, float cv) const
     {
         if (io.x_traj == nullptr) return;
         const int64_t o = (q * io.n_ck + ck) * sys.s + i;
-        io.x_traj[o] = (double)x - (double)cx;
-        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+        io.x_traj[o] = (double)x + (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
     }
     __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
     {
-        io.x_out[q * sys.s + i] = (double)x - (double)cx;
-        io.v_out[q * sys.s + i] = (double)v - (double)cv;
+        io.x_out[q * sys.s + i] = (double)x + (double)cx;
+        io.v_out[q * sys.s + i] = (double)v + (double)cv;
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
 };
@@ -201,32 +201,32 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
             for (int p = 0; p < P; ++p) {
                 kx[p] = v[p];
                 kv[p] = a[p];
-                xs[p] = x[p] + hs.h2 * v[p];
-                vs[p] = v[p] + hs.h2 * a[p];
+                xs[p] = fmar(hs.h2, v[p], x[p]);
+                vs[p] = fmar(hs.h2, a[p], v[p]);
             }
             accel(xs, a);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                kx[p] = kx[p] + (Real)2 * vs[p];
-                kv[p] = kv[p] + (Real)2 * a[p];
-                xs[p] = x[p] + hs.h2 * vs[p];
-                vs[p] = v[p] + hs.h2 * a[p];
+                kx[p] = fmar((Real)2, vs[p], kx[p]);
+                kv[p] = fmar((Real)2, a[p], kv[p]);
+                xs[p] = fmar(hs.h2, vs[p], x[p]);
+                vs[p] = fmar(hs.h2, a[p], v[p]);
             }
             accel(xs, a);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                kx[p] = kx[p] + (Real)2 * vs[p];
-                kv[p] = kv[p] + (Real)2 * a[p];
-                xs[p] = x[p] + hs.h * vs[p];
-                vs[p] = v[p] + hs.h * a[p];
+                kx[p] = fmar((Real)2, vs[p], kx[p]);
+                kv[p] = fmar((Real)2, a[p], kv[p]);
+                xs[p] = fmar(hs.h, vs[p], x[p]);
+                vs[p] = fmar(hs.h, a[p], v[p]);
             }
             accel(xs, a);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                kx[p] = kx[p] + vs[p];
-                kv[p] = kv[p] + a[p];
-                state_add<F64>(x[p], cx[p], hs.inc(kx[p]));
-                state_add<F64>(v[p], cv[p], hs.inc(kv[p]));
+                kx[p] = addr(kx[p], vs[p]);
+                kv[p] = addr(kv[p], a[p]);
+                state_update<F64>(x[p], cx[p], kx[p], hs);
+                state_update<F64>(v[p], cv[p], kv[p], hs);
             }
         }
         if (src.ckpt_every() > 0) {

@@ -7,20 +7,25 @@
 
 namespace cho {
 
-// Kahan-compensated x += inc.  `c` carries the rounding error of the running
-// sum with the sign convention "represented value = x - c".  The _rn
-// intrinsics keep the compiler from contracting or reassociating the steps.
-__device__ __forceinline__ void kahan_add(float& x, float& c, float inc)
+// Compensated state update x += (h6 + h6lo) k in FP32.  The state is carried
+// as the unevaluated sum x + e (e holds what the rounded sum x has lost, as
+// in Kahan summation).  The operations are the explicit round-to-nearest
+// intrinsics, so the compiler neither fuses nor reorders them and every kernel
+// that uses this sequence (packed or not) rounds identically.
+__device__ __forceinline__ void comp_update(float& x, float& e, float k, float h6, float h6lo)
 {
-    const float y = __fsub_rn(inc, c);
+    float y = __fmaf_rn(h6lo, k, e);
+    y = __fmaf_rn(h6, k, y);
     const float t = __fadd_rn(x, y);
-    c = __fsub_rn(__fsub_rn(t, x), y);
+    e = __fsub_rn(y, __fsub_rn(t, x));
     x = t;
 }
 
 // Fused multiply-add in the precision of the operands.
 __device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double addr(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float addr(float a, float b) { return __fadd_rn(a, b); }
 
 // Split an FP64 value into an unevaluated FP32 pair hi + lo.
 __host__ __device__ __forceinline__ void split_ff(double d, float& hi, float& lo)
@@ -30,7 +35,7 @@ __host__ __device__ __forceinline__ void split_ff(double d, float& hi, float& lo
 }
 
 // Per-instance step constants.  FP64: h, h/2, h/6.  FP32: h and h/2 rounded
-// to FP32 (exact when h is an FP32 number), h/6 as an FP32 pair.
+// to FP32 (exact when h is an FP32 number), h/6 as the FP32 pair h6 + h6lo.
 template <bool F64>
 struct StepSize {
     using Real = std::conditional_t<F64, double, float>;
@@ -44,27 +49,18 @@ struct StepSize {
         h6 = (Real)s6;
         h6lo = F64 ? 0.f : (float)(s6 - (double)(float)s6);
     }
-    // increment h/6 * k for the state update
-    __device__ __forceinline__ Real inc(Real k) const
-    {
-        if constexpr (F64) {
-            return h6 * k;
-        } else {
-            return fmaf(h6, k, h6lo * k);
-        }
-    }
 };
 
-// State update of the RK4 step (both precisions).
+// State update of the RK4 step: x += h/6 k (FP64), compensated in FP32.
 template <bool F64>
-__device__ __forceinline__ void state_add(std::conditional_t<F64, double, float>& x, float& c,
-                                          std::conditional_t<F64, double, float> inc)
+__device__ __forceinline__ void state_update(std::conditional_t<F64, double, float>& x, float& e,
+                                             std::conditional_t<F64, double, float> k, const StepSize<F64>& hs)
 {
     if constexpr (F64) {
-        x = x + inc;
-        (void)c;
+        x = __fma_rn(hs.h6, k, x);
+        (void)e;
     } else {
-        kahan_add(x, c, inc);
+        comp_update(x, e, k, hs.h6, hs.h6lo);
     }
 }
 

@@ -40,20 +40,20 @@ struct DenseBatchSrc {
         const double vd = io.v0[q * s + i];
         x = (Real)xd;
         v = (Real)vd;
-        cx = F64 ? 0.f : (float)((double)x - xd);
-        cv = F64 ? 0.f : (float)((double)v - vd);
+        cx = F64 ? 0.f : (float)(xd - (double)x);
+        cv = F64 ? 0.f : (float)(vd - (double)v);
     }
     __device__ void checkpoint(int64_t q, int64_t ck, int i, Real x, Real v, float cx, float cv) const
     {
         if (io.x_traj == nullptr) return;
         const int64_t o = (q * io.n_ck + ck) * s + i;
-        io.x_traj[o] = (double)x - (double)cx;
-        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+        io.x_traj[o] = (double)x + (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
     }
     __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
     {
-        io.x_out[q * s + i] = (double)x - (double)cx;
-        io.v_out[q * s + i] = (double)v - (double)cv;
+        io.x_out[q * s + i] = (double)x + (double)cx;
+        io.v_out[q * s + i] = (double)v + (double)cv;
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
 };
@@ -194,33 +194,33 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
             for (int k = 0; k < RI; ++k) {
                 kx[k] = v[k];
                 kv[k] = a[k];
-                xs[k] = x[k] + hs.h2 * v[k];
-                vs[k] = v[k] + hs.h2 * a[k];
+                xs[k] = fmar(hs.h2, v[k], x[k]);
+                vs[k] = fmar(hs.h2, a[k], v[k]);
             }
             accel(xs, a);
 #pragma unroll
             for (int k = 0; k < RI; ++k) {
-                kx[k] = kx[k] + (Real)2 * vs[k];
-                kv[k] = kv[k] + (Real)2 * a[k];
-                xs[k] = x[k] + hs.h2 * vs[k];
-                vs[k] = v[k] + hs.h2 * a[k];
+                kx[k] = fmar((Real)2, vs[k], kx[k]);
+                kv[k] = fmar((Real)2, a[k], kv[k]);
+                xs[k] = fmar(hs.h2, vs[k], x[k]);
+                vs[k] = fmar(hs.h2, a[k], v[k]);
             }
             accel(xs, a);
 #pragma unroll
             for (int k = 0; k < RI; ++k) {
-                kx[k] = kx[k] + (Real)2 * vs[k];
-                kv[k] = kv[k] + (Real)2 * a[k];
-                xs[k] = x[k] + hs.h * vs[k];
-                vs[k] = v[k] + hs.h * a[k];
+                kx[k] = fmar((Real)2, vs[k], kx[k]);
+                kv[k] = fmar((Real)2, a[k], kv[k]);
+                xs[k] = fmar(hs.h, vs[k], x[k]);
+                vs[k] = fmar(hs.h, a[k], v[k]);
             }
             accel(xs, a);
             if (step < my_steps) {                   // instances past their horizon hold still
 #pragma unroll
                 for (int k = 0; k < RI; ++k) {
-                    kx[k] = kx[k] + vs[k];
-                    kv[k] = kv[k] + a[k];
-                    state_add<F64>(x[k], cx[k], hs.inc(kx[k]));
-                    state_add<F64>(v[k], cv[k], hs.inc(kv[k]));
+                    kx[k] = addr(kx[k], vs[k]);
+                    kv[k] = addr(kv[k], a[k]);
+                    state_update<F64>(x[k], cx[k], kx[k], hs);
+                    state_update<F64>(v[k], cv[k], kv[k], hs);
                 }
             }
         }

@@ -1,14 +1,498 @@
-// rk4_dense_tc.cu -- tensor-core (tcgen05) split-BF16 variant of rk4_dense.
+// rk4_dense_tc.cu -- rk4_dense on the tensor cores: each RK4 stage's B Xs
+// (B = M^{-1}K shared by all instances, Xs the stage displacements of a tile of
+// 32 instances) is a tcgen05.mma contraction with split-BF16 operands and FP32
+// accumulation in tensor memory; the stage combinations and the Kahan-
+// compensated FP32 state update run on the CUDA cores.
+//
+// Split-BF16.  B = b0 + b1 + b2 and Xs = p0 + p1 + p2 with each piece the
+// BF16 rounding of what the previous pieces leave.  The product keeps the
+// partial products whose order is at most 2^-16 relative:
+//   bf16x3: b0 p0 + b0 p1 + b1 p0
+//   bf16x5: bf16x3 + b1 p1 + b2 p0
+//   bf16x6: bf16x5 + b0 p2
+// (smallest terms are accumulated first).
+//
+// Work split.  s <= 128: one CTA per tile of 32 instances.  128 < s <= 256: a
+// cluster of two CTAs per tile; CTA r owns rows [128 r, 128 r + 128) of B
+// (resident in its shared memory for the whole run) and the same rows of the
+// state, and writes its rows of each stage's Xs into both CTAs' shared memory,
+// so each CTA multiplies its 128 rows of B by the full Xs.  B is fetched once
+// per CTA with bulk (TMA) copies; it is never re-read from L2.
+//
+// Per CTA: 16 warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of its
+// 128-row block) and columns 8 (w / 4) .. +7 (instances); each thread keeps the
+// state of one row for eight instances in registers.  Thread 0 issues the MMAs.
+//
+// Operand layouts in shared memory (no swizzle, 16-byte core matrices of
+// 8 rows x 16 bytes):
+//   B (A operand, K-major): row m, column k of a 16-column chunk at
+//     (m / 8) * 256 + ((k % 16) / 8) * 128 + (m % 8) * 16 + (k % 8) * 2, chunks 4096 B
+//     apart: descriptor LBO = 128 (K direction), SBO = 256 (M direction).
+//   Xs (B operand, MN-major): instance n, DOF k of a 16-DOF chunk at
+//     ((k % 16) / 8) * 512 + (n / 8) * 128 + (k % 8) * 16 + (n % 8) * 2, chunks 1024 B
+//     apart: descriptor LBO = 512 (K direction), SBO = 128 (N direction).
+// Every wait on an mbarrier gives up after about a second; the kernel then
+// records the failure in an error word and leaves the integration.
 #include "cho_internal.h"
 #include "ctx.h"
+#include "rk4_common.cuh"
+
+#include <cuda_bf16.h>
+#include <cstring>
+#include <vector>
 
 namespace cho {
+namespace {
 
-cudaError_t launch_rk4_dense_tc(const DenseSys&, const BatchIO&, int, cudaStream_t)
+constexpr int kTcWarps = 16;
+constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kNT = 32;            // instances per tile (MMA N)
+constexpr int kCPT = 8;            // instances per thread
+constexpr int kAChunk = 4096;      // bytes of one 128 x 16 chunk of B
+constexpr int kXChunk = 1024;      // bytes of one 16 x 32 chunk of Xs
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer()
 {
-    return cudaErrorNotSupported;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-cudaError_t build_dense_tc_device(cho_system_impl*, const double*) { return cudaSuccess; }
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version of tcgen05
+    return d;                        // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the phase with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank)
+{
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+    return out;
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat16 a = __float2bfloat16_rn(lo);
+    const __nv_bfloat16 b = __float2bfloat16_rn(hi);
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Partial products (piece of B, piece of Xs), smallest first, for bf16x3 / x5 / x6.
+__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
+__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
+
+// PA pieces of B, PB pieces of Xs, CS CTAs per cluster.
+template <int PA, int PB, int CS>
+__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, BatchIO io)
+{
+    constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
+    constexpr int A_BYTES = PA * KC * kAChunk;
+    constexpr int X_BYTES = PB * KC * kXChunk;
+    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces
+    unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
+    __shared__ __align__(8) uint64_t bar_load;
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag[2];
+    __shared__ float sh_h[kNT][4];                   // h, h/2, h/6 hi, h/6 lo of each instance
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const uint32_t rank = CS > 1 ? cluster_rank() : 0;
+    const int64_t tile = blockIdx.x / CS;
+    const int quad = warp & 3;
+    const int colgrp = warp >> 2;
+    const int row = 32 * quad + lane;                // row of this CTA's block
+    const int k = 128 * (int)rank + row;             // DOF
+    const int s = sys.s;
+    const bool live_row = k < s;
+    const int n0 = colgrp * kCPT;                    // first instance column of this thread
+
+    // ---- set-up: barriers, TMEM, B into shared memory ----
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        abort_flag[0] = abort_flag[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kNT) {
+        const int64_t q = tile * kNT + tid;
+        const double hd = q < io.n_inst ? io.h[io.h_per_inst ? q : 0] : 1.0;
+        const double h6 = hd / 6.0;
+        sh_h[tid][0] = (float)hd;
+        sh_h[tid][1] = (float)(0.5 * hd);
+        sh_h[tid][2] = (float)h6;
+        sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kNT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    if (CS > 1) cluster_sync();   // the peer's shared memory is initialised before any remote write
+
+    // Cluster-wide agreement on a local outcome: a failing thread flags its own CTA and
+    // the peer, then every thread passes the same barrier and reads the same flags.
+    auto agree = [&](bool mine) -> bool {
+        if (!mine) {
+            atomicExch(&abort_flag[0], 1);
+            if (CS > 1) {
+                const uint32_t peer = mapa(smem_u32(&abort_flag[1]), rank ^ 1u);
+                asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
+            }
+        }
+        if (CS > 1) cluster_sync(); else __syncthreads();
+        return abort_flag[0] == 0 && abort_flag[1] == 0;
+    };
+    bool ok = true;
+    if (tid == 0) {
+        const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * 3 * KC * kAChunk;
+        mbar_expect_tx(&bar_load, A_BYTES);
+        for (int off = 0; off < A_BYTES; off += 16384) {
+            const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
+            bulk_g2s(sA + off, src + off, (uint32_t)n, &bar_load);
+        }
+    }
+    ok = agree(mbar_wait(&bar_load, 0));
+
+    // ---- state of this thread: row k of instances n0 .. n0+7 ----
+    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+#pragma unroll
+    for (int j = 0; j < kCPT; ++j) {
+        const int64_t q = tile * kNT + n0 + j;
+        const bool live = live_row && q < io.n_inst;
+        const double xd = live ? io.x0[q * s + k] : 0.0;
+        const double vd = live ? io.v0[q * s + k] : 0.0;
+        x[j] = (float)xd;
+        v[j] = (float)vd;
+        cx[j] = (float)(xd - (double)x[j]);
+        cv[j] = (float)(vd - (double)v[j]);
+    }
+
+    // Xs addresses of this thread's DOF k in every CTA of the cluster
+    const int kc = k / 16, kk = k % 16;
+    const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
+    uint32_t xdst[CS];
+#pragma unroll
+    for (int c = 0; c < CS; ++c) xdst[c] = CS > 1 ? mapa(smem_u32(sX) + xoff, (uint32_t)c) : smem_u32(sX) + xoff;
+
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
+    uint32_t phase = 0;
+
+    // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
+    auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
+        float r[kCPT];
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) r[j] = xs[j];
+#pragma unroll
+        for (int p = 0; p < PB; ++p) {
+            uint4 w;
+            w.x = pack_bf16(r[0], r[1]);
+            w.y = pack_bf16(r[2], r[3]);
+            w.z = pack_bf16(r[4], r[5]);
+            w.w = pack_bf16(r[6], r[7]);
+#pragma unroll
+            for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * KC * kXChunk), w);
+            if (p + 1 < PB) {
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (CS > 1) cluster_sync(); else __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
+            int first = 1;
+#pragma unroll
+            for (int pr = 0; pr < NPROD; ++pr) {
+                const int ia = kProdA[NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2][pr];
+                const int ib = kProdB[NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2][pr];
+                for (int c = 0; c < KC; ++c) {
+                    const uint64_t ad = smem_desc(a0 + (uint32_t)((ia * KC + c) * kAChunk), 128, 256);
+                    const uint64_t bd = smem_desc(x0 + (uint32_t)((ib * KC + c) * kXChunk), 512, 128);
+                    mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
+                    first = 0;
+                }
+            }
+            mma_commit(&bar_mma);
+        }
+        // the whole warp takes the same branch around the .sync.aligned TMEM load
+        const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma, phase));
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc[kCPT];
+        if (done) tmem_ld8(taddr, acc);
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        // every CTA of the cluster has its MMA done (so Xs may be rewritten) and agrees on aborts
+        return agree(done);
+    };
+
+    const int64_t nsteps = ok ? io.n_steps : 0;
+    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (nsteps > 0 ? nsteps : 1);
+    int64_t ck = 0;
+    for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
+        for (int64_t it = 0; it < every && ok; ++it) {
+            float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vs[kCPT];
+            ok = stage(x, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h2 = sh_h[n0 + j][1];
+                kx[j] = v[j];
+                kv[j] = a[j];
+                xs[j] = __fmaf_rn(h2, v[j], x[j]);
+                vs[j] = __fmaf_rn(h2, a[j], v[j]);
+            }
+            if (ok) ok = stage(xs, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h2 = sh_h[n0 + j][1];
+                kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
+                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
+                xs[j] = __fmaf_rn(h2, vs[j], x[j]);
+                vs[j] = __fmaf_rn(h2, a[j], v[j]);
+            }
+            if (ok) ok = stage(xs, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h = sh_h[n0 + j][0];
+                kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
+                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
+                xs[j] = __fmaf_rn(h, vs[j], x[j]);
+                vs[j] = __fmaf_rn(h, a[j], v[j]);
+            }
+            if (ok) ok = stage(xs, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h6 = sh_h[n0 + j][2], h6l = sh_h[n0 + j][3];
+                kx[j] = addr(kx[j], vs[j]);
+                kv[j] = addr(kv[j], a[j]);
+                comp_update(x[j], cx[j], kx[j], h6, h6l);
+                comp_update(v[j], cv[j], kv[j], h6, h6l);
+            }
+        }
+        if (io.ckpt_every > 0 && ok) {
+            if (io.x_traj && live_row) {
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) {
+                    const int64_t q = tile * kNT + n0 + j;
+                    if (q < io.n_inst) {
+                        const int64_t o = (q * io.n_ck + ck) * s + k;
+                        io.x_traj[o] = (double)x[j] + (double)cx[j];
+                        if (io.v_traj) io.v_traj[o] = (double)v[j] + (double)cv[j];
+                    }
+                }
+            }
+            ++ck;
+        }
+    }
+    if (live_row) {
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) {
+            const int64_t q = tile * kNT + n0 + j;
+            if (q < io.n_inst) {
+                io.x_out[q * s + k] = (double)x[j] + (double)cx[j];
+                io.v_out[q * s + k] = (double)v[j] + (double)cv[j];
+            }
+        }
+    }
+    if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT));
+    if (CS > 1) cluster_sync();   // the peer may still write into this CTA's shared memory until here
+}
+
+template <int PA, int PB, int CS>
+cudaError_t launch_tc(const DenseSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    constexpr int KC = 8 * CS;
+    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (io.n_inst + kNT - 1) / kNT;
+    if (tiles <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(tiles * CS), 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, sys, io);
+}
+
+// Round to the nearest BF16 (ties to even) of an FP32 value, as bits.
+uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+}  // namespace
+
+cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st)
+{
+    if (io.n_inst == 0) return cudaSuccess;
+    if (!sys.Bbf || sys.s_tc == 0) return cudaErrorNotSupported;
+    const bool two = sys.s_tc == 256;
+    switch (prec) {
+        case CHO_DENSE_BF16X3: return two ? launch_tc<2, 2, 2>(sys, io, st) : launch_tc<2, 2, 1>(sys, io, st);
+        case CHO_DENSE_BF16X5: return two ? launch_tc<3, 2, 2>(sys, io, st) : launch_tc<3, 2, 1>(sys, io, st);
+        case CHO_DENSE_BF16X6:
+            if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
+            return launch_tc<3, 3, 1>(sys, io, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// BF16 pieces of B for the tensor-core kernel, laid out per CTA rank as the exact
+// shared-memory image the kernel copies: [rank][piece 0..2][K chunk][4096 B].
+cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B)
+{
+    const int s = sys->s;
+    if (s > 256) {
+        sys->s_tc = 0;
+        return cudaSuccess;
+    }
+    const int st = s <= 128 ? 128 : 256;
+    const int CS = st / 128, KC = st / 16;
+    sys->s_tc = st;
+    const size_t per_rank = (size_t)3 * KC * kAChunk;
+    std::vector<unsigned char> img((size_t)CS * per_rank, 0);
+    for (int r = 0; r < CS; ++r)
+        for (int m = 0; m < 128; ++m) {
+            const int i = 128 * r + m;
+            for (int kk = 0; kk < st; ++kk) {
+                double rem = (i < s && kk < s) ? B[(size_t)i * s + kk] : 0.0;
+                for (int p = 0; p < 3; ++p) {
+                    const uint16_t b = bf16_bits((float)rem);
+                    rem -= (double)bf16_value(b);
+                    const int c = kk / 16, k16 = kk % 16;
+                    const size_t off = (size_t)r * per_rank + ((size_t)p * KC + c) * kAChunk + (m / 8) * 256 +
+                                       (k16 / 8) * 128 + (m % 8) * 16 + (k16 % 8) * 2;
+                    std::memcpy(&img[off], &b, 2);
+                }
+            }
+        }
+    cudaError_t e = cudaMalloc(&sys->d_Bbf, img.size());
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_Bbf, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(sys->d_err, 0, sizeof(int));
+    return e;
+}
 
 }  // namespace cho

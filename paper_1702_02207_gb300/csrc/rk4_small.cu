@@ -61,23 +61,23 @@ struct BatchSrc {
         x = (Real)xd;
         v = (Real)vd;
         // Kahan convention: represented value = x - c
-        cx = F64 ? 0.f : (float)((double)x - xd);
-        cv = F64 ? 0.f : (float)((double)v - vd);
+        cx = F64 ? 0.f : (float)(xd - (double)x);
+        cv = F64 ? 0.f : (float)(vd - (double)v);
     }
     __device__ void checkpoint(int64_t q, int64_t ck, int row, Real x, Real v, float cx, float cv) const
     {
         const int sz = sys.s;
         if (row >= sz || io.x_traj == nullptr) return;
         const int64_t o = (q * io.n_ck + ck) * sz + row;
-        io.x_traj[o] = (double)x - (double)cx;
-        if (io.v_traj) io.v_traj[o] = (double)v - (double)cv;
+        io.x_traj[o] = (double)x + (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
     }
     __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool) const
     {
         const int sz = sys.s;
         if (row >= sz) return;
-        io.x_out[q * sz + row] = (double)x - (double)cx;
-        io.v_out[q * sz + row] = (double)v - (double)cv;
+        io.x_out[q * sz + row] = (double)x + (double)cx;
+        io.v_out[q * sz + row] = (double)v + (double)cv;
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
 };
@@ -217,32 +217,32 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
             for (int r = 0; r < R; ++r) {
                 kx[r] = v[r];
                 kv[r] = a[r];
-                xs[r] = x[r] + hs.h2 * v[r];
-                vs[r] = v[r] + hs.h2 * a[r];
+                xs[r] = fmar(hs.h2, v[r], x[r]);
+                vs[r] = fmar(hs.h2, a[r], v[r]);
             }
             accel(xs, a);                                  // stage 2
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                kx[r] = kx[r] + (Real)2 * vs[r];
-                kv[r] = kv[r] + (Real)2 * a[r];
-                xs[r] = x[r] + hs.h2 * vs[r];
-                vs[r] = v[r] + hs.h2 * a[r];
+                kx[r] = fmar((Real)2, vs[r], kx[r]);
+                kv[r] = fmar((Real)2, a[r], kv[r]);
+                xs[r] = fmar(hs.h2, vs[r], x[r]);
+                vs[r] = fmar(hs.h2, a[r], v[r]);
             }
             accel(xs, a);                                  // stage 3
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                kx[r] = kx[r] + (Real)2 * vs[r];
-                kv[r] = kv[r] + (Real)2 * a[r];
-                xs[r] = x[r] + hs.h * vs[r];
-                vs[r] = v[r] + hs.h * a[r];
+                kx[r] = fmar((Real)2, vs[r], kx[r]);
+                kv[r] = fmar((Real)2, a[r], kv[r]);
+                xs[r] = fmar(hs.h, vs[r], x[r]);
+                vs[r] = fmar(hs.h, a[r], v[r]);
             }
             accel(xs, a);                                  // stage 4
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                kx[r] = kx[r] + vs[r];
-                kv[r] = kv[r] + a[r];
-                state_add<F64>(x[r], cx[r], hs.inc(kx[r]));
-                state_add<F64>(v[r], cv[r], hs.inc(kv[r]));
+                kx[r] = addr(kx[r], vs[r]);
+                kv[r] = addr(kv[r], a[r]);
+                state_update<F64>(x[r], cx[r], kx[r], hs);
+                state_update<F64>(v[r], cv[r], kv[r], hs);
             }
         }
         if (src.ckpt_every() > 0) {
@@ -290,10 +290,149 @@ cudaError_t dispatch(int S, bool fp64, int64_t n, cudaStream_t st, const Init& i
 #undef CHO_SMALL_CASE
 }
 
+// ---- 2-DOF systems in FP32, two instances per thread in packed FP32x2 arithmetic ----
+//
+// The same step as rk4_small_kernel<2, false> (identical rounding: every packed
+// operation rounds each lane as the scalar intrinsic does), with lane 0 and
+// lane 1 of every float2 holding instances 2t and 2t+1.  Packing halves the
+// instructions issued per instance; the coefficients are stored negated so
+// that the packed accumulation yields a = -B x directly.
+
+constexpr int kPairThreads = 32;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ void pair_update(float2& x, float2& e, float2 k, float2 h6, float2 h6lo)
+{
+    const float2 m1 = f2(-1.f, -1.f);
+    float2 y = __ffma2_rn(h6lo, k, e);
+    y = __ffma2_rn(h6, k, y);
+    const float2 t = __fadd2_rn(x, y);
+    const float2 d = __ffma2_rn(x, m1, t);       // t - x
+    e = __ffma2_rn(d, m1, y);                    // y - (t - x)
+    x = t;
+}
+
+__global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys sys, const BatchIO io)
+{
+    const int64_t t = (int64_t)blockIdx.x * kPairThreads + threadIdx.x;
+    const int64_t q0 = 2 * t;
+    if (q0 >= io.n_inst) return;
+    const bool has1 = q0 + 1 < io.n_inst;
+    const int64_t q1 = has1 ? q0 + 1 : q0;       // odd count: lane 1 repeats lane 0, not stored
+    const int64_t s0 = sys.per_inst_sys ? q0 : 0, s1 = sys.per_inst_sys ? q1 : 0;
+    const float* b0 = sys.B32 + s0 * 8;          // [hi 2x2][lo 2x2]
+    const float* b1 = sys.B32 + s1 * 8;
+    float2 nbh[2][2], nbl[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            nbh[r][j] = f2(-b0[r * 2 + j], -b1[r * 2 + j]);
+            nbl[r][j] = f2(-b0[4 + r * 2 + j], -b1[4 + r * 2 + j]);
+        }
+    const StepSize<false> hs0(io.h[io.h_per_inst ? q0 : 0]), hs1(io.h[io.h_per_inst ? q1 : 0]);
+    const float2 h = f2(hs0.h, hs1.h), h2 = f2(hs0.h2, hs1.h2), h6 = f2(hs0.h6, hs1.h6),
+                 h6lo = f2(hs0.h6lo, hs1.h6lo), two = f2(2.f, 2.f);
+    float2 x[2], v[2], ex[2], ev[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
+        const double va = io.v0[q0 * 2 + r], vb = io.v0[q1 * 2 + r];
+        x[r] = f2((float)xa, (float)xb);
+        v[r] = f2((float)va, (float)vb);
+        ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
+        ev[r] = f2((float)(va - (double)v[r].x), (float)(vb - (double)v[r].y));
+    }
+    auto accel = [&](const float2 (&xs)[2], float2 (&a)[2]) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float2 acc = __fmul2_rn(nbl[r][0], xs[0]);
+            acc = __ffma2_rn(nbl[r][1], xs[1], acc);
+            acc = __ffma2_rn(nbh[r][0], xs[0], acc);
+            a[r] = __ffma2_rn(nbh[r][1], xs[1], acc);
+        }
+    };
+    auto step = [&]() {
+        float2 a[2], xs[2], kx[2], kv[2], vs[2];
+        accel(x, a);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            kx[r] = v[r];
+            kv[r] = a[r];
+            xs[r] = __ffma2_rn(h2, v[r], x[r]);
+            vs[r] = __ffma2_rn(h2, a[r], v[r]);
+        }
+        accel(xs, a);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            kx[r] = __ffma2_rn(two, vs[r], kx[r]);
+            kv[r] = __ffma2_rn(two, a[r], kv[r]);
+            xs[r] = __ffma2_rn(h2, vs[r], x[r]);
+            vs[r] = __ffma2_rn(h2, a[r], v[r]);
+        }
+        accel(xs, a);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            kx[r] = __ffma2_rn(two, vs[r], kx[r]);
+            kv[r] = __ffma2_rn(two, a[r], kv[r]);
+            xs[r] = __ffma2_rn(h, vs[r], x[r]);
+            vs[r] = __ffma2_rn(h, a[r], v[r]);
+        }
+        accel(xs, a);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            kx[r] = __fadd2_rn(kx[r], vs[r]);
+            kv[r] = __fadd2_rn(kv[r], a[r]);
+            pair_update(x[r], ex[r], kx[r], h6, h6lo);
+            pair_update(v[r], ev[r], kv[r], h6, h6lo);
+        }
+    };
+    const int64_t n = io.n_steps;
+    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        for (int64_t base = 0; base < every; base += 0x40000000LL) {
+            const int32_t m = (int32_t)(every - base < 0x40000000LL ? every - base : 0x40000000LL);
+#pragma unroll 2
+            for (int32_t it = 0; it < m; ++it) step();
+        }
+        if (io.ckpt_every > 0 && io.x_traj) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
+                if (io.v_traj) io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)v[r].x + (double)ev[r].x;
+                if (has1) {
+                    io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                    if (io.v_traj) io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)v[r].y + (double)ev[r].y;
+                }
+            }
+        }
+        ++ck;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
+        io.v_out[q0 * 2 + r] = (double)v[r].x + (double)ev[r].x;
+        if (has1) {
+            io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
+            io.v_out[q1 * 2 + r] = (double)v[r].y + (double)ev[r].y;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
+    if (sys.S == 2 && !fp64) {
+        const int64_t threads = (io.n_inst + 1) / 2;
+        const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
+        if (blocks <= 0) return cudaSuccess;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        rk4_pair2_kernel<<<(unsigned)blocks, kPairThreads, 0, st>>>(sys, io);
+        return cudaGetLastError();
+    }
     return dispatch<BatchSrc>(sys.S, fp64, io.n_inst, st, [&](auto& s) {
         s.sys = sys;
         s.io = io;

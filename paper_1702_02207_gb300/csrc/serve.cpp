@@ -365,8 +365,8 @@ void ServeEngine::run()
                     const double xd = i < s ? r->x0[i] : 0.0, vd = i < s ? r->v0[i] : 0.0;
                     f[i] = (float)xd;
                     f[n + i] = (float)vd;
-                    f[2 * n + i] = (float)((double)f[i] - xd);
-                    f[3 * n + i] = (float)((double)f[n + i] - vd);
+                    f[2 * n + i] = (float)(xd - (double)f[i]);          // compensation: x + e
+                    f[3 * n + i] = (float)(vd - (double)f[n + i]);
                 }
             }
             e = cudaMemcpyAsync(r->block, dst, state_bytes(sys, r->prec), cudaMemcpyHostToDevice, st);
@@ -444,7 +444,7 @@ void ServeEngine::run()
                     e = launch_rk4_chain_slots(s_max, io, f64, st);
                 } else {
                     cho_system_impl* sys = std::get<3>(kv.first);
-                    DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf};
+                    DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
                     e = launch_rk4_dense_slots(ds, io, f64, st);
                 }
                 o += kv.second.size();
@@ -503,8 +503,8 @@ void ServeEngine::run()
                         } else {
                             const float* f = (const float*)src;
                             for (int i = 0; i < s; ++i) {
-                                r->x[i] = (double)f[i] - (double)f[2 * n + i];
-                                r->v[i] = (double)f[n + i] - (double)f[3 * n + i];
+                                r->x[i] = (double)f[i] + (double)f[2 * n + i];
+                                r->v[i] = (double)f[n + i] + (double)f[3 * n + i];
                             }
                         }
                         r->status = CHO_OK;

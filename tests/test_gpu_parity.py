@@ -317,3 +317,34 @@ def test_omega_max_matches_library_eigensolvers(ctx):
         assert cho.cho_system_info(sys_)[0] == pytest.approx(cfg["omega_max"], rel=1e-10)
     finally:
         cho.cho_destroy_system(sys_)
+
+
+# ---- dense shared systems on the tensor cores (split BF16) ---------------------------------
+
+# bf16x3 drops the 2^-16-relative partial products, so its error is stated, not 1e-5:
+# about n * theta * 2^-16 of phase after n steps of angle theta (1e-3 at 1000 steps here).
+TOL_BF16 = {"bf16x3": 3e-3, "bf16x5": TOL_FP32, "bf16x6": TOL_FP32}
+
+
+def test_dense_tensor_core_first_light(ctx):
+    """One tile, s = 128, a few steps: the tensor-core path agrees with the FP32 CUDA-core path."""
+    cfg = inputs.dense_group(s=128, n_inst=32, n_steps=10)
+    simt = run_gpu(ctx, cfg, "fp32_simt", 0)
+    tc = run_gpu(ctx, cfg, "bf16x5", 0)
+    assert rel_err(tc["x"][:, None], simt["x"][:, None]).max() < 1e-5
+
+
+@pytest.mark.parametrize("s", [33, 64, 100, 128, 129, 200, 256])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x5", "bf16x6"])
+def test_dense_tensor_core(ctx, s, prec):
+    if prec == "bf16x6" and s > 128:
+        cfg = inputs.dense_group(s=s, n_inst=3, n_steps=10)
+        with pytest.raises(cho.ChoError) as ei:
+            run_gpu(ctx, cfg, prec, 0)
+        assert ei.value.status == cho.CHO_EINVAL
+        return
+    cfg = inputs.dense_group(s=s, n_inst=45, n_steps=1000)
+    out = run_gpu(ctx, cfg, prec, 125)
+    ref = oracle_run(cfg, ckpt_every=125)
+    ex, ev = check(out, ref, TOL_BF16[prec])
+    print(f"dense s={s} {prec}: max rel err x {ex:.3e} v {ev:.3e}")
