@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
-    if (sys.S == 2 && !fp64) {
+    if (sys.s == 2 && !fp64) {     // s = 1 is also padded to S = 2 but keeps the generic layout
         const int64_t threads = (io.n_inst + 1) / 2;
         const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
         if (blocks <= 0) return cudaSuccess;
