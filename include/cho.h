@@ -212,6 +212,24 @@ cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* batch, void* 
  * Uses a device work buffer of 10 s doubles held by the context. */
 cho_status cho_integrate_plain(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
 
+/* The plain form without allocating: the same integration as cho_integrate_plain, for
+ * callers that must not allocate device memory once they run -- a real-time or
+ * hardware-in-the-loop stepping loop, where cudaMalloc can block on the device and break
+ * a step's deadline, or an application that hands all device memory to its own pool.
+ * The paper has no counterpart; this is a deployment variant.
+ * Its scratch (state and stage buffers of one instance, 10 s doubles) is a fixed array
+ * compiled into the library, so s must be <= 4096 (CHO_EINVAL above).  Every GPU that
+ * loads the library holds that array (320 KiB) until the process exits.  All calls share
+ * it: calls whose work overlaps on the GPU race on it and must be serialised by the
+ * caller (same stream, or synchronised streams).  Each call rewrites all scratch it
+ * reads, so nothing in it has to start at zero.
+ * The first call on a device looks up the array's device address (this loads it onto
+ * that device); make that first call before any stream capture.
+ * Arrays: device pointers only (batch->mem == CHO_MEM_DEVICE), prec == CHO_FP64, h read
+ * on the device, no checkpoints or energy.  Asynchronous on `stream`; no allocation, host
+ * or device, at any call.  Errors: CHO_EINVAL, CHO_ECUDA. */
+cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
+
 /* FP64 energy 1/2 v^T M v + 1/2 x^T K x of states x, v (n_inst, n_per, s); state (i, c)
  * uses parameter set i (or 0 when the system has one set).  E is (n_inst, n_per).
  * mem selects host or device pointers as in cho_batch_desc.  Errors: CHO_EINVAL, CHO_ECUDA. */

@@ -27,6 +27,7 @@ SOURCES = [
     "rk4_dense_tc.cu",
     "energy.cu",
     "plain.cu",
+    "plain_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -37,6 +37,7 @@ PRECS = {"fp64": CHO_FP64, "fp32_kahan": CHO_FP32_KAHAN, "bf16x3": CHO_DENSE_BF1
 EXPORTED = [
     "cho_init", "cho_shutdown", "cho_last_error", "cho_create_system", "cho_system_info",
     "cho_system_omegas", "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
+    "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
 ]
 
@@ -106,6 +107,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_destroy_system": ([V], None),
             "cho_integrate_batch": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
             "cho_integrate_plain": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
+            "cho_integrate_plain_noalloc": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
             "cho_energy": ([V, V, V, V, I64, I64, I32, V, V], I32),
             "cho_submit": ([V, ctypes.POINTER(cho_request), ctypes.POINTER(ctypes.c_uint64)], I32),
             "cho_poll": ([V, ctypes.c_uint64, ctypes.POINTER(cho_result)], I32),
@@ -296,6 +298,16 @@ def cho_integrate_batch(ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_eve
 def cho_integrate_plain(ctx, system, x0, v0, h, n_steps, out=None, stream=None):
     """The plain form: one launch per stage, one system at a time, FP64."""
     return _batch("cho_integrate_plain", ctx, system, x0, v0, h, n_steps, CHO_FP64, 0, False, False,
+                  out, stream)
+
+
+def cho_integrate_plain_noalloc(ctx, system, x0, v0, h, n_steps, out=None, stream=None):
+    """The plain form with its scratch in the library's fixed device array (no allocation
+    in the call).  Device (CUDA tensor) arrays only; pass ``out`` to avoid the binding
+    allocating the result tensors."""
+    if not _is_cuda(x0):
+        raise ValueError("cho_integrate_plain_noalloc takes device arrays")
+    return _batch("cho_integrate_plain_noalloc", ctx, system, x0, v0, h, n_steps, CHO_FP64, 0, False, False,
                   out, stream)
 
 
