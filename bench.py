@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=20000)
     return p.parse_args()
 
 
@@ -123,6 +124,92 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def percentile(a, q):
+    return float(np.percentile(np.asarray(a), q)) if len(a) else None
+
+
+def run_serving(cho, inputs, ctx, n_req, load=0.8):
+    """Mixed request stream through cho_submit / cho_poll (continuous batching).
+
+    Requests follow the mixed-load recipe of request_stream: Poisson arrivals, s
+    log-uniform over {2..512} (2-DOF, chains, dense groups of 8 sizes), horizons
+    log-uniform 1e3..1e5 steps, three priority classes 20/30/50 %, FP32 + Kahan.
+    A saturated burst of n_req // 10 requests first measures the service rate; the
+    stream then arrives at `load` times that rate.  Returns throughput and the
+    p50/p99 submit-to-done latency per class.
+    """
+    import time as _t
+
+    st = inputs.request_stream(n_req=n_req, rate_per_s=1.0)
+    systems = {}
+
+    def system_for(kind, s_):
+        key = (kind, s_)
+        if key not in systems:
+            if kind == 0:
+                c = inputs.two_dof_batch(n_inst=4096, n_steps=1)
+                systems[key] = (cho.cho_create_system(ctx, "two_dof", masses=c["masses"], springs=c["springs"]), c["h"])
+            elif kind == 1:
+                c = inputs.chain_batch(n_inst=4, s=s_, n_steps=1, seed=inputs.SEED_BASE + 50_000 + s_)
+                systems[key] = (cho.cho_create_system(ctx, "chain", masses=c["masses"], springs=c["springs"]), c["h"])
+            else:
+                c = inputs.dense_group(s=s_, n_inst=1, n_steps=1)
+                systems[key] = (cho.cho_create_system(ctx, "dense", M=c["M"], K=c["K"]), c["h"])
+        return systems[key]
+
+    rng = np.random.default_rng(inputs.SEED_BASE + 99)
+    reqs = []
+    for i in range(n_req):
+        kind, s_ = int(st["kind"][i]), int(st["s"][i])
+        sys_, hs = system_for(kind, s_)
+        k = i % len(hs)
+        reqs.append((sys_, k, rng.uniform(-1, 1, s_), np.zeros(s_), float(hs[k]), int(st["n_steps"][i]),
+                     int(st["priority"][i]), s_))
+    work = np.array([r[7] * r[5] for r in reqs], dtype=np.float64)
+
+    def drive(idx, gaps):
+        tickets = {}
+        t0 = _t.perf_counter()
+        next_t = 0.0
+        pending = {}
+        lat = {0: [], 1: [], 2: []}
+        for j, i in enumerate(idx):
+            next_t += gaps[j]
+            while _t.perf_counter() - t0 < next_t:
+                _t.sleep(min(0.0005, max(0.0, next_t - (_t.perf_counter() - t0))))
+            sys_, k, x0, v0, h, n, pr, s_ = reqs[i]
+            t = cho.cho_submit(ctx, sys_, x0, v0, h, n, "fp32_kahan", pr, k)
+            pending[t] = (i, pr, s_)
+        while pending:
+            for t in list(pending):
+                i, pr, s_ = pending[t]
+                stt, res = cho.cho_poll(ctx, t, s_)
+                if stt == cho.CHO_OK:
+                    lat[pr].append(res["t_done"] - res["t_submit"])
+                    del pending[t]
+            _t.sleep(0.0005)
+        return _t.perf_counter() - t0, lat
+
+    n_cal = max(50, n_req // 10)
+    cal = np.arange(n_cal)
+    t_cal, _ = drive(cal, np.zeros(n_cal))
+    rate_dof = work[cal].sum() / t_cal                      # saturated DOF-steps/s
+    lam = load * rate_dof / work.mean()                      # requests per second at this load
+    idx = np.arange(n_cal, n_req)
+    gaps = np.random.default_rng(inputs.SEED_BASE + 98).exponential(1.0 / lam, size=len(idx))
+    t_run, lat = drive(idx, gaps)
+    for sys_, _ in systems.values():
+        cho.cho_destroy_system(sys_)
+    out = {"requests": int(n_req), "burst_requests": int(n_cal), "saturated_dof_steps_per_s": rate_dof,
+           "offered_load": load, "arrival_rate_per_s": lam,
+           "stream_dof_steps_per_s": work[idx].sum() / t_run, "stream_seconds": t_run,
+           "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
+                         for c in range(3)},
+           "mix": "s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5, "
+                  "classes 20/30/50 %, Poisson arrivals, FP32 + Kahan"}
+    return out
+
+
 def oracle_sample_rate(cfg, n_sample, threads=1):
     """Time the FP64 oracle on the first n_sample instances; DOF-steps/s and seconds."""
     import oracle
@@ -167,6 +254,52 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
+    """The chain (s = 1024 x 4096, 1e4 steps) and dense (s = 64/128/256 x 8192, 5e3 steps)
+    workloads, one timed run each after a warm-up, with their roofline fractions."""
+    import torch
+
+    res = {}
+
+    def timed(sys_, cfg, prec, n):
+        x0 = torch.as_tensor(cfg["x0"], device=dev)
+        v0 = torch.as_tensor(cfg["v0"], device=dev)
+        h = torch.as_tensor(cfg["h"], device=dev)
+        out = {"x": torch.empty_like(x0), "v": torch.empty_like(v0)}
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, min(n, 100), prec, out=out, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, n, prec, out=out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    alu_peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+    cfg = inputs.chain_batch()
+    s_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])
+    dof = cfg["x0"].size * cfg["n_steps"]
+    ach = dof * 52 / t / 1e12            # 26 FMA per DOF-step (4 x 3-point stencil, 6 combine, 6 sums, 2 update)
+    res["chain_s1024_x4096_fp32_kahan"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak,
+                                                         "unit": "TFLOP/s", "frac": ach / alu_peak}}
+    cho.cho_destroy_system(s_)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    for s in (64, 128, 256):
+        cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
+        s_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
+        for prec in ("bf16x5", "bf16x3"):
+            t = timed(s_, cfg, prec, cfg["n_steps"])
+            dof = cfg["x0"].size * cfg["n_steps"]
+            ach = dof * 8 * s / t / 1e12     # four B x products of 2 s flops per DOF per step
+            res[f"dense_s{s}_x8192_{prec}"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                               "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                                                            "unit": "TFLOP/s", "frac": ach / bf16_peak}}
+        cho.cho_destroy_system(s_)
+    return res
 
 
 def main():
@@ -324,6 +457,10 @@ def main():
             line["plain_form"] = {"value": plain_rate, "unit": UNIT,
                                   "sample": f"{n_plain} systems x {n_plain_steps} steps, FP64, 5 launches per step",
                                   "batched_over_plain": value / world / plain_rate}
+        if not args.no_extras:
+            line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks)
+            if args.serve_requests > 0:
+                line["serving"] = run_serving(cho, inputs, ctx, args.serve_requests)
         if not args.no_cpu_baseline:
             n_cpu = 16384
             rate, dt = oracle_sample_rate(cfg, n_cpu)

@@ -21,6 +21,9 @@
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
 
+#include <cstdlib>
+#include <cstring>
+
 namespace cho {
 namespace {
 
@@ -176,15 +179,16 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     // acc[r] = -(B xs)[row g*R + r]
     auto accel = [&](const Real (&xs)[R], Real (&acc)[R]) {
         if constexpr (G == 1) {
+            // row r sums its columns starting at the diagonal: j = r, r+1, ... (mod S)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 Real t = 0;
                 if constexpr (!F64) {
 #pragma unroll
-                    for (int j = 0; j < S; ++j) t = fmaf(bl[r][j], xs[j], t);
+                    for (int jj = 0; jj < S; ++jj) t = fmaf(bl[r][(r + jj) % S], xs[(r + jj) % S], t);
                 }
 #pragma unroll
-                for (int j = 0; j < S; ++j) t = fmar(bh[r][j], xs[j], t);
+                for (int jj = 0; jj < S; ++jj) t = fmar(bh[r][(r + jj) % S], xs[(r + jj) % S], t);
                 acc[r] = -t;
             }
         } else {
@@ -346,11 +350,11 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
     }
     auto accel = [&](const float2 (&xs)[2], float2 (&a)[2]) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            float2 acc = __fmul2_rn(nbl[r][0], xs[0]);
-            acc = __ffma2_rn(nbl[r][1], xs[1], acc);
-            acc = __ffma2_rn(nbh[r][0], xs[0], acc);
-            a[r] = __ffma2_rn(nbh[r][1], xs[1], acc);
+        for (int r = 0; r < 2; ++r) {            // diagonal first, as rk4_small_kernel
+            float2 acc = __fmul2_rn(nbl[r][r], xs[r]);
+            acc = __ffma2_rn(nbl[r][1 - r], xs[1 - r], acc);
+            acc = __ffma2_rn(nbh[r][r], xs[r], acc);
+            a[r] = __ffma2_rn(nbh[r][1 - r], xs[1 - r], acc);
         }
     };
     auto step = [&]() {
@@ -421,11 +425,105 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
     }
 }
 
+// One 2-DOF instance per thread with the two DOFs packed in FP32x2 lanes: lane r
+// holds row r.  The off-diagonal products take the displacement with its lanes
+// swapped.  Same rounding as rk4_small_kernel<2, false>.
+constexpr int kTwoDofThreads = 64;
+
+__global__ void __launch_bounds__(kTwoDofThreads) rk4_two_dof_packed_kernel(const SmallSys sys, const BatchIO io)
+{
+    const int64_t q = (int64_t)blockIdx.x * kTwoDofThreads + threadIdx.x;
+    if (q >= io.n_inst) return;
+    const float* b = sys.B32 + (sys.per_inst_sys ? q : 0) * 8;      // [hi 2x2][lo 2x2]
+    const float2 dh = f2(-b[0], -b[3]), oh = f2(-b[1], -b[2]);      // -diag, -offdiag
+    const float2 dl = f2(-b[4], -b[7]), ol = f2(-b[5], -b[6]);
+    const StepSize<false> hs(io.h[io.h_per_inst ? q : 0]);
+    const float2 h = f2(hs.h, hs.h), h2 = f2(hs.h2, hs.h2), h6 = f2(hs.h6, hs.h6), h6lo = f2(hs.h6lo, hs.h6lo),
+                 two = f2(2.f, 2.f);
+    const double x0a = io.x0[q * 2], x0b = io.x0[q * 2 + 1], v0a = io.v0[q * 2], v0b = io.v0[q * 2 + 1];
+    float2 x = f2((float)x0a, (float)x0b), v = f2((float)v0a, (float)v0b);
+    float2 ex = f2((float)(x0a - (double)x.x), (float)(x0b - (double)x.y));
+    float2 ev = f2((float)(v0a - (double)v.x), (float)(v0b - (double)v.y));
+    auto accel = [&](float2 xs) {
+        const float2 xw = f2(xs.y, xs.x);
+        float2 acc = __fmul2_rn(dl, xs);
+        acc = __ffma2_rn(ol, xw, acc);
+        acc = __ffma2_rn(dh, xs, acc);
+        return __ffma2_rn(oh, xw, acc);
+    };
+    auto step = [&]() {
+        float2 a = accel(x);
+        float2 kx = v, kv = a;
+        float2 xs = __ffma2_rn(h2, v, x), vs = __ffma2_rn(h2, a, v);
+        a = accel(xs);
+        kx = __ffma2_rn(two, vs, kx);
+        kv = __ffma2_rn(two, a, kv);
+        xs = __ffma2_rn(h2, vs, x);
+        vs = __ffma2_rn(h2, a, v);
+        a = accel(xs);
+        kx = __ffma2_rn(two, vs, kx);
+        kv = __ffma2_rn(two, a, kv);
+        xs = __ffma2_rn(h, vs, x);
+        vs = __ffma2_rn(h, a, v);
+        a = accel(xs);
+        kx = __fadd2_rn(kx, vs);
+        kv = __fadd2_rn(kv, a);
+        pair_update(x, ex, kx, h6, h6lo);
+        pair_update(v, ev, kv, h6, h6lo);
+    };
+    const int64_t n = io.n_steps;
+    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        for (int64_t base = 0; base < every; base += 0x40000000LL) {
+            const int32_t m = (int32_t)(every - base < 0x40000000LL ? every - base : 0x40000000LL);
+#pragma unroll 2
+            for (int32_t it = 0; it < m; ++it) step();
+        }
+        if (io.ckpt_every > 0 && io.x_traj) {
+            const int64_t o = (q * io.n_ck + ck) * 2;
+            io.x_traj[o] = (double)x.x + (double)ex.x;
+            io.x_traj[o + 1] = (double)x.y + (double)ex.y;
+            if (io.v_traj) {
+                io.v_traj[o] = (double)v.x + (double)ev.x;
+                io.v_traj[o + 1] = (double)v.y + (double)ev.y;
+            }
+        }
+        ++ck;
+    }
+    io.x_out[q * 2] = (double)x.x + (double)ex.x;
+    io.x_out[q * 2 + 1] = (double)x.y + (double)ex.y;
+    io.v_out[q * 2] = (double)v.x + (double)ev.x;
+    io.v_out[q * 2 + 1] = (double)v.y + (double)ev.y;
+}
+
+// Which 2-DOF FP32 kernel runs: "pair" (two instances per thread), "packed" (one
+// instance per thread, DOFs packed) or "generic" (rk4_small_kernel<2>); all give the
+// same bits.  CHO_TWO_DOF_KERNEL overrides the default.
+int two_dof_variant()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("CHO_TWO_DOF_KERNEL");
+        v = 0;
+        if (e && std::strcmp(e, "packed") == 0) v = 1;
+        if (e && std::strcmp(e, "generic") == 0) v = 2;
+    }
+    return v;
+}
+
 }  // namespace
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
-    if (sys.s == 2 && !fp64) {     // s = 1 is also padded to S = 2 but keeps the generic layout
+    if (sys.s == 2 && !fp64 && two_dof_variant() == 1) {
+        const int64_t blocks = (io.n_inst + kTwoDofThreads - 1) / kTwoDofThreads;
+        if (blocks <= 0) return cudaSuccess;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        rk4_two_dof_packed_kernel<<<(unsigned)blocks, kTwoDofThreads, 0, st>>>(sys, io);
+        return cudaGetLastError();
+    }
+    if (sys.s == 2 && !fp64 && two_dof_variant() == 0) {   // s = 1 is also padded to S = 2 but keeps the generic layout
         const int64_t threads = (io.n_inst + 1) / 2;
         const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
         if (blocks <= 0) return cudaSuccess;

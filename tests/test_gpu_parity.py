@@ -8,6 +8,7 @@ the same phase every time (e.g. always at its turning points, where v ~ 0) and t
 normalisation would not see the horizon's true maximum.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +17,7 @@ from paper_1702_02207_gb300 import cho, inputs
 from parity_util import TOL_FP32, TOL_FP64, oracle_run, rel_err, sample_indices
 
 pytestmark = pytest.mark.gpu
+ROOT_DIR = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -348,3 +350,32 @@ def test_dense_tensor_core(ctx, s, prec):
     ref = oracle_run(cfg, ckpt_every=125)
     ex, ev = check(out, ref, TOL_BF16[prec])
     print(f"dense s={s} {prec}: max rel err x {ex:.3e} v {ev:.3e}")
+
+
+def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
+    """The pair-packed, DOF-packed and generic 2-DOF FP32 kernels round identically."""
+    import subprocess
+    import sys as _sys
+
+    code = (
+        "import sys, numpy as np, torch\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_1702_02207_gb300 import cho, inputs\n"
+        "cfg = inputs.two_dof_batch(n_inst=999, n_steps=3000)\n"
+        "ctx = cho.cho_init(0)\n"
+        "s = cho.cho_create_system(ctx, 'two_dof', masses=cfg['masses'], springs=cfg['springs'])\n"
+        "d = torch.device('cuda:0')\n"
+        "o = cho.cho_integrate_batch(ctx, s, torch.as_tensor(cfg['x0'], device=d), torch.as_tensor(cfg['v0'], device=d),"
+        " torch.as_tensor(cfg['h'], device=d), 3000, 'fp32_kahan', 1000, trajectory=True)\n"
+        "torch.cuda.synchronize()\n"
+        "np.savez(sys.argv[1], **{k: v.cpu().numpy() for k, v in o.items()})\n"
+    ) % ROOT_DIR
+    res = {}
+    for variant in ("pair", "packed", "generic"):
+        path = str(tmp_path / f"{variant}.npz")
+        env = dict(os.environ, CHO_TWO_DOF_KERNEL=variant)
+        subprocess.run([_sys.executable, "-c", code, path], check=True, env=env, timeout=300)
+        res[variant] = np.load(path)
+    for variant in ("packed", "generic"):
+        for k in ("x", "v", "x_traj", "v_traj"):
+            assert np.array_equal(res["pair"][k], res[variant][k]), (variant, k)
