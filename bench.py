@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=20000)
+    p.add_argument("--serve-requests", type=int, default=4000)
     return p.parse_args()
 
 
@@ -124,11 +124,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def log(msg):
+    """Progress on stderr (the JSON result line goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def percentile(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
 
 
-def run_serving(cho, inputs, ctx, n_req, load=0.8):
+def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
     """Mixed request stream through cho_submit / cho_poll (continuous batching).
 
     Requests follow the mixed-load recipe of request_stream: Poisson arrivals, s
@@ -180,7 +185,8 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8):
             sys_, k, x0, v0, h, n, pr, s_ = reqs[i]
             t = cho.cho_submit(ctx, sys_, x0, v0, h, n, "fp32_kahan", pr, k)
             pending[t] = (i, pr, s_)
-        while pending:
+        deadline = _t.perf_counter() + 300.0
+        while pending and _t.perf_counter() < deadline:
             for t in list(pending):
                 i, pr, s_ = pending[t]
                 stt, res = cho.cho_poll(ctx, t, s_)
@@ -188,19 +194,30 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8):
                     lat[pr].append(res["t_done"] - res["t_submit"])
                     del pending[t]
             _t.sleep(0.0005)
+        if pending:
+            log(f"serving: {len(pending)} requests unfinished after the deadline; cancelling")
+            for t in list(pending):
+                cho.cho_cancel(ctx, t)
         return _t.perf_counter() - t0, lat
 
+    # service rate: a burst of n_cal requests submitted at once (its makespan includes the
+    # longest horizon, so this rate is a lower bound and the offered load errs low)
     n_cal = max(50, n_req // 10)
     cal = np.arange(n_cal)
+    log(f"serving: burst of {n_cal} requests")
     t_cal, _ = drive(cal, np.zeros(n_cal))
     rate_dof = work[cal].sum() / t_cal                      # saturated DOF-steps/s
     lam = load * rate_dof / work.mean()                      # requests per second at this load
-    idx = np.arange(n_cal, n_req)
+    # the Poisson stream: at most stream_seconds of arrivals
+    n_stream = int(min(n_req - n_cal, max(20, lam * stream_seconds)))
+    idx = np.arange(n_cal, n_cal + n_stream)
     gaps = np.random.default_rng(inputs.SEED_BASE + 98).exponential(1.0 / lam, size=len(idx))
+    log(f"serving: burst took {t_cal:.1f} s ({rate_dof:.3e} DOF-steps/s); stream of {n_stream} requests at {lam:.1f}/s")
     t_run, lat = drive(idx, gaps)
+    log(f"serving: stream took {t_run:.1f} s")
     for sys_, _ in systems.values():
         cho.cho_destroy_system(sys_)
-    out = {"requests": int(n_req), "burst_requests": int(n_cal), "saturated_dof_steps_per_s": rate_dof,
+    out = {"requests": int(n_cal + n_stream), "burst_requests": int(n_cal), "saturated_dof_steps_per_s": rate_dof,
            "offered_load": load, "arrival_rate_per_s": lam,
            "stream_dof_steps_per_s": work[idx].sum() / t_run, "stream_seconds": t_run,
            "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
@@ -354,6 +371,7 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms
 
+    log("set-up done; headline run")
     # ---- headline: FP32 + Kahan ----
     sampler = ClockSampler(local_rank)
     for _ in range(args.warmup):
@@ -458,10 +476,12 @@ def main():
                                   "sample": f"{n_plain} systems x {n_plain_steps} steps, FP64, 5 launches per step",
                                   "batched_over_plain": value / world / plain_rate}
         if not args.no_extras:
+            log("other configurations")
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks)
             if args.serve_requests > 0:
                 line["serving"] = run_serving(cho, inputs, ctx, args.serve_requests)
         if not args.no_cpu_baseline:
+            log("CPU baseline (oracle)")
             n_cpu = 16384
             rate, dt = oracle_sample_rate(cfg, n_cpu)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -163,14 +163,22 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     }
 
     int buf = 0;
+    // neighbours of warp edges come from shared memory; every lane reads the same
+    // word (a broadcast) and selects, so no lane branches
+    const int wl = warp > 0 ? warp - 1 : 0;
+    const int wr = warp + 1 < nwarp ? warp + 1 : warp;
+    const Real has_left = warp > 0 ? (Real)1 : (Real)0;
+    const Real has_right = warp + 1 < nwarp ? (Real)1 : (Real)0;
     auto accel = [&](const Real (&xs)[P], Real (&acc)[P]) {
-        Real left = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
-        Real right = __shfl_down_sync(0xffffffffu, xs[0], 1);
+        const Real up = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
+        const Real dn = __shfl_down_sync(0xffffffffu, xs[0], 1);
         if (lane == 31) edge_last[buf][warp] = xs[P - 1];
         if (lane == 0) edge_first[buf][warp] = xs[0];
         __syncthreads();
-        if (lane == 0) left = warp > 0 ? edge_last[buf][warp - 1] : (Real)0;
-        if (lane == 31) right = warp + 1 < nwarp ? edge_first[buf][warp + 1] : (Real)0;
+        const Real el = edge_last[buf][wl] * has_left;
+        const Real ef = edge_first[buf][wr] * has_right;
+        const Real left = lane == 0 ? el : up;
+        const Real right = lane == 31 ? ef : dn;
         buf ^= 1;
         Real e[P + 1];                       // spring extensions e_{i0} .. e_{i0+P}
         e[0] = xs[0] - left;
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
     int64_t ck = 0;
     for (int64_t done = 0; done < n; done += every) {
-        for (int64_t it = 0; it < every; ++it) {
+        repeat_steps(every, [&]() {
             Real a[P], xs[P], kx[P], kv[P], vs[P];
             accel(x, a);
 #pragma unroll
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
                 state_update<F64>(x[p], cx[p], kx[p], hs);
                 state_update<F64>(v[p], cv[p], kv[p], hs);
             }
-        }
+        });
         if (src.ckpt_every() > 0) {
 #pragma unroll
             for (int p = 0; p < P; ++p)

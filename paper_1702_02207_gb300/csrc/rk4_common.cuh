@@ -64,4 +64,15 @@ __device__ __forceinline__ void state_update(std::conditional_t<F64, double, flo
     }
 }
 
+// Run f() n times with a 32-bit inner counter (64-bit compares cost extra
+// instructions and a branch every step).
+template <class F>
+__device__ __forceinline__ void repeat_steps(int64_t n, F&& f)
+{
+    for (int64_t base = 0; base < n; base += 0x40000000LL) {
+        const int32_t m = (int32_t)(n - base < 0x40000000LL ? n - base : 0x40000000LL);
+        for (int32_t i = 0; i < m; ++i) f();
+    }
+}
+
 }  // namespace cho

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
     int64_t ck = 0;
     for (int64_t done = 0; done < n; done += every) {
-        for (int64_t it = 0; it < every; ++it) {
+        repeat_steps(every, [&]() {
             Real a[R], xs[R], kx[R], kv[R], vs[R];
             accel(x, a);                                   // stage 1
 #pragma unroll
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
                 state_update<F64>(x[r], cx[r], kx[r], hs);
                 state_update<F64>(v[r], cv[r], kv[r], hs);
             }
-        }
+        });
         if (src.ckpt_every() > 0) {
 #pragma unroll
             for (int r = 0; r < R; ++r) src.checkpoint(q, ck, g * R + r, x[r], v[r], cx[r], cv[r]);
