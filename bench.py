@@ -343,7 +343,9 @@ def main():
         torch.cuda.synchronize()
 
     # ---- set-up (off the timed region): inputs, system, device arrays ----
-    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS, seed=inputs.SEED_BASE + 1 + 1000 * rank)
+    from paper_1702_02207_gb300 import shard
+
+    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS, seed=shard.rank_seed(inputs.SEED_BASE + 1, rank))
     ctx = cho.cho_init(local_rank)
     sys_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
     x0 = torch.as_tensor(cfg["x0"], device=dev)
@@ -380,12 +382,7 @@ def main():
     ms = timed("fp32_kahan", args.steps, 0)
     clocks = sampler.stop()
     t_rank = sum(ms) / 1e3
-    if pg is not None:
-        t = torch.tensor([t_rank], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_rank
+    t_max = shard.max_over_ranks(t_rank, pg, dev)
     value = world * args.steps * DOF_STEPS / t_max
     avg_kernel_s = t_rank / args.steps
 
