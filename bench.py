@@ -168,8 +168,10 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
         kind, s_ = int(st["kind"][i]), int(st["s"][i])
         sys_, hs = system_for(kind, s_)
         k = i % len(hs)
+        # dense groups with 32 < s <= 256 run on the tensor cores (bf16x5, error <= 1e-5)
+        prec = "bf16x5" if kind == 2 and 32 < s_ <= 256 else "fp32_kahan"
         reqs.append((sys_, k, rng.uniform(-1, 1, s_), np.zeros(s_), float(hs[k]), int(st["n_steps"][i]),
-                     int(st["priority"][i]), s_))
+                     int(st["priority"][i]), s_, prec))
     work = np.array([r[7] * r[5] for r in reqs], dtype=np.float64)
 
     def drive(idx, gaps):
@@ -182,8 +184,8 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
             next_t += gaps[j]
             while _t.perf_counter() - t0 < next_t:
                 _t.sleep(min(0.0005, max(0.0, next_t - (_t.perf_counter() - t0))))
-            sys_, k, x0, v0, h, n, pr, s_ = reqs[i]
-            t = cho.cho_submit(ctx, sys_, x0, v0, h, n, "fp32_kahan", pr, k)
+            sys_, k, x0, v0, h, n, pr, s_, prec = reqs[i]
+            t = cho.cho_submit(ctx, sys_, x0, v0, h, n, prec, pr, k)
             pending[t] = (i, pr, s_)
         deadline = _t.perf_counter() + 300.0
         while pending and _t.perf_counter() < deadline:
@@ -223,7 +225,7 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
            "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
                          for c in range(3)},
            "mix": "s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5, "
-                  "classes 20/30/50 %, Poisson arrivals, FP32 + Kahan"}
+                  "classes 20/30/50 %, Poisson arrivals; FP32 + compensation, dense 32 < s <= 256 in bf16x5"}
     return out
 
 

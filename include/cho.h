@@ -152,7 +152,8 @@ typedef struct cho_request {
     const double* v0;       /* host, (s) */
     double h;
     int64_t n_steps;
-    int32_t prec;           /* CHO_FP64 or CHO_FP32_KAHAN */
+    int32_t prec;           /* CHO_FP64, CHO_FP32_KAHAN, or for shared dense systems with
+                               32 < s <= 256 a BF16 tensor-core mode */
     int32_t priority;       /* 0 (highest), 1, 2 */
 } cho_request;
 

@@ -28,6 +28,7 @@ SOURCES = [
     "energy.cu",
     "plain.cu",
     "plain_noalloc.cu",
+    "serve_kernels.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

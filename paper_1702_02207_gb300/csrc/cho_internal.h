@@ -71,6 +71,9 @@ struct SlotIO {
     int64_t chunk;          // each slot runs min(chunk, remaining) steps
 };
 
+cudaError_t launch_gather_status(const int32_t* ids, const int32_t* status, int32_t* out, int64_t n,
+                                 cudaStream_t st);
+
 // ---- rk4_small ----------------------------------------------------------------
 // Coefficients per parameter set: FP64 B (S*S), or FP32 hi (S*S) followed by lo (S*S).
 struct SmallSys {
@@ -113,6 +116,7 @@ cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, c
 cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st);
 // tensor-core split-BF16 variant (rk4_dense_tc.cu)
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
+cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int prec, cudaStream_t st);
 
 // ---- energy -------------------------------------------------------------------
 struct EnergySys {

@@ -165,9 +165,72 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 __constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
 __constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
 
+// Batch form: FP64 arrays in and out, shared step count, checkpoints.
+struct TcBatchSrc {
+    BatchIO io;
+    int s;
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ double h(int64_t q) const { return io.h[io.h_per_inst ? q : 0]; }
+    __device__ int64_t steps(int64_t) const { return io.n_steps; }
+    __device__ int64_t ckpt_every() const { return io.ckpt_every; }
+    __device__ void load(int64_t q, int k, float& x, float& v, float& cx, float& cv) const
+    {
+        const double xd = io.x0[q * s + k], vd = io.v0[q * s + k];
+        x = (float)xd;
+        v = (float)vd;
+        cx = (float)(xd - (double)x);
+        cv = (float)(vd - (double)v);
+    }
+    __device__ void checkpoint(int64_t q, int64_t ck, int k, float x, float v, float cx, float cv) const
+    {
+        if (!io.x_traj) return;
+        const int64_t o = (q * io.n_ck + ck) * s + k;
+        io.x_traj[o] = (double)x + (double)cx;
+        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
+    }
+    __device__ void store(int64_t q, int k, float x, float v, float cx, float cv) const
+    {
+        io.x_out[q * s + k] = (double)x + (double)cx;
+        io.v_out[q * s + k] = (double)v + (double)cv;
+    }
+    __device__ void flag(int64_t, int) const {}
+    __device__ void book(int64_t, int64_t) const {}
+};
+
+// Slot form (serving): FP32 state block [x(s), v(s), cx(s), cv(s)]; each slot runs
+// min(chunk, remaining) steps, the tile loops to its largest count.
+struct TcSlotSrc {
+    SlotIO io;
+    int s;
+    __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
+    __device__ int64_t count() const { return io.n_inst; }
+    __device__ double h(int64_t q) const { return d(q).h; }
+    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
+    __device__ int64_t ckpt_every() const { return 0; }
+    __device__ void load(int64_t q, int k, float& x, float& v, float& cx, float& cv) const
+    {
+        const float* st = (const float*)d(q).state;
+        x = st[k];
+        v = st[s + k];
+        cx = st[2 * s + k];
+        cv = st[3 * s + k];
+    }
+    __device__ void checkpoint(int64_t, int64_t, int, float, float, float, float) const {}
+    __device__ void store(int64_t q, int k, float x, float v, float cx, float cv) const
+    {
+        float* st = (float*)d(q).state;
+        st[k] = x;
+        st[s + k] = v;
+        st[2 * s + k] = cx;
+        st[3 * s + k] = cv;
+    }
+    __device__ void flag(int64_t q, int code) const { io.status[io.slot_ids[q]] = code; }
+    __device__ void book(int64_t q, int64_t ran) const { io.slots[io.slot_ids[q]].remaining -= ran; }
+};
+
 // PA pieces of B, PB pieces of Xs, CS CTAs per cluster.
-template <int PA, int PB, int CS>
-__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, BatchIO io)
+template <int PA, int PB, int CS, class Src>
+__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
 {
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
     constexpr int A_BYTES = PA * KC * kAChunk;
@@ -181,6 +244,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag[2];
     __shared__ float sh_h[kNT][4];                   // h, h/2, h/6 hi, h/6 lo of each instance
+    __shared__ long long sh_steps[kNT];              // steps of each instance in this launch
+    __shared__ long long sh_max_steps;
+    __shared__ int sh_bad[kNT];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -204,7 +270,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     }
     if (tid < kNT) {
         const int64_t q = tile * kNT + tid;
-        const double hd = q < io.n_inst ? io.h[io.h_per_inst ? q : 0] : 1.0;
+        const bool live = q < src.count();
+        const double hd = live ? src.h(q) : 1.0;
+        sh_steps[tid] = live ? (long long)src.steps(q) : 0;
+        sh_bad[tid] = 0;
         const double h6 = hd / 6.0;
         sh_h[tid][0] = (float)hd;
         sh_h[tid][1] = (float)(0.5 * hd);
@@ -251,14 +320,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 #pragma unroll
     for (int j = 0; j < kCPT; ++j) {
         const int64_t q = tile * kNT + n0 + j;
-        const bool live = live_row && q < io.n_inst;
-        const double xd = live ? io.x0[q * s + k] : 0.0;
-        const double vd = live ? io.v0[q * s + k] : 0.0;
-        x[j] = (float)xd;
-        v[j] = (float)vd;
-        cx[j] = (float)(xd - (double)x[j]);
-        cv[j] = (float)(vd - (double)v[j]);
+        if (live_row && q < src.count()) {
+            src.load(q, k, x[j], v[j], cx[j], cv[j]);
+        } else {
+            x[j] = v[j] = cx[j] = cv[j] = 0.f;
+        }
     }
+    if (tid == 0) {
+        long long m = 0;
+        for (int j = 0; j < kNT; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+        sh_max_steps = m;
+    }
+    __syncthreads();
 
     // Xs addresses of this thread's DOF k in every CTA of the cluster
     const int kc = k / 16, kk = k % 16;
@@ -324,11 +397,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         return agree(done);
     };
 
-    const int64_t nsteps = ok ? io.n_steps : 0;
-    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (nsteps > 0 ? nsteps : 1);
-    int64_t ck = 0;
+    const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
+    int64_t ck = 0, step = 0;
     for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
-        for (int64_t it = 0; it < every && ok; ++it) {
+        for (int64_t it = 0; it < every && ok; ++it, ++step) {
             float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vs[kCPT];
             ok = stage(x, a);
 #pragma unroll
@@ -360,23 +433,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h6 = sh_h[n0 + j][2], h6l = sh_h[n0 + j][3];
-                kx[j] = addr(kx[j], vs[j]);
-                kv[j] = addr(kv[j], a[j]);
-                comp_update(x[j], cx[j], kx[j], h6, h6l);
-                comp_update(v[j], cv[j], kv[j], h6, h6l);
+                if (step < sh_steps[n0 + j]) {       // instances past their count hold still
+                    const float h6 = sh_h[n0 + j][2], h6l = sh_h[n0 + j][3];
+                    kx[j] = addr(kx[j], vs[j]);
+                    kv[j] = addr(kv[j], a[j]);
+                    comp_update(x[j], cx[j], kx[j], h6, h6l);
+                    comp_update(v[j], cv[j], kv[j], h6, h6l);
+                }
             }
         }
-        if (io.ckpt_every > 0 && ok) {
-            if (io.x_traj && live_row) {
+        if (src.ckpt_every() > 0 && ok) {
+            if (live_row) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) {
                     const int64_t q = tile * kNT + n0 + j;
-                    if (q < io.n_inst) {
-                        const int64_t o = (q * io.n_ck + ck) * s + k;
-                        io.x_traj[o] = (double)x[j] + (double)cx[j];
-                        if (io.v_traj) io.v_traj[o] = (double)v[j] + (double)cv[j];
-                    }
+                    if (q < src.count()) src.checkpoint(q, ck, k, x[j], v[j], cx[j], cv[j]);
                 }
             }
             ++ck;
@@ -386,28 +457,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) {
             const int64_t q = tile * kNT + n0 + j;
-            if (q < io.n_inst) {
-                io.x_out[q * s + k] = (double)x[j] + (double)cx[j];
-                io.v_out[q * s + k] = (double)v[j] + (double)cv[j];
+            if (q < src.count()) {
+                src.store(q, k, x[j], v[j], cx[j], cv[j]);
+                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[n0 + j] = 1;
             }
         }
     }
     if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (tid < kNT) {
+        const int64_t q = tile * kNT + tid;
+        if (q < src.count()) {
+            if (!ok) src.flag(q, CHO_ETIMEOUT);
+            else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
+            if (rank == 0) src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
+        }
+    }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT));
     if (CS > 1) cluster_sync();   // the peer may still write into this CTA's shared memory until here
 }
 
-template <int PA, int PB, int CS>
-cudaError_t launch_tc(const DenseSys& sys, const BatchIO& io, cudaStream_t st)
+template <int PA, int PB, int CS, class Src>
+cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
-    auto kern = rk4_dense_tc_kernel<PA, PB, CS>;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (io.n_inst + kNT - 1) / kNT;
+    const int64_t tiles = (n_inst + kNT - 1) / kNT;
     if (tiles <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(tiles * CS), 1, 1);
@@ -421,7 +500,25 @@ cudaError_t launch_tc(const DenseSys& sys, const BatchIO& io, cudaStream_t st)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, sys, io);
+    return cudaLaunchKernelEx(&cfg, kern, sys, src);
+}
+
+template <class Src>
+cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int prec, cudaStream_t st)
+{
+    if (n_inst == 0) return cudaSuccess;
+    if (!sys.Bbf || sys.s_tc == 0) return cudaErrorNotSupported;
+    const bool two = sys.s_tc == 256;
+    switch (prec) {
+        case CHO_DENSE_BF16X3:
+            return two ? launch_tc<2, 2, 2>(sys, src, n_inst, st) : launch_tc<2, 2, 1>(sys, src, n_inst, st);
+        case CHO_DENSE_BF16X5:
+            return two ? launch_tc<3, 2, 2>(sys, src, n_inst, st) : launch_tc<3, 2, 1>(sys, src, n_inst, st);
+        case CHO_DENSE_BF16X6:
+            if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
+            return launch_tc<3, 3, 1>(sys, src, n_inst, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Round to the nearest BF16 (ties to even) of an FP32 value, as bits.
@@ -446,17 +543,12 @@ float bf16_value(uint16_t b)
 
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st)
 {
-    if (io.n_inst == 0) return cudaSuccess;
-    if (!sys.Bbf || sys.s_tc == 0) return cudaErrorNotSupported;
-    const bool two = sys.s_tc == 256;
-    switch (prec) {
-        case CHO_DENSE_BF16X3: return two ? launch_tc<2, 2, 2>(sys, io, st) : launch_tc<2, 2, 1>(sys, io, st);
-        case CHO_DENSE_BF16X5: return two ? launch_tc<3, 2, 2>(sys, io, st) : launch_tc<3, 2, 1>(sys, io, st);
-        case CHO_DENSE_BF16X6:
-            if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
-            return launch_tc<3, 3, 1>(sys, io, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return dispatch_tc(sys, TcBatchSrc{io, sys.s}, io.n_inst, prec, st);
+}
+
+cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int prec, cudaStream_t st)
+{
+    return dispatch_tc(sys, TcSlotSrc{io, sys.s}, io.n_inst, prec, st);
 }
 
 // BF16 pieces of B for the tensor-core kernel, laid out per CTA rank as the exact

@@ -139,6 +139,7 @@ public:
         cap_ = want;
         return p_;
     }
+    T* ptr() const { return p_; }
     void release()
     {
         if (p_) cudaFreeHost(p_);
@@ -193,6 +194,28 @@ private:
 
 }  // namespace
 
+// Requests that run in one kernel launch: same kernel family, size class and
+// precision (and, for dense systems, the same shared B).
+using GroupKey = std::tuple<int, int, int, cho_system_impl*>;
+
+struct Group {
+    GroupKey key;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    int64_t chunk = 0;
+    std::vector<Req*> members;      // resident
+    std::vector<Req*> incoming;     // admitted, state not uploaded yet
+    std::vector<Req*> launched;     // advanced by the launch in flight
+    PinnedBuf<int32_t> h_ids;
+    DevBuf<int32_t> d_ids;
+    DevBuf<int32_t> d_st;
+    PinnedBuf<int32_t> h_st;
+    PinnedBuf<unsigned char> h_up;
+    PinnedBuf<unsigned char> h_down;
+    PinnedBuf<SlotDesc> h_desc;
+};
+
 struct ServeEngine {
     cho_ctx* ctx = nullptr;
     std::thread worker;
@@ -202,111 +225,297 @@ struct ServeEngine {
     bool failed = false;
     std::deque<Req*> queue[3];
     std::unordered_map<uint64_t, Req*> reqs;
-    std::vector<Req*> resident;
+    int64_t n_resident = 0;
     uint64_t next_ticket = 1;
     int64_t resident_bytes = 0;
     int64_t completed = 0;
     int64_t n_queued = 0;
     // device side (worker thread only)
-    cudaStream_t st = nullptr;
     int32_t slot_cap = 0;
     std::vector<int32_t> free_slots;
-    DevBuf<SlotDesc> d_slots;
+    DevBuf<SlotDesc> d_slots;       // slot table, allocated once (kernels in flight read it)
     DevBuf<int32_t> d_status;
-    DevBuf<int32_t> d_ids;
-    PinnedBuf<SlotDesc> h_slot_stage;
-    PinnedBuf<int32_t> h_ids;
-    PinnedBuf<int32_t> h_status;
-    PinnedBuf<unsigned char> h_up;
-    PinnedBuf<unsigned char> h_down;
     BlockPool pool;
+    std::map<GroupKey, Group*> groups;
 
     void run();
-    bool grow_slots(int32_t need, cudaError_t* err);
+    Group* group_for(Req* r, cudaError_t* e);
+    cudaError_t launch(Group* g);
+    void retire(Group* g);          // caller holds mu
     void fail_all(cho_status st_code);
+    void release(Req* r);           // caller holds mu
 };
-
-bool ServeEngine::grow_slots(int32_t need, cudaError_t* err)
-{
-    *err = cudaSuccess;
-    if (need <= slot_cap) return true;
-    int32_t cap = std::max<int32_t>(1024, slot_cap);
-    while (cap < need) cap *= 2;
-    cap = std::min<int32_t>(cap, std::max<int32_t>(ctx->cfg.max_slots, need));
-    // preserve the descriptors of resident slots
-    SlotDesc* old = d_slots.ptr();
-    int32_t* olds = d_status.ptr();
-    DevBuf<SlotDesc> ns;
-    DevBuf<int32_t> nst;
-    if (!ns.get((size_t)cap, err) || !nst.get((size_t)cap, err)) return false;
-    if (old && slot_cap > 0) {
-        *err = cudaMemcpyAsync(ns.ptr(), old, sizeof(SlotDesc) * slot_cap, cudaMemcpyDeviceToDevice, st);
-        if (*err == cudaSuccess)
-            *err = cudaMemcpyAsync(nst.ptr(), olds, sizeof(int32_t) * slot_cap, cudaMemcpyDeviceToDevice, st);
-        if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
-        if (*err != cudaSuccess) return false;
-    }
-    d_slots.swap(ns);     // the old buffers are freed when ns/nst leave scope
-    d_status.swap(nst);
-    for (int32_t i = cap - 1; i >= slot_cap; --i) free_slots.push_back(i);
-    slot_cap = cap;
-    return true;
-}
 
 void ServeEngine::fail_all(cho_status code)
 {
     // caller holds mu
     failed = true;
-    for (Req* r : resident) {
-        r->state = RQ_DONE;
-        r->status = code;
-        r->t_done = now_s();
+    const double t = now_s();
+    for (auto& kv : groups) {
+        Group* g = kv.second;
+        for (auto* list : {&g->members, &g->incoming})
+            for (Req* r : *list) {
+                r->state = RQ_DONE;
+                r->status = code;
+                r->t_done = t;
+            }
+        g->members.clear();
+        g->incoming.clear();
+        g->launched.clear();
     }
-    resident.clear();
     for (auto& q : queue) {
         for (Req* r : q) {
             r->state = RQ_DONE;
             r->status = code;
-            r->t_done = now_s();
+            r->t_done = t;
         }
         q.clear();
     }
     n_queued = 0;
+    n_resident = 0;
     cv.notify_all();
+}
+
+void ServeEngine::release(Req* r)
+{
+    resident_bytes -= (int64_t)r->bytes;
+    if (r->block) pool.put(r->bytes, r->block);
+    r->block = nullptr;
+    if (r->slot >= 0) free_slots.push_back(r->slot);
+    r->slot = -1;
+    --n_resident;
+    ++completed;
+}
+
+static int64_t group_chunk(const cho_ctx* ctx) { return ctx->cfg.chunk_steps; }
+
+Group* ServeEngine::group_for(Req* r, cudaError_t* e)
+{
+    *e = cudaSuccess;
+    const cho_system_impl* sys = r->sys;
+    const int size = sys->path == PATH_SMALL ? sys->S : (sys->path == PATH_CHAIN ? chain_dofs_per_thread(sys->s) : sys->s);
+    GroupKey key(sys->path, size, r->prec, sys->path == PATH_DENSE ? r->sys : nullptr);
+    auto it = groups.find(key);
+    if (it != groups.end()) return it->second;
+    Group* g = new (std::nothrow) Group();
+    if (!g) {
+        *e = cudaErrorMemoryAllocation;
+        return nullptr;
+    }
+    g->key = key;
+    g->chunk = group_chunk(ctx);
+    *e = cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking);
+    if (*e == cudaSuccess) *e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (*e != cudaSuccess) {
+        if (g->st) cudaStreamDestroy(g->st);
+        delete g;
+        return nullptr;
+    }
+    groups[key] = g;
+    return g;
+}
+
+// Upload the group's new requests, advance every member by one chunk, and queue the
+// read-back of status words and of the states that finish in this chunk.
+cudaError_t ServeEngine::launch(Group* g)
+{
+    cudaError_t e = cudaSuccess;
+    const int64_t L = g->chunk;
+    size_t up_bytes = 0;
+    for (Req* r : g->incoming) up_bytes += r->bytes;
+    unsigned char* up = g->h_up.get(std::max<size_t>(up_bytes, 1), &e);
+    SlotDesc* hd = e == cudaSuccess ? g->h_desc.get(std::max<size_t>(g->incoming.size(), 1), &e) : nullptr;
+    size_t off = 0;
+    for (size_t k = 0; k < g->incoming.size() && e == cudaSuccess; ++k) {
+        Req* r = g->incoming[k];
+        const cho_system_impl* sys = r->sys;
+        const int n = sys->path == PATH_SMALL ? sys->S : sys->s;
+        const int s = sys->s;
+        unsigned char* dst = up + off;
+        if (fp64_prec(r->prec)) {
+            double* d = (double*)dst;
+            for (int i = 0; i < n; ++i) {
+                d[i] = i < s ? r->x0[i] : 0.0;
+                d[n + i] = i < s ? r->v0[i] : 0.0;
+            }
+        } else {
+            float* f = (float*)dst;
+            for (int i = 0; i < n; ++i) {
+                const double xd = i < s ? r->x0[i] : 0.0, vd = i < s ? r->v0[i] : 0.0;
+                f[i] = (float)xd;
+                f[n + i] = (float)vd;
+                f[2 * n + i] = (float)(xd - (double)f[i]);          // compensation: x + e
+                f[3 * n + i] = (float)(vd - (double)f[n + i]);
+            }
+        }
+        e = cudaMemcpyAsync(r->block, dst, state_bytes(sys, r->prec), cudaMemcpyHostToDevice, g->st);
+        off += r->bytes;
+        SlotDesc sd{};
+        if (sys->path == PATH_SMALL) {
+            const size_t SS = (size_t)sys->S * sys->S;
+            sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * SS)
+                                          : (const void*)(sys->d_B32 + r->set * 2 * SS);
+        } else if (sys->path == PATH_CHAIN) {
+            sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * 2 * s)
+                                          : (const void*)(sys->d_B32 + r->set * 4 * s);
+        }
+        sd.state = r->block;
+        sd.h = r->h;
+        sd.remaining = r->n_steps;
+        sd.s = s;
+        hd[k] = sd;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_slots.ptr() + r->slot, &hd[k], sizeof(SlotDesc), cudaMemcpyHostToDevice, g->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_status.ptr() + r->slot, 0, sizeof(int32_t), g->st);
+    }
+    if (e != cudaSuccess) return e;
+    g->members.insert(g->members.end(), g->incoming.begin(), g->incoming.end());
+    g->incoming.clear();
+    g->launched = g->members;
+    const size_t n_ids = g->launched.size();
+    if (n_ids == 0) return cudaSuccess;
+    int32_t* ids = g->h_ids.get(n_ids, &e);
+    if (e == cudaSuccess) g->d_ids.get(n_ids, &e);
+    if (e == cudaSuccess) g->d_st.get(n_ids, &e);
+    int32_t* hst = e == cudaSuccess ? g->h_st.get(n_ids, &e) : nullptr;
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i < n_ids; ++i) ids[i] = g->launched[i]->slot;
+    e = cudaMemcpyAsync(g->d_ids.ptr(), ids, n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, g->st);
+    if (e != cudaSuccess) return e;
+    const int path = std::get<0>(g->key), size = std::get<1>(g->key), prec = std::get<2>(g->key);
+    const bool f64 = fp64_prec(prec);
+    SlotIO io{(int64_t)n_ids, g->d_ids.ptr(), d_slots.ptr(), d_status.ptr(), L};
+    if (path == PATH_SMALL) {
+        e = launch_rk4_small_slots(size, io, f64, g->st);
+    } else if (path == PATH_CHAIN) {
+        int s_max = 0;
+        for (Req* r : g->launched) s_max = std::max(s_max, r->sys->s);
+        e = launch_rk4_chain_slots(s_max, io, f64, g->st);
+    } else {
+        cho_system_impl* sys = std::get<3>(g->key);
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
+        if (prec == CHO_DENSE_BF16X3 || prec == CHO_DENSE_BF16X5 || prec == CHO_DENSE_BF16X6)
+            e = launch_rk4_dense_tc_slots(ds, io, prec, g->st);
+        else
+            e = launch_rk4_dense_slots(ds, io, f64, g->st);
+    }
+    if (e == cudaSuccess) e = launch_gather_status(g->d_ids.ptr(), d_status.ptr(), g->d_st.ptr(), (int64_t)n_ids, g->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hst, g->d_st.ptr(), n_ids * sizeof(int32_t), cudaMemcpyDeviceToHost, g->st);
+    size_t down_bytes = 0;
+    for (Req* r : g->launched)
+        if (r->remaining <= L) down_bytes += r->bytes;
+    unsigned char* down = e == cudaSuccess ? g->h_down.get(std::max<size_t>(down_bytes, 1), &e) : nullptr;
+    size_t doff = 0;
+    for (Req* r : g->launched) {
+        if (e != cudaSuccess) break;
+        r->reading_back = r->remaining <= L;
+        if (r->reading_back) {
+            r->readback_off = doff;
+            e = cudaMemcpyAsync(down + doff, r->block, state_bytes(r->sys, r->prec), cudaMemcpyDeviceToHost, g->st);
+            doff += r->bytes;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev, g->st);
+    if (e == cudaSuccess) g->busy = true;
+    return e;
+}
+
+// The group's launch has finished: book the steps, hand out finished results,
+// return their slots and memory.  Caller holds mu.
+void ServeEngine::retire(Group* g)
+{
+    const double t = now_s();
+    const int64_t L = g->chunk;
+    const int32_t* hst = g->h_st.ptr();
+    const unsigned char* down = g->h_down.ptr();
+    for (size_t i = 0; i < g->launched.size(); ++i) {
+        Req* r = g->launched[i];
+        r->remaining -= std::min<int64_t>(L, r->remaining);
+        const int32_t code = hst ? hst[i] : 0;
+        if (code != 0) {
+            r->status = (cho_status)code;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        } else if (r->remaining == 0 && r->reading_back) {
+            const cho_system_impl* sys = r->sys;
+            const int n = sys->path == PATH_SMALL ? sys->S : sys->s;
+            const int s = sys->s;
+            r->x.resize(s);
+            r->v.resize(s);
+            const unsigned char* src = down + r->readback_off;
+            if (fp64_prec(r->prec)) {
+                const double* d = (const double*)src;
+                for (int k = 0; k < s; ++k) {
+                    r->x[k] = d[k];
+                    r->v[k] = d[n + k];
+                }
+            } else {
+                const float* f = (const float*)src;
+                for (int k = 0; k < s; ++k) {
+                    r->x[k] = (double)f[k] + (double)f[2 * n + k];
+                    r->v[k] = (double)f[n + k] + (double)f[3 * n + k];
+                }
+            }
+            r->status = CHO_OK;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        } else if (r->cancel) {
+            r->status = CHO_ECANCELLED;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        }
+    }
+    auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
+        if (r->state != RQ_DONE) return false;
+        release(r);
+        return true;
+    });
+    g->members.erase(it, g->members.end());
+    g->launched.clear();
+    g->busy = false;
 }
 
 void ServeEngine::run()
 {
-    DeviceGuard g(ctx->device);
-    const int64_t L = ctx->cfg.chunk_steps;
-    std::vector<Req*> admitted, batch, finished;
-    // group key: (path, size, fp64, system for dense)
-    using Key = std::tuple<int, int, int, cho_system_impl*>;
-    std::map<Key, std::vector<int32_t>> groups;
+    DeviceGuard dg(ctx->device);
+    std::vector<Group*> to_launch;
     while (true) {
-        cudaError_t e = cudaSuccess;
-        admitted.clear();
+        bool progressed = false;
+        to_launch.clear();
         {
             std::unique_lock<std::mutex> lk(mu);
-            while (!stop && resident.empty() && n_queued == 0) cv.wait(lk);
+            while (!stop && n_resident == 0 && n_queued == 0) cv.wait(lk);
             if (stop) break;
-            // drop cancelled requests
-            for (Req* r : resident)
-                if (r->cancel) {
+            // finished launches
+            for (auto& kv : groups) {
+                Group* g = kv.second;
+                if (!g->busy) continue;
+                const cudaError_t q = cudaEventQuery(g->ev);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) {
+                    fail_all(CHO_ECUDA);
+                    return;
+                }
+                retire(g);
+                progressed = true;
+            }
+            // cancelled requests of idle groups leave before their next launch
+            for (auto& kv : groups) {
+                Group* g = kv.second;
+                if (g->busy) continue;
+                auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
+                    if (!r->cancel) return false;
                     r->state = RQ_DONE;
                     r->status = CHO_ECANCELLED;
                     r->t_done = now_s();
-                }
-            auto it = std::remove_if(resident.begin(), resident.end(), [&](Req* r) {
-                if (r->state != RQ_DONE) return false;
-                resident_bytes -= (int64_t)r->bytes;
-                pool.put(r->bytes, r->block);
-                free_slots.push_back(r->slot);
-                ++completed;
-                return true;
-            });
-            resident.erase(it, resident.end());
-            // admission: strict fixed priority, FIFO within a class
+                    release(r);
+                    return true;
+                });
+                if (it != g->members.end()) progressed = true;
+                g->members.erase(it, g->members.end());
+            }
+            // admission: strict fixed priority, FIFO within a class, slots and budget permitting
             const int64_t budget = ctx->cfg.budget_bytes;
             for (int p = 0; p < 3; ++p) {
                 bool blocked = false;
@@ -321,209 +530,48 @@ void ServeEngine::run()
                         ++completed;
                         continue;
                     }
-                    if ((int64_t)resident.size() + (int64_t)admitted.size() >= ctx->cfg.max_slots ||
-                        resident_bytes + (int64_t)r->bytes > budget) {
+                    if (free_slots.empty() || resident_bytes + (int64_t)r->bytes > budget) {
                         blocked = true;
                         break;
                     }
+                    cudaError_t e;
+                    Group* g = group_for(r, &e);
+                    void* block = g ? pool.get(r->bytes, &e) : nullptr;
+                    if (!block) {
+                        fail_all(e == cudaErrorMemoryAllocation ? CHO_ENOMEM : CHO_ECUDA);
+                        return;
+                    }
                     queue[p].pop_front();
                     --n_queued;
+                    r->block = block;
+                    r->slot = free_slots.back();
+                    free_slots.pop_back();
                     resident_bytes += (int64_t)r->bytes;
-                    admitted.push_back(r);
+                    ++n_resident;
+                    r->state = RQ_RESIDENT;
+                    r->remaining = r->n_steps;
+                    r->t_admit = now_s();
+                    g->incoming.push_back(r);
+                    progressed = true;
                 }
                 if (blocked) break;
             }
-            cv.notify_all();
+            for (auto& kv : groups)
+                if (!kv.second->busy && (!kv.second->members.empty() || !kv.second->incoming.empty()))
+                    to_launch.push_back(kv.second);
+            if (progressed) cv.notify_all();
         }
-        // ---- device work of this chunk (no lock held) ----
-        size_t up_bytes = 0;
-        for (Req* r : admitted) up_bytes += r->bytes;
-        unsigned char* up = h_up.get(std::max<size_t>(up_bytes, 1), &e);
-        if (e == cudaSuccess) grow_slots((int32_t)(resident.size() + admitted.size()), &e);
-        SlotDesc* hs = e == cudaSuccess ? h_slot_stage.get(std::max<size_t>(admitted.size(), 1), &e) : nullptr;
-        size_t off = 0;
-        for (size_t k = 0; k < admitted.size() && e == cudaSuccess; ++k) {
-            Req* r = admitted[k];
-            r->block = pool.get(r->bytes, &e);
-            if (!r->block) break;
-            r->slot = free_slots.back();
-            free_slots.pop_back();
-            // initial state in kernel precision and layout
-            const cho_system_impl* sys = r->sys;
-            const int n = sys->path == PATH_SMALL ? sys->S : sys->s;
-            const int s = sys->s;
-            unsigned char* dst = up + off;
-            if (fp64_prec(r->prec)) {
-                double* d = (double*)dst;
-                for (int i = 0; i < n; ++i) {
-                    d[i] = i < s ? r->x0[i] : 0.0;
-                    d[n + i] = i < s ? r->v0[i] : 0.0;
-                }
-            } else {
-                float* f = (float*)dst;
-                for (int i = 0; i < n; ++i) {
-                    const double xd = i < s ? r->x0[i] : 0.0, vd = i < s ? r->v0[i] : 0.0;
-                    f[i] = (float)xd;
-                    f[n + i] = (float)vd;
-                    f[2 * n + i] = (float)(xd - (double)f[i]);          // compensation: x + e
-                    f[3 * n + i] = (float)(vd - (double)f[n + i]);
-                }
-            }
-            e = cudaMemcpyAsync(r->block, dst, state_bytes(sys, r->prec), cudaMemcpyHostToDevice, st);
-            off += r->bytes;
-            if (e != cudaSuccess) break;
-            SlotDesc sd{};
-            if (sys->path == PATH_SMALL) {
-                const size_t SS = (size_t)sys->S * sys->S;
-                sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * SS)
-                                              : (const void*)(sys->d_B32 + r->set * 2 * SS);
-            } else if (sys->path == PATH_CHAIN) {
-                sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * 2 * s)
-                                              : (const void*)(sys->d_B32 + r->set * 4 * s);
-            } else {
-                sd.coef = nullptr;
-            }
-            sd.state = r->block;
-            sd.h = r->h;
-            sd.remaining = r->n_steps;
-            sd.s = s;
-            hs[k] = sd;
-            e = cudaMemcpyAsync(d_slots.ptr() + r->slot, &hs[k], sizeof(SlotDesc), cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_status.ptr() + r->slot, 0, sizeof(int32_t), st);
-            if (e != cudaSuccess) break;
-        }
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            const double t = now_s();
-            for (Req* r : admitted) {
-                r->state = RQ_RESIDENT;
-                r->remaining = r->n_steps;
-                r->t_admit = t;
-                resident.push_back(r);
-            }
+        // launches outside the lock (only this thread touches the groups' device side)
+        for (Group* g : to_launch) {
+            const cudaError_t e = launch(g);
             if (e != cudaSuccess) {
+                std::lock_guard<std::mutex> lk(mu);
                 fail_all(CHO_ECUDA);
                 return;
             }
-            batch.assign(resident.begin(), resident.end());
+            progressed = true;
         }
-        // launches: one per kernel group
-        groups.clear();
-        int32_t max_slot = 0;
-        for (Req* r : batch) {
-            const cho_system_impl* sys = r->sys;
-            int size = sys->path == PATH_SMALL ? sys->S : (sys->path == PATH_CHAIN ? chain_dofs_per_thread(sys->s) : sys->s_pad);
-            cho_system_impl* key_sys = sys->path == PATH_DENSE ? r->sys : nullptr;
-            groups[Key(sys->path, size, fp64_prec(r->prec) ? 1 : 0, key_sys)].push_back(r->slot);
-            max_slot = std::max(max_slot, r->slot + 1);
-        }
-        size_t n_ids = 0;
-        for (auto& kv : groups) n_ids += kv.second.size();
-        int32_t* ids = e == cudaSuccess ? h_ids.get(std::max<size_t>(n_ids, 1), &e) : nullptr;
-        if (e == cudaSuccess) d_ids.get(std::max<size_t>(n_ids, 1), &e);
-        if (e == cudaSuccess && n_ids > 0) {
-            size_t o = 0;
-            for (auto& kv : groups) {
-                std::memcpy(ids + o, kv.second.data(), kv.second.size() * sizeof(int32_t));
-                o += kv.second.size();
-            }
-            e = cudaMemcpyAsync(d_ids.ptr(), ids, n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-            o = 0;
-            for (auto& kv : groups) {
-                if (e != cudaSuccess) break;
-                const int path = std::get<0>(kv.first), size = std::get<1>(kv.first);
-                const bool f64 = std::get<2>(kv.first) != 0;
-                SlotIO io{(int64_t)kv.second.size(), d_ids.ptr() + o, d_slots.ptr(), d_status.ptr(), L};
-                if (path == PATH_SMALL) {
-                    e = launch_rk4_small_slots(size, io, f64, st);
-                } else if (path == PATH_CHAIN) {
-                    int s_max = 0;
-                    for (Req* r : batch)
-                        if (r->sys->path == PATH_CHAIN && chain_dofs_per_thread(r->sys->s) == size)
-                            s_max = std::max(s_max, r->sys->s);
-                    e = launch_rk4_chain_slots(s_max, io, f64, st);
-                } else {
-                    cho_system_impl* sys = std::get<3>(kv.first);
-                    DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
-                    e = launch_rk4_dense_slots(ds, io, f64, st);
-                }
-                o += kv.second.size();
-            }
-        }
-        // read back: per-slot status, and the state of requests that finish in this chunk
-        int32_t* hst = nullptr;
-        finished.clear();
-        if (e == cudaSuccess && max_slot > 0) {
-            hst = h_status.get((size_t)max_slot, &e);
-            if (hst) e = cudaMemcpyAsync(hst, d_status.ptr(), sizeof(int32_t) * max_slot, cudaMemcpyDeviceToHost, st);
-        }
-        size_t down_bytes = 0;
-        for (Req* r : batch)
-            if (r->remaining <= L) down_bytes += r->bytes;
-        unsigned char* down = e == cudaSuccess ? h_down.get(std::max<size_t>(down_bytes, 1), &e) : nullptr;
-        size_t doff = 0;
-        for (Req* r : batch) {
-            if (e != cudaSuccess) break;
-            if (r->remaining <= L) {
-                r->readback_off = doff;
-                r->reading_back = true;
-                e = cudaMemcpyAsync(down + doff, r->block, state_bytes(r->sys, r->prec), cudaMemcpyDeviceToHost, st);
-                doff += r->bytes;
-                finished.push_back(r);
-            }
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        // ---- retire ----
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            if (e != cudaSuccess) {
-                fail_all(CHO_ECUDA);
-                return;
-            }
-            const double t = now_s();
-            for (Req* r : batch) {
-                r->remaining -= std::min<int64_t>(L, r->remaining);
-                const bool bad = hst && hst[r->slot] != 0;
-                if (r->remaining == 0 || bad) {
-                    if (bad) {
-                        r->status = CHO_ENONFINITE;
-                    } else {
-                        const cho_system_impl* sys = r->sys;
-                        const int n = sys->path == PATH_SMALL ? sys->S : sys->s;
-                        const int s = sys->s;
-                        r->x.resize(s);
-                        r->v.resize(s);
-                        const unsigned char* src = down + r->readback_off;
-                        if (fp64_prec(r->prec)) {
-                            const double* d = (const double*)src;
-                            for (int i = 0; i < s; ++i) {
-                                r->x[i] = d[i];
-                                r->v[i] = d[n + i];
-                            }
-                        } else {
-                            const float* f = (const float*)src;
-                            for (int i = 0; i < s; ++i) {
-                                r->x[i] = (double)f[i] + (double)f[2 * n + i];
-                                r->v[i] = (double)f[n + i] + (double)f[3 * n + i];
-                            }
-                        }
-                        r->status = CHO_OK;
-                    }
-                    r->state = RQ_DONE;
-                    r->t_done = t;
-                }
-            }
-            auto it = std::remove_if(resident.begin(), resident.end(), [&](Req* r) {
-                if (r->state != RQ_DONE) return false;
-                resident_bytes -= (int64_t)r->bytes;
-                pool.put(r->bytes, r->block);
-                free_slots.push_back(r->slot);
-                ++completed;
-                return true;
-            });
-            resident.erase(it, resident.end());
-            cv.notify_all();
-        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
@@ -538,12 +586,16 @@ static ServeEngine* engine(cho_ctx* ctx, cho_status* err)
     }
     en->ctx = ctx;
     DeviceGuard g(ctx->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&en->st, cudaStreamNonBlocking);
+    cudaError_t e = cudaSuccess;
+    en->slot_cap = ctx->cfg.max_slots;
+    en->d_slots.get((size_t)en->slot_cap, &e);
+    if (e == cudaSuccess) en->d_status.get((size_t)en->slot_cap, &e);
     if (e != cudaSuccess) {
         delete en;
-        *err = fail(CHO_ECUDA, "cho_submit: cudaStreamCreate: %s", cudaGetErrorString(e));
+        *err = fail(CHO_ENOMEM, "cho_submit: slot table of %d slots: %s", ctx->cfg.max_slots, cudaGetErrorString(e));
         return nullptr;
     }
+    for (int32_t i = en->slot_cap - 1; i >= 0; --i) en->free_slots.push_back(i);
     en->worker = std::thread([en] { en->run(); });
     ctx->serve = en;
     return en;
@@ -566,21 +618,19 @@ void serve_stop(cho_ctx* ctx)
     if (en->worker.joinable()) en->worker.join();
     {
         DeviceGuard g(ctx->device);
-        if (en->st) {
-            cudaStreamSynchronize(en->st);
-            cudaStreamDestroy(en->st);
+        for (auto& kv : en->groups) {
+            Group* gr = kv.second;
+            cudaStreamSynchronize(gr->st);
+            cudaEventDestroy(gr->ev);
+            cudaStreamDestroy(gr->st);
+            delete gr;
         }
+        en->groups.clear();
         for (auto& kv : en->reqs) delete kv.second;
         en->reqs.clear();
         en->pool.release();
         en->d_slots.release();
         en->d_status.release();
-        en->d_ids.release();
-        en->h_slot_stage.release();
-        en->h_ids.release();
-        en->h_status.release();
-        en->h_up.release();
-        en->h_down.release();
     }
     delete en;
 }
@@ -600,8 +650,11 @@ extern "C" cho_status cho_submit(cho_ctx* ctx, const cho_request* rq, uint64_t* 
     if (rq->n_steps < 0) return fail(CHO_EINVAL, "cho_submit: n_steps < 0");
     if (rq->priority < 0 || rq->priority > 2) return fail(CHO_EINVAL, "cho_submit: priority must be 0, 1 or 2");
     const bool dense_simt = rq->prec == CHO_DENSE_FP32_SIMT && sys->kind == CHO_DENSE;
-    if (rq->prec != CHO_FP64 && rq->prec != CHO_FP32_KAHAN && !dense_simt)
-        return fail(CHO_EINVAL, "cho_submit: serving runs CHO_FP64 or CHO_FP32_KAHAN");
+    const bool bf16 = rq->prec == CHO_DENSE_BF16X3 || rq->prec == CHO_DENSE_BF16X5 || rq->prec == CHO_DENSE_BF16X6;
+    if (bf16 && (sys->path != PATH_DENSE || sys->s_tc == 0 || (rq->prec == CHO_DENSE_BF16X6 && sys->s_tc > 128)))
+        return fail(CHO_EINVAL, "cho_submit: BF16 modes need a shared dense system with 32 < s <= 256 (x6: s <= 128)");
+    if (rq->prec != CHO_FP64 && rq->prec != CHO_FP32_KAHAN && !dense_simt && !bf16)
+        return fail(CHO_EINVAL, "cho_submit: unknown or unsupported precision %d", rq->prec);
     if (!(rq->h > 0.0) || !std::isfinite(rq->h)) return fail(CHO_EINVAL, "cho_submit: h must be finite and > 0");
     const double w = sys->omegas[(size_t)rq->sys_index];
     if (w * rq->h > 2.0 * std::sqrt(2.0))
@@ -708,7 +761,7 @@ extern "C" cho_status cho_serve_stats(cho_ctx* ctx, int64_t* queued, int64_t* re
     if (en) {
         std::lock_guard<std::mutex> lk(en->mu);
         q = en->n_queued;
-        r = (int64_t)en->resident.size();
+        r = en->n_resident;
         c = en->completed;
         b = en->resident_bytes;
     }

@@ -283,3 +283,36 @@ def test_request_errors_and_cancel():
     finally:
         mix.close()
         cho.cho_shutdown(ctx)
+
+
+def test_dense_requests_on_tensor_cores():
+    """Dense requests in a BF16 mode run on the tensor-core kernel in slot form: same bits as the
+    batch call, within the bf16x5 tolerance of the oracle, and the same alone and in a mix."""
+    ctx = cho.cho_init(0, chunk_steps=300)
+    try:
+        systems = []
+        for s in (64, 200):
+            dn = inputs.dense_group(s=s, n_inst=1, n_steps=1)
+            systems.append((cho.cho_create_system(ctx, "dense", M=dn["M"], K=dn["K"]), dn, s))
+        rng = np.random.default_rng(9)
+        reqs = []
+        for k in range(40):
+            sys_, dn, s = systems[k % 2]
+            reqs.append(dict(kind="dense", sys=sys_, cfg=dn, s=s, idx=0, x0=rng.uniform(-1, 1, s), v0=np.zeros(s),
+                             h=float(dn["h"][0]), n=int(rng.integers(200, 1500)), prec="bf16x5"))
+        tickets = [cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], r["n"], "bf16x5", k % 3) for k, r in enumerate(reqs)]
+        res = wait_all(ctx, tickets, [r["s"] for r in reqs])
+        for t, r in list(zip(tickets, reqs))[:6]:
+            b = batch_result(ctx, r)
+            assert np.array_equal(res[t]["x"], b["x"][0])
+            ref = reference(r)
+            assert relerr(res[t]["x"], ref["x"][0]) < 5 * TOL_FP32
+        # alone
+        r = reqs[3]
+        t = cho.cho_submit(ctx, r["sys"], r["x0"], r["v0"], r["h"], r["n"], "bf16x5", 0)
+        alone = wait_all(ctx, [t], [r["s"]])[t]
+        assert np.array_equal(alone["x"], res[tickets[3]]["x"])
+        for sys_, _, _ in systems:
+            cho.cho_destroy_system(sys_)
+    finally:
+        cho.cho_shutdown(ctx)
