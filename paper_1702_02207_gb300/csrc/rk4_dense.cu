@@ -7,9 +7,11 @@
 // Thread (r, n) holds rows [r RI, r RI + RI) of instance n: its state, stage
 // values and accumulators stay in registers.  Per stage the threads publish
 // their stage displacements to shared memory (double-buffered, one barrier
-// per stage), then each thread forms its RI rows of B Xs column by column,
-// reading B transposed from global memory (L1/L2 resident, four rows per
-// vector load) and Xs from shared memory.
+// per stage), then each thread forms its RI rows of B Xs column by column.
+// B (transposed, L2-resident) is streamed through shared memory in chunks of
+// kJC columns with cp.async, double-buffered so that the copy of the next
+// chunk overlaps the products of the current one; each thread reads its rows
+// of a column with vector shared-memory loads.
 //
 // The tensor-core split-BF16 variant lives in rk4_dense_tc.cu.
 #include "cho_internal.h"
@@ -23,6 +25,16 @@ namespace cho {
 namespace {
 
 constexpr int kDenseThreads = 256;
+constexpr int kJC = 8;               // columns of B^T per shared-memory chunk
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Batch form: FP64 x0/v0 in, FP64 outputs, shared step count, checkpoints.
 template <bool F64>
@@ -107,8 +119,10 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
     using Real = std::conditional_t<F64, double, float>;
     constexpr int RG = kDenseThreads / NT;          // row groups
     constexpr int SP = RG * RI;                     // padded size handled by this instantiation
+    constexpr int NB = F64 ? 1 : 2;                 // B pieces: FP64, or FP32 hi and lo
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* xsh = (Real*)smem_raw;                    // [2][SP][NT]
+    Real* bsh = xsh + 2 * SP * NT;                  // [2 buffers][NB][kJC][SP]
     __shared__ long long max_steps;
     __shared__ int any_bad[NT];
 
@@ -119,9 +133,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
     const int64_t q = (int64_t)blockIdx.x * NT + n;
     const bool live = q < src.count();
     const int s = sys.s;
-    const int ld = sys.s_pad;                       // leading dimension of the transposed B
-    const Real* Bt = F64 ? (const Real*)sys.B64 : (const Real*)sys.B32;   // [SP][SP] = B^T
-    const float* Btl = sys.B32 + (size_t)ld * ld;                          // lo part (FP32 only)
+    const Real* Bt = F64 ? (const Real*)sys.B64 : (const Real*)sys.B32;   // [SP][SP] = B^T (then lo, FP32)
 
     // every instance of the tile runs its own step count; the tile loops to the largest
     const int64_t my_steps = live ? src.steps(q) : 0;
@@ -146,37 +158,63 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
         }
     }
 
+    // copy columns [c kJC, c kJC + kJC) of B^T (each piece) into chunk buffer b
+    constexpr int CHUNK = kJC * SP;                 // elements per piece per chunk
+    constexpr int VEC = 16 / sizeof(Real);
+    const int n_chunks = (s + kJC - 1) / kJC;
+    auto load_chunk = [&](int c, int b) {
+#pragma unroll
+        for (int pc = 0; pc < NB; ++pc) {
+            const Real* src_c = Bt + (size_t)pc * SP * SP + (size_t)c * CHUNK;
+            Real* dst = bsh + ((size_t)b * NB + pc) * CHUNK;
+            for (int e = t * VEC; e < CHUNK; e += kDenseThreads * VEC) cp_async16(dst + e, src_c + e);
+        }
+        cp_async_commit();
+    };
+
     int buf = 0;
     auto accel = [&](const Real (&xs)[RI], Real (&acc)[RI]) {
         Real* X = xsh + buf * SP * NT;
 #pragma unroll
         for (int k = 0; k < RI; ++k) X[(row0 + k) * NT + n] = xs[k];
-        __syncthreads();
         Real t0[RI];
 #pragma unroll
         for (int k = 0; k < RI; ++k) t0[k] = 0;
-        for (int j = 0; j < s; ++j) {                // columns beyond s are zero
-            const Real xj = X[j * NT + n];
-            const Real* col = Bt + (size_t)j * ld + row0;
-            if constexpr (F64) {
-#pragma unroll
-                for (int k = 0; k < RI; k += 2) {
-                    const double2 b = __ldg((const double2*)(col + k));
-                    t0[k] = fmar(b.x, xj, t0[k]);
-                    t0[k + 1] = fmar(b.y, xj, t0[k + 1]);
-                }
+        load_chunk(0, 0);
+        for (int c = 0; c < n_chunks; ++c) {
+            if (c + 1 < n_chunks) {
+                load_chunk(c + 1, (c + 1) & 1);
+                cp_async_wait<1>();
             } else {
-                const float* coll = Btl + (size_t)j * ld + row0;
+                cp_async_wait<0>();
+            }
+            __syncthreads();                         // chunk c (and, at c = 0, Xs) visible to all
+            const Real* bh = bsh + (size_t)(c & 1) * NB * CHUNK;
+            const int jn = s - c * kJC < kJC ? s - c * kJC : kJC;   // columns beyond s are zero
+            for (int jj = 0; jj < jn; ++jj) {
+                const Real xj = X[(c * kJC + jj) * NT + n];
+                const Real* col = bh + jj * SP + row0;
+                if constexpr (F64) {
 #pragma unroll
-                for (int k = 0; k < RI; k += 4) {
-                    const float4 bh = __ldg((const float4*)(col + k));
-                    const float4 bl = __ldg((const float4*)(coll + k));
-                    t0[k] = fmaf(bh.x, xj, fmaf(bl.x, xj, t0[k]));
-                    t0[k + 1] = fmaf(bh.y, xj, fmaf(bl.y, xj, t0[k + 1]));
-                    t0[k + 2] = fmaf(bh.z, xj, fmaf(bl.z, xj, t0[k + 2]));
-                    t0[k + 3] = fmaf(bh.w, xj, fmaf(bl.w, xj, t0[k + 3]));
+                    for (int k = 0; k < RI; k += 2) {
+                        const double2 b = *(const double2*)(col + k);
+                        t0[k] = fmar(b.x, xj, t0[k]);
+                        t0[k + 1] = fmar(b.y, xj, t0[k + 1]);
+                    }
+                } else {
+                    const float* coll = col + CHUNK;
+#pragma unroll
+                    for (int k = 0; k < RI; k += 4) {
+                        const float4 b_hi = *(const float4*)(col + k);
+                        const float4 b_lo = *(const float4*)(coll + k);
+                        t0[k] = fmaf(b_hi.x, xj, fmaf(b_lo.x, xj, t0[k]));
+                        t0[k + 1] = fmaf(b_hi.y, xj, fmaf(b_lo.y, xj, t0[k + 1]));
+                        t0[k + 2] = fmaf(b_hi.z, xj, fmaf(b_lo.z, xj, t0[k + 2]));
+                        t0[k + 3] = fmaf(b_hi.w, xj, fmaf(b_lo.w, xj, t0[k + 3]));
+                    }
                 }
             }
+            __syncthreads();                         // buffer c & 1 free for chunk c + 2
         }
 #pragma unroll
         for (int k = 0; k < RI; ++k) acc[k] = -t0[k];
@@ -253,8 +291,9 @@ cudaError_t launch_simt(const DenseSys& sys, const Src& src, int64_t n_inst, cud
 {
     using Real = std::conditional_t<F64, double, float>;
     constexpr int SP = (kDenseThreads / NT) * RI;
+    constexpr int NB = F64 ? 1 : 2;
     if (sys.s_pad != SP) return cudaErrorInvalidValue;
-    const size_t smem = 2 * sizeof(Real) * SP * NT;
+    const size_t smem = sizeof(Real) * (2 * (size_t)SP * NT + 2 * (size_t)NB * kJC * SP);
     auto kern = rk4_dense_simt_kernel<RI, NT, F64, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
