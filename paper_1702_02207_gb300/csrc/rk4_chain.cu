@@ -112,8 +112,8 @@ template <int P, bool F64, int MAXT, class Src>
 __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
 {
     using Real = std::conditional_t<F64, double, float>;
-    __shared__ Real edge_last[2][32];   // last DOF of each warp
-    __shared__ Real edge_first[2][32];  // first DOF of each warp
+    __shared__ Real edge_last[2][32][32];   // last DOF of every thread, [buffer][warp][lane]
+    __shared__ Real edge_first[2][32][32];  // first DOF of every thread
     __shared__ int any_bad;
 
     const int64_t q = blockIdx.x;
@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     }
 
     int buf = 0;
-    // neighbours of warp edges come from shared memory; every lane reads the same
-    // word (a broadcast) and selects, so no lane branches
+    // neighbours across warp edges come from shared memory: every lane stores its
+    // edge values (no lane-dependent branch), then reads its neighbour warp's edge
+    // lane as a broadcast and selects
     const int wl = warp > 0 ? warp - 1 : 0;
     const int wr = warp + 1 < nwarp ? warp + 1 : warp;
     const Real has_left = warp > 0 ? (Real)1 : (Real)0;
@@ -172,11 +173,11 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     auto accel = [&](const Real (&xs)[P], Real (&acc)[P]) {
         const Real up = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
         const Real dn = __shfl_down_sync(0xffffffffu, xs[0], 1);
-        if (lane == 31) edge_last[buf][warp] = xs[P - 1];
-        if (lane == 0) edge_first[buf][warp] = xs[0];
+        edge_last[buf][warp][lane] = xs[P - 1];
+        edge_first[buf][warp][lane] = xs[0];
         __syncthreads();
-        const Real el = edge_last[buf][wl] * has_left;
-        const Real ef = edge_first[buf][wr] * has_right;
+        const Real el = edge_last[buf][wl][31] * has_left;
+        const Real ef = edge_first[buf][wr][0] * has_right;
         const Real left = lane == 0 ? el : up;
         const Real right = lane == 31 ? ef : dn;
         buf ^= 1;
