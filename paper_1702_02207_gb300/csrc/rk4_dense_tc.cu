@@ -22,6 +22,9 @@
 // Per CTA: 16 warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of its
 // 128-row block) and columns 8 (w / 4) .. +7 (instances); each thread keeps the
 // state of one row for eight instances in registers.  Thread 0 issues the MMAs.
+// (Splitting a CTA into two independent 16-instance tiles that share B, so that
+// one tile's MMAs overlap the other's epilogue, was measured slower: the MMAs are
+// half as wide and twice as many, s = 128 bf16x3 75.8 ms against 61.4 ms.)
 //
 // Operand layouts in shared memory (no swizzle, 16-byte core matrices of
 // 8 rows x 16 bytes):
@@ -228,61 +231,48 @@ struct TcSlotSrc {
     __device__ void book(int64_t q, int64_t ran) const { io.slots[io.slot_ids[q]].remaining -= ran; }
 };
 
-// PA pieces of B, PB pieces of Xs, CS CTAs per cluster, TILES independent tiles per CTA.
-// With TILES = 2 (no cluster) each half of the CTA (8 warps) integrates its own tile
-// of 16 instances against the one copy of B in shared memory, with its own MMAs,
-// mbarrier and named barrier: while one half waits for its MMAs the other runs its
-// epilogue, so the tensor pipe and the CUDA cores overlap.
-template <int PA, int PB, int CS, int TILES, class Src>
+// PA pieces of B, PB pieces of Xs, CS CTAs per cluster.
+template <int PA, int PB, int CS, class Src>
 __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
 {
-    static_assert(TILES == 1 || CS == 1, "two tiles per CTA only without clusters");
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
-    constexpr int NTG = kNT / TILES;                 // instances per tile (MMA N)
-    constexpr int GW = kTcWarps / TILES;             // warps per tile
-    constexpr int XCH = 16 * NTG * 2;                // bytes of one 16 x NTG chunk of Xs
-    constexpr int XLBO = (NTG / 8) * 128;            // Xs core-matrix stride along K
     constexpr int A_BYTES = PA * KC * kAChunk;
-    constexpr int XG_BYTES = PB * KC * XCH;          // Xs of one tile
+    constexpr int X_BYTES = PB * KC * kXChunk;
     constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces
+    unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
     __shared__ __align__(8) uint64_t bar_load;
-    __shared__ __align__(8) uint64_t bar_mma[TILES];
+    __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag[2];
     __shared__ float sh_h[kNT][4];                   // h, h/2, h/6 hi, h/6 lo of each instance
     __shared__ long long sh_steps[kNT];              // steps of each instance in this launch
-    __shared__ long long sh_max_steps[TILES];
+    __shared__ long long sh_max_steps;
     __shared__ int sh_bad[kNT];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int g = warp / GW;                         // tile of this thread within the CTA
-    const int wg = warp % GW;
-    const int quad = wg & 3;
-    const int colgrp = wg >> 2;
     const uint32_t rank = CS > 1 ? cluster_rank() : 0;
-    const int64_t tile = (int64_t)(blockIdx.x / CS) * TILES + g;
+    const int64_t tile = blockIdx.x / CS;
+    const int quad = warp & 3;
+    const int colgrp = warp >> 2;
     const int row = 32 * quad + lane;                // row of this CTA's block
     const int k = 128 * (int)rank + row;             // DOF
     const int s = sys.s;
     const bool live_row = k < s;
-    const int n0 = colgrp * kCPT;                    // first instance column of this thread in its tile
-    const int c0 = g * NTG + n0;                     // the same column among the CTA's kNT
-    unsigned char* sX = smem + A_BYTES + g * XG_BYTES;   // this tile's Xs, PB pieces
-    const bool issuer = tid == g * GW * 32;
+    const int n0 = colgrp * kCPT;                    // first instance column of this thread
 
     // ---- set-up: barriers, TMEM, B into shared memory ----
     if (tid == 0) {
         mbar_init(&bar_load, 1);
-        for (int t = 0; t < TILES; ++t) mbar_init(&bar_mma[t], 1);
+        mbar_init(&bar_mma, 1);
         abort_flag[0] = abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < kNT) {
-        const int64_t q = (int64_t)(blockIdx.x / CS) * kNT + tid;
+        const int64_t q = tile * kNT + tid;
         const bool live = q < src.count();
         const double hd = live ? src.h(q) : 1.0;
         sh_steps[tid] = live ? (long long)src.steps(q) : 0;
@@ -317,61 +307,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         if (CS > 1) cluster_sync(); else __syncthreads();
         return abort_flag[0] == 0 && abort_flag[1] == 0;
     };
-    // OR of a flag over the threads of this tile (a named barrier per tile)
-    auto tile_or = [&](bool p) -> bool {
-        if constexpr (TILES == 1) {
-            return __syncthreads_or(p) != 0;
-        } else {
-            uint32_t r;
-            asm volatile("{\n.reg .pred a, b;\nsetp.ne.u32 a, %1, 0;\nbar.red.or.pred b, %2, %3, a;\nselp.u32 %0, 1, 0, b;\n}\n"
-                         : "=r"(r)
-                         : "r"((uint32_t)p), "r"(1 + g), "r"(GW * 32)
-                         : "memory");
-            return r != 0;
-        }
-    };
     bool ok = true;
     if (tid == 0) {
-        const unsigned char* src_b = (const unsigned char*)sys.Bbf + (size_t)rank * 3 * KC * kAChunk;
+        const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * 3 * KC * kAChunk;
         mbar_expect_tx(&bar_load, A_BYTES);
         for (int off = 0; off < A_BYTES; off += 16384) {
             const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
-            bulk_g2s(sA + off, src_b + off, (uint32_t)n, &bar_load);
+            bulk_g2s(sA + off, src + off, (uint32_t)n, &bar_load);
         }
     }
     ok = agree(mbar_wait(&bar_load, 0));
 
-    // ---- state of this thread: row k of instances n0 .. n0+7 of its tile ----
+    // ---- state of this thread: row k of instances n0 .. n0+7 ----
     float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
 #pragma unroll
     for (int j = 0; j < kCPT; ++j) {
-        const int64_t q = tile * NTG + n0 + j;
+        const int64_t q = tile * kNT + n0 + j;
         if (live_row && q < src.count()) {
             src.load(q, k, x[j], v[j], cx[j], cv[j]);
         } else {
             x[j] = v[j] = cx[j] = cv[j] = 0.f;
         }
     }
-    if (issuer) {
+    if (tid == 0) {
         long long m = 0;
-        for (int j = 0; j < NTG; ++j) m = sh_steps[g * NTG + j] > m ? sh_steps[g * NTG + j] : m;
-        sh_max_steps[g] = m;
+        for (int j = 0; j < kNT; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+        sh_max_steps = m;
     }
     __syncthreads();
 
     // Xs addresses of this thread's DOF k in every CTA of the cluster
     const int kc = k / 16, kk = k % 16;
-    const uint32_t xoff = (uint32_t)(kc * XCH + (kk / 8) * XLBO + (n0 / 8) * 128 + (kk % 8) * 16);
+    const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
     uint32_t xdst[CS];
 #pragma unroll
     for (int c = 0; c < CS; ++c) xdst[c] = CS > 1 ? mapa(smem_u32(sX) + xoff, (uint32_t)c) : smem_u32(sX) + xoff;
 
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(NTG >> 3) << 17) |
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
-    const uint32_t tcol = tmem + (uint32_t)(g * NTG);               // this tile's accumulator columns
-    const uint32_t taddr = tcol + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
+    const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
     uint32_t phase = 0;
-    bool pending_abort = false;                     // a failed wait, reported at the next barrier
 
     // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
     auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
@@ -386,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             w.z = pack_bf16(r[4], r[5]);
             w.w = pack_bf16(r[6], r[7]);
 #pragma unroll
-            for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * KC * XCH), w);
+            for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * KC * kXChunk), w);
             if (p + 1 < PB) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
@@ -394,13 +369,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
         asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if constexpr (CS > 1) {
-            cluster_sync();
-        } else {
-            if (tile_or(pending_abort)) return false;   // uniform across the tile
-        }
+        if (CS > 1) cluster_sync(); else __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (issuer) {
+        if (tid == 0) {
             const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
             int first = 1;
 #pragma unroll
@@ -409,15 +380,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
                 const int ib = kProdB[NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2][pr];
                 for (int c = 0; c < KC; ++c) {
                     const uint64_t ad = smem_desc(a0 + (uint32_t)((ia * KC + c) * kAChunk), 128, 256);
-                    const uint64_t bd = smem_desc(x0 + (uint32_t)((ib * KC + c) * XCH), XLBO, 128);
-                    mma_bf16(tcol, ad, bd, idesc, first ? 0u : 1u);
+                    const uint64_t bd = smem_desc(x0 + (uint32_t)((ib * KC + c) * kXChunk), 512, 128);
+                    mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
                     first = 0;
                 }
             }
-            mma_commit(&bar_mma[g]);
+            mma_commit(&bar_mma);
         }
         // the whole warp takes the same branch around the .sync.aligned TMEM load
-        const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma[g], phase));
+        const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma, phase));
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
@@ -425,17 +396,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if constexpr (CS > 1) {
-            // every CTA of the cluster has its MMA done (so Xs may be rewritten) and agrees on aborts
-            return agree(done);
-        } else {
-            // this thread's own wait covers its own Xs; a failure stops the tile at the next barrier
-            pending_abort = pending_abort || !done;
-            return true;
-        }
+        // every CTA of the cluster has its MMA done (so Xs may be rewritten) and agrees on aborts
+        return agree(done);
     };
 
-    const int64_t nsteps = ok ? (int64_t)sh_max_steps[g] : 0;
+    const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
     int64_t ck = 0, step = 0;
     for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
@@ -444,7 +409,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             ok = stage(x, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[c0 + j][1];
+                const float h2 = sh_h[n0 + j][1];
                 kx[j] = v[j];
                 kv[j] = a[j];
                 xs[j] = __fmaf_rn(h2, v[j], x[j]);
@@ -453,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[c0 + j][1];
+                const float h2 = sh_h[n0 + j][1];
                 kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
                 kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
                 xs[j] = __fmaf_rn(h2, vs[j], x[j]);
@@ -462,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h = sh_h[c0 + j][0];
+                const float h = sh_h[n0 + j][0];
                 kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
                 kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
                 xs[j] = __fmaf_rn(h, vs[j], x[j]);
@@ -471,8 +436,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                if (step < sh_steps[c0 + j]) {       // instances past their count hold still
-                    const float h6 = sh_h[c0 + j][2], h6l = sh_h[c0 + j][3];
+                if (step < sh_steps[n0 + j]) {       // instances past their count hold still
+                    const float h6 = sh_h[n0 + j][2], h6l = sh_h[n0 + j][3];
                     kx[j] = addr(kx[j], vs[j]);
                     kv[j] = addr(kv[j], a[j]);
                     comp_update(x[j], cx[j], kx[j], h6, h6l);
@@ -481,42 +446,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             }
         }
         if (src.ckpt_every() > 0 && ok) {
-            if (CS == 1 && tile_or(pending_abort)) {
-                ok = false;
-                break;
-            }
             if (live_row) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) {
-                    const int64_t q = tile * NTG + n0 + j;
+                    const int64_t q = tile * kNT + n0 + j;
                     if (q < src.count()) src.checkpoint(q, ck, k, x[j], v[j], cx[j], cv[j]);
                 }
             }
             ++ck;
         }
     }
-    if (CS == 1 && ok && tile_or(pending_abort)) ok = false;
     if (live_row) {
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) {
-            const int64_t q = tile * NTG + n0 + j;
+            const int64_t q = tile * kNT + n0 + j;
             if (q < src.count()) {
                 src.store(q, k, x[j], v[j], cx[j], cv[j]);
-                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[c0 + j] = 1;
+                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[n0 + j] = 1;
             }
         }
     }
-    if (!ok && issuer && sys.err) atomicExch(sys.err, 1);
-    __shared__ int tile_failed[TILES];
-    if (issuer) tile_failed[g] = ok ? 0 : 1;
+    if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid < kNT) {
-        const int64_t q = (int64_t)(blockIdx.x / CS) * kNT + tid;
+        const int64_t q = tile * kNT + tid;
         if (q < src.count()) {
-            if (tile_failed[tid / NTG]) src.flag(q, CHO_ETIMEOUT);
+            if (!ok) src.flag(q, CHO_ETIMEOUT);
             else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
-            if (rank == 0) src.book(q, tile_failed[tid / NTG] ? 0 : (int64_t)sh_steps[tid]);
+            if (rank == 0) src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
         }
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT));
@@ -527,9 +485,8 @@ template <int PA, int PB, int CS, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
-    constexpr int TILES = CS == 1 ? 2 : 1;          // two independent tiles per CTA without clusters
-    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;   // the tiles share kXChunk
-    auto kern = rk4_dense_tc_kernel<PA, PB, CS, TILES, Src>;
+    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n_inst + kNT - 1) / kNT;
