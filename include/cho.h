@@ -193,6 +193,13 @@ cho_status cho_system_info(cho_system sys, double* omega_max, int32_t* s, int64_
 /* Largest natural frequency of each parameter set, omega (n_sys), host memory. */
 cho_status cho_system_omegas(cho_system sys, double* omega);
 
+/* Device-side status of a system: waits for the device, then returns CHO_ETIMEOUT (and
+ * clears it) if a tensor-core run on this system gave up one of its bounded waits (each
+ * waits at most about a second; the run then stops and its results are invalid), else
+ * CHO_OK.  Host-memory batches report this themselves; device-memory batches, which return
+ * before the kernel ends, report it here.  Errors: CHO_EINVAL, CHO_ECUDA. */
+cho_status cho_system_status(cho_system sys);
+
 void cho_destroy_system(cho_system sys);
 
 /* ---- batched integration (steps a1-a5) -------------------------------------------- */

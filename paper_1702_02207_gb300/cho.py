@@ -36,7 +36,7 @@ PRECS = {"fp64": CHO_FP64, "fp32_kahan": CHO_FP32_KAHAN, "bf16x3": CHO_DENSE_BF1
 
 EXPORTED = [
     "cho_init", "cho_shutdown", "cho_last_error", "cho_create_system", "cho_system_info",
-    "cho_system_omegas", "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
+    "cho_system_omegas", "cho_system_status", "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
 ]
@@ -104,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_create_system": ([V, ctypes.POINTER(cho_system_desc), ctypes.POINTER(V)], I32),
             "cho_system_info": ([V, _dp, ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
             "cho_system_omegas": ([V, _dp], I32),
+            "cho_system_status": ([V], I32),
             "cho_destroy_system": ([V], None),
             "cho_integrate_batch": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
             "cho_integrate_plain": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
@@ -226,6 +227,11 @@ def cho_system_omegas(system):
     out = np.empty(n)
     _check(load().cho_system_omegas(system, out.ctypes.data_as(_dp)))
     return out
+
+
+def cho_system_status(system):
+    """CHO_OK, or raises ChoError(CHO_ETIMEOUT) if a tensor-core run on the system gave up a wait."""
+    return _check(load().cho_system_status(system))
 
 
 def cho_destroy_system(system):

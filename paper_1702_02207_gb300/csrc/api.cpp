@@ -111,6 +111,20 @@ static bool all_finite(const double* p, size_t n)
     return true;
 }
 
+// Read and clear the device error word of a system (the tensor-core kernel sets it
+// when one of its bounded waits gives up).  Synchronous; CHO_OK or CHO_ETIMEOUT.
+static cho_status take_device_error(cho_system_impl* sys, const char* who)
+{
+    if (!sys->d_err) return CHO_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, sys->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(sys->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(CHO_ECUDA, "%s: reading the device error word: %s", who, cudaGetErrorString(e));
+    if (h) return fail(CHO_ETIMEOUT, "%s: a tensor-core wait gave up after its time limit; results are invalid", who);
+    return CHO_OK;
+}
+
+
 }  // namespace cho
 
 using namespace cho;
@@ -378,6 +392,17 @@ extern "C" cho_status cho_system_omegas(cho_system sys, double* omega)
     return CHO_OK;
 }
 
+extern "C" cho_status cho_system_status(cho_system sys)
+{
+    clear_error();
+    if (!sys) return fail(CHO_EINVAL, "cho_system_status: NULL system");
+    DeviceGuard g(sys->ctx->device);
+    if (!g.ok()) return fail(CHO_ECUDA, "cho_system_status: cudaSetDevice failed");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(CHO_ECUDA, "cho_system_status: %s", cudaGetErrorString(e));
+    return take_device_error(sys, "cho_system_status");
+}
+
 extern "C" void cho_destroy_system(cho_system sys)
 {
     if (!sys) return;
@@ -487,7 +512,7 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         e = launch_rk4_chain(cs, io, fp64, st);
     } else {
-        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0};
         e = launch_rk4_dense(ds, io, b->prec, st);
     }
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: kernel launch: %s", cudaGetErrorString(e));
@@ -557,7 +582,7 @@ static cho_status run_staged(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t
 #undef CHO_STAGE
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: %s", cudaGetErrorString(e));
-    return CHO_OK;
+    return take_device_error(b->system, "integrate");
 }
 
 static cho_status run_plain_device(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st)

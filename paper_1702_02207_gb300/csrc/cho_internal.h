@@ -110,7 +110,13 @@ struct DenseSys {
     const uint16_t* Bbf;    // tensor-core kernel: shared-memory images of the BF16 pieces of B
     int32_t s_tc;           // tensor-core padded size: 128 or 256 (0: no tensor-core data)
     int* err;               // device error word of the tensor-core kernel (bounded waits)
+    int32_t stall_mma;      // test hook: issue no MMA, so the bounded wait on it runs out
 };
+
+// Test hook for the bounded device waits: CHO_TEST_STALL_MMA=1 in the environment makes
+// the tensor-core kernel skip its MMAs, so its wait on their completion gives up after
+// about a second and the run reports CHO_ETIMEOUT.  Read at every launch.
+int test_stall_mma();
 int dense_pad(int s);
 cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
 cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st);

@@ -41,6 +41,7 @@
 #include "rk4_common.cuh"
 
 #include <cuda_bf16.h>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         if (CS > 1) cluster_sync(); else __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
+        if (tid == 0 && !sys.stall_mma) {
             const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
             int first = 1;
 #pragma unroll
@@ -544,14 +545,24 @@ float bf16_value(uint16_t b)
 
 }  // namespace
 
+int test_stall_mma()
+{
+    const char* e = std::getenv("CHO_TEST_STALL_MMA");
+    return e && e[0] == '1' ? 1 : 0;
+}
+
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st)
 {
-    return dispatch_tc(sys, TcBatchSrc{io, sys.s}, io.n_inst, prec, st);
+    DenseSys d = sys;
+    d.stall_mma = test_stall_mma();
+    return dispatch_tc(d, TcBatchSrc{io, sys.s}, io.n_inst, prec, st);
 }
 
 cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int prec, cudaStream_t st)
 {
-    return dispatch_tc(sys, TcSlotSrc{io, sys.s}, io.n_inst, prec, st);
+    DenseSys d = sys;
+    d.stall_mma = test_stall_mma();
+    return dispatch_tc(d, TcSlotSrc{io, sys.s}, io.n_inst, prec, st);
 }
 
 // BF16 pieces of B for the tensor-core kernel, laid out per CTA rank as the exact

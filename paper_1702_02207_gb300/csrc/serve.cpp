@@ -393,7 +393,7 @@ cudaError_t ServeEngine::launch(Group* g)
         e = launch_rk4_chain_slots(s_max, io, f64, g->st);
     } else {
         cho_system_impl* sys = std::get<3>(g->key);
-        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err};
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0};
         if (prec == CHO_DENSE_BF16X3 || prec == CHO_DENSE_BF16X5 || prec == CHO_DENSE_BF16X6)
             e = launch_rk4_dense_tc_slots(ds, io, prec, g->st);
         else

@@ -379,3 +379,112 @@ def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
     for variant in ("packed", "generic"):
         for k in ("x", "v", "x_traj", "v_traj"):
             assert np.array_equal(res["pair"][k], res[variant][k]), (variant, k)
+
+
+# ---- full-size workloads, sampled against the oracle ------------------------------------------
+
+@pytest.mark.parametrize("s", [64, 128, 256])
+def test_dense_full_size_sampled_bf16x5(ctx, s):
+    """8192 instances sharing one (M, K), 5e3 steps, bf16x5 on the tensor cores (the benchmark launch)."""
+    cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
+    out = run_gpu(ctx, cfg, "bf16x5", 625)
+    idx = sample_indices(8192, 6)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=625)
+    ex, ev = check(out, ref, TOL_FP32, idx)
+    print(f"dense s={s} 8192 x 5000 bf16x5 sampled: x {ex:.3e} v {ev:.3e}")
+
+
+def test_chain_full_size_sampled_fp64(ctx):
+    """4096 chains of 1024 masses x 1e4 steps in FP64, sampled against the oracle."""
+    cfg = inputs.chain_batch()
+    out = run_gpu(ctx, cfg, "fp64", 625)
+    idx = sample_indices(cfg["x0"].shape[0], 8)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=625)
+    check(out, ref, TOL_FP64, idx)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_largest_chain(ctx, prec, tol):
+    """s = 8192 (eight DOFs per thread on 1024 threads), the largest chain the library takes."""
+    cfg = inputs.chain_batch(n_inst=2, s=8192, n_steps=250, seed=8192)
+    out = run_gpu(ctx, cfg, prec, 125)
+    ref = oracle_run(cfg, ckpt_every=125)
+    check(out, ref, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_simt", TOL_FP32)])
+def test_largest_dense_simt(ctx, prec, tol):
+    """s = 512 (the largest dense system on the CUDA cores)."""
+    cfg = inputs.dense_group(s=512, n_inst=9, n_steps=250)
+    out = run_gpu(ctx, cfg, prec, 125)
+    ref = oracle_run(cfg, ckpt_every=125)
+    check(out, ref, tol)
+
+
+def test_energy_dense_checkpoints(ctx):
+    import oracle
+
+    cfg = inputs.dense_group(s=100, n_inst=6, n_steps=500)
+    sys_ = make_system(ctx, cfg)
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 500, "fp64", 125, energy=True)
+    finally:
+        cho.cho_destroy_system(sys_)
+    E_ref = oracle.energy_dense(cfg["M"][0], cfg["K"][0], out["x_traj"].reshape(-1, 100),
+                                out["v_traj"].reshape(-1, 100)).reshape(6, -1)
+    assert np.allclose(out["energy"], E_ref, rtol=1e-12)
+    # RK4 loses energy: every instance's energy decreases monotonically over the checkpoints
+    assert np.all(np.diff(out["energy"], axis=1) <= 0)
+
+
+def test_many_parameter_sets_small_dense(ctx):
+    """S = 32 lane groups with 4099 distinct parameter sets (ragged last block)."""
+    n = 4099
+    rng = np.random.default_rng(31)
+    s = 20
+    M, K = [], []
+    base_M, base_K, _, _ = inputs.dense_system(s, 2020)
+    for i in range(n):
+        scale = rng.uniform(0.5, 2.0)
+        M.append(base_M)
+        K.append(base_K * scale)
+    M = np.stack(M)
+    K = np.stack(K)
+    w = inputs.omega_max_dense(base_M, base_K) * np.sqrt(2.0)
+    cfg = {"kind": "dense", "s": s, "M": M, "K": K, "x0": rng.normal(size=(n, s)), "v0": np.zeros((n, s)),
+           "h": np.full(n, float(inputs.fp32_exact(2 * math.pi / w / 100))), "n_steps": 500}
+    out = run_gpu(ctx, cfg, "fp32_kahan", 125)
+    idx = sample_indices(n, 40)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=125)
+    check(out, ref, TOL_FP32, idx)
+
+
+def test_tensor_core_wait_gives_up_and_reports(ctx):
+    """Bounded device waits: with the MMAs withheld (test hook), the wait for their completion
+    runs out after about a second, the kernel leaves cleanly and the call reports
+    CHO_ETIMEOUT; the context stays usable and the next run is correct."""
+    cfg = inputs.dense_group(s=64, n_inst=40, n_steps=20)
+    sys_ = make_system(ctx, cfg)
+    try:
+        os.environ["CHO_TEST_STALL_MMA"] = "1"
+        try:
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 20, "bf16x5")
+            assert ei.value.status == cho.CHO_ETIMEOUT
+            import torch
+
+            d = torch.device("cuda:0")
+            cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                    torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                    20, "bf16x5")
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_system_status(sys_)
+            assert ei.value.status == cho.CHO_ETIMEOUT
+        finally:
+            del os.environ["CHO_TEST_STALL_MMA"]
+        assert cho.cho_system_status(sys_) == cho.CHO_OK
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 20, "bf16x5")
+        ref = oracle_run(cfg)
+        assert rel_err(out["x"][:, None], ref["x"][:, None]).max() < TOL_FP32
+    finally:
+        cho.cho_destroy_system(sys_)
