@@ -4,13 +4,18 @@
 // accumulation in tensor memory; the stage combinations and the Kahan-
 // compensated FP32 state update run on the CUDA cores.
 //
-// Split-BF16.  B = b0 + b1 + b2 and Xs = p0 + p1 + p2 with each piece the
-// BF16 rounding of what the previous pieces leave.  The product keeps the
-// partial products whose order is at most 2^-16 relative:
-//   bf16x3: b0 p0 + b0 p1 + b1 p0
-//   bf16x5: bf16x3 + b1 p1 + b2 p0
-//   bf16x6: bf16x5 + b0 p2
-// (smallest terms are accumulated first).
+// Split-BF16.  B = b0 + b1 + b2 + b3 and Xs = p0 + p1 with each piece the BF16
+// rounding of what the previous pieces leave (8 significant bits each).  The
+// product keeps the partial products down to a chosen order:
+//   bf16x3: b0 p0 + b0 p1 + b1 p0                 (B to 16 bits)
+//   bf16x5: bf16x3 + b1 p1 + b2 p0                (B to 24 bits, like FP32)
+//   bf16x6: bf16x5 + b3 p0                        (B to 32 bits)
+// (smallest terms are accumulated first).  The error B - sum(b) is a fixed
+// perturbation of the system, so it shifts the frequencies coherently and the
+// phase error grows with the horizon; the rounding of Xs to p0 + p1 changes
+// from stage to stage and does not accumulate coherently.  bf16x6 removes the
+// coherent part for long horizons (s <= 128: four pieces of B must fit in
+// shared memory).
 //
 // Work split.  s <= 128: one CTA per tile of 32 instances.  128 < s <= 256: a
 // cluster of two CTAs per tile; CTA r owns rows [128 r, 128 r + 128) of B
@@ -54,6 +59,7 @@ constexpr int kNT = 32;            // instances per tile (MMA N)
 constexpr int kCPT = 8;            // instances per thread
 constexpr int kAChunk = 4096;      // bytes of one 128 x 16 chunk of B
 constexpr int kXChunk = 1024;      // bytes of one 16 x 32 chunk of Xs
+constexpr int kBPieces = 4;        // BF16 pieces of B kept per CTA rank
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -166,8 +172,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 // Partial products (piece of B, piece of Xs), smallest first, for bf16x3 / x5 / x6.
-__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
-__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
+__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {3, 2, 1, 1, 0, 0}};
+__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 0, 1, 0, 1, 0}};
 
 // Batch form: FP64 arrays in and out, shared step count, checkpoints.
 struct TcBatchSrc {
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
     constexpr int A_BYTES = PA * KC * kAChunk;
     constexpr int X_BYTES = PB * KC * kXChunk;
-    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
+    constexpr int NPROD = PA == 2 ? 3 : (PA == 3 ? 5 : 6);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces
     unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     };
     bool ok = true;
     if (tid == 0) {
-        const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * 3 * KC * kAChunk;
+        const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * kBPieces * KC * kAChunk;
         mbar_expect_tx(&bar_load, A_BYTES);
         for (int off = 0; off < A_BYTES; off += 16384) {
             const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
@@ -519,8 +525,8 @@ cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int
         case CHO_DENSE_BF16X5:
             return two ? launch_tc<3, 2, 2>(sys, src, n_inst, st) : launch_tc<3, 2, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
-            if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
-            return launch_tc<3, 3, 1>(sys, src, n_inst, st);
+            if (two) return cudaErrorNotSupported;   // four 64 KB pieces of B per CTA exceed shared memory
+            return launch_tc<4, 2, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -566,7 +572,7 @@ cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int
 }
 
 // BF16 pieces of B for the tensor-core kernel, laid out per CTA rank as the exact
-// shared-memory image the kernel copies: [rank][piece 0..2][K chunk][4096 B].
+// shared-memory image the kernel copies: [rank][piece 0..3][K chunk][4096 B].
 cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B)
 {
     const int s = sys->s;
@@ -577,14 +583,14 @@ cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B)
     const int st = s <= 128 ? 128 : 256;
     const int CS = st / 128, KC = st / 16;
     sys->s_tc = st;
-    const size_t per_rank = (size_t)3 * KC * kAChunk;
+    const size_t per_rank = (size_t)kBPieces * KC * kAChunk;
     std::vector<unsigned char> img((size_t)CS * per_rank, 0);
     for (int r = 0; r < CS; ++r)
         for (int m = 0; m < 128; ++m) {
             const int i = 128 * r + m;
             for (int kk = 0; kk < st; ++kk) {
                 double rem = (i < s && kk < s) ? B[(size_t)i * s + kk] : 0.0;
-                for (int p = 0; p < 3; ++p) {
+                for (int p = 0; p < kBPieces; ++p) {
                     const uint16_t b = bf16_bits((float)rem);
                     rem -= (double)bf16_value(b);
                     const int c = kk / 16, k16 = kk % 16;

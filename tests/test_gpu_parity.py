@@ -383,15 +383,21 @@ def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
 
 # ---- full-size workloads, sampled against the oracle ------------------------------------------
 
-@pytest.mark.parametrize("s", [64, 128, 256])
-def test_dense_full_size_sampled_bf16x5(ctx, s):
-    """8192 instances sharing one (M, K), 5e3 steps, bf16x5 on the tensor cores (the benchmark launch)."""
+# Over the full 5e3-step horizon the 24-bit B of bf16x5 shifts the frequencies enough to
+# reach ~1.5e-5 (stated bar 3e-5); bf16x6 (32-bit B) stays within 1e-5.
+TOL_BF16_FULL = {"bf16x5": 3e-5, "bf16x6": TOL_FP32}
+
+
+@pytest.mark.parametrize("s,prec", [(64, "bf16x5"), (128, "bf16x5"), (256, "bf16x5"), (64, "bf16x6"),
+                                    (128, "bf16x6")])
+def test_dense_full_size_sampled(ctx, s, prec):
+    """8192 instances sharing one (M, K), 5e3 steps on the tensor cores (the benchmark launch)."""
     cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
-    out = run_gpu(ctx, cfg, "bf16x5", 625)
+    out = run_gpu(ctx, cfg, prec, 625)
     idx = sample_indices(8192, 6)
     ref = oracle_run(cfg, idx=idx, ckpt_every=625)
-    ex, ev = check(out, ref, TOL_FP32, idx)
-    print(f"dense s={s} 8192 x 5000 bf16x5 sampled: x {ex:.3e} v {ev:.3e}")
+    ex, ev = check(out, ref, TOL_BF16_FULL[prec], idx)
+    print(f"dense s={s} 8192 x 5000 {prec} sampled: x {ex:.3e} v {ev:.3e}")
 
 
 def test_chain_full_size_sampled_fp64(ctx):
