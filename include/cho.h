@@ -71,11 +71,11 @@ typedef enum cho_kind {
  *   CHO_DENSE_BF16X3/X5/X6  dense systems with a shared (M, K): the product
  *                        M^{-1}K X on tensor cores with M^{-1}K and X split into
  *                        BF16 pieces, FP32 accumulation, FP32 + Kahan state.
- *                        x3: 3 partial products, M^{-1}K to 16 bits; x5: 5 products,
- *                        to 24 bits; x6: 6 products, to 32 bits (s <= 128).  The
- *                        truncation of M^{-1}K shifts frequencies, so its error grows
- *                        with the horizon: x5 ~1e-5 over 5e3 steps at h = T_min/100,
- *                        x6 below that.                                             */
+ *                        x3: 3 partial products, operands to 16 bits (~1e-3 error);
+ *                        x5: 5 products, M^{-1}K to 24 bits, X to 16; x6: 6 products,
+ *                        both to 24 bits (s <= 128).  x5/x6 keep each 16-wide K chunk
+ *                        in its own accumulator and add the chunks in FP32 (<= 1e-5
+ *                        over 5e3 steps at h = T_min/100).                          */
 typedef enum cho_prec {
     CHO_FP64 = 0,
     CHO_FP32_KAHAN = 1,

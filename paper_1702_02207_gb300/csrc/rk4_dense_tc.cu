@@ -4,19 +4,22 @@
 // accumulation in tensor memory; the stage combinations and the Kahan-
 // compensated FP32 state update run on the CUDA cores.
 //
-// Split-BF16.  B = b0 + b1 + b2 + b3 and Xs = p0 + p1 with each piece the BF16
+// Split-BF16.  B = b0 + b1 + b2 and Xs = p0 + p1 + p2 with each piece the BF16
 // rounding of what the previous pieces leave (8 significant bits each).  The
 // product keeps the partial products down to a chosen order:
-//   bf16x3: b0 p0 + b0 p1 + b1 p0                 (B to 16 bits)
-//   bf16x5: bf16x3 + b1 p1 + b2 p0                (B to 24 bits, like FP32)
-//   bf16x6: bf16x5 + b3 p0                        (B to 32 bits)
-// (smallest terms are accumulated first).  The error B - sum(b) is a fixed
-// perturbation of the system, so it shifts the frequencies coherently and the
-// phase error grows with the horizon; the rounding of Xs to p0 + p1 changes
-// from stage to stage and does not accumulate coherently.  bf16x6 removes the
-// coherent part for long horizons (s <= 128: four pieces of B must fit in
-// shared memory).
+//   bf16x3: b0 p0 + b0 p1 + b1 p0                 (operands to 16 bits)
+//   bf16x5: bf16x3 + b1 p1 + b2 p0                (B to 24 bits, Xs to 16)
+//   bf16x6: bf16x5 + b0 p2                        (both to 24 bits; s <= 128)
+// (smallest terms are accumulated first).
 //
+// Accumulation.  Summing all K/16 chunk products of a stage into one TMEM
+// accumulator lets the tensor core's accumulation rounding build up a bias that
+// acts like a frequency shift, so the error grew with the horizon (bf16x5 at
+// s = 256: 2.4e-5 after 5e3 steps).  bf16x5 and bf16x6 therefore give each
+// 16-wide K chunk its own accumulator (K/16 x 32 TMEM columns) and add the
+// chunk sums on the CUDA cores in FP32 round-to-nearest (s = 256: 5.9e-6, for
+// 10 % more time); bf16x3, whose truncation error dominates, keeps one.
+
 // Work split.  s <= 128: one CTA per tile of 32 instances.  128 < s <= 256: a
 // cluster of two CTAs per tile; CTA r owns rows [128 r, 128 r + 128) of B
 // (resident in its shared memory for the whole run) and the same rows of the
@@ -59,7 +62,7 @@ constexpr int kNT = 32;            // instances per tile (MMA N)
 constexpr int kCPT = 8;            // instances per thread
 constexpr int kAChunk = 4096;      // bytes of one 128 x 16 chunk of B
 constexpr int kXChunk = 1024;      // bytes of one 16 x 32 chunk of Xs
-constexpr int kBPieces = 4;        // BF16 pieces of B kept per CTA rank
+constexpr int kBPieces = 3;        // BF16 pieces of B kept per CTA rank
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -172,8 +175,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 // Partial products (piece of B, piece of Xs), smallest first, for bf16x3 / x5 / x6.
-__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {3, 2, 1, 1, 0, 0}};
-__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 0, 1, 0, 1, 0}};
+__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
+__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
 
 // Batch form: FP64 arrays in and out, shared step count, checkpoints.
 struct TcBatchSrc {
@@ -239,13 +242,13 @@ struct TcSlotSrc {
 };
 
 // PA pieces of B, PB pieces of Xs, CS CTAs per cluster.
-template <int PA, int PB, int CS, class Src>
+template <int PA, int PB, int CS, int NACC, class Src>
 __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
 {
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
     constexpr int A_BYTES = PA * KC * kAChunk;
     constexpr int X_BYTES = PB * KC * kXChunk;
-    constexpr int NPROD = PA == 2 ? 3 : (PA == 3 ? 5 : 6);
+    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces
     unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kNT));
+                     "r"(kNT * NACC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -380,16 +383,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0 && !sys.stall_mma) {
             const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
-            int first = 1;
+            uint32_t started = 0;                    // accumulators already written this stage
 #pragma unroll
             for (int pr = 0; pr < NPROD; ++pr) {
-                const int ia = kProdA[NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2][pr];
-                const int ib = kProdB[NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2][pr];
+                constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
+                const int ia = kProdA[TBL][pr];
+                const int ib = kProdB[TBL][pr];
                 for (int c = 0; c < KC; ++c) {
                     const uint64_t ad = smem_desc(a0 + (uint32_t)((ia * KC + c) * kAChunk), 128, 256);
                     const uint64_t bd = smem_desc(x0 + (uint32_t)((ib * KC + c) * kXChunk), 512, 128);
-                    mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
-                    first = 0;
+                    const int slot = c % NACC;
+                    mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
+                    started |= 1u << slot;
                 }
             }
             mma_commit(&bar_mma);
@@ -399,7 +404,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
-        if (done) tmem_ld8(taddr, acc);
+        if (done) {
+            tmem_ld8(taddr, acc);
+#pragma unroll
+            for (int k2 = 1; k2 < NACC; ++k2) {
+                float part[kCPT];
+                tmem_ld8(taddr + (uint32_t)(k2 * kNT), part);
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(acc[j], part[j]);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -484,16 +498,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (rank == 0) src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
         }
     }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT * NACC));
     if (CS > 1) cluster_sync();   // the peer may still write into this CTA's shared memory until here
 }
 
-template <int PA, int PB, int CS, class Src>
-cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+template <int PA, int PB, int CS, int NACC, class Src>
+cudaError_t launch_tc_n(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
-    auto kern = rk4_dense_tc_kernel<PA, PB, CS, Src>;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n_inst + kNT - 1) / kNT;
@@ -513,6 +527,15 @@ cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaS
     return cudaLaunchKernelEx(&cfg, kern, sys, src);
 }
 
+// bf16x3 accumulates in one TMEM accumulator, bf16x5/x6 in one per K chunk.
+template <int PA, int PB, int CS, class Src>
+cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+{
+    constexpr int NACC = PA == 2 ? 1 : 8 * CS;
+    return launch_tc_n<PA, PB, CS, NACC>(sys, src, n_inst, st);
+}
+
+
 template <class Src>
 cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int prec, cudaStream_t st)
 {
@@ -525,8 +548,8 @@ cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int
         case CHO_DENSE_BF16X5:
             return two ? launch_tc<3, 2, 2>(sys, src, n_inst, st) : launch_tc<3, 2, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
-            if (two) return cudaErrorNotSupported;   // four 64 KB pieces of B per CTA exceed shared memory
-            return launch_tc<4, 2, 1>(sys, src, n_inst, st);
+            if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
+            return launch_tc<3, 3, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -572,7 +595,7 @@ cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int
 }
 
 // BF16 pieces of B for the tensor-core kernel, laid out per CTA rank as the exact
-// shared-memory image the kernel copies: [rank][piece 0..3][K chunk][4096 B].
+// shared-memory image the kernel copies: [rank][piece 0..2][K chunk][4096 B].
 cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B)
 {
     const int s = sys->s;

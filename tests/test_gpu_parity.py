@@ -383,9 +383,9 @@ def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
 
 # ---- full-size workloads, sampled against the oracle ------------------------------------------
 
-# Over the full 5e3-step horizon the 24-bit B of bf16x5 shifts the frequencies enough to
-# reach ~1.5e-5 (stated bar 3e-5); bf16x6 (32-bit B) stays within 1e-5.
-TOL_BF16_FULL = {"bf16x5": 3e-5, "bf16x6": TOL_FP32}
+# Over the full 5e3-step horizon bf16x5 and bf16x6 stay within 1e-5 (each K chunk in its own
+# accumulator, chunks added in FP32 round-to-nearest).
+TOL_BF16_FULL = {"bf16x5": TOL_FP32, "bf16x6": TOL_FP32}
 
 
 @pytest.mark.parametrize("s,prec", [(64, "bf16x5"), (128, "bf16x5"), (256, "bf16x5"), (64, "bf16x6"),
