@@ -282,6 +282,32 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
 
     res = {}
 
+    def sampled_err(sys_, cfg, prec, n_sample=2, every=625):
+        """max relative error of a few instances against the oracle (x and v, over checkpoints)."""
+        import oracle
+
+        k = cfg["x0"].shape[0]
+        idx = np.array([0, k - 1][:n_sample])
+        x0 = torch.as_tensor(cfg["x0"][idx], device=dev)
+        v0 = torch.as_tensor(cfg["v0"][idx], device=dev)
+        h = torch.as_tensor(cfg["h"][idx], device=dev)
+        if cfg["kind"] == "dense":
+            r = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
+            ref = oracle.rk4_dense(cfg["M"][0], cfg["K"][0], cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx],
+                                   cfg["n_steps"], every, threads=n_sample)
+        else:
+            s2 = cho.cho_create_system(ctx, "chain", masses=cfg["masses"][idx], springs=cfg["springs"][idx])
+            r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
+            cho.cho_destroy_system(s2)
+            ref = oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx], cfg["v0"][idx],
+                                   cfg["h"][idx], cfg["n_steps"], every, threads=n_sample)
+        torch.cuda.synchronize()
+        e = 0.0
+        for key in ("x_traj", "v_traj"):
+            g = r[key].cpu().numpy()
+            e = max(e, float(np.max(np.max(np.abs(g - ref[key]), axis=(1, 2)) / np.max(np.abs(ref[key]), axis=(1, 2)))))
+        return {"max": e, "instances": int(len(idx))}
+
     def timed(sys_, cfg, prec, n):
         x0 = torch.as_tensor(cfg["x0"], device=dev)
         v0 = torch.as_tensor(cfg["v0"], device=dev)
@@ -303,6 +329,7 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
     dof = cfg["x0"].size * cfg["n_steps"]
     ach = dof * 52 / t / 1e12            # 26 FMA per DOF-step (4 x 3-point stencil, 6 combine, 6 sums, 2 update)
     res["chain_s1024_x4096_fp32_kahan"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                            "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan"),
                                             "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak,
                                                          "unit": "TFLOP/s", "frac": ach / alu_peak}}
     cho.cho_destroy_system(s_)
@@ -315,6 +342,7 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
             dof = cfg["x0"].size * cfg["n_steps"]
             ach = dof * 8 * s / t / 1e12     # four B x products of 2 s flops per DOF per step
             res[f"dense_s{s}_x8192_{prec}"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                               "error_vs_oracle": sampled_err(s_, cfg, prec),
                                                "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
                                                             "unit": "TFLOP/s", "frac": ach / bf16_peak}}
         cho.cho_destroy_system(s_)
