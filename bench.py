@@ -471,7 +471,10 @@ def main():
                        "parallelism": f"instances sharded over {world} GPU(s)"},
             "error_vs_oracle": err32,
             "roofline": {"bound": "alu", "kernel": "rk4_small<S=2,FP32+Kahan>", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         # DRAM bytes per launch (read + write) from the ncu capture of this kernel on this
+                         # workload (profiles/rk4_pair2_two_dof_65536.md)
+                         "traffic": 4740608,
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
             "clocks": clocks,
             "e2e": {"value": DOF_STEPS / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
