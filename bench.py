@@ -472,8 +472,8 @@ def main():
             "error_vs_oracle": err32,
             "roofline": {"bound": "alu", "kernel": "rk4_small<S=2,FP32+Kahan>", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         # DRAM bytes per launch (read + write) from the ncu capture of this kernel on this
-                         # workload (profiles/rk4_pair2_two_dof_65536.md)
+                         # DRAM bytes per launch (read + write) measured by an ncu capture of this
+                         # kernel on this workload
                          "traffic": 4740608,
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
             "clocks": clocks,

@@ -7,7 +7,7 @@ import oracle
 
 THREADS = max(1, min(16, os.cpu_count() or 1))
 
-# Tolerances (relative max-norm over the checkpoints of the horizon; see DESIGN.md):
+# Tolerances (relative max-norm over the checkpoints of the horizon):
 TOL_FP64 = 1e-10
 TOL_FP32 = 1e-5
 
