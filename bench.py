@@ -470,7 +470,7 @@ def main():
                        "prec": "fp32_kahan", "l2": "flushed between timed iterations (512 MiB write)",
                        "parallelism": f"instances sharded over {world} GPU(s)"},
             "error_vs_oracle": err32,
-            "roofline": {"bound": "alu", "kernel": "rk4_small<S=2,FP32+Kahan>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "rk4_pair2_balanced (2-DOF, FP32 + compensated state)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          # DRAM bytes per launch (read + write) measured by an ncu capture of this
                          # kernel on this workload

@@ -198,8 +198,10 @@ cho_status cho_system_info(cho_system sys, double* omega_max, int32_t* s, int64_
 cho_status cho_system_omegas(cho_system sys, double* omega);
 
 /* Device-side status of a system: waits for the device, then returns CHO_ETIMEOUT (and
- * clears it) if a tensor-core run on this system gave up one of its bounded waits (each
- * waits at most about a second; the run then stops and its results are invalid), else
+ * clears it) if a run on this system gave up one of its bounded waits (the tensor-core
+ * kernel's waits on its MMAs, about a second each, after which it stops; the balanced 2-DOF
+ * kernel's wait for a hand-over between warps, one second plus the time run so far, after
+ * which that unit finishes as NaN); its results are then invalid.  Otherwise
  * CHO_OK.  Host-memory batches report this themselves; device-memory batches, which return
  * before the kernel ends, report it here.  Errors: CHO_EINVAL, CHO_ECUDA. */
 cho_status cho_system_status(cho_system sys);

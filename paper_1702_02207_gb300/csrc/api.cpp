@@ -111,8 +111,9 @@ static bool all_finite(const double* p, size_t n)
     return true;
 }
 
-// Read and clear the device error word of a system (the tensor-core kernel sets it
-// when one of its bounded waits gives up).  Synchronous; CHO_OK or CHO_ETIMEOUT.
+// Read and clear the device error word of a system (the tensor-core kernel and
+// the balanced 2-DOF kernel set it when one of their bounded waits gives up).
+// Synchronous; CHO_OK or CHO_ETIMEOUT.
 static cho_status take_device_error(cho_system_impl* sys, const char* who)
 {
     if (!sys->d_err) return CHO_OK;
@@ -120,7 +121,7 @@ static cho_status take_device_error(cho_system_impl* sys, const char* who)
     cudaError_t e = cudaMemcpy(&h, sys->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && h) e = cudaMemset(sys->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return fail(CHO_ECUDA, "%s: reading the device error word: %s", who, cudaGetErrorString(e));
-    if (h) return fail(CHO_ETIMEOUT, "%s: a tensor-core wait gave up after its time limit; results are invalid", who);
+    if (h) return fail(CHO_ETIMEOUT, "%s: a bounded device wait gave up after its time limit; results are invalid", who);
     return CHO_OK;
 }
 
@@ -330,6 +331,8 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
                 split_pair(B64[(size_t)p * SS + k], B32[(size_t)p * 2 * SS + k], B32[(size_t)p * 2 * SS + SS + k]);
         e = upload(&sys->d_B64, B64.data(), B64.size());
         if (e == cudaSuccess) e = upload(&sys->d_B32, B32.data(), B32.size());
+        if (e == cudaSuccess) e = cudaMalloc(&sys->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(sys->d_err, 0, sizeof(int));
     } else if (sys->path == PATH_CHAIN) {
         // spring form of eq. 2: g_i = C_i / m_i, u_i = C_{i+1} / m_i
         std::vector<double> C64((size_t)n_sys * 2 * s);
@@ -506,7 +509,7 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     const bool fp64 = b->prec == CHO_FP64;
     cudaError_t e;
     if (sys->path == PATH_SMALL) {
-        SmallSys ss{sys->s, sys->S, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
+        SmallSys ss{sys->s, sys->S, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32, sys->d_err};
         e = launch_rk4_small(ss, io, fp64, st);
     } else if (sys->path == PATH_CHAIN) {
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};

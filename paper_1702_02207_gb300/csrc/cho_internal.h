@@ -82,6 +82,7 @@ struct SmallSys {
     int32_t per_inst_sys;   // 1: set = instance index, 0: set 0
     const double* B64;      // [n_sys][S][S]
     const float* B32;       // [n_sys][2][S][S] (hi then lo)
+    int* err;               // device error word: set when a bounded wait gives up (may be null)
 };
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);

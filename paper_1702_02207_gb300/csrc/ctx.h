@@ -63,7 +63,7 @@ struct cho_system_impl {
     double* d_springs = nullptr;
     double* d_M = nullptr;
     double* d_K = nullptr;
-    int* d_err = nullptr;               // tensor-core kernel error word
+    int* d_err = nullptr;               // device error word of the kernels with bounded waits
     double* d_plain = nullptr;          // FP64 plain-form coefficients: tridiagonal [3][s] or dense [s][s]
 };
 

@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     const int wr = warp + 1 < nwarp ? warp + 1 : warp;
     const Real has_left = warp > 0 ? (Real)1 : (Real)0;
     const Real has_right = warp + 1 < nwarp ? (Real)1 : (Real)0;
-    auto accel = [&](const Real (&xs)[P], Real (&acc)[P]) {
+    // FP32: the lo parts of g and u multiply the stage-1 extensions and the sum is
+    // reused by stages 2-4 (frozen lo, as in rk4_small.cu).
+    float lo1[P];
+    auto accel = [&](const Real (&xs)[P], Real (&acc)[P], bool first) {
         const Real up = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
         const Real dn = __shfl_down_sync(0xffffffffu, xs[0], 1);
         edge_last[buf][warp][lane] = xs[P - 1];
@@ -192,8 +195,8 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
             if constexpr (F64) {
                 a = fmar(uh[p], e[p + 1], -gh[p] * e[p]);
             } else {
-                const float lo = fmaf(ul[p], e[p + 1], -gl[p] * e[p]);
-                a = fmaf(uh[p], e[p + 1], fmaf(-gh[p], e[p], lo));
+                if (first) lo1[p] = fmaf(ul[p], e[p + 1], -gl[p] * e[p]);
+                a = fmaf(uh[p], e[p + 1], fmaf(-gh[p], e[p], lo1[p]));
             }
             acc[p] = a;
         }
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     for (int64_t done = 0; done < n; done += every) {
         repeat_steps(every, [&]() {
             Real a[P], xs[P], kx[P], kv[P], vs[P];
-            accel(x, a);
+            accel(x, a, true);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = v[p];
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
                 xs[p] = fmar(hs.h2, v[p], x[p]);
                 vs[p] = fmar(hs.h2, a[p], v[p]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = fmar((Real)2, vs[p], kx[p]);
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
                 xs[p] = fmar(hs.h2, vs[p], x[p]);
                 vs[p] = fmar(hs.h2, a[p], v[p]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = fmar((Real)2, vs[p], kx[p]);
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
                 xs[p] = fmar(hs.h, vs[p], x[p]);
                 vs[p] = fmar(hs.h, a[p], v[p]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = addr(kx[p], vs[p]);

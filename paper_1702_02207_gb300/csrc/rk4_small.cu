@@ -21,6 +21,7 @@
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -176,16 +177,26 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     for (int r = 0; r < R; ++r) src.load(q, g * R + r, x[r], v[r], cx[r], cv[r]);
 
     int buf = 0;
-    // acc[r] = -(B xs)[row g*R + r]
-    auto accel = [&](const Real (&xs)[R], Real (&acc)[R]) {
+    // acc[r] = -(B xs)[row g*R + r].  FP32: B = hi + lo; the lo product is formed
+    // at stage 1 (first == true) and reused by stages 2-4 ("frozen lo"): it
+    // differs from lo * xs by lo * (xs - x), a relative 2^-24 * omega h of the
+    // acceleration, far below the rounding of the hi product, and saves 3/4 of
+    // the lo multiply-adds.
+    Real lo1[R];
+    auto accel = [&](const Real (&xs)[R], Real (&acc)[R], bool first) {
         if constexpr (G == 1) {
             // row r sums its columns starting at the diagonal: j = r, r+1, ... (mod S)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 Real t = 0;
                 if constexpr (!F64) {
+                    if (first) {
 #pragma unroll
-                    for (int jj = 0; jj < S; ++jj) t = fmaf(bl[r][(r + jj) % S], xs[(r + jj) % S], t);
+                        for (int jj = 0; jj < S; ++jj) t = fmaf(bl[r][(r + jj) % S], xs[(r + jj) % S], t);
+                        lo1[r] = t;
+                    } else {
+                        t = lo1[r];
+                    }
                 }
 #pragma unroll
                 for (int jj = 0; jj < S; ++jj) t = fmar(bh[r][(r + jj) % S], xs[(r + jj) % S], t);
@@ -199,8 +210,13 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
             for (int r = 0; r < R; ++r) {
                 Real t = 0;
                 if constexpr (!F64) {
+                    if (first) {
 #pragma unroll
-                    for (int j = 0; j < S; ++j) t = fmaf(bl[r][j], xch[buf][grp][j], t);
+                        for (int j = 0; j < S; ++j) t = fmaf(bl[r][j], xch[buf][grp][j], t);
+                        lo1[r] = t;
+                    } else {
+                        t = lo1[r];
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < S; ++j) t = fmar(bh[r][j], xch[buf][grp][j], t);
@@ -216,7 +232,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     for (int64_t done = 0; done < n; done += every) {
         repeat_steps(every, [&]() {
             Real a[R], xs[R], kx[R], kv[R], vs[R];
-            accel(x, a);                                   // stage 1
+            accel(x, a, true);                             // stage 1
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = v[r];
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
                 xs[r] = fmar(hs.h2, v[r], x[r]);
                 vs[r] = fmar(hs.h2, a[r], v[r]);
             }
-            accel(xs, a);                                  // stage 2
+            accel(xs, a, false);                           // stage 2
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = fmar((Real)2, vs[r], kx[r]);
@@ -232,7 +248,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
                 xs[r] = fmar(hs.h2, vs[r], x[r]);
                 vs[r] = fmar(hs.h2, a[r], v[r]);
             }
-            accel(xs, a);                                  // stage 3
+            accel(xs, a, false);                           // stage 3
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = fmar((Real)2, vs[r], kx[r]);
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
                 xs[r] = fmar(hs.h, vs[r], x[r]);
                 vs[r] = fmar(hs.h, a[r], v[r]);
             }
-            accel(xs, a);                                  // stage 4
+            accel(xs, a, false);                           // stage 4
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = addr(kx[r], vs[r]);
@@ -317,49 +333,69 @@ __device__ __forceinline__ void pair_update(float2& x, float2& e, float2 k, floa
     x = t;
 }
 
-__global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys sys, const BatchIO io)
-{
-    const int64_t t = (int64_t)blockIdx.x * kPairThreads + threadIdx.x;
-    const int64_t q0 = 2 * t;
-    if (q0 >= io.n_inst) return;
-    const bool has1 = q0 + 1 < io.n_inst;
-    const int64_t q1 = has1 ? q0 + 1 : q0;       // odd count: lane 1 repeats lane 0, not stored
-    const int64_t s0 = sys.per_inst_sys ? q0 : 0, s1 = sys.per_inst_sys ? q1 : 0;
-    const float* b0 = sys.B32 + s0 * 8;          // [hi 2x2][lo 2x2]
-    const float* b1 = sys.B32 + s1 * 8;
+// Two instances of the 2-DOF FP32 step held by one thread (lanes .x and .y of
+// every float2).  Shared by the one-launch kernel and the balanced kernel so
+// that both issue exactly the same operations.
+struct Pair2 {
     float2 nbh[2][2], nbl[2][2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            nbh[r][j] = f2(-b0[r * 2 + j], -b1[r * 2 + j]);
-            nbl[r][j] = f2(-b0[4 + r * 2 + j], -b1[4 + r * 2 + j]);
-        }
-    const StepSize<false> hs0(io.h[io.h_per_inst ? q0 : 0]), hs1(io.h[io.h_per_inst ? q1 : 0]);
-    const float2 h = f2(hs0.h, hs1.h), h2 = f2(hs0.h2, hs1.h2), h6 = f2(hs0.h6, hs1.h6),
-                 h6lo = f2(hs0.h6lo, hs1.h6lo), two = f2(2.f, 2.f);
+    float2 h, h2, h6, h6lo;
     float2 x[2], v[2], ex[2], ev[2];
+    int64_t q0, q1;
+    bool has1;
+
+    // Instances q and q + 1 (q + 1 < n); an odd count repeats q in lane .y.
+    __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
+    {
+        q0 = q;
+        has1 = q0 + 1 < io.n_inst;
+        q1 = has1 ? q0 + 1 : q0;
+        const int64_t s0 = sys.per_inst_sys ? q0 : 0, s1 = sys.per_inst_sys ? q1 : 0;
+        const float* b0 = sys.B32 + s0 * 8;      // [hi 2x2][lo 2x2]
+        const float* b1 = sys.B32 + s1 * 8;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
-        const double va = io.v0[q0 * 2 + r], vb = io.v0[q1 * 2 + r];
-        x[r] = f2((float)xa, (float)xb);
-        v[r] = f2((float)va, (float)vb);
-        ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
-        ev[r] = f2((float)(va - (double)v[r].x), (float)(vb - (double)v[r].y));
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                nbh[r][j] = f2(-b0[r * 2 + j], -b1[r * 2 + j]);
+                nbl[r][j] = f2(-b0[4 + r * 2 + j], -b1[4 + r * 2 + j]);
+            }
+        const StepSize<false> hs0(io.h[io.h_per_inst ? q0 : 0]), hs1(io.h[io.h_per_inst ? q1 : 0]);
+        h = f2(hs0.h, hs1.h);
+        h2 = f2(hs0.h2, hs1.h2);
+        h6 = f2(hs0.h6, hs1.h6);
+        h6lo = f2(hs0.h6lo, hs1.h6lo);
     }
-    auto accel = [&](const float2 (&xs)[2], float2 (&a)[2]) {
+    __device__ __forceinline__ void load_initial(const BatchIO& io)
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
+            const double va = io.v0[q0 * 2 + r], vb = io.v0[q1 * 2 + r];
+            x[r] = f2((float)xa, (float)xb);
+            v[r] = f2((float)va, (float)vb);
+            ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
+            ev[r] = f2((float)(va - (double)v[r].x), (float)(vb - (double)v[r].y));
+        }
+    }
+    // Stage 1 forms the lo product and keeps it; stages 2-4 reuse it (frozen lo,
+    // as rk4_small_kernel).
+    __device__ __forceinline__ void accel(const float2 (&xs)[2], float2 (&a)[2], float2 (&lo)[2], bool first) const
+    {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {            // diagonal first, as rk4_small_kernel
-            float2 acc = __fmul2_rn(nbl[r][r], xs[r]);
-            acc = __ffma2_rn(nbl[r][1 - r], xs[1 - r], acc);
-            acc = __ffma2_rn(nbh[r][r], xs[r], acc);
+            if (first) {
+                lo[r] = __fmul2_rn(nbl[r][r], xs[r]);
+                lo[r] = __ffma2_rn(nbl[r][1 - r], xs[1 - r], lo[r]);
+            }
+            const float2 acc = __ffma2_rn(nbh[r][r], xs[r], lo[r]);
             a[r] = __ffma2_rn(nbh[r][1 - r], xs[1 - r], acc);
         }
-    };
-    auto step = [&]() {
-        float2 a[2], xs[2], kx[2], kv[2], vs[2];
-        accel(x, a);
+    }
+    __device__ __forceinline__ void step()
+    {
+        const float2 two = f2(2.f, 2.f);
+        float2 a[2], xs[2], kx[2], kv[2], vs[2], lo[2];
+        accel(x, a, lo, true);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = v[r];
@@ -367,7 +403,7 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
             xs[r] = __ffma2_rn(h2, v[r], x[r]);
             vs[r] = __ffma2_rn(h2, a[r], v[r]);
         }
-        accel(xs, a);
+        accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __ffma2_rn(two, vs[r], kx[r]);
@@ -375,7 +411,7 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
             xs[r] = __ffma2_rn(h2, vs[r], x[r]);
             vs[r] = __ffma2_rn(h2, a[r], v[r]);
         }
-        accel(xs, a);
+        accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __ffma2_rn(two, vs[r], kx[r]);
@@ -383,7 +419,7 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
             xs[r] = __ffma2_rn(h, vs[r], x[r]);
             vs[r] = __ffma2_rn(h, a[r], v[r]);
         }
-        accel(xs, a);
+        accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __fadd2_rn(kx[r], vs[r]);
@@ -391,37 +427,177 @@ __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys 
             pair_update(x[r], ex[r], kx[r], h6, h6lo);
             pair_update(v[r], ev[r], kv[r], h6, h6lo);
         }
-    };
-    const int64_t n = io.n_steps;
-    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (n > 0 ? n : 1);
-    int64_t ck = 0;
-    for (int64_t done = 0; done < n; done += every) {
-        for (int64_t base = 0; base < every; base += 0x40000000LL) {
-            const int32_t m = (int32_t)(every - base < 0x40000000LL ? every - base : 0x40000000LL);
+    }
+    __device__ __forceinline__ void steps(int64_t n)
+    {
+        for (int64_t base = 0; base < n; base += 0x40000000LL) {
+            const int32_t m = (int32_t)(n - base < 0x40000000LL ? n - base : 0x40000000LL);
 #pragma unroll 2
             for (int32_t it = 0; it < m; ++it) step();
         }
-        if (io.ckpt_every > 0 && io.x_traj) {
+    }
+    // Checkpoint ck (state after (ck + 1) * ckpt_every steps).
+    __device__ __forceinline__ void store_ckpt(const BatchIO& io, int64_t ck) const
+    {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
-                if (io.v_traj) io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)v[r].x + (double)ev[r].x;
-                if (has1) {
-                    io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
-                    if (io.v_traj) io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)v[r].y + (double)ev[r].y;
-                }
+        for (int r = 0; r < 2; ++r) {
+            io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            if (io.v_traj) io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)v[r].x + (double)ev[r].x;
+            if (has1) {
+                io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                if (io.v_traj) io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)v[r].y + (double)ev[r].y;
             }
         }
-        ++ck;
     }
+    __device__ __forceinline__ void store_final(const BatchIO& io) const
+    {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
-        io.v_out[q0 * 2 + r] = (double)v[r].x + (double)ev[r].x;
-        if (has1) {
-            io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
-            io.v_out[q1 * 2 + r] = (double)v[r].y + (double)ev[r].y;
+        for (int r = 0; r < 2; ++r) {
+            io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            io.v_out[q0 * 2 + r] = (double)v[r].x + (double)ev[r].x;
+            if (has1) {
+                io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                io.v_out[q1 * 2 + r] = (double)v[r].y + (double)ev[r].y;
+            }
         }
+    }
+    // Steps [first, last) of the horizon; checkpoints where ckpt_every divides
+    // the step count reached (first and last are multiples of ckpt_every when
+    // checkpoints are written).
+    __device__ __forceinline__ void run(const BatchIO& io, int64_t first, int64_t last, bool store)
+    {
+        if (io.ckpt_every > 0 && io.x_traj) {
+            for (int64_t done = first; done < last; done += io.ckpt_every) {
+                steps(io.ckpt_every);
+                if (store) store_ckpt(io, done / io.ckpt_every);
+            }
+        } else {
+            steps(last - first);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys sys, const BatchIO io)
+{
+    const int64_t t = (int64_t)blockIdx.x * kPairThreads + threadIdx.x;
+    if (2 * t >= io.n_inst) return;
+    Pair2 p;
+    p.init(sys, io, 2 * t);
+    p.load_initial(io);
+    p.run(io, 0, io.n_steps, true);
+    p.store_final(io);
+}
+
+// ---- balanced schedule for the 2-DOF FP32 batch --------------------------------
+//
+// A unit is 64 instances (one warp of Pair2 threads); one warp per SM
+// sub-partition already keeps the FP32 pipe busy.  With U units on P warps a
+// launch of one warp per unit leaves some sub-partitions with one unit more
+// than others (65,536 instances: 1,024 units on 608 sub-partitions, 2 against
+// an average of 1.68).  Instead the horizon of every unit is cut in blocks
+// (of ckpt_every steps, or single steps) and the U x Tb blocks are dealt to the
+// P warps in order, C = max(Tb, ceil(U Tb / P)) blocks each (McNaughton's
+// wrap-around rule for preemptive scheduling on identical machines).  A unit
+// cut between warps m and m+1 runs its first part at the start of warp m+1,
+// which then publishes the state; warp m runs the rest at its end.  Because
+// C >= Tb, warp m reaches that point no earlier (in its own progress) than
+// warp m+1 finishes the first part, so the wait is normally empty.  It is
+// bounded all the same: after 1 s plus the time the warp has run so far it
+// gives up, marks the error word and finishes the unit with NaN.
+constexpr int kBalWarps = 4;                 // one warp per sub-partition; one CTA per SM
+constexpr int kBalSmemBytes = 120 * 1024;    // reserves more than half the SM's shared memory
+
+struct BalanceSched {
+    int64_t units;          // U
+    int64_t blocks;         // Tb, blocks per unit
+    int64_t block_steps;    // steps per block
+    int64_t cap;            // C, blocks per warp
+    float2* xfer;           // [P][8][32] state of the unit cut at the start of warp p
+    unsigned* flag;         // [P], zero before the launch
+    int* err;               // error word (may be null)
+    int withhold;           // test hook: publish no hand-over, so that every wait runs out
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(kBalWarps * 32, 1)
+rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSched sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * kBalWarps + (threadIdx.x >> 5);
+    const int64_t total = sc.units * sc.blocks;
+    const int64_t p0 = m * sc.cap;
+    const int64_t p1 = p0 + sc.cap < total ? p0 + sc.cap : total;
+    const uint64_t t_start = global_ns();
+    for (int64_t pos = p0; pos < p1;) {
+        const int64_t u = pos / sc.blocks;
+        const int64_t j0 = u * sc.blocks, j1 = j0 + sc.blocks;
+        const int64_t end = j1 < p1 ? j1 : p1;
+        const int64_t q = u * 64 + 2 * lane;
+        const bool live = q < io.n_inst;
+        Pair2 p;
+        p.init(sys, io, live ? q : (io.n_inst - 1) & ~(int64_t)1);
+        if (pos > j0) {
+            // Started on warp m - 1's range: the first blocks of the unit, then hand over.
+            const int64_t nb = end - pos;
+            p.load_initial(io);
+            p.run(io, 0, nb * sc.block_steps, live);
+            float2* dst = sc.xfer + m * 8 * 32 + lane;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                dst[(0 + r) * 32] = p.x[r];
+                dst[(2 + r) * 32] = p.v[r];
+                dst[(4 + r) * 32] = p.ex[r];
+                dst[(6 + r) * 32] = p.ev[r];
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0 && !sc.withhold)
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sc.flag + m), "r"(1u) : "memory");
+        } else if (j1 > p1) {
+            // Continues on warp m + 1, which runs its first blocks: wait for them, finish.
+            const int64_t nb = end - pos;
+            const int64_t first = sc.blocks - nb;
+            const unsigned* f = sc.flag + m + 1;
+            const uint64_t t_wait = global_ns();
+            const uint64_t limit = 1000000000ull + (t_wait - t_start);
+            unsigned seen = 0;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(f) : "memory");
+                if (seen) break;
+                if (global_ns() - t_wait > limit) break;
+                __nanosleep(256);
+            }
+            const bool ok = __all_sync(0xffffffffu, seen != 0);
+            if (ok) {
+                const float2* src = sc.xfer + (m + 1) * 8 * 32 + lane;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    p.x[r] = src[(0 + r) * 32];
+                    p.v[r] = src[(2 + r) * 32];
+                    p.ex[r] = src[(4 + r) * 32];
+                    p.ev[r] = src[(6 + r) * 32];
+                }
+            } else {
+                if (lane == 0 && sc.err) atomicExch(sc.err, 1);
+                const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) p.x[r] = p.v[r] = p.ex[r] = p.ev[r] = f2(nan, nan);
+            }
+            p.run(io, first * sc.block_steps, sc.blocks * sc.block_steps, live);
+            if (live) p.store_final(io);
+        } else {
+            // The whole unit.
+            p.load_initial(io);
+            p.run(io, 0, sc.blocks * sc.block_steps, live);
+            if (live) p.store_final(io);
+        }
+        pos = end;
     }
 }
 
@@ -444,28 +620,31 @@ __global__ void __launch_bounds__(kTwoDofThreads) rk4_two_dof_packed_kernel(cons
     float2 x = f2((float)x0a, (float)x0b), v = f2((float)v0a, (float)v0b);
     float2 ex = f2((float)(x0a - (double)x.x), (float)(x0b - (double)x.y));
     float2 ev = f2((float)(v0a - (double)v.x), (float)(v0b - (double)v.y));
-    auto accel = [&](float2 xs) {
+    float2 lo;                                   // frozen lo product, as rk4_small_kernel
+    auto accel = [&](float2 xs, bool first) {
         const float2 xw = f2(xs.y, xs.x);
-        float2 acc = __fmul2_rn(dl, xs);
-        acc = __ffma2_rn(ol, xw, acc);
-        acc = __ffma2_rn(dh, xs, acc);
+        if (first) {
+            lo = __fmul2_rn(dl, xs);
+            lo = __ffma2_rn(ol, xw, lo);
+        }
+        const float2 acc = __ffma2_rn(dh, xs, lo);
         return __ffma2_rn(oh, xw, acc);
     };
     auto step = [&]() {
-        float2 a = accel(x);
+        float2 a = accel(x, true);
         float2 kx = v, kv = a;
         float2 xs = __ffma2_rn(h2, v, x), vs = __ffma2_rn(h2, a, v);
-        a = accel(xs);
+        a = accel(xs, false);
         kx = __ffma2_rn(two, vs, kx);
         kv = __ffma2_rn(two, a, kv);
         xs = __ffma2_rn(h2, vs, x);
         vs = __ffma2_rn(h2, a, v);
-        a = accel(xs);
+        a = accel(xs, false);
         kx = __ffma2_rn(two, vs, kx);
         kv = __ffma2_rn(two, a, kv);
         xs = __ffma2_rn(h, vs, x);
         vs = __ffma2_rn(h, a, v);
-        a = accel(xs);
+        a = accel(xs, false);
         kx = __fadd2_rn(kx, vs);
         kv = __fadd2_rn(kv, a);
         pair_update(x, ex, kx, h6, h6lo);
@@ -497,9 +676,11 @@ __global__ void __launch_bounds__(kTwoDofThreads) rk4_two_dof_packed_kernel(cons
     io.v_out[q * 2 + 1] = (double)v.y + (double)ev.y;
 }
 
-// Which 2-DOF FP32 kernel runs: "pair" (two instances per thread), "packed" (one
-// instance per thread, DOFs packed) or "generic" (rk4_small_kernel<2>); all give the
-// same bits.  CHO_TWO_DOF_KERNEL overrides the default.
+// Which 2-DOF FP32 kernel runs: "balanced" (the default: two instances per
+// thread on the balanced schedule), "pair" (two instances per thread, one warp
+// per 64 instances), "packed" (one instance per thread, DOFs packed) or
+// "generic" (rk4_small_kernel<2>); all give the same bits.  CHO_TWO_DOF_KERNEL
+// overrides the default.
 int two_dof_variant()
 {
     static int v = -1;
@@ -508,29 +689,86 @@ int two_dof_variant()
         v = 0;
         if (e && std::strcmp(e, "packed") == 0) v = 1;
         if (e && std::strcmp(e, "generic") == 0) v = 2;
+        if (e && std::strcmp(e, "pair") == 0) v = 3;
     }
     return v;
+}
+
+cudaError_t launch_pair2(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    const int64_t threads = (io.n_inst + 1) / 2;
+    const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rk4_pair2_kernel<<<(unsigned)blocks, kPairThreads, 0, st>>>(sys, io);
+    return cudaGetLastError();
+}
+
+// The balanced schedule when it helps (more units than warps, a cooperative
+// launch is available); otherwise the one-launch pair kernel.  The hand-over
+// buffer and flags are taken from the stream-ordered allocator and freed after
+// the kernel on the same stream, so concurrent calls on other streams do not
+// share them.
+cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    int dev = 0, sms = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t P = (int64_t)sms * kBalWarps;
+    const int64_t U = (io.n_inst + 63) / 64;
+    const bool ckpt = io.ckpt_every > 0 && io.x_traj;
+    const int64_t g = ckpt ? io.ckpt_every : 1;
+    const int64_t Tb = io.n_steps / g;
+    if (!coop || U <= P || Tb <= 0 || Tb > ((int64_t)1 << 62) / U) return launch_pair2(sys, io, st);
+    static bool attr_set[64] = {};
+    if (dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(rk4_pair2_balanced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBalSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    BalanceSched sc{};
+    sc.units = U;
+    sc.blocks = Tb;
+    sc.block_steps = g;
+    sc.cap = std::max(Tb, (U * Tb + P - 1) / P);
+    sc.err = sys.err;
+    const char* hook = std::getenv("CHO_TEST_WITHHOLD_HANDOVER");
+    sc.withhold = hook && hook[0] == '1' ? 1 : 0;
+    const size_t xfer_bytes = (size_t)P * 8 * 32 * sizeof(float2);
+    void* buf = nullptr;
+    e = cudaMallocAsync(&buf, xfer_bytes + (size_t)P * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    sc.xfer = (float2*)buf;
+    sc.flag = (unsigned*)((char*)buf + xfer_bytes);
+    e = cudaMemsetAsync(sc.flag, 0, (size_t)P * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        SmallSys a0 = sys;
+        BatchIO a1 = io;
+        void* args[] = {&a0, &a1, &sc};
+        e = cudaLaunchCooperativeKernel((const void*)rk4_pair2_balanced_kernel, dim3((unsigned)sms), dim3(kBalWarps * 32),
+                                        args, (size_t)kBalSmemBytes, st);
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 }  // namespace
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
-    if (sys.s == 2 && !fp64 && two_dof_variant() == 1) {
+    const int variant = two_dof_variant();
+    if (sys.s == 2 && !fp64 && variant == 1) {
         const int64_t blocks = (io.n_inst + kTwoDofThreads - 1) / kTwoDofThreads;
         if (blocks <= 0) return cudaSuccess;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
         rk4_two_dof_packed_kernel<<<(unsigned)blocks, kTwoDofThreads, 0, st>>>(sys, io);
         return cudaGetLastError();
     }
-    if (sys.s == 2 && !fp64 && two_dof_variant() == 0) {   // s = 1 is also padded to S = 2 but keeps the generic layout
-        const int64_t threads = (io.n_inst + 1) / 2;
-        const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
-        if (blocks <= 0) return cudaSuccess;
-        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-        rk4_pair2_kernel<<<(unsigned)blocks, kPairThreads, 0, st>>>(sys, io);
-        return cudaGetLastError();
-    }
+    // s = 1 is also padded to S = 2 but keeps the generic layout
+    if (sys.s == 2 && !fp64 && variant == 3) return launch_pair2(sys, io, st);
+    if (sys.s == 2 && !fp64 && variant == 0) return launch_pair2_balanced(sys, io, st);
     return dispatch<BatchSrc>(sys.S, fp64, io.n_inst, st, [&](auto& s) {
         s.sys = sys;
         s.io = io;

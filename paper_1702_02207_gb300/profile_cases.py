@@ -3,7 +3,7 @@
     python -m paper_1702_02207_gb300.profile_cases <case> [<case> ...]
 
 Cases (each one cho_integrate_batch call, a few MB of device memory):
-  pair      65,536 two-DOF systems, 1e4 steps, fp32_kahan   (rk4_pair2, the benchmark launch)
+  pair      65,536 two-DOF systems, 1e4 steps, fp32_kahan   (rk4_pair2_balanced, the benchmark launch)
   chain     512 chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain<4>)
   dense_tc  s = 128, 2048 instances, 500 steps, bf16x5       (rk4_dense_tc, one CTA per SM)
   dense_tc2 s = 256, 2048 instances, 200 steps, bf16x5       (rk4_dense_tc, 2-CTA clusters)

@@ -381,6 +381,77 @@ def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
             assert np.array_equal(res["pair"][k], res[variant][k]), (variant, k)
 
 
+_VARIANT_RUN = (
+    "import sys, numpy as np, torch\n"
+    "sys.path.insert(0, %r)\n"
+    "from paper_1702_02207_gb300 import cho, inputs\n"
+    "n_inst, n_steps, every = int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4])\n"
+    "cfg = inputs.two_dof_batch(n_inst=n_inst, n_steps=n_steps)\n"
+    "ctx = cho.cho_init(0)\n"
+    "s = cho.cho_create_system(ctx, 'two_dof', masses=cfg['masses'], springs=cfg['springs'])\n"
+    "d = torch.device('cuda:0')\n"
+    "o = cho.cho_integrate_batch(ctx, s, torch.as_tensor(cfg['x0'], device=d), torch.as_tensor(cfg['v0'], device=d),"
+    " torch.as_tensor(cfg['h'], device=d), n_steps, 'fp32_kahan', every, trajectory=every > 0)\n"
+    "torch.cuda.synchronize()\n"
+    "assert cho.cho_system_status(s) == cho.CHO_OK\n"
+    "np.savez(sys.argv[1], **{k: v.cpu().numpy() for k, v in o.items()})\n"
+) % ROOT_DIR
+
+
+@pytest.mark.parametrize("n_inst,n_steps,every", [(45001, 3000, 1000), (45001, 3000, 0), (38913, 7, 0),
+                                                  (100000, 13, 0)])
+def test_two_dof_balanced_schedule_is_bitwise_equal(tmp_path, n_inst, n_steps, every):
+    """The balanced schedule (instances' horizons cut between warps, state handed over through
+    global memory) gives the same bits as one warp per 64 instances: ragged last unit, odd
+    instance count, hand-over at checkpoint blocks and at single steps."""
+    import subprocess
+    import sys as _sys
+
+    res = {}
+    for variant in ("balanced", "pair"):
+        path = str(tmp_path / f"{variant}.npz")
+        env = dict(os.environ, CHO_TWO_DOF_KERNEL=variant)
+        subprocess.run([_sys.executable, "-c", _VARIANT_RUN, path, str(n_inst), str(n_steps), str(every)],
+                       check=True, env=env, timeout=300)
+        res[variant] = np.load(path)
+    for k in res["pair"].files:
+        assert np.isfinite(res["balanced"][k]).all(), k
+        assert np.array_equal(res["pair"][k], res["balanced"][k]), k
+
+
+def test_balanced_handover_wait_gives_up_and_reports(ctx):
+    """Test hook CHO_TEST_WITHHOLD_HANDOVER=1: no warp publishes its hand-over, every wait runs
+    out (after about a second), the units concerned finish as NaN, the call reports
+    CHO_ETIMEOUT, and the context stays usable."""
+    import torch
+
+    cfg = inputs.two_dof_batch(n_inst=45001, n_steps=300)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        os.environ["CHO_TEST_WITHHOLD_HANDOVER"] = "1"
+        try:
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 300, "fp32_kahan")
+            assert ei.value.status == cho.CHO_ETIMEOUT
+            o = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                        torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                        300, "fp32_kahan")
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_system_status(sys_)
+            assert ei.value.status == cho.CHO_ETIMEOUT
+            assert np.isnan(o["x"].cpu().numpy()).any()
+        finally:
+            del os.environ["CHO_TEST_WITHHOLD_HANDOVER"]
+        assert cho.cho_system_status(sys_) == cho.CHO_OK
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 300, "fp32_kahan")
+        idx = sample_indices(45001, 64)
+        ref = oracle_run(cfg, idx=idx)
+        assert rel_err(out["x"][idx][:, None], ref["x"][:, None]).max() < TOL_FP32
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
 # ---- full-size workloads, sampled against the oracle ------------------------------------------
 
 # Over the full 5e3-step horizon bf16x5 and bf16x6 stay within 1e-5 (each K chunk in its own
