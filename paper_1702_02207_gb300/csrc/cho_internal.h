@@ -109,7 +109,7 @@ struct DenseSys {
     const double* B64;      // [s_pad][s_pad] = B^T, zero padded
     const float* B32;       // [2][s_pad][s_pad] (hi, lo) of B^T, zero padded
     const uint16_t* Bbf;    // tensor-core kernel: shared-memory images of the BF16 pieces of B
-    int32_t s_tc;           // tensor-core padded size: 128 or 256 (0: no tensor-core data)
+    int32_t s_tc;           // tensor-core layout: 64 (two tiles on a block diagonal), 128 or 256 (0: none)
     int* err;               // device error word of the tensor-core kernel (bounded waits)
     int32_t stall_mma;      // test hook: issue no MMA, so the bounded wait on it runs out
 };

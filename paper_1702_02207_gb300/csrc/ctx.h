@@ -50,7 +50,7 @@ struct cho_system_impl {
     int32_t path = 0;
     int32_t S = 0;          // rk4_small padded size
     int32_t s_pad = 0;      // rk4_dense padded size (CUDA cores)
-    int32_t s_tc = 0;       // rk4_dense padded size (tensor cores)
+    int32_t s_tc = 0;       // rk4_dense tensor-core layout: 64, 128 or 256 (0: none)
     double omega_max = 0.0;
     std::vector<double> omegas;
     // host copies of the description

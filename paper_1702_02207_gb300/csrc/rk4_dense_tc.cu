@@ -20,12 +20,22 @@
 // chunk sums on the CUDA cores in FP32 round-to-nearest (s = 256: 5.9e-6, for
 // 10 % more time); bf16x3, whose truncation error dominates, keeps one.
 
-// Work split.  s <= 128: one CTA per tile of 32 instances.  128 < s <= 256: a
-// cluster of two CTAs per tile; CTA r owns rows [128 r, 128 r + 128) of B
-// (resident in its shared memory for the whole run) and the same rows of the
+// Work split.  s <= 64: one CTA per 64 instances, two tiles of 32 stacked along
+// the 128 rows against the block-diagonal [B 0; 0 B] (the MMA shape is fixed at
+// 128 rows; a padded 64 x 64 B would leave half of every MMA idle).  64 < s <=
+// 128: one CTA per tile of 32 instances.  In both, B's BF16 pieces are written
+// once into tensor memory next to the accumulators and the MMAs read their A
+// operand from there.  128 < s <= 256: a cluster of two CTAs per tile; CTA r
+// owns rows [128 r, 128 r + 128) of B (resident in its shared memory for the
+// whole run, fetched once with bulk (TMA) copies) and the same rows of the
 // state, and writes its rows of each stage's Xs into both CTAs' shared memory,
-// so each CTA multiplies its 128 rows of B by the full Xs.  B is fetched once
-// per CTA with bulk (TMA) copies; it is never re-read from L2.
+// so each CTA multiplies its 128 rows of B by the full Xs.
+//
+// Measured cost (GB300, 128 x 32 x 16 BF16 MMAs): about 75 cycles per MMA
+// whether A comes from shared or tensor memory, plus about 1,100 cycles per
+// stage for publishing Xs, the barrier, the completion wait and the epilogue;
+// the MMA issue loop is unrolled with constant operand offsets (computing
+// descriptors per MMA cost another ~15 cycles each).
 //
 // Per CTA: 16 warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of its
 // 128-row block) and columns 8 (w / 4) .. +7 (instances); each thread keeps the
@@ -125,6 +135,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// The same MMA with the A operand (128 rows x 16 K, two BF16 per 32-bit column)
+// read from tensor memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, uint4 lo, uint4 hi)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(lo.x),
+                 "r"(lo.y), "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -140,6 +168,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Two accumulators' x8 column groups (kNT columns apart) with a single wait.
+__device__ __forceinline__ void tmem_ld8_x2(uint32_t taddr, float (&v)[2][8])
+{
+    uint32_t r[2][8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+          "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+          "=r"(r[1][6]), "=r"(r[1][7])
+        : "r"(taddr), "r"(taddr + (uint32_t)kNT)
+        : "memory");
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[g][i] = __uint_as_float(r[g][i]);
 }
 
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -175,8 +222,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 // Partial products (piece of B, piece of Xs), smallest first, for bf16x3 / x5 / x6.
-__constant__ int kProdA[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
-__constant__ int kProdB[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
+// (compile-time tables: the MMA issue loop is fully unrolled, so every operand
+// offset and accumulate flag is a constant)
+__host__ __device__ constexpr int prod_a(int tbl, int pr)
+{
+    constexpr int t[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
+    return t[tbl][pr];
+}
+__host__ __device__ constexpr int prod_b(int tbl, int pr)
+{
+    constexpr int t[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
+    return t[tbl][pr];
+}
 
 // Batch form: FP64 arrays in and out, shared step count, checkpoints.
 struct TcBatchSrc {
@@ -241,25 +298,44 @@ struct TcSlotSrc {
     __device__ void book(int64_t q, int64_t ran) const { io.slots[io.slot_ids[q]].remaining -= ran; }
 };
 
-// PA pieces of B, PB pieces of Xs, CS CTAs per cluster.
-template <int PA, int PB, int CS, int NACC, class Src>
+// One CTA per tile (s <= 128): the B pieces live in tensor memory next to the
+// accumulators and the MMAs read A from there, so that shared memory serves only
+// the narrow Xs operand (an MMA of 128 x 32 x 16 reads 4 KB of A and 1 KB of Xs;
+// from shared memory the A reads set its pace).  Clusters (s <= 256) keep B in
+// shared memory: their 16 accumulators and B pieces would not fit 512 columns.
+constexpr bool tc_a_in_tmem(int CS) { return CS == 1; }
+constexpr uint32_t tc_pow2(uint32_t n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512))); }
+constexpr uint32_t tc_tmem_cols(int PA, int CS, int NACC)
+{
+    return tc_pow2((uint32_t)(NACC * kNT + (tc_a_in_tmem(CS) ? PA * 8 * CS * 8 : 0)));
+}
+
+// PA pieces of B, PB pieces of Xs, CS CTAs per cluster, NACC accumulators, PK
+// tiles stacked along the rows (PK = 2 for s <= 64: rows 64 h + i hold DOF i of
+// the tile's half h, against the block-diagonal [B 0; 0 B]).
+template <int PA, int PB, int CS, int NACC, int PK, class Src>
 __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
 {
+    static_assert(PK == 1 || CS == 1, "stacked tiles use one CTA");
+    constexpr int NI = kNT * PK;                     // instances per CTA
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
-    constexpr int A_BYTES = PA * KC * kAChunk;
+    constexpr bool ATM = tc_a_in_tmem(CS);           // B pieces in tensor memory (else shared)
+    constexpr int A_BYTES = ATM ? 0 : PA * KC * kAChunk;
     constexpr int X_BYTES = PB * KC * kXChunk;
     constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
+    constexpr int ACOL = NACC * kNT;                 // first TMEM column of the B pieces
+    constexpr uint32_t TCOLS = tc_tmem_cols(PA, CS, NACC);
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces
+    unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces (shared-memory form)
     unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
     __shared__ __align__(8) uint64_t bar_load;
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag[2];
-    __shared__ float sh_h[kNT][4];                   // h, h/2, h/6 hi, h/6 lo of each instance
-    __shared__ long long sh_steps[kNT];              // steps of each instance in this launch
+    __shared__ float sh_h[NI][4];                    // h, h/2, h/6 hi, h/6 lo of each instance
+    __shared__ long long sh_steps[NI];               // steps of each instance in this launch
     __shared__ long long sh_max_steps;
-    __shared__ int sh_bad[kNT];
+    __shared__ int sh_bad[NI];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -269,9 +345,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const int quad = warp & 3;
     const int colgrp = warp >> 2;
     const int row = 32 * quad + lane;                // row of this CTA's block
-    const int k = 128 * (int)rank + row;             // DOF
+    const int k = 128 * (int)rank + row;             // K index of the MMA (row of Xs)
+    const int kio = PK == 2 ? (row & 63) : k;        // DOF
+    const int ib = PK == 2 ? (row >> 6) * kNT : 0;   // first instance slot of this row's tile half
     const int s = sys.s;
-    const bool live_row = k < s;
+    const bool live_row = kio < s;
     const int n0 = colgrp * kCPT;                    // first instance column of this thread
 
     // ---- set-up: barriers, TMEM, B into shared memory ----
@@ -281,8 +359,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         abort_flag[0] = abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kNT) {
-        const int64_t q = tile * kNT + tid;
+    if (tid < NI) {
+        const int64_t q = tile * NI + tid;
         const bool live = q < src.count();
         const double hd = live ? src.h(q) : 1.0;
         sh_steps[tid] = live ? (long long)src.steps(q) : 0;
@@ -295,7 +373,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kNT * NACC));
+                     "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -318,30 +396,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         return abort_flag[0] == 0 && abort_flag[1] == 0;
     };
     bool ok = true;
-    if (tid == 0) {
-        const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * kBPieces * KC * kAChunk;
-        mbar_expect_tx(&bar_load, A_BYTES);
-        for (int off = 0; off < A_BYTES; off += 16384) {
-            const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
-            bulk_g2s(sA + off, src + off, (uint32_t)n, &bar_load);
+    if constexpr (ATM) {
+        // Row `row` of each 16-wide chunk of each piece into this warp's TMEM lanes:
+        // the chunk's two 16-byte core-matrix rows (K 0-7, K 8-15) are its 8 columns.
+        const unsigned char* img = (const unsigned char*)sys.Bbf;
+        const uint32_t roff = (uint32_t)((row / 8) * 256 + (row % 8) * 16);
+        for (int idx = colgrp; idx < PA * KC; idx += 4) {
+            const unsigned char* chunk = img + (size_t)idx * kAChunk;   // piece idx / KC, chunk idx % KC
+            const uint4 lo = *(const uint4*)(chunk + roff);
+            const uint4 hi = *(const uint4*)(chunk + roff + 128);
+            tmem_st8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ACOL + idx * 8), lo, hi);
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ok = agree(true);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    } else {
+        if (tid == 0) {
+            const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * kBPieces * KC * kAChunk;
+            mbar_expect_tx(&bar_load, A_BYTES);
+            for (int off = 0; off < A_BYTES; off += 16384) {
+                const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
+                bulk_g2s(sA + off, src + off, (uint32_t)n, &bar_load);
+            }
+        }
+        ok = agree(mbar_wait(&bar_load, 0));
     }
-    ok = agree(mbar_wait(&bar_load, 0));
 
     // ---- state of this thread: row k of instances n0 .. n0+7 ----
     float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
 #pragma unroll
     for (int j = 0; j < kCPT; ++j) {
-        const int64_t q = tile * kNT + n0 + j;
+        const int64_t q = tile * NI + ib + n0 + j;
         if (live_row && q < src.count()) {
-            src.load(q, k, x[j], v[j], cx[j], cv[j]);
+            src.load(q, kio, x[j], v[j], cx[j], cv[j]);
         } else {
             x[j] = v[j] = cx[j] = cv[j] = 0.f;
         }
     }
     if (tid == 0) {
         long long m = 0;
-        for (int j = 0; j < kNT; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+        for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
         sh_max_steps = m;
     }
     __syncthreads();
@@ -356,7 +451,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
     const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
+    // operand descriptors of chunk 0; the others add their byte offset / 16
+    // (shared-memory addresses stay below 2^18, inside the 14-bit field)
+    const uint64_t bdesc0 = smem_desc(smem_u32(sX), 512, 128);
+    const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
     uint32_t phase = 0;
+    bool prev_done = true;                           // one CTA: the last wait not yet agreed on
 
     // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
     auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
@@ -379,22 +479,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
         asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (CS > 1) cluster_sync(); else __syncthreads();
+        // One CTA: this barrier also settles the previous stage's wait (a thread
+        // past its wait knows the MMAs that read Xs and wrote TMEM are complete,
+        // and every thread reaches here after its TMEM loads).  Clusters keep a
+        // barrier at the end of the stage: the peer writes into this CTA's Xs.
+        bool go = true;
+        if (CS > 1) cluster_sync(); else go = agree(prev_done);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!go) {
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) a[j] = 0.f;
+            return false;
+        }
         if (tid == 0 && !sys.stall_mma) {
-            const uint32_t a0 = smem_u32(sA), x0 = smem_u32(sX);
             uint32_t started = 0;                    // accumulators already written this stage
 #pragma unroll
             for (int pr = 0; pr < NPROD; ++pr) {
                 constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
-                const int ia = kProdA[TBL][pr];
-                const int ib = kProdB[TBL][pr];
+                const int ia = prod_a(TBL, pr);
+                const int ib = prod_b(TBL, pr);
+                // descriptor address fields count 16-byte units; clusters (16 chunks) unroll
+                // by 4 only: fully unrolled, the offsets held in registers spill
+                uint64_t bd = bdesc0 + (uint64_t)((ib * KC * kXChunk) >> 4);
+                uint64_t ad = adesc0 + (uint64_t)((ia * KC * kAChunk) >> 4);
+                uint32_t at = tmem + (uint32_t)(ACOL + ia * KC * 8);
+#pragma unroll(CS == 1 ? KC : 4)
                 for (int c = 0; c < KC; ++c) {
-                    const uint64_t ad = smem_desc(a0 + (uint32_t)((ia * KC + c) * kAChunk), 128, 256);
-                    const uint64_t bd = smem_desc(x0 + (uint32_t)((ib * KC + c) * kXChunk), 512, 128);
                     const int slot = c % NACC;
-                    mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
+                    if constexpr (ATM) {
+                        mma_bf16_ta(tmem + (uint32_t)(slot * kNT), at, bd, idesc, (started >> slot) & 1u);
+                    } else {
+                        mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
+                    }
                     started |= 1u << slot;
+                    bd += kXChunk >> 4;
+                    ad += kAChunk >> 4;
+                    at += 8;
                 }
             }
             mma_commit(&bar_mma);
@@ -405,20 +525,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
         if (done) {
-            tmem_ld8(taddr, acc);
+            if constexpr (NACC == 1) {
+                tmem_ld8(taddr, acc);
+            } else {
+                static_assert(NACC % 2 == 0, "accumulators are read two at a time");
 #pragma unroll
-            for (int k2 = 1; k2 < NACC; ++k2) {
-                float part[kCPT];
-                tmem_ld8(taddr + (uint32_t)(k2 * kNT), part);
+                for (int g2 = 0; g2 < NACC / 2; ++g2) {
+                    float part[2][kCPT];
+                    tmem_ld8_x2(taddr + (uint32_t)(2 * g2 * kNT), part);
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(acc[j], part[j]);
+                    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+                        for (int j = 0; j < kCPT; ++j) acc[j] = (g2 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
+                    }
+                }
             }
         }
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        // every CTA of the cluster has its MMA done (so Xs may be rewritten) and agrees on aborts
-        return agree(done);
+        // clusters: every CTA has its MMA done (so Xs may be rewritten) and agrees on aborts
+        if (CS > 1) return agree(done);
+        prev_done = done;
+        return true;
     };
 
     const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
@@ -430,7 +559,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             ok = stage(x, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[n0 + j][1];
+                const float h2 = sh_h[ib + n0 + j][1];
                 kx[j] = v[j];
                 kv[j] = a[j];
                 xs[j] = __fmaf_rn(h2, v[j], x[j]);
@@ -439,7 +568,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[n0 + j][1];
+                const float h2 = sh_h[ib + n0 + j][1];
                 kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
                 kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
                 xs[j] = __fmaf_rn(h2, vs[j], x[j]);
@@ -448,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                const float h = sh_h[n0 + j][0];
+                const float h = sh_h[ib + n0 + j][0];
                 kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
                 kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
                 xs[j] = __fmaf_rn(h, vs[j], x[j]);
@@ -457,8 +586,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (ok) ok = stage(xs, a);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                if (step < sh_steps[n0 + j]) {       // instances past their count hold still
-                    const float h6 = sh_h[n0 + j][2], h6l = sh_h[n0 + j][3];
+                if (step < sh_steps[ib + n0 + j]) {       // instances past their count hold still
+                    const float h6 = sh_h[ib + n0 + j][2], h6l = sh_h[ib + n0 + j][3];
                     kx[j] = addr(kx[j], vs[j]);
                     kv[j] = addr(kv[j], a[j]);
                     comp_update(x[j], cx[j], kx[j], h6, h6l);
@@ -470,47 +599,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if (live_row) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) {
-                    const int64_t q = tile * kNT + n0 + j;
-                    if (q < src.count()) src.checkpoint(q, ck, k, x[j], v[j], cx[j], cv[j]);
+                    const int64_t q = tile * NI + ib + n0 + j;
+                    if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
                 }
             }
             ++ck;
         }
     }
+    if (CS == 1 && ok) ok = agree(prev_done);
     if (live_row) {
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) {
-            const int64_t q = tile * kNT + n0 + j;
+            const int64_t q = tile * NI + ib + n0 + j;
             if (q < src.count()) {
-                src.store(q, k, x[j], v[j], cx[j], cv[j]);
-                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[n0 + j] = 1;
+                src.store(q, kio, x[j], v[j], cx[j], cv[j]);
+                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
             }
         }
     }
     if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid < kNT) {
-        const int64_t q = tile * kNT + tid;
+    if (tid < NI) {
+        const int64_t q = tile * NI + tid;
         if (q < src.count()) {
             if (!ok) src.flag(q, CHO_ETIMEOUT);
             else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
             if (rank == 0) src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
         }
     }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNT * NACC));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
     if (CS > 1) cluster_sync();   // the peer may still write into this CTA's shared memory until here
 }
 
-template <int PA, int PB, int CS, int NACC, class Src>
+template <int PA, int PB, int CS, int NACC, int PK, class Src>
 cudaError_t launch_tc_n(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
-    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
-    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
+    static_assert(tc_tmem_cols(PA, CS, NACC) <= 512, "tensor memory holds 512 columns");
+    const size_t smem = (tc_a_in_tmem(CS) ? 0 : (size_t)PA * KC * kAChunk) + (size_t)PB * KC * kXChunk;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, PK, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (n_inst + kNT - 1) / kNT;
+    const int64_t tiles = (n_inst + kNT * PK - 1) / (kNT * PK);
     if (tiles <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(tiles * CS), 1, 1);
@@ -528,11 +659,11 @@ cudaError_t launch_tc_n(const DenseSys& sys, const Src& src, int64_t n_inst, cud
 }
 
 // bf16x3 accumulates in one TMEM accumulator, bf16x5/x6 in one per K chunk.
-template <int PA, int PB, int CS, class Src>
+template <int PA, int PB, int CS, int PK = 1, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int NACC = PA == 2 ? 1 : 8 * CS;
-    return launch_tc_n<PA, PB, CS, NACC>(sys, src, n_inst, st);
+    return launch_tc_n<PA, PB, CS, NACC, PK>(sys, src, n_inst, st);
 }
 
 
@@ -541,14 +672,17 @@ cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int
 {
     if (n_inst == 0) return cudaSuccess;
     if (!sys.Bbf || sys.s_tc == 0) return cudaErrorNotSupported;
-    const bool two = sys.s_tc == 256;
+    const bool two = sys.s_tc == 256, pack = sys.s_tc == 64;
     switch (prec) {
         case CHO_DENSE_BF16X3:
+            if (pack) return launch_tc<2, 2, 1, 2>(sys, src, n_inst, st);
             return two ? launch_tc<2, 2, 2>(sys, src, n_inst, st) : launch_tc<2, 2, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X5:
+            if (pack) return launch_tc<3, 2, 1, 2>(sys, src, n_inst, st);
             return two ? launch_tc<3, 2, 2>(sys, src, n_inst, st) : launch_tc<3, 2, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
             if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
+            if (pack) return launch_tc<3, 3, 1, 2>(sys, src, n_inst, st);
             return launch_tc<3, 3, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
@@ -603,16 +737,23 @@ cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B)
         sys->s_tc = 0;
         return cudaSuccess;
     }
-    const int st = s <= 128 ? 128 : 256;
-    const int CS = st / 128, KC = st / 16;
+    // s <= 64: two copies of B on the diagonal of a 128 x 128 block (two tiles of
+    // instances stacked along the rows); else B padded to 128 or 256.
+    const int st = s <= 64 ? 64 : (s <= 128 ? 128 : 256);
+    const int CS = st == 256 ? 2 : 1, KC = st == 256 ? 16 : 8;
     sys->s_tc = st;
     const size_t per_rank = (size_t)kBPieces * KC * kAChunk;
     std::vector<unsigned char> img((size_t)CS * per_rank, 0);
     for (int r = 0; r < CS; ++r)
         for (int m = 0; m < 128; ++m) {
-            const int i = 128 * r + m;
-            for (int kk = 0; kk < st; ++kk) {
-                double rem = (i < s && kk < s) ? B[(size_t)i * s + kk] : 0.0;
+            for (int kk = 0; kk < 16 * KC; ++kk) {
+                int i = 128 * r + m, j = kk;
+                if (st == 64) {
+                    if (m / 64 != kk / 64) continue;
+                    i = m % 64;
+                    j = kk % 64;
+                }
+                double rem = (i < s && j < s) ? B[(size_t)i * s + j] : 0.0;
                 for (int p = 0; p < kBPieces; ++p) {
                     const uint16_t b = bf16_bits((float)rem);
                     rem -= (double)bf16_value(b);
