@@ -282,12 +282,12 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
 
     res = {}
 
-    def sampled_err(sys_, cfg, prec, n_sample=2, every=625):
+    def sampled_err(sys_, cfg, prec, n_sample=2, every=625, poly=0):
         """max relative error of a few instances against the oracle (x and v, over checkpoints)."""
         import oracle
 
         k = cfg["x0"].shape[0]
-        idx = np.array([0, k - 1][:n_sample])
+        idx = np.array([0, k - 1][:n_sample]) if n_sample <= 2 else np.linspace(0, k - 1, n_sample).astype(int)
         x0 = torch.as_tensor(cfg["x0"][idx], device=dev)
         v0 = torch.as_tensor(cfg["v0"][idx], device=dev)
         h = torch.as_tensor(cfg["h"][idx], device=dev)
@@ -297,7 +297,8 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                                    cfg["n_steps"], every, threads=n_sample)
         else:
             s2 = cho.cho_create_system(ctx, "chain", masses=cfg["masses"][idx], springs=cfg["springs"][idx])
-            r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
+            r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
+                                        poly_jump=poly)
             cho.cho_destroy_system(s2)
             ref = oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx], cfg["v0"][idx],
                                    cfg["h"][idx], cfg["n_steps"], every, threads=n_sample)
@@ -308,21 +309,36 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
             e = max(e, float(np.max(np.max(np.abs(g - ref[key]), axis=(1, 2)) / np.max(np.abs(ref[key]), axis=(1, 2)))))
         return {"max": e, "instances": int(len(idx))}
 
-    def timed(sys_, cfg, prec, n):
+    def timed(sys_, cfg, prec, n, poly=0):
         x0 = torch.as_tensor(cfg["x0"], device=dev)
         v0 = torch.as_tensor(cfg["v0"], device=dev)
         h = torch.as_tensor(cfg["h"], device=dev)
         out = {"x": torch.empty_like(x0), "v": torch.empty_like(v0)}
-        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, min(n, 100), prec, out=out, stream=stream)
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, 8 * max(poly, 1), prec, out=out, stream=stream,
+                                poly_jump=poly)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
-        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, n, prec, out=out, stream=stream)
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, n, prec, out=out, stream=stream, poly_jump=poly)
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3
 
     alu_peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+    # The polynomial form of the headline workload: the same RK4 map, k steps per update
+    # y <- y + (P(hA)^k - I) y; its own work is 36 flop per instance-update (16 FMA + 4 adds).
+    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS)
+    s_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
+    for k in (1, 5, 25):
+        t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"], poly=k)
+        dof = cfg["x0"].size * cfg["n_steps"]
+        ach = N_INST * (cfg["n_steps"] // k) * 36 / t / 1e12
+        res[f"two_dof_x65536_poly_k{k}_fp32_kahan"] = {
+            "value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+            "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan", n_sample=8, every=125, poly=k),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                         "note": "flops of the polynomial form itself (36 per instance-update)"}}
+    cho.cho_destroy_system(s_)
     cfg = inputs.chain_batch()
     s_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
     t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])

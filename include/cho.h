@@ -128,7 +128,15 @@ typedef struct cho_system_desc {
  *                             state after (c + 1) * ckpt_every steps
  *   energy (optional)         (n_inst, n_steps / ckpt_every): energy of each checkpoint,
  *                             1/2 v^T M v + 1/2 x^T K x in FP64; needs x_traj and v_traj
- * x_out/v_out may alias x0/v0.  ckpt_every must divide n_steps when it is non-zero. */
+ * x_out/v_out may alias x0/v0.  ckpt_every must divide n_steps when it is non-zero.
+ *
+ * Polynomial form (poly_jump = k >= 1).  For the linear system y' = A y, A = [[0, I], [-B, 0]],
+ * one classical RK4 step is exactly y <- P(hA) y with P(z) = 1 + z + z^2/2 + z^3/6 + z^4/24
+ * (the four stages of Section 3 composed).  The library forms E = P(hA)^k - I per instance in
+ * FP64 and advances y <- y + E y (FP32: E as FP32 pairs, compensated state), k steps per
+ * update: the same result up to rounding with fewer dependent operations.  Supported for
+ * s = 2 systems (TWO_DOF, or CHAIN with s = 2) in CHO_FP64 and CHO_FP32_KAHAN; k must divide
+ * n_steps and ckpt_every.  Errors: CHO_EINVAL otherwise. */
 typedef struct cho_batch_desc {
     cho_system system;
     int64_t n_inst;
@@ -138,7 +146,8 @@ typedef struct cho_batch_desc {
     const double* v0;
     const double* h;
     int32_t h_per_inst;
-    int32_t reserved0;
+    int32_t poly_jump;      /* 0: RK4 stage by stage (Section 3's D(1)..D(4)).  k >= 1: the
+                               polynomial form of the same map, k steps at a time (see below) */
     int64_t n_steps;
     int64_t ckpt_every;
     double* x_out;

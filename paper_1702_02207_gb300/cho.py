@@ -58,7 +58,7 @@ class cho_system_desc(ctypes.Structure):
 class cho_batch_desc(ctypes.Structure):
     _fields_ = [("system", ctypes.c_void_p), ("n_inst", ctypes.c_int64), ("prec", ctypes.c_int32),
                 ("mem", ctypes.c_int32), ("x0", ctypes.c_void_p), ("v0", ctypes.c_void_p),
-                ("h", ctypes.c_void_p), ("h_per_inst", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("h", ctypes.c_void_p), ("h_per_inst", ctypes.c_int32), ("poly_jump", ctypes.c_int32),
                 ("n_steps", ctypes.c_int64), ("ckpt_every", ctypes.c_int64),
                 ("x_out", ctypes.c_void_p), ("v_out", ctypes.c_void_p), ("x_traj", ctypes.c_void_p),
                 ("v_traj", ctypes.c_void_p), ("energy", ctypes.c_void_p)]
@@ -241,7 +241,7 @@ def cho_destroy_system(system):
 # ---- batches -----------------------------------------------------------------------
 
 def _batch(fn_name, ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_every=0, trajectory=False,
-           energy=False, out=None, stream=None):
+           energy=False, out=None, stream=None, poly_jump=0):
     prec = PRECS.get(prec, prec)
     _, s, _ = cho_system_info(system)
     device = _is_cuda(x0)
@@ -283,6 +283,7 @@ def _batch(fn_name, ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_every=0
     b.mem = mem
     b.x0, b.v0, b.h = _ptr(x0), _ptr(v0), _ptr(h)
     b.h_per_inst = h_per_inst
+    b.poly_jump = int(poly_jump)
     b.n_steps = int(n_steps)
     b.ckpt_every = int(ckpt_every)
     b.x_out, b.v_out = _ptr(res["x"]), _ptr(res["v"])
@@ -294,11 +295,12 @@ def _batch(fn_name, ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_every=0
 
 
 def cho_integrate_batch(ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_every=0, trajectory=False,
-                        energy=False, out=None, stream=None):
+                        energy=False, out=None, stream=None, poly_jump=0):
     """Integrate a batch (see include/cho.h).  Returns a dict with x, v and, when asked, x_traj,
-    v_traj (n_inst, n_steps // ckpt_every, s) and energy (n_inst, n_steps // ckpt_every)."""
+    v_traj (n_inst, n_steps // ckpt_every, s) and energy (n_inst, n_steps // ckpt_every).
+    ``poly_jump`` = k >= 1 selects the polynomial form (k RK4 steps per update, s = 2)."""
     return _batch("cho_integrate_batch", ctx, system, x0, v0, h, n_steps, prec, ckpt_every, trajectory,
-                  energy, out, stream)
+                  energy, out, stream, poly_jump)
 
 
 def cho_integrate_plain(ctx, system, x0, v0, h, n_steps, out=None, stream=None):

@@ -444,6 +444,16 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     if ((b->x_traj || b->v_traj) && b->ckpt_every == 0)
         return fail(CHO_EINVAL, "%s: trajectories need ckpt_every > 0", who);
     const int p = b->prec;
+    if (b->poly_jump < 0) return fail(CHO_EINVAL, "%s: poly_jump < 0", who);
+    if (b->poly_jump > 0) {
+        if (plain_form) return fail(CHO_EINVAL, "%s: the plain form runs RK4 stage by stage", who);
+        if (sys->path != PATH_SMALL || sys->s != 2)
+            return fail(CHO_EINVAL, "%s: the polynomial form is built for s = 2 systems", who);
+        if (p != CHO_FP64 && p != CHO_FP32_KAHAN)
+            return fail(CHO_EINVAL, "%s: the polynomial form runs in CHO_FP64 or CHO_FP32_KAHAN", who);
+        if (b->n_steps % b->poly_jump != 0 || (b->ckpt_every > 0 && b->ckpt_every % b->poly_jump != 0))
+            return fail(CHO_EINVAL, "%s: poly_jump must divide n_steps and ckpt_every", who);
+    }
     if (plain_form) {
         if (p != CHO_FP64) return fail(CHO_EINVAL, "%s: the plain form is FP64 only", who);
         if (b->x_traj || b->v_traj || b->energy) return fail(CHO_EINVAL, "%s: no checkpoints in the plain form", who);
@@ -501,6 +511,7 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     io.n_steps = b->n_steps;
     io.ckpt_every = b->ckpt_every;
     io.n_ck = b->ckpt_every > 0 ? b->n_steps / b->ckpt_every : 0;
+    io.poly_jump = b->poly_jump;
     io.x_out = b->x_out;
     io.v_out = b->v_out;
     io.x_traj = b->x_traj;

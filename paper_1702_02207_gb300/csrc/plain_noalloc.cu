@@ -104,6 +104,8 @@ extern "C" cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_
     if (b->mem != CHO_MEM_DEVICE)
         return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: device pointers only (host arrays would need staging)");
     if (b->prec != CHO_FP64) return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: the plain form is FP64 only");
+    if (b->poly_jump != 0)
+        return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: the plain form runs RK4 stage by stage");
     if (sys->s > kNoAllocMaxS)
         return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: s = %d exceeds the fixed scratch limit of %d DOF",
                     sys->s, kNoAllocMaxS);

@@ -22,6 +22,7 @@
 #include "../../include/cho.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 
@@ -333,22 +334,85 @@ __device__ __forceinline__ void pair_update(float2& x, float2& e, float2 k, floa
     x = t;
 }
 
-// Two instances of the 2-DOF FP32 step held by one thread (lanes .x and .y of
-// every float2).  Shared by the one-launch kernel and the balanced kernel so
-// that both issue exactly the same operations.
-struct Pair2 {
-    float2 nbh[2][2], nbl[2][2];
-    float2 h, h2, h6, h6lo;
+// Compensated x += k (the increment without a step-size factor).
+__device__ __forceinline__ void pair_add(float2& x, float2& e, float2 k)
+{
+    const float2 m1 = f2(-1.f, -1.f);
+    const float2 y = __fadd2_rn(k, e);
+    const float2 t = __fadd2_rn(x, y);
+    const float2 d = __ffma2_rn(x, m1, t);       // t - x
+    e = __ffma2_rn(d, m1, y);                    // y - (t - x)
+    x = t;
+}
+
+// State of two 2-DOF instances held by one thread (lanes .x and .y of every
+// float2): x, v and their compensations, FP32.  An odd instance count repeats
+// the last instance in lane .y, which is never stored.
+struct Pair2State {
     float2 x[2], v[2], ex[2], ev[2];
     int64_t q0, q1;
     bool has1;
 
-    // Instances q and q + 1 (q + 1 < n); an odd count repeats q in lane .y.
-    __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
+    __device__ __forceinline__ void set_instances(const BatchIO& io, int64_t q)
     {
         q0 = q;
         has1 = q0 + 1 < io.n_inst;
         q1 = has1 ? q0 + 1 : q0;
+    }
+    __device__ __forceinline__ void load_initial(const BatchIO& io)
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
+            const double va = io.v0[q0 * 2 + r], vb = io.v0[q1 * 2 + r];
+            x[r] = f2((float)xa, (float)xb);
+            v[r] = f2((float)va, (float)vb);
+            ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
+            ev[r] = f2((float)(va - (double)v[r].x), (float)(vb - (double)v[r].y));
+        }
+    }
+    // The eight state registers in a fixed order (hand-over between warps).
+    __device__ __forceinline__ float2& reg(int i)
+    {
+        return i < 2 ? x[i] : (i < 4 ? v[i - 2] : (i < 6 ? ex[i - 4] : ev[i - 6]));
+    }
+    // Checkpoint ck (state after (ck + 1) * ckpt_every steps).
+    __device__ __forceinline__ void store_ckpt(const BatchIO& io, int64_t ck) const
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            if (io.v_traj) io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)v[r].x + (double)ev[r].x;
+            if (has1) {
+                io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                if (io.v_traj) io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)v[r].y + (double)ev[r].y;
+            }
+        }
+    }
+    __device__ __forceinline__ void store_final(const BatchIO& io) const
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            io.v_out[q0 * 2 + r] = (double)v[r].x + (double)ev[r].x;
+            if (has1) {
+                io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                io.v_out[q1 * 2 + r] = (double)v[r].y + (double)ev[r].y;
+            }
+        }
+    }
+};
+
+// RK4 stage by stage (Section 3): the same step as rk4_small_kernel<2, false>.
+// Shared by the one-launch kernel and the balanced kernel so that both issue
+// exactly the same operations.
+struct Pair2 : Pair2State {
+    float2 nbh[2][2], nbl[2][2];
+    float2 h, h2, h6, h6lo;
+
+    __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
+    {
+        set_instances(io, q);
         const int64_t s0 = sys.per_inst_sys ? q0 : 0, s1 = sys.per_inst_sys ? q1 : 0;
         const float* b0 = sys.B32 + s0 * 8;      // [hi 2x2][lo 2x2]
         const float* b1 = sys.B32 + s1 * 8;
@@ -365,18 +429,7 @@ struct Pair2 {
         h6 = f2(hs0.h6, hs1.h6);
         h6lo = f2(hs0.h6lo, hs1.h6lo);
     }
-    __device__ __forceinline__ void load_initial(const BatchIO& io)
-    {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
-            const double va = io.v0[q0 * 2 + r], vb = io.v0[q1 * 2 + r];
-            x[r] = f2((float)xa, (float)xb);
-            v[r] = f2((float)va, (float)vb);
-            ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
-            ev[r] = f2((float)(va - (double)v[r].x), (float)(vb - (double)v[r].y));
-        }
-    }
+    __device__ __forceinline__ int64_t quantum() const { return 1; }
     // Stage 1 forms the lo product and keeps it; stages 2-4 reuse it (frozen lo,
     // as rk4_small_kernel).
     __device__ __forceinline__ void accel(const float2 (&xs)[2], float2 (&a)[2], float2 (&lo)[2], bool first) const
@@ -428,63 +481,198 @@ struct Pair2 {
             pair_update(v[r], ev[r], kv[r], h6, h6lo);
         }
     }
-    __device__ __forceinline__ void steps(int64_t n)
-    {
-        for (int64_t base = 0; base < n; base += 0x40000000LL) {
-            const int32_t m = (int32_t)(n - base < 0x40000000LL ? n - base : 0x40000000LL);
-#pragma unroll 2
-            for (int32_t it = 0; it < m; ++it) step();
+};
+
+// ---- polynomial form of the same map ----------------------------------------------
+//
+// For the linear system y' = A y, y = (x0, x1, v0, v1), A = [[0, I], [-B, 0]], one
+// classical RK4 step is exactly y <- P(hA) y with
+//     P(hA) = I + hA + (hA)^2/2 + (hA)^3/6 + (hA)^4/24
+// (the stage values of Section 3 are linear in y; composing them gives P).  k
+// steps are y <- P(hA)^k y.  The jump matrix E = P(hA)^k - I is formed in FP64 per
+// instance (Horner for P, binary powers for the k-th power), so the update is
+// y <- y + E y: with E as an unevaluated FP32 pair and the compensated state of
+// the stage form, 48 FP32 operations per k steps against 64 per step.
+struct Mat4 {
+    double m[4][4];
+};
+
+__device__ __forceinline__ Mat4 mat4_mul(const Mat4& a, const Mat4& b)
+{
+    Mat4 c;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            double t = 0.0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) t = __fma_rn(a.m[i][l], b.m[l][j], t);
+            c.m[i][j] = t;
         }
+    return c;
+}
+
+// E = P(hA)^k - I for the 2 x 2 matrix B (row-major b[4]).
+__device__ Mat4 poly_jump_matrix(const double (&b)[4], double h, int k)
+{
+    Mat4 hA{}, I{};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) I.m[i][i] = 1.0;
+    hA.m[0][2] = h;
+    hA.m[1][3] = h;
+    hA.m[2][0] = -h * b[0];
+    hA.m[2][1] = -h * b[1];
+    hA.m[3][0] = -h * b[2];
+    hA.m[3][1] = -h * b[3];
+    // P = I + hA (I + hA/2 (I + hA/3 (I + hA/4)))
+    Mat4 P = I;
+    for (int d = 4; d >= 1; --d) {
+        Mat4 T = mat4_mul(hA, P);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) P.m[i][j] = I.m[i][j] + T.m[i][j] / (double)d;
     }
-    // Checkpoint ck (state after (ck + 1) * ckpt_every steps).
-    __device__ __forceinline__ void store_ckpt(const BatchIO& io, int64_t ck) const
+    Mat4 R = I, base = P;
+    for (int kk = k; kk > 0; kk >>= 1) {
+        if (kk & 1) R = mat4_mul(R, base);
+        if (kk > 1) base = mat4_mul(base, base);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) R.m[i][i] -= 1.0;
+    return R;
+}
+
+struct Pair2Poly : Pair2State {
+    float2 eh[4][4], el[4][4];
+    int32_t k;
+
+    __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
     {
+        set_instances(io, q);
+        k = io.poly_jump;
+        Mat4 E[2];
+#pragma unroll
+        for (int lane = 0; lane < 2; ++lane) {
+            const int64_t qq = lane ? q1 : q0;
+            const float* bp = sys.B32 + (sys.per_inst_sys ? qq : 0) * 8;   // the FP32 pair of B, as the stage form
+            double b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] = (double)bp[i] + (double)bp[4 + i];
+            E[lane] = poly_jump_matrix(b, io.h[io.h_per_inst ? qq : 0], k);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float h0 = (float)E[0].m[i][j], h1 = (float)E[1].m[i][j];
+                eh[i][j] = f2(h0, h1);
+                el[i][j] = f2((float)(E[0].m[i][j] - (double)h0), (float)(E[1].m[i][j] - (double)h1));
+            }
+    }
+    __device__ __forceinline__ int64_t quantum() const { return k; }
+    // k RK4 steps: y <- y + E y (lo products first), compensated.
+    __device__ __forceinline__ void step()
+    {
+        const float2 y[4] = {x[0], x[1], v[0], v[1]};
+        float2 z[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 acc = __fmul2_rn(el[i][0], y[0]);
+#pragma unroll
+            for (int j = 1; j < 4; ++j) acc = __ffma2_rn(el[i][j], y[j], acc);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc = __ffma2_rn(eh[i][j], y[j], acc);
+            z[i] = acc;
+        }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
-            if (io.v_traj) io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)v[r].x + (double)ev[r].x;
-            if (has1) {
-                io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
-                if (io.v_traj) io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)v[r].y + (double)ev[r].y;
-            }
-        }
-    }
-    __device__ __forceinline__ void store_final(const BatchIO& io) const
-    {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
-            io.v_out[q0 * 2 + r] = (double)v[r].x + (double)ev[r].x;
-            if (has1) {
-                io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
-                io.v_out[q1 * 2 + r] = (double)v[r].y + (double)ev[r].y;
-            }
-        }
-    }
-    // Steps [first, last) of the horizon; checkpoints where ckpt_every divides
-    // the step count reached (first and last are multiples of ckpt_every when
-    // checkpoints are written).
-    __device__ __forceinline__ void run(const BatchIO& io, int64_t first, int64_t last, bool store)
-    {
-        if (io.ckpt_every > 0 && io.x_traj) {
-            for (int64_t done = first; done < last; done += io.ckpt_every) {
-                steps(io.ckpt_every);
-                if (store) store_ckpt(io, done / io.ckpt_every);
-            }
-        } else {
-            steps(last - first);
+            pair_add(x[r], ex[r], z[r]);
+            pair_add(v[r], ev[r], z[2 + r]);
         }
     }
 };
 
+// Steps [first, last) of the horizon (multiples of the thread type's quantum),
+// checkpoints where ckpt_every divides the step count reached (first and last
+// are then multiples of ckpt_every).
+template <class T>
+__device__ __forceinline__ void advance(T& p, int64_t n_steps)
+{
+    const int64_t n = n_steps / p.quantum();
+    for (int64_t base = 0; base < n; base += 0x40000000LL) {
+        const int32_t m = (int32_t)(n - base < 0x40000000LL ? n - base : 0x40000000LL);
+#pragma unroll 2
+        for (int32_t it = 0; it < m; ++it) p.step();
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void run_steps(T& p, const BatchIO& io, int64_t first, int64_t last, bool store)
+{
+    if (io.ckpt_every > 0 && io.x_traj) {
+        for (int64_t done = first; done < last; done += io.ckpt_every) {
+            advance(p, io.ckpt_every);
+            if (store) p.store_ckpt(io, done / io.ckpt_every);
+        }
+    } else {
+        advance(p, last - first);
+    }
+}
+
+// The polynomial form in FP64: one instance per thread, y <- y + E y.
+__global__ void __launch_bounds__(64) rk4_poly64_kernel(const SmallSys sys, const BatchIO io)
+{
+    const int64_t q = (int64_t)blockIdx.x * 64 + threadIdx.x;
+    if (q >= io.n_inst) return;
+    const double* bp = sys.B64 + (sys.per_inst_sys ? q : 0) * 4;
+    const double b[4] = {bp[0], bp[1], bp[2], bp[3]};
+    const Mat4 E = poly_jump_matrix(b, io.h[io.h_per_inst ? q : 0], io.poly_jump);
+    double y[4] = {io.x0[q * 2], io.x0[q * 2 + 1], io.v0[q * 2], io.v0[q * 2 + 1]};
+    auto jumps = [&](int64_t n) {
+        for (int64_t it = 0; it < n; ++it) {
+            double z[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                double t = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t = __fma_rn(E.m[i][j], y[j], t);
+                z[i] = t;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) y[i] = __dadd_rn(y[i], z[i]);
+        }
+    };
+    const int64_t k = io.poly_jump;
+    if (io.ckpt_every > 0 && io.x_traj) {
+        for (int64_t done = 0; done < io.n_steps; done += io.ckpt_every) {
+            jumps(io.ckpt_every / k);
+            const int64_t o = (q * io.n_ck + done / io.ckpt_every) * 2;
+            io.x_traj[o] = y[0];
+            io.x_traj[o + 1] = y[1];
+            if (io.v_traj) {
+                io.v_traj[o] = y[2];
+                io.v_traj[o + 1] = y[3];
+            }
+        }
+    } else {
+        jumps(io.n_steps / k);
+    }
+    io.x_out[q * 2] = y[0];
+    io.x_out[q * 2 + 1] = y[1];
+    io.v_out[q * 2] = y[2];
+    io.v_out[q * 2 + 1] = y[3];
+}
+
+template <class T>
 __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys sys, const BatchIO io)
 {
     const int64_t t = (int64_t)blockIdx.x * kPairThreads + threadIdx.x;
     if (2 * t >= io.n_inst) return;
-    Pair2 p;
+    T p;
     p.init(sys, io, 2 * t);
     p.load_initial(io);
-    p.run(io, 0, io.n_steps, true);
+    run_steps(p, io, 0, io.n_steps, true);
     p.store_final(io);
 }
 
@@ -525,6 +713,7 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+template <class T>
 __global__ void __launch_bounds__(kBalWarps * 32, 1)
 rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSched sc)
 {
@@ -540,21 +729,16 @@ rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSch
         const int64_t end = j1 < p1 ? j1 : p1;
         const int64_t q = u * 64 + 2 * lane;
         const bool live = q < io.n_inst;
-        Pair2 p;
+        T p;
         p.init(sys, io, live ? q : (io.n_inst - 1) & ~(int64_t)1);
         if (pos > j0) {
             // Started on warp m - 1's range: the first blocks of the unit, then hand over.
             const int64_t nb = end - pos;
             p.load_initial(io);
-            p.run(io, 0, nb * sc.block_steps, live);
+            run_steps(p, io, 0, nb * sc.block_steps, live);
             float2* dst = sc.xfer + m * 8 * 32 + lane;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                dst[(0 + r) * 32] = p.x[r];
-                dst[(2 + r) * 32] = p.v[r];
-                dst[(4 + r) * 32] = p.ex[r];
-                dst[(6 + r) * 32] = p.ev[r];
-            }
+            for (int i = 0; i < 8; ++i) dst[i * 32] = p.reg(i);
             __threadfence();
             __syncwarp();
             if (lane == 0 && !sc.withhold)
@@ -577,24 +761,19 @@ rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSch
             if (ok) {
                 const float2* src = sc.xfer + (m + 1) * 8 * 32 + lane;
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    p.x[r] = src[(0 + r) * 32];
-                    p.v[r] = src[(2 + r) * 32];
-                    p.ex[r] = src[(4 + r) * 32];
-                    p.ev[r] = src[(6 + r) * 32];
-                }
+                for (int i = 0; i < 8; ++i) p.reg(i) = src[i * 32];
             } else {
                 if (lane == 0 && sc.err) atomicExch(sc.err, 1);
                 const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
-                for (int r = 0; r < 2; ++r) p.x[r] = p.v[r] = p.ex[r] = p.ev[r] = f2(nan, nan);
+                for (int i = 0; i < 8; ++i) p.reg(i) = f2(nan, nan);
             }
-            p.run(io, first * sc.block_steps, sc.blocks * sc.block_steps, live);
+            run_steps(p, io, first * sc.block_steps, sc.blocks * sc.block_steps, live);
             if (live) p.store_final(io);
         } else {
             // The whole unit.
             p.load_initial(io);
-            p.run(io, 0, sc.blocks * sc.block_steps, live);
+            run_steps(p, io, 0, sc.blocks * sc.block_steps, live);
             if (live) p.store_final(io);
         }
         pos = end;
@@ -694,13 +873,14 @@ int two_dof_variant()
     return v;
 }
 
+template <class T>
 cudaError_t launch_pair2(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
 {
     const int64_t threads = (io.n_inst + 1) / 2;
     const int64_t blocks = (threads + kPairThreads - 1) / kPairThreads;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rk4_pair2_kernel<<<(unsigned)blocks, kPairThreads, 0, st>>>(sys, io);
+    rk4_pair2_kernel<T><<<(unsigned)blocks, kPairThreads, 0, st>>>(sys, io);
     return cudaGetLastError();
 }
 
@@ -709,6 +889,7 @@ cudaError_t launch_pair2(const SmallSys& sys, const BatchIO& io, cudaStream_t st
 // buffer and flags are taken from the stream-ordered allocator and freed after
 // the kernel on the same stream, so concurrent calls on other streams do not
 // share them.
+template <class T>
 cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
 {
     int dev = 0, sms = 0, coop = 0;
@@ -719,14 +900,17 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
     const int64_t P = (int64_t)sms * kBalWarps;
     const int64_t U = (io.n_inst + 63) / 64;
     const bool ckpt = io.ckpt_every > 0 && io.x_traj;
-    const int64_t g = ckpt ? io.ckpt_every : 1;
+    // blocks of ckpt_every steps, else of one update (one step, or poly_jump steps)
+    const int64_t g = ckpt ? io.ckpt_every : (io.poly_jump > 0 ? io.poly_jump : 1);
     const int64_t Tb = io.n_steps / g;
-    if (!coop || U <= P || Tb <= 0 || Tb > ((int64_t)1 << 62) / U) return launch_pair2(sys, io, st);
-    static bool attr_set[64] = {};
-    if (dev < 64 && !attr_set[dev]) {
-        e = cudaFuncSetAttribute(rk4_pair2_balanced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBalSmemBytes);
+    if (!coop || U <= P || Tb <= 0 || Tb > ((int64_t)1 << 62) / U) return launch_pair2<T>(sys, io, st);
+    auto kern = rk4_pair2_balanced_kernel<T>;
+    static bool attr_set[2][64] = {};
+    bool& done = attr_set[std::is_same<T, Pair2>::value ? 0 : 1][dev < 64 ? dev : 63];
+    if (!done) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kBalSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        done = true;
     }
     BalanceSched sc{};
     sc.units = U;
@@ -747,8 +931,8 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
         SmallSys a0 = sys;
         BatchIO a1 = io;
         void* args[] = {&a0, &a1, &sc};
-        e = cudaLaunchCooperativeKernel((const void*)rk4_pair2_balanced_kernel, dim3((unsigned)sms), dim3(kBalWarps * 32),
-                                        args, (size_t)kBalSmemBytes, st);
+        e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)sms), dim3(kBalWarps * 32), args,
+                                        (size_t)kBalSmemBytes, st);
     }
     const cudaError_t ef = cudaFreeAsync(buf, st);
     return e != cudaSuccess ? e : ef;
@@ -758,6 +942,18 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
+    if (io.poly_jump > 0) {                      // polynomial form (s = 2, checked by the caller)
+        if (sys.s != 2) return cudaErrorInvalidValue;
+        if (fp64) {
+            const int64_t blocks = (io.n_inst + 63) / 64;
+            if (blocks <= 0) return cudaSuccess;
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+            rk4_poly64_kernel<<<(unsigned)blocks, 64, 0, st>>>(sys, io);
+            return cudaGetLastError();
+        }
+        return two_dof_variant() == 3 ? launch_pair2<Pair2Poly>(sys, io, st)
+                                      : launch_pair2_balanced<Pair2Poly>(sys, io, st);
+    }
     const int variant = two_dof_variant();
     if (sys.s == 2 && !fp64 && variant == 1) {
         const int64_t blocks = (io.n_inst + kTwoDofThreads - 1) / kTwoDofThreads;
@@ -767,8 +963,8 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
         return cudaGetLastError();
     }
     // s = 1 is also padded to S = 2 but keeps the generic layout
-    if (sys.s == 2 && !fp64 && variant == 3) return launch_pair2(sys, io, st);
-    if (sys.s == 2 && !fp64 && variant == 0) return launch_pair2_balanced(sys, io, st);
+    if (sys.s == 2 && !fp64 && variant == 3) return launch_pair2<Pair2>(sys, io, st);
+    if (sys.s == 2 && !fp64 && variant == 0) return launch_pair2_balanced<Pair2>(sys, io, st);
     return dispatch<BatchSrc>(sys.S, fp64, io.n_inst, st, [&](auto& s) {
         s.sys = sys;
         s.io = io;

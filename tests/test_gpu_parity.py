@@ -452,6 +452,104 @@ def test_balanced_handover_wait_gives_up_and_reports(ctx):
         cho.cho_destroy_system(sys_)
 
 
+# ---- polynomial form (k RK4 steps per update with P(hA)^k) ---------------------------------------
+
+@pytest.mark.parametrize("prec,tol,k", [("fp32_kahan", TOL_FP32, 1), ("fp32_kahan", TOL_FP32, 5),
+                                        ("fp32_kahan", TOL_FP32, 25), ("fp64", TOL_FP64, 1),
+                                        ("fp64", TOL_FP64, 5), ("fp64", TOL_FP64, 125)])
+def test_poly_form_matches_oracle(ctx, prec, tol, k):
+    """y <- y + (P(hA)^k - I) y reproduces the stage-by-stage FP64 oracle (999 systems, odd count).
+    FP32 stays within 1e-5 while k omega h <= 1 (here k <= 25 at h = T_min/200); at k = 125
+    (k omega h = 3.9) the increment E y is as large as y and its rounding reached 1.2e-5."""
+    import torch
+
+    cfg = inputs.two_dof_batch(n_inst=999, n_steps=10000)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                      10000, prec, 125, trajectory=True, poly_jump=k)
+        torch.cuda.synchronize()
+        out = {key: val.cpu().numpy() for key, val in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+    ref = oracle_run(cfg, ckpt_every=125)
+    ex, ev = check(out, ref, tol)
+    print(f"poly k={k} {prec}: x {ex:.3e} v {ev:.3e}")
+
+
+@pytest.mark.parametrize("k", [1, 5, 25])
+def test_poly_form_full_size_sampled(ctx, k):
+    """65,536 systems x 1e4 steps in the polynomial form on the balanced schedule, sampled
+    (checkpoints every 125 steps: a multiple of T_min / h = 200 would see the fastest mode
+    only at its turning points)."""
+    cfg = inputs.two_dof_batch()
+    import torch
+
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                      10000, "fp32_kahan", 125, trajectory=True, poly_jump=k)
+        torch.cuda.synchronize()
+        out = {key: val.cpu().numpy() for key, val in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+    idx = sample_indices(cfg["x0"].shape[0], 128)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=125)
+    check(out, ref, TOL_FP32, idx)
+
+
+def test_poly_form_balanced_is_bitwise_equal(tmp_path):
+    """The polynomial form on the balanced schedule gives the bits of one warp per 64 instances."""
+    import subprocess
+    import sys as _sys
+
+    code = _VARIANT_RUN.replace("'fp32_kahan', every, trajectory=every > 0)",
+                                "'fp32_kahan', every, trajectory=every > 0, poly_jump=5)")
+    assert code != _VARIANT_RUN
+    res = {}
+    for variant in ("balanced", "pair"):
+        path = str(tmp_path / f"{variant}.npz")
+        env = dict(os.environ, CHO_TWO_DOF_KERNEL=variant)
+        subprocess.run([_sys.executable, "-c", code, path, "45001", "3000", "1000"], check=True, env=env,
+                       timeout=300)
+        res[variant] = np.load(path)
+    for key in res["pair"].files:
+        assert np.isfinite(res["balanced"][key]).all(), key
+        assert np.array_equal(res["pair"][key], res["balanced"][key]), key
+
+
+def test_poly_form_rejects_what_it_does_not_cover(ctx):
+    cfg = inputs.two_dof_batch(n_inst=4, n_steps=100)
+    two = make_system(ctx, cfg)
+    ch = inputs.chain_batch(n_inst=2, s=5, n_steps=100)
+    chain = cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"])
+    try:
+        bad = [
+            lambda: cho.cho_integrate_batch(ctx, two, cfg["x0"], cfg["v0"], cfg["h"], 100, "fp32_kahan",
+                                            poly_jump=3),                       # 3 does not divide 100
+            lambda: cho.cho_integrate_batch(ctx, two, cfg["x0"], cfg["v0"], cfg["h"], 100, "fp32_kahan", 50,
+                                            trajectory=True, poly_jump=20),     # 20 does not divide 50
+            lambda: cho.cho_integrate_batch(ctx, two, cfg["x0"], cfg["v0"], cfg["h"], 100, "fp32_kahan",
+                                            poly_jump=-1),
+            lambda: cho.cho_integrate_batch(ctx, chain, ch["x0"], ch["v0"], ch["h"], 100, "fp32_kahan",
+                                            poly_jump=1),                       # s = 5
+        ]
+        for call in bad:
+            with pytest.raises(cho.ChoError) as ei:
+                call()
+            assert ei.value.status == cho.CHO_EINVAL
+        # zero instances and zero steps are accepted
+        out = cho.cho_integrate_batch(ctx, two, cfg["x0"], cfg["v0"], cfg["h"], 0, "fp32_kahan", poly_jump=4)
+        assert np.allclose(out["x"], cfg["x0"], rtol=0, atol=1e-7)
+    finally:
+        cho.cho_destroy_system(chain)
+        cho.cho_destroy_system(two)
+
+
 # ---- full-size workloads, sampled against the oracle ------------------------------------------
 
 # Over the full 5e3-step horizon bf16x5 and bf16x6 stay within 1e-5 (each K chunk in its own
