@@ -46,6 +46,7 @@ struct BatchIO {
     int64_t ckpt_every;     // 0: no checkpoints
     int64_t n_ck;
     int32_t poly_jump;      // 0: RK4 stages; k >= 1: polynomial form, k steps per update (s = 2)
+    const double* poly_E;   // polynomial form: E = P(hA)^k - I per instance, [n_inst][4][4] (set by the launcher)
     double* x_out;
     double* v_out;
     double* x_traj;

@@ -547,27 +547,21 @@ struct Pair2Poly : Pair2State {
     float2 eh[4][4], el[4][4];
     int32_t k;
 
-    __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
+    // E of both instances from the set-up kernel's FP64 table, split into FP32 pairs.
+    __device__ __forceinline__ void init(const SmallSys&, const BatchIO& io, int64_t q)
     {
         set_instances(io, q);
         k = io.poly_jump;
-        Mat4 E[2];
-#pragma unroll
-        for (int lane = 0; lane < 2; ++lane) {
-            const int64_t qq = lane ? q1 : q0;
-            const float* bp = sys.B32 + (sys.per_inst_sys ? qq : 0) * 8;   // the FP32 pair of B, as the stage form
-            double b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) b[i] = (double)bp[i] + (double)bp[4 + i];
-            E[lane] = poly_jump_matrix(b, io.h[io.h_per_inst ? qq : 0], k);
-        }
+        const double* E0 = io.poly_E + q0 * 16;
+        const double* E1 = io.poly_E + q1 * 16;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float h0 = (float)E[0].m[i][j], h1 = (float)E[1].m[i][j];
+                const double d0 = E0[i * 4 + j], d1 = E1[i * 4 + j];
+                const float h0 = (float)d0, h1 = (float)d1;
                 eh[i][j] = f2(h0, h1);
-                el[i][j] = f2((float)(E[0].m[i][j] - (double)h0), (float)(E[1].m[i][j] - (double)h1));
+                el[i][j] = f2((float)(d0 - (double)h0), (float)(d1 - (double)h1));
             }
     }
     __device__ __forceinline__ int64_t quantum() const { return k; }
@@ -620,14 +614,42 @@ __device__ __forceinline__ void run_steps(T& p, const BatchIO& io, int64_t first
     }
 }
 
+// Set-up of the polynomial form: E = P(hA)^k - I of every instance in FP64,
+// [n_inst][4][4], one instance per thread at full occupancy (the FP64 matrix
+// products are latency bound; inside the integration kernels they ran on one
+// warp per sub-partition and cost more than the integration at k >= 5).  B is
+// the FP32 pair (FP32 mode, as the stage form uses) or the FP64 matrix.
+__global__ void __launch_bounds__(64) poly_setup_kernel(const SmallSys sys, const BatchIO io, bool fp64,
+                                                        double* E)
+{
+    const int64_t q = (int64_t)blockIdx.x * 64 + threadIdx.x;
+    if (q >= io.n_inst) return;
+    const int64_t set = sys.per_inst_sys ? q : 0;
+    double b[4];
+    if (fp64) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = sys.B64[set * 4 + i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = (double)sys.B32[set * 8 + i] + (double)sys.B32[set * 8 + 4 + i];
+    }
+    const Mat4 m = poly_jump_matrix(b, io.h[io.h_per_inst ? q : 0], io.poly_jump);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E[q * 16 + i * 4 + j] = m.m[i][j];
+}
+
 // The polynomial form in FP64: one instance per thread, y <- y + E y.
 __global__ void __launch_bounds__(64) rk4_poly64_kernel(const SmallSys sys, const BatchIO io)
 {
     const int64_t q = (int64_t)blockIdx.x * 64 + threadIdx.x;
     if (q >= io.n_inst) return;
-    const double* bp = sys.B64 + (sys.per_inst_sys ? q : 0) * 4;
-    const double b[4] = {bp[0], bp[1], bp[2], bp[3]};
-    const Mat4 E = poly_jump_matrix(b, io.h[io.h_per_inst ? q : 0], io.poly_jump);
+    Mat4 E;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E.m[i][j] = io.poly_E[q * 16 + i * 4 + j];
     double y[4] = {io.x0[q * 2], io.x0[q * 2 + 1], io.v0[q * 2], io.v0[q * 2 + 1]};
     auto jumps = [&](int64_t n) {
         for (int64_t it = 0; it < n; ++it) {
@@ -944,15 +966,28 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
 {
     if (io.poly_jump > 0) {                      // polynomial form (s = 2, checked by the caller)
         if (sys.s != 2) return cudaErrorInvalidValue;
-        if (fp64) {
-            const int64_t blocks = (io.n_inst + 63) / 64;
-            if (blocks <= 0) return cudaSuccess;
-            if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-            rk4_poly64_kernel<<<(unsigned)blocks, 64, 0, st>>>(sys, io);
-            return cudaGetLastError();
+        const int64_t blocks = (io.n_inst + 63) / 64;
+        if (blocks <= 0) return cudaSuccess;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        // the jump matrices live for this call only, in stream order
+        void* buf = nullptr;
+        cudaError_t e = cudaMallocAsync(&buf, (size_t)io.n_inst * 16 * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+        BatchIO pio = io;
+        pio.poly_E = (const double*)buf;
+        poly_setup_kernel<<<(unsigned)blocks, 64, 0, st>>>(sys, io, fp64, (double*)buf);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            if (fp64) {
+                rk4_poly64_kernel<<<(unsigned)blocks, 64, 0, st>>>(sys, pio);
+                e = cudaGetLastError();
+            } else {
+                e = two_dof_variant() == 3 ? launch_pair2<Pair2Poly>(sys, pio, st)
+                                           : launch_pair2_balanced<Pair2Poly>(sys, pio, st);
+            }
         }
-        return two_dof_variant() == 3 ? launch_pair2<Pair2Poly>(sys, io, st)
-                                      : launch_pair2_balanced<Pair2Poly>(sys, io, st);
+        const cudaError_t ef = cudaFreeAsync(buf, st);
+        return e != cudaSuccess ? e : ef;
     }
     const int variant = two_dof_variant();
     if (sys.s == 2 && !fp64 && variant == 1) {
