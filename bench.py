@@ -133,6 +133,35 @@ def percentile(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
 
 
+def run_periodic_mode(cho, inputs, seconds=5.0):
+    """Fixed-priority periodic tasks (rate-monotonic classes, implicit deadlines) on their own
+    context: a 2-DOF system every 20 ms, a 256-mass chain every 50 ms and a dense s = 128
+    system (bf16x5) every 100 ms, each job 1e4 / 1e4 / 2e3 RK4 steps."""
+    from paper_1702_02207_gb300 import periodic
+
+    ctx = cho.cho_init(0, chunk_steps=2000)
+    two = inputs.two_dof_batch(n_inst=1, n_steps=1)
+    ch = inputs.chain_batch(n_inst=1, s=256, n_steps=1, seed=93)
+    dn = inputs.dense_group(s=128, n_inst=1, n_steps=1)
+    systems = [cho.cho_create_system(ctx, "two_dof", masses=two["masses"], springs=two["springs"]),
+               cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"]),
+               cho.cho_create_system(ctx, "dense", M=dn["M"], K=dn["K"])]
+    tasks = [periodic.PeriodicTask(systems[0], two["x0"][0], two["v0"][0], float(two["h"][0]), 10000, 0.02,
+                                   name="two_dof_1e4_steps"),
+             periodic.PeriodicTask(systems[1], ch["x0"][0], ch["v0"][0], float(ch["h"][0]), 10000, 0.05,
+                                   name="chain256_1e4_steps"),
+             periodic.PeriodicTask(systems[2], dn["x0"][0], dn["v0"][0], float(dn["h"][0]), 2000, 0.1,
+                                   prec="bf16x5", name="dense128_2e3_steps_bf16x5")]
+    for t in tasks:                          # one job each before the clock starts (module loading)
+        periodic.run_periodic(ctx, [periodic.PeriodicTask(**{**t.__dict__, "priority": 0})], 1e-3)
+    res = periodic.run_periodic(ctx, tasks, seconds)
+    for sy in systems:
+        cho.cho_destroy_system(sy)
+    cho.cho_shutdown(ctx)
+    res["note"] = "implicit deadlines (deadline = period), jobs submitted through cho_submit at their releases"
+    return res
+
+
 def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
     """Mixed request stream through cho_submit / cho_poll (continuous batching).
 
@@ -526,6 +555,8 @@ def main():
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks)
             if args.serve_requests > 0:
                 line["serving"] = run_serving(cho, inputs, ctx, args.serve_requests)
+                log("periodic mode")
+                line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:
             log("CPU baseline (oracle)")
             n_cpu = 16384

@@ -316,3 +316,65 @@ def test_dense_requests_on_tensor_cores():
             cho.cho_destroy_system(sys_)
     finally:
         cho.cho_shutdown(ctx)
+
+
+# ---- fixed-priority periodic mode (the paper's real-time framing) ----------------------------
+
+def _periodic_tasks(ctx):
+    from paper_1702_02207_gb300 import periodic
+
+    two = inputs.two_dof_batch(n_inst=1, n_steps=1)
+    ch = inputs.chain_batch(n_inst=1, s=64, n_steps=1, seed=91)
+    dn = inputs.dense_group(s=64, n_inst=1, n_steps=1)
+    s2 = cho.cho_create_system(ctx, "two_dof", masses=two["masses"], springs=two["springs"])
+    sc = cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"])
+    sd = cho.cho_create_system(ctx, "dense", M=dn["M"], K=dn["K"])
+    tasks = [
+        periodic.PeriodicTask(s2, two["x0"][0], two["v0"][0], float(two["h"][0]), 2000, 0.05, name="two_dof"),
+        periodic.PeriodicTask(sc, ch["x0"][0], ch["v0"][0], float(ch["h"][0]), 2000, 0.1, name="chain64"),
+        periodic.PeriodicTask(sd, dn["x0"][0], dn["v0"][0], float(dn["h"][0]), 1000, 0.2, prec="bf16x5",
+                              name="dense64"),
+    ]
+    return tasks, (s2, sc, sd)
+
+
+def test_periodic_mode_meets_light_deadlines():
+    """Three periodic tasks (50, 100, 200 ms) with jobs of a few ms: rate-monotonic classes,
+    every job on time, results equal to the batch API."""
+    from paper_1702_02207_gb300 import periodic
+
+    ctx = cho.cho_init(0, chunk_steps=1000)
+    try:
+        tasks, systems = _periodic_tasks(ctx)
+        warm = [cho.cho_submit(ctx, t.system, t.x0, t.v0, t.h, t.n_steps, t.prec, 0) for t in tasks]
+        got = wait_all(ctx, warm, [2, 64, 64])
+        ref = cho.cho_integrate_batch(ctx, tasks[0].system, tasks[0].x0[None], tasks[0].v0[None], tasks[0].h,
+                                      2000, "fp32_kahan")
+        assert np.array_equal(got[warm[0]]["x"], ref["x"][0])
+        res = periodic.run_periodic(ctx, tasks, 1.5)
+        by = {t["name"]: t for t in res["tasks"]}
+        assert [by[n]["priority"] for n in ("two_dof", "chain64", "dense64")] == [0, 1, 2]
+        assert by["two_dof"]["jobs"] == 30 and by["chain64"]["jobs"] == 15 and by["dense64"]["jobs"] == 8
+        assert res["misses"] == 0, res
+        for s in systems:
+            cho.cho_destroy_system(s)
+    finally:
+        cho.cho_shutdown(ctx)
+
+
+def test_periodic_mode_reports_overload():
+    """A task whose job (a 1024-mass chain for 1e5 steps) outlasts its 10 ms period misses every
+    deadline and the count says so."""
+    from paper_1702_02207_gb300 import periodic
+
+    ctx = cho.cho_init(0, chunk_steps=5000)
+    try:
+        ch = inputs.chain_batch(n_inst=1, s=1024, n_steps=1, seed=92)
+        sc = cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"])
+        task = periodic.PeriodicTask(sc, ch["x0"][0], ch["v0"][0], float(ch["h"][0]), 100000, 0.01, name="heavy")
+        res = periodic.run_periodic(ctx, [task], 0.05)
+        t = res["tasks"][0]
+        assert t["jobs"] == 5 and t["misses"] == 5 and t["response_p50_s"] > 0.01
+        cho.cho_destroy_system(sc)
+    finally:
+        cho.cho_shutdown(ctx)
