@@ -292,11 +292,8 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
         sys->path = PATH_SMALL;
     } else if (springs) {
         sys->path = PATH_CHAIN;
-    } else if (n_sys == 1) {
-        sys->path = PATH_DENSE;
     } else {
-        delete sys;
-        return fail(CHO_EINVAL, "cho_create_system: dense systems above 32 DOF must share one parameter set");
+        sys->path = PATH_DENSE;     // one shared (M, K), or one per instance (CUDA cores only)
     }
 
     DeviceGuard g(ctx->device);
@@ -461,7 +458,7 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     } else if (p == CHO_DENSE_FP32_SIMT || p == CHO_DENSE_BF16X3 || p == CHO_DENSE_BF16X5 || p == CHO_DENSE_BF16X6) {
         if (sys->kind != CHO_DENSE) return fail(CHO_EINVAL, "%s: precision %d is for dense systems", who, p);
         if ((p != CHO_DENSE_FP32_SIMT) && (sys->path != PATH_DENSE || sys->s_tc == 0))
-            return fail(CHO_EINVAL, "%s: BF16 tensor-core modes need a shared dense system with 32 < s <= 256", who);
+            return fail(CHO_EINVAL, "%s: BF16 tensor-core modes need one shared dense system with 32 < s <= 256", who);
         if (p == CHO_DENSE_BF16X6 && sys->s_tc > 128)
             return fail(CHO_EINVAL, "%s: bf16x6 needs s <= 128 (its operands exceed shared memory above)", who);
     } else {
@@ -526,7 +523,8 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         e = launch_rk4_chain(cs, io, fp64, st);
     } else {
-        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0};
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
+                    sys->n_sys != 1 ? 1 : 0};
         e = launch_rk4_dense(ds, io, b->prec, st);
     }
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: kernel launch: %s", cudaGetErrorString(e));

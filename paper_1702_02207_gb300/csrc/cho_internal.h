@@ -114,6 +114,7 @@ struct DenseSys {
     int32_t s_tc;           // tensor-core layout: 64 (two tiles on a block diagonal), 128 or 256 (0: none)
     int* err;               // device error word of the tensor-core kernel (bounded waits)
     int32_t stall_mma;      // test hook: issue no MMA, so the bounded wait on it runs out
+    int32_t per_inst;       // 1: one (M, K) per instance, B64/B32 hold n_sys matrices back to back
 };
 
 // Test hook for the bounded device waits: CHO_TEST_STALL_MMA=1 in the environment makes

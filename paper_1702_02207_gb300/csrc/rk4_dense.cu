@@ -1,5 +1,6 @@
-// rk4_dense.cu -- classical RK4 for dense systems (eq. 1) whose instances share
-// one (M, K), on the CUDA cores (FP64, or FP32 with FP32-pair coefficients).
+// rk4_dense.cu -- classical RK4 for dense systems (eq. 1) on the CUDA cores
+// (FP64, or FP32 with FP32-pair coefficients), for instances that share one
+// (M, K) or that each have their own.
 //
 // Each stage needs A = -B Xs for a tile of instances: a matrix product of the
 // shared iteration matrix B = M^{-1}K (s x s) with the tile's stage
@@ -12,6 +13,11 @@
 // kJC columns with cp.async, double-buffered so that the copy of the next
 // chunk overlaps the products of the current one; each thread reads its rows
 // of a column with vector shared-memory loads.
+//
+// One (M, K) per instance: the same kernel with one instance per CTA (NT = 1)
+// and the CTA's own B^T streamed through the chunk buffers; B is read from L2 or
+// HBM every stage (hi and lo at stage 1, hi alone at stages 2-4: 20 s^2 bytes per
+// instance-step in FP32), so this form is bound by memory bandwidth.
 //
 // The tensor-core split-BF16 variant lives in rk4_dense_tc.cu.
 #include "cho_internal.h"
@@ -68,6 +74,14 @@ struct DenseBatchSrc {
         io.v_out[q * s + i] = (double)v + (double)cv;
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
+    // B^T (FP64) or its FP32 pair of instance q's parameter set
+    __device__ const void* bt(const DenseSys& sys, int64_t q) const
+    {
+        const int64_t set = sys.per_inst ? q : 0;
+        const size_t n = (size_t)sys.s_pad * sys.s_pad;
+        if constexpr (F64) return sys.B64 + (size_t)set * n;
+        else return sys.B32 + (size_t)set * 2 * n;
+    }
 };
 
 // Slot form (serving): state block [x(s), v(s), cx(s), cv(s)] in kernel precision;
@@ -111,13 +125,54 @@ struct DenseSlotSrc {
         io.slots[slot].remaining -= ran;
         if (bad) io.status[slot] = CHO_ENONFINITE;
     }
+    // the slot's coefficient block (its parameter set's B^T) or the shared one
+    __device__ const void* bt(const DenseSys& sys, int64_t q) const
+    {
+        if (q < io.n_inst && d(q).coef) return d(q).coef;
+        if constexpr (F64) return sys.B64;
+        else return sys.B32;
+    }
 };
 
-template <int RI, int NT, bool F64, class Src>
-__global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys sys, const Src src)
+// acc[k] += col[k] * xj for k < RI, reading col with the widest vector loads that
+// RI allows (col is aligned to RI elements: rows are split in blocks of RI).
+template <int RI, class Real>
+__device__ __forceinline__ void col_fma(const Real* col, Real xj, Real (&acc)[RI])
+{
+    if constexpr (sizeof(Real) == 8 && RI % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < RI; k += 2) {
+            const double2 b = *(const double2*)(col + k);
+            acc[k] = fmar(b.x, xj, acc[k]);
+            acc[k + 1] = fmar(b.y, xj, acc[k + 1]);
+        }
+    } else if constexpr (sizeof(Real) == 4 && RI % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < RI; k += 4) {
+            const float4 b = *(const float4*)(col + k);
+            acc[k] = fmar(b.x, xj, acc[k]);
+            acc[k + 1] = fmar(b.y, xj, acc[k + 1]);
+            acc[k + 2] = fmar(b.z, xj, acc[k + 2]);
+            acc[k + 3] = fmar(b.w, xj, acc[k + 3]);
+        }
+    } else if constexpr (sizeof(Real) == 4 && RI % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < RI; k += 2) {
+            const float2 b = *(const float2*)(col + k);
+            acc[k] = fmar(b.x, xj, acc[k]);
+            acc[k + 1] = fmar(b.y, xj, acc[k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RI; ++k) acc[k] = fmar(col[k], xj, acc[k]);
+    }
+}
+
+template <int RI, int NT, bool F64, class Src, int NTHR = kDenseThreads>
+__global__ void __launch_bounds__(NTHR) rk4_dense_simt_kernel(DenseSys sys, const Src src)
 {
     using Real = std::conditional_t<F64, double, float>;
-    constexpr int RG = kDenseThreads / NT;          // row groups
+    constexpr int RG = NTHR / NT;                   // row groups
     constexpr int SP = RG * RI;                     // padded size handled by this instantiation
     constexpr int NB = F64 ? 1 : 2;                 // B pieces: FP64, or FP32 hi and lo
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -133,7 +188,8 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
     const int64_t q = (int64_t)blockIdx.x * NT + n;
     const bool live = q < src.count();
     const int s = sys.s;
-    const Real* Bt = F64 ? (const Real*)sys.B64 : (const Real*)sys.B32;   // [SP][SP] = B^T (then lo, FP32)
+    // [SP][SP] = B^T (then lo, FP32): shared, or the CTA's own instance (NT = 1)
+    const Real* Bt = (const Real*)src.bt(sys, (int64_t)blockIdx.x * NT);
 
     // every instance of the tile runs its own step count; the tile loops to the largest
     const int64_t my_steps = live ? src.steps(q) : 0;
@@ -158,32 +214,39 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
         }
     }
 
-    // copy columns [c kJC, c kJC + kJC) of B^T (each piece) into chunk buffer b
+    // copy columns [c kJC, c kJC + kJC) of B^T (np pieces) into chunk buffer b
     constexpr int CHUNK = kJC * SP;                 // elements per piece per chunk
     constexpr int VEC = 16 / sizeof(Real);
     const int n_chunks = (s + kJC - 1) / kJC;
-    auto load_chunk = [&](int c, int b) {
-#pragma unroll
-        for (int pc = 0; pc < NB; ++pc) {
+    auto load_chunk = [&](int c, int b, int np) {
+        for (int pc = 0; pc < np; ++pc) {
             const Real* src_c = Bt + (size_t)pc * SP * SP + (size_t)c * CHUNK;
             Real* dst = bsh + ((size_t)b * NB + pc) * CHUNK;
-            for (int e = t * VEC; e < CHUNK; e += kDenseThreads * VEC) cp_async16(dst + e, src_c + e);
+            for (int e = t * VEC; e < CHUNK; e += NTHR * VEC) cp_async16(dst + e, src_c + e);
         }
         cp_async_commit();
     };
 
     int buf = 0;
-    auto accel = [&](const Real (&xs)[RI], Real (&acc)[RI]) {
+    // FP32: B = hi + lo.  The lo product is formed at stage 1 only, in its own
+    // accumulator, and reused by stages 2-4 ("frozen lo", as rk4_small.cu): those
+    // stages stream and multiply the hi piece alone.
+    Real lo1[RI];
+    auto accel = [&](const Real (&xs)[RI], Real (&acc)[RI], bool first) {
         Real* X = xsh + buf * SP * NT;
 #pragma unroll
         for (int k = 0; k < RI; ++k) X[(row0 + k) * NT + n] = xs[k];
         Real t0[RI];
 #pragma unroll
-        for (int k = 0; k < RI; ++k) t0[k] = 0;
-        load_chunk(0, 0);
+        for (int k = 0; k < RI; ++k) {
+            t0[k] = 0;
+            if (first) lo1[k] = 0;
+        }
+        const int np = (!F64 && first) ? 2 : 1;
+        load_chunk(0, 0, np);
         for (int c = 0; c < n_chunks; ++c) {
             if (c + 1 < n_chunks) {
-                load_chunk(c + 1, (c + 1) & 1);
+                load_chunk(c + 1, (c + 1) & 1, np);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -194,30 +257,15 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
             for (int jj = 0; jj < jn; ++jj) {
                 const Real xj = X[(c * kJC + jj) * NT + n];
                 const Real* col = bh + jj * SP + row0;
-                if constexpr (F64) {
-#pragma unroll
-                    for (int k = 0; k < RI; k += 2) {
-                        const double2 b = *(const double2*)(col + k);
-                        t0[k] = fmar(b.x, xj, t0[k]);
-                        t0[k + 1] = fmar(b.y, xj, t0[k + 1]);
-                    }
-                } else {
-                    const float* coll = col + CHUNK;
-#pragma unroll
-                    for (int k = 0; k < RI; k += 4) {
-                        const float4 b_hi = *(const float4*)(col + k);
-                        const float4 b_lo = *(const float4*)(coll + k);
-                        t0[k] = fmaf(b_hi.x, xj, fmaf(b_lo.x, xj, t0[k]));
-                        t0[k + 1] = fmaf(b_hi.y, xj, fmaf(b_lo.y, xj, t0[k + 1]));
-                        t0[k + 2] = fmaf(b_hi.z, xj, fmaf(b_lo.z, xj, t0[k + 2]));
-                        t0[k + 3] = fmaf(b_hi.w, xj, fmaf(b_lo.w, xj, t0[k + 3]));
-                    }
+                col_fma(col, xj, t0);
+                if constexpr (!F64) {
+                    if (first) col_fma(col + CHUNK, xj, lo1);
                 }
             }
             __syncthreads();                         // buffer c & 1 free for chunk c + 2
         }
 #pragma unroll
-        for (int k = 0; k < RI; ++k) acc[k] = -t0[k];
+        for (int k = 0; k < RI; ++k) acc[k] = F64 ? -t0[k] : -addr(t0[k], lo1[k]);
         buf ^= 1;
     };
 
@@ -227,7 +275,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
     for (int64_t done = 0; done < nsteps; done += every) {
         for (int64_t it = 0; it < every; ++it, ++step) {
             Real a[RI], xs[RI], kx[RI], kv[RI], vs[RI];
-            accel(x, a);
+            accel(x, a, true);
 #pragma unroll
             for (int k = 0; k < RI; ++k) {
                 kx[k] = v[k];
@@ -235,7 +283,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
                 xs[k] = fmar(hs.h2, v[k], x[k]);
                 vs[k] = fmar(hs.h2, a[k], v[k]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
 #pragma unroll
             for (int k = 0; k < RI; ++k) {
                 kx[k] = fmar((Real)2, vs[k], kx[k]);
@@ -243,7 +291,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
                 xs[k] = fmar(hs.h2, vs[k], x[k]);
                 vs[k] = fmar(hs.h2, a[k], v[k]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
 #pragma unroll
             for (int k = 0; k < RI; ++k) {
                 kx[k] = fmar((Real)2, vs[k], kx[k]);
@@ -251,7 +299,7 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
                 xs[k] = fmar(hs.h, vs[k], x[k]);
                 vs[k] = fmar(hs.h, a[k], v[k]);
             }
-            accel(xs, a);
+            accel(xs, a, false);
             if (step < my_steps) {                   // instances past their horizon hold still
 #pragma unroll
                 for (int k = 0; k < RI; ++k) {
@@ -286,20 +334,20 @@ __global__ void __launch_bounds__(kDenseThreads) rk4_dense_simt_kernel(DenseSys 
     if (live && r == 0) src.finish(q, my_steps, any_bad[n] != 0);
 }
 
-template <int RI, int NT, bool F64, class Src>
+template <int RI, int NT, bool F64, class Src, int NTHR = kDenseThreads>
 cudaError_t launch_simt(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     using Real = std::conditional_t<F64, double, float>;
-    constexpr int SP = (kDenseThreads / NT) * RI;
+    constexpr int SP = (NTHR / NT) * RI;
     constexpr int NB = F64 ? 1 : 2;
     if (sys.s_pad != SP) return cudaErrorInvalidValue;
     const size_t smem = sizeof(Real) * (2 * (size_t)SP * NT + 2 * (size_t)NB * kJC * SP);
-    auto kern = rk4_dense_simt_kernel<RI, NT, F64, Src>;
+    auto kern = rk4_dense_simt_kernel<RI, NT, F64, Src, NTHR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (n_inst + NT - 1) / NT;
     if (blocks <= 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, kDenseThreads, smem, st>>>(sys, src);
+    kern<<<(unsigned)blocks, NTHR, smem, st>>>(sys, src);
     return cudaGetLastError();
 }
 
@@ -310,6 +358,19 @@ cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaSt
     case SPV:                                                                                         \
         if (fp64) { SrcT<true> src; init(src); return launch_simt<RI64, NT64, true>(sys, src, n_inst, st); } \
         else { SrcT<false> src; init(src); return launch_simt<RI32, NT32, false>(sys, src, n_inst, st); }
+#define CHO_DENSE_OWN_CASE(SPV, RI)                                                                   \
+    case SPV:                                                                                         \
+        if (fp64) { SrcT<true> src; init(src); return launch_simt<RI, 1, true, SrcT<true>, SPV / RI>(sys, src, n_inst, st); } \
+        else { SrcT<false> src; init(src); return launch_simt<RI, 1, false, SrcT<false>, SPV / RI>(sys, src, n_inst, st); }
+    if (sys.per_inst) {                             // one instance (and its own B) per CTA of 64 threads
+        switch (sys.s_pad) {
+            CHO_DENSE_OWN_CASE(64, 1)
+            CHO_DENSE_OWN_CASE(128, 2)
+            CHO_DENSE_OWN_CASE(256, 4)
+            CHO_DENSE_OWN_CASE(512, 8)
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (sys.s_pad) {
         CHO_DENSE_CASE(64, 2, 8, 4, 16)
         CHO_DENSE_CASE(128, 4, 8, 8, 16)
@@ -318,6 +379,7 @@ cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaSt
         default: return cudaErrorInvalidValue;
     }
 #undef CHO_DENSE_CASE
+#undef CHO_DENSE_OWN_CASE
 }
 
 }  // namespace
@@ -350,8 +412,9 @@ cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool f
     });
 }
 
-// Device data of a dense system: B^T padded to s_pad in FP64 and as FP32 pairs
-// (hi block then lo block), plus the BF16 pieces the tensor-core kernel reads.
+// Device data of a dense system: for each of its n_sys parameter sets B^T padded
+// to s_pad in FP64 and as FP32 pairs (hi block then lo block), back to back; for a
+// single shared set also the BF16 pieces the tensor-core kernel reads.
 cudaError_t build_dense_device(cho_system_impl* sys, const double* B)
 {
     const int s = sys->s;
@@ -359,16 +422,30 @@ cudaError_t build_dense_device(cho_system_impl* sys, const double* B)
     if (sp > 512) return cudaErrorInvalidValue;
     sys->s_pad = sp;
     const size_t n = (size_t)sp * sp;
-    std::vector<double> Bt(n, 0.0);
-    for (int i = 0; i < s; ++i)
-        for (int j = 0; j < s; ++j) Bt[(size_t)j * sp + i] = B[(size_t)i * s + j];
-    std::vector<float> B32(2 * n);
-    for (size_t k = 0; k < n; ++k) split_ff(Bt[k], B32[k], B32[n + k]);
-    cudaError_t e = cudaMalloc(&sys->d_B64, n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpy(sys->d_B64, Bt.data(), n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&sys->d_B32, 2 * n * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(sys->d_B32, B32.data(), 2 * n * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = build_dense_tc_device(sys, B);
+    const size_t sets = (size_t)sys->n_sys;
+    std::vector<double> Bt(sets * n, 0.0);
+    std::vector<float> B32(sets * 2 * n);
+    for (size_t p = 0; p < sets; ++p) {
+        const double* Bp = B + p * (size_t)s * s;
+        double* T = &Bt[p * n];
+        for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j) T[(size_t)j * sp + i] = Bp[(size_t)i * s + j];
+        float* F = &B32[p * 2 * n];
+        for (size_t k = 0; k < n; ++k) split_ff(T[k], F[k], F[n + k]);
+    }
+    cudaError_t e = cudaMalloc(&sys->d_B64, Bt.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_B64, Bt.data(), Bt.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&sys->d_B32, B32.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(sys->d_B32, B32.data(), B32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (sets == 1) {
+            e = build_dense_tc_device(sys, B);
+        } else {
+            sys->s_tc = 0;
+            e = cudaMalloc(&sys->d_err, sizeof(int));
+            if (e == cudaSuccess) e = cudaMemset(sys->d_err, 0, sizeof(int));
+        }
+    }
     return e;
 }
 

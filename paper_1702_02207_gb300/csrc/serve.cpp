@@ -358,6 +358,10 @@ cudaError_t ServeEngine::launch(Group* g)
         } else if (sys->path == PATH_CHAIN) {
             sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * 2 * s)
                                           : (const void*)(sys->d_B32 + r->set * 4 * s);
+        } else if (sys->n_sys != 1 && (fp64_prec(r->prec) || r->prec == CHO_FP32_KAHAN)) {
+            const size_t n = (size_t)sys->s_pad * sys->s_pad;   // dense, one (M, K) per set: its B^T
+            sd.coef = fp64_prec(r->prec) ? (const void*)(sys->d_B64 + r->set * n)
+                                          : (const void*)(sys->d_B32 + r->set * 2 * n);
         }
         sd.state = r->block;
         sd.h = r->h;
@@ -393,7 +397,8 @@ cudaError_t ServeEngine::launch(Group* g)
         e = launch_rk4_chain_slots(s_max, io, f64, g->st);
     } else {
         cho_system_impl* sys = std::get<3>(g->key);
-        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0};
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
+                    sys->n_sys != 1 ? 1 : 0};
         if (prec == CHO_DENSE_BF16X3 || prec == CHO_DENSE_BF16X5 || prec == CHO_DENSE_BF16X6)
             e = launch_rk4_dense_tc_slots(ds, io, prec, g->st);
         else

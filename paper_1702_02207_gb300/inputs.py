@@ -194,6 +194,26 @@ def dense_group(s=128, n_inst=8192, n_steps=5000, steps_per_period=100, seed=Non
             "v0": v0, "h": np.full(n_inst, h), "n_steps": int(n_steps), "omega_max": w}
 
 
+def dense_own(s=128, n_inst=64, n_steps=1000, steps_per_period=100, seed=None):
+    """n_inst independent dense systems of size s, each with its own (M, K) drawn as in
+    ``dense_system`` (seed + instance index), h = T_min/steps_per_period per instance."""
+    if seed is None:
+        seed = SEED_BASE + 5 + 1000 * s
+    Ms, Ks, ws = [], [], []
+    for i in range(n_inst):
+        M, K, _, _ = dense_system(s, seed + i)
+        Ms.append(M)
+        Ks.append(K)
+        ws.append(omega_max_dense(M, K))
+    rng = _rng(seed + 10 ** 6)
+    x0 = rng.normal(0.0, 1.0, size=(n_inst, s))
+    v0 = np.zeros((n_inst, s))
+    w = np.asarray(ws)
+    h = fp32_exact(2.0 * math.pi / w / steps_per_period)
+    return {"kind": "dense", "s": s, "M": np.stack(Ms), "K": np.stack(Ks), "x0": x0, "v0": v0, "h": h,
+            "n_steps": int(n_steps), "omega_max": w}
+
+
 def uniform_chain(s, m=1.0, C=1.0):
     """Uniform fixed-free chain: all masses m, all springs C."""
     return np.full((1, s), float(m)), np.full((1, s), float(C))

@@ -452,6 +452,38 @@ def test_balanced_handover_wait_gives_up_and_reports(ctx):
         cho.cho_destroy_system(sys_)
 
 
+# ---- dense systems with one (M, K) per instance (CUDA cores) ----------------------------------
+
+@pytest.mark.parametrize("s", [33, 64, 100, 128, 256, 300])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_dense_per_instance(ctx, s, prec, tol):
+    """Seven instances, each with its own M and K (and its own h = T_min/100), 1000 steps."""
+    cfg = inputs.dense_own(s=s, n_inst=7, n_steps=1000)
+    out = run_gpu(ctx, cfg, prec, 125)
+    ref = oracle_run(cfg, ckpt_every=125)
+    ex, ev = check(out, ref, tol)
+    print(f"dense own-K s={s} {prec}: x {ex:.3e} v {ev:.3e}")
+
+
+def test_dense_per_instance_energy_and_errors(ctx):
+    """FP64 energy per checkpoint from each instance's own M and K; BF16 modes are refused."""
+    import oracle
+
+    cfg = inputs.dense_own(s=48, n_inst=3, n_steps=500)
+    sys_ = make_system(ctx, cfg)
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 500, "fp64", 100, energy=True)
+        for i in range(3):
+            e_ref = oracle.energy_dense(cfg["M"][i], cfg["K"][i], out["x_traj"][i], out["v_traj"][i])
+            assert np.allclose(out["energy"][i], e_ref, rtol=1e-12)
+        for prec in ("bf16x3", "bf16x5"):
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 10, prec)
+            assert ei.value.status == cho.CHO_EINVAL
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
 # ---- polynomial form (k RK4 steps per update with P(hA)^k) ---------------------------------------
 
 @pytest.mark.parametrize("prec,tol,k", [("fp32_kahan", TOL_FP32, 1), ("fp32_kahan", TOL_FP32, 5),

@@ -378,3 +378,26 @@ def test_periodic_mode_reports_overload():
         cho.cho_destroy_system(sc)
     finally:
         cho.cho_shutdown(ctx)
+
+
+def test_dense_requests_with_their_own_k():
+    """Dense requests on a system with one (M, K) per parameter set: each request runs on its
+    set's B, with the bits of the batch API and within tolerance of the oracle."""
+    ctx = cho.cho_init(0, chunk_steps=250)
+    try:
+        cfg = inputs.dense_own(s=70, n_inst=5, n_steps=600)
+        sys_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
+        tickets = [cho.cho_submit(ctx, sys_, cfg["x0"][i], cfg["v0"][i], float(cfg["h"][i]), 600, "fp32_kahan",
+                                  i % 3, sys_index=i) for i in range(5)]
+        got = wait_all(ctx, tickets, [70] * 5)
+        b = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 600, "fp32_kahan")
+        ref = oracle_run(cfg)
+        for i, t in enumerate(tickets):
+            assert np.array_equal(got[t]["x"], b["x"][i]) and np.array_equal(got[t]["v"], b["v"][i])
+            assert np.max(np.abs(got[t]["x"] - ref["x"][i])) / np.max(np.abs(ref["x"][i])) < TOL_FP32
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_submit(ctx, sys_, cfg["x0"][0], cfg["v0"][0], float(cfg["h"][0]), 10, "bf16x5", 0)
+        assert ei.value.status == cho.CHO_EINVAL
+        cho.cho_destroy_system(sys_)
+    finally:
+        cho.cho_shutdown(ctx)
