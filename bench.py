@@ -327,7 +327,8 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
             ref = oracle.rk4_dense(cfg["M"][idx], cfg["K"][idx], cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx],
                                    cfg["n_steps"], every, threads=n_sample)
         elif cfg["kind"] == "dense":
-            r = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
+            r = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
+                                        poly_jump=poly)
             ref = oracle.rk4_dense(cfg["M"][0], cfg["K"][0], cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx],
                                    cfg["n_steps"], every, threads=n_sample)
         else:
@@ -411,6 +412,19 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                                                "error_vs_oracle": sampled_err(s_, cfg, prec),
                                                "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
                                                             "unit": "TFLOP/s", "frac": ach / bf16_peak}}
+        if s == 128:
+            # the polynomial form with k-step jumps on the CUDA cores (FP32 pairs): three
+            # s x s jump blocks, four products per k steps; flops of the form itself
+            for k in (5, 25):
+                t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"], poly=k)
+                dof = cfg["x0"].size * cfg["n_steps"]
+                ach = cfg["x0"].shape[0] * (cfg["n_steps"] // k) * 16 * s * s / t / 1e12
+                res[f"dense_s{s}_x8192_poly_k{k}_fp32"] = {
+                    "value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                    "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan", poly=k),
+                    "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                                 "frac": ach / alu_peak,
+                                 "note": "flops of the form: 4 products x 2 (hi, lo) x 2 s^2 per instance-jump"}}
         cho.cho_destroy_system(s_)
     return res
 

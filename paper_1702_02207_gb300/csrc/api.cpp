@@ -83,6 +83,11 @@ static cudaError_t upload(T** dst, const T* src, size_t n)
 
 static void free_system_device(cho_system_impl* s)
 {
+    for (auto& pb : s->poly) {
+        if (pb.d64) cudaFree(pb.d64);
+        if (pb.d32) cudaFree(pb.d32);
+    }
+    s->poly.clear();
     void* ptrs[] = {s->d_B64, s->d_B32, s->d_Bbf, s->d_masses, s->d_springs, s->d_M, s->d_K, s->d_plain, s->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -349,6 +354,7 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
         if (e == cudaSuccess) e = upload(&sys->d_B32, C32.data(), C32.size());
     } else {
         e = build_dense_device(sys, plain.data());
+        if (n_sys == 1) sys->h_B = plain;
     }
     if (e == cudaSuccess) {
         if (springs) {
@@ -444,10 +450,12 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     if (b->poly_jump < 0) return fail(CHO_EINVAL, "%s: poly_jump < 0", who);
     if (b->poly_jump > 0) {
         if (plain_form) return fail(CHO_EINVAL, "%s: the plain form runs RK4 stage by stage", who);
-        if (sys->path != PATH_SMALL || sys->s != 2)
-            return fail(CHO_EINVAL, "%s: the polynomial form is built for s = 2 systems", who);
-        if (p != CHO_FP64 && p != CHO_FP32_KAHAN)
-            return fail(CHO_EINVAL, "%s: the polynomial form runs in CHO_FP64 or CHO_FP32_KAHAN", who);
+        const bool small2 = sys->path == PATH_SMALL && sys->s == 2;
+        const bool dense1 = sys->path == PATH_DENSE && sys->n_sys == 1;
+        if (!small2 && !dense1)
+            return fail(CHO_EINVAL, "%s: the polynomial form is built for s = 2 systems and shared dense systems", who);
+        if (p != CHO_FP64 && p != CHO_FP32_KAHAN && !(dense1 && p == CHO_DENSE_FP32_SIMT))
+            return fail(CHO_EINVAL, "%s: the polynomial form runs in CHO_FP64 or FP32 (compensated)", who);
         if (b->n_steps % b->poly_jump != 0 || (b->ckpt_every > 0 && b->ckpt_every % b->poly_jump != 0))
             return fail(CHO_EINVAL, "%s: poly_jump must divide n_steps and ckpt_every", who);
     }
@@ -495,6 +503,46 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     return CHO_OK;
 }
 
+// The k-step jump blocks of a shared dense system for step h (polynomial form), built
+// on first use in FP64 on the host (O(s^3 log k)), uploaded transposed and padded to
+// s_pad, FP64 and FP32 pairs, and kept with the system.
+static cho_status dense_poly_blocks(cho_system_impl* sys, double h, int k, bool fp64, const void** out)
+{
+    std::lock_guard<std::mutex> lk(sys->poly_mu);
+    for (const auto& pb : sys->poly)
+        if (pb.h == h && pb.k == k) {
+            *out = fp64 ? (const void*)pb.d64 : (const void*)pb.d32;
+            return CHO_OK;
+        }
+    const int s = sys->s, sp = sys->s_pad;
+    std::vector<double> blk[3];
+    linalg::rk4_jump_blocks(s, sys->h_B.data(), h, k, blk[0], blk[1], blk[2]);
+    const size_t n = (size_t)sp * sp;
+    std::vector<double> T64(3 * n, 0.0);
+    std::vector<float> T32(6 * n, 0.0f);
+    for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j) {
+                const double e = blk[m][(size_t)i * s + j];
+                T64[m * n + (size_t)j * sp + i] = e;
+                split_pair(e, T32[2 * m * n + (size_t)j * sp + i], T32[(2 * m + 1) * n + (size_t)j * sp + i]);
+            }
+    cho_system_impl::PolyBlocks pb{h, k, nullptr, nullptr};
+    cudaError_t e = cudaMalloc(&pb.d64, T64.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(pb.d64, T64.data(), T64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&pb.d32, T32.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(pb.d32, T32.data(), T32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (pb.d64) cudaFree(pb.d64);
+        if (pb.d32) cudaFree(pb.d32);
+        return fail(e == cudaErrorMemoryAllocation ? CHO_ENOMEM : CHO_ECUDA, "integrate: jump blocks: %s",
+                    cudaGetErrorString(e));
+    }
+    sys->poly.push_back(pb);
+    *out = fp64 ? (const void*)pb.d64 : (const void*)pb.d32;
+    return CHO_OK;
+}
+
 // Run one batch whose arrays are all device pointers.
 static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st)
 {
@@ -522,6 +570,20 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     } else if (sys->path == PATH_CHAIN) {
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         e = launch_rk4_chain(cs, io, fp64, st);
+    } else if (b->poly_jump > 0) {
+        // polynomial form of a shared dense system: one h for the whole batch
+        const size_t nh = b->h_per_inst ? (size_t)b->n_inst : 1;
+        std::vector<double> hv(nh);
+        e = cudaMemcpyAsync(hv.data(), b->h, nh * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: reading h: %s", cudaGetErrorString(e));
+        for (double hh : hv)
+            if (hh != hv[0]) return fail(CHO_EINVAL, "integrate: the dense polynomial form needs one h for the batch");
+        const void* E = nullptr;
+        cho_status rc = dense_poly_blocks(sys, hv[0], b->poly_jump, fp64, &E);
+        if (rc != CHO_OK) return rc;
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0, 0};
+        e = launch_rk4_dense_poly(ds, E, io, fp64, st);
     } else {
         DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
                     sys->n_sys != 1 ? 1 : 0};

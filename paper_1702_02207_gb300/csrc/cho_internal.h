@@ -123,6 +123,9 @@ struct DenseSys {
 int test_stall_mma();
 int dense_pad(int s);
 cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
+// Polynomial form with k-step jumps (io.poly_jump = k) of a shared dense system: E holds
+// the transposed jump blocks [3][s_pad][s_pad] (FP64) or [3][2][s_pad][s_pad] (FP32 pairs).
+cudaError_t launch_rk4_dense_poly(const DenseSys& sys, const void* E, const BatchIO& io, bool fp64, cudaStream_t st);
 cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st);
 // tensor-core split-BF16 variant (rk4_dense_tc.cu)
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);

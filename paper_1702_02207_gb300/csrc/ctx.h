@@ -65,6 +65,17 @@ struct cho_system_impl {
     double* d_K = nullptr;
     int* d_err = nullptr;               // device error word of the kernels with bounded waits
     double* d_plain = nullptr;          // FP64 plain-form coefficients: tridiagonal [3][s] or dense [s][s]
+    // dense, one shared (M, K): B row-major FP64 (host) and the k-step jump blocks of the
+    // polynomial form per (h, k): [3][s_pad][s_pad] transposed FP64 and [3][2][s_pad][s_pad] FP32 pairs
+    std::vector<double> h_B;
+    struct PolyBlocks {
+        double h;
+        int32_t k;
+        double* d64;
+        float* d32;
+    };
+    std::mutex poly_mu;
+    std::vector<PolyBlocks> poly;
 };
 
 struct cho_ctx {

@@ -186,5 +186,82 @@ double omega_max_dense(int s, const std::vector<double>& L, const double* K)
     return std::sqrt(std::max(0.0, tridiag_max_eig(s, d.data(), e.data())));
 }
 
+
+// C = A B (row-major s x s), i-k-j order.
+static void matmul(int s, const std::vector<double>& A, const std::vector<double>& B, std::vector<double>& C)
+{
+    C.assign((size_t)s * s, 0.0);
+    for (int i = 0; i < s; ++i)
+        for (int l = 0; l < s; ++l) {
+            const double a = A[(size_t)i * s + l];
+            if (a == 0.0) continue;
+            const double* b = &B[(size_t)l * s];
+            double* c = &C[(size_t)i * s];
+            for (int j = 0; j < s; ++j) c[j] += a * b[j];
+        }
+}
+
+namespace {
+// A matrix of the form [[C, H], [G, C]] with commuting blocks.
+struct Jump {
+    std::vector<double> C, H, G;
+};
+
+// X Y for two such matrices: [[Cx Cy + Hx Gy, Cx Hy + Hx Cy], [Gx Cy + Cx Gy, ...]]
+Jump jump_mul(int s, const Jump& X, const Jump& Y)
+{
+    Jump Z;
+    std::vector<double> t;
+    const size_t n = (size_t)s * s;
+    matmul(s, X.C, Y.C, Z.C);
+    matmul(s, X.H, Y.G, t);
+    for (size_t i = 0; i < n; ++i) Z.C[i] += t[i];
+    matmul(s, X.C, Y.H, Z.H);
+    matmul(s, X.H, Y.C, t);
+    for (size_t i = 0; i < n; ++i) Z.H[i] += t[i];
+    matmul(s, X.G, Y.C, Z.G);
+    matmul(s, X.C, Y.G, t);
+    for (size_t i = 0; i < n; ++i) Z.G[i] += t[i];
+    return Z;
+}
+}  // namespace
+
+void rk4_jump_blocks(int s, const double* B, double h, int k, std::vector<double>& Cm1, std::vector<double>& H,
+                     std::vector<double>& G)
+{
+    const size_t n = (size_t)s * s;
+    std::vector<double> Bm(B, B + n), W(n), W2;
+    for (size_t i = 0; i < n; ++i) W[i] = h * h * Bm[i];
+    matmul(s, W, W, W2);
+    Jump P;
+    P.C.resize(n);
+    P.H.resize(n);
+    std::vector<double> S(n);
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) {
+            const size_t ij = (size_t)i * s + j;
+            const double I = i == j ? 1.0 : 0.0;
+            P.C[ij] = I - W[ij] / 2.0 + W2[ij] / 24.0;
+            S[ij] = I - W[ij] / 6.0;
+            P.H[ij] = h * S[ij];
+        }
+    matmul(s, Bm, S, P.G);
+    for (size_t i = 0; i < n; ++i) P.G[i] *= -h;
+    Jump R;
+    bool have = false;
+    Jump base = P;
+    for (int kk = k; kk > 0; kk >>= 1) {
+        if (kk & 1) {
+            R = have ? jump_mul(s, R, base) : base;
+            have = true;
+        }
+        if (kk > 1) base = jump_mul(s, base, base);
+    }
+    Cm1 = R.C;
+    for (int i = 0; i < s; ++i) Cm1[(size_t)i * s + i] -= 1.0;
+    H = R.H;
+    G = R.G;
+}
+
 }  // namespace linalg
 }  // namespace cho

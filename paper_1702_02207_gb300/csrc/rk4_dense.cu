@@ -254,14 +254,21 @@ __global__ void __launch_bounds__(NTHR) rk4_dense_simt_kernel(DenseSys sys, cons
             __syncthreads();                         // chunk c (and, at c = 0, Xs) visible to all
             const Real* bh = bsh + (size_t)(c & 1) * NB * CHUNK;
             const int jn = s - c * kJC < kJC ? s - c * kJC : kJC;   // columns beyond s are zero
+            // blocked summation: the chunk's kJC terms go into a partial sum that is then
+            // added to the total, so the rounding error grows with kJC + s / kJC, not with s
+            Real part[RI];
+#pragma unroll
+            for (int k = 0; k < RI; ++k) part[k] = 0;
             for (int jj = 0; jj < jn; ++jj) {
                 const Real xj = X[(c * kJC + jj) * NT + n];
                 const Real* col = bh + jj * SP + row0;
-                col_fma(col, xj, t0);
+                col_fma(col, xj, part);
                 if constexpr (!F64) {
                     if (first) col_fma(col + CHUNK, xj, lo1);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < RI; ++k) t0[k] = addr(t0[k], part[k]);
             __syncthreads();                         // buffer c & 1 free for chunk c + 2
         }
 #pragma unroll
@@ -382,6 +389,186 @@ cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaSt
 #undef CHO_DENSE_OWN_CASE
 }
 
+// ---- polynomial form with k-step jumps (one shared (M, K), one shared h) ------------
+//
+// For y = (x, v), one RK4 step is y <- P y with P = [[C, H], [G, C]] (blocks
+// polynomials in B; see rk4_jump_blocks), and k steps are P^k = [[C_k, H_k], [G_k, C_k]].
+// With E_xx = C_k - I, E_xv = H_k, E_vx = G_k formed in FP64 on the host, a jump is
+//     x <- x + E_xx x + E_xv v,    v <- v + E_vx x + E_xx v,
+// four products of s x s matrices with the tile's x and v per k steps, against
+// four B-products per step for the stage form.  Same tiling as rk4_dense_simt:
+// the three matrices (transposed; FP32 as hi/lo pairs) are streamed through
+// shared memory in chunks of kJP columns; x and v of the tile are published
+// once per jump; the state update is compensated in FP32.
+constexpr int kJP = 4;
+
+template <int RI, int NT, bool F64>
+__global__ void __launch_bounds__(kDenseThreads) rk4_dense_poly_kernel(DenseSys sys, const void* Ev, BatchIO io)
+{
+    using Real = std::conditional_t<F64, double, float>;
+    constexpr int RG = kDenseThreads / NT;
+    constexpr int SP = RG * RI;
+    constexpr int NB = F64 ? 1 : 2;
+    constexpr int NPC = 3 * NB;                     // pieces: E_xx, E_xv, E_vx (hi, lo)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* xv = (Real*)smem_raw;                     // [2 buffers][x | v][SP][NT]
+    Real* csh = xv + 4 * SP * NT;                   // [2 buffers][NPC][kJP][SP]
+
+    const int t = threadIdx.x;
+    const int n = t % NT;
+    const int r = t / NT;
+    const int row0 = r * RI;
+    const int64_t q = (int64_t)blockIdx.x * NT + n;
+    const bool live = q < io.n_inst;
+    const int s = sys.s;
+    const Real* E = (const Real*)Ev;               // [NPC][SP][SP]
+
+    Real x[RI], v[RI];
+    float cx[RI], cv[RI];
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        const int i = row0 + k;
+        x[k] = v[k] = 0;
+        cx[k] = cv[k] = 0.f;
+        if (live && i < s) {
+            const double xd = io.x0[q * s + i], vd = io.v0[q * s + i];
+            x[k] = (Real)xd;
+            v[k] = (Real)vd;
+            if constexpr (!F64) {
+                cx[k] = (float)(xd - (double)x[k]);
+                cv[k] = (float)(vd - (double)v[k]);
+            }
+        }
+    }
+
+    constexpr int CHUNK = kJP * SP;
+    constexpr int VEC = 16 / sizeof(Real);
+    const int n_chunks = (s + kJP - 1) / kJP;
+    auto load_chunk = [&](int c, int b) {
+#pragma unroll
+        for (int pc = 0; pc < NPC; ++pc) {
+            const Real* src_c = E + (size_t)pc * SP * SP + (size_t)c * CHUNK;
+            Real* dst = csh + ((size_t)b * NPC + pc) * CHUNK;
+            for (int e = t * VEC; e < CHUNK; e += kDenseThreads * VEC) cp_async16(dst + e, src_c + e);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    auto jump = [&]() {
+        Real* X = xv + (size_t)buf * 2 * SP * NT;
+        Real* V = X + SP * NT;
+#pragma unroll
+        for (int k = 0; k < RI; ++k) {
+            X[(row0 + k) * NT + n] = x[k];
+            V[(row0 + k) * NT + n] = v[k];
+        }
+        Real zx[RI], zv[RI];
+#pragma unroll
+        for (int k = 0; k < RI; ++k) zx[k] = zv[k] = 0;
+        load_chunk(0, 0);
+        for (int c = 0; c < n_chunks; ++c) {
+            if (c + 1 < n_chunks) {
+                load_chunk(c + 1, (c + 1) & 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();                         // chunk c (and, at c = 0, x and v) visible to all
+            const Real* ch = csh + (size_t)(c & 1) * NPC * CHUNK;
+            const int jn = s - c * kJP < kJP ? s - c * kJP : kJP;
+            // blocked summation: each chunk's 4 kJP terms per output go into a partial sum
+            // that is then added to the total (the rounding error of the 4 s-term sums grows
+            // with the chunk length plus the number of chunks, not with 4 s)
+            Real px[RI], pv[RI];
+#pragma unroll
+            for (int k = 0; k < RI; ++k) px[k] = pv[k] = 0;
+            for (int jj = 0; jj < jn; ++jj) {
+                const int j = c * kJP + jj;
+                const Real xj = X[j * NT + n], vj = V[j * NT + n];
+                const Real* exx = ch + (0 * NB) * CHUNK + jj * SP + row0;
+                const Real* exv = ch + (1 * NB) * CHUNK + jj * SP + row0;
+                const Real* evx = ch + (2 * NB) * CHUNK + jj * SP + row0;
+                if constexpr (!F64) {                // lo pieces first
+                    col_fma(exx + CHUNK, xj, px);
+                    col_fma(exv + CHUNK, vj, px);
+                    col_fma(evx + CHUNK, xj, pv);
+                    col_fma(exx + CHUNK, vj, pv);
+                }
+                col_fma(exx, xj, px);
+                col_fma(exv, vj, px);
+                col_fma(evx, xj, pv);
+                col_fma(exx, vj, pv);
+            }
+#pragma unroll
+            for (int k = 0; k < RI; ++k) {
+                zx[k] = addr(zx[k], px[k]);
+                zv[k] = addr(zv[k], pv[k]);
+            }
+            __syncthreads();                         // buffer c & 1 free for chunk c + 2
+        }
+#pragma unroll
+        for (int k = 0; k < RI; ++k) {
+            if constexpr (F64) {
+                x[k] = addr(x[k], zx[k]);
+                v[k] = addr(v[k], zv[k]);
+            } else {
+                const float yx = addr(zx[k], cx[k]), tx = addr(x[k], yx);
+                cx[k] = __fsub_rn(yx, __fsub_rn(tx, x[k]));
+                x[k] = tx;
+                const float yv = addr(zv[k], cv[k]), tv = addr(v[k], yv);
+                cv[k] = __fsub_rn(yv, __fsub_rn(tv, v[k]));
+                v[k] = tv;
+            }
+        }
+        buf ^= 1;
+    };
+
+    const int64_t kj = io.poly_jump;
+    const int64_t jumps = io.n_steps / kj;
+    const int64_t per_ck = io.ckpt_every > 0 && io.x_traj ? io.ckpt_every / kj : (jumps > 0 ? jumps : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < jumps; done += per_ck) {
+        for (int64_t it = 0; it < per_ck; ++it) jump();
+        if (io.ckpt_every > 0 && io.x_traj && live) {
+#pragma unroll
+            for (int k = 0; k < RI; ++k) {
+                const int i = row0 + k;
+                if (i >= s) continue;
+                const int64_t o = (q * io.n_ck + ck) * s + i;
+                io.x_traj[o] = (double)x[k] + (double)cx[k];
+                if (io.v_traj) io.v_traj[o] = (double)v[k] + (double)cv[k];
+            }
+        }
+        ++ck;
+    }
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < RI; ++k) {
+            const int i = row0 + k;
+            if (i >= s) continue;
+            io.x_out[q * s + i] = (double)x[k] + (double)cx[k];
+            io.v_out[q * s + i] = (double)v[k] + (double)cv[k];
+        }
+    }
+}
+
+template <int RI, int NT, bool F64>
+cudaError_t launch_poly(const DenseSys& sys, const void* E, const BatchIO& io, cudaStream_t st)
+{
+    using Real = std::conditional_t<F64, double, float>;
+    constexpr int SP = (kDenseThreads / NT) * RI;
+    constexpr int NPC = 3 * (F64 ? 1 : 2);
+    if (sys.s_pad != SP) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(Real) * (4 * (size_t)SP * NT + 2 * (size_t)NPC * kJP * SP);
+    auto kern = rk4_dense_poly_kernel<RI, NT, F64>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (io.n_inst + NT - 1) / NT;
+    if (blocks <= 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, kDenseThreads, smem, st>>>(sys, E, io);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // s_pad: next power of two >= max(s, 64); the SIMT kernels cover s_pad <= 512.
@@ -401,6 +588,22 @@ cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, c
         src.io = io;
         src.s = sys.s;
     });
+}
+
+cudaError_t launch_rk4_dense_poly(const DenseSys& sys, const void* E, const BatchIO& io, bool fp64, cudaStream_t st)
+{
+    if (io.n_inst == 0) return cudaSuccess;
+#define CHO_POLY_CASE(SPV, RI64, NT64, RI32, NT32)                                                  \
+    case SPV:                                                                                        \
+        return fp64 ? launch_poly<RI64, NT64, true>(sys, E, io, st) : launch_poly<RI32, NT32, false>(sys, E, io, st);
+    switch (sys.s_pad) {
+        CHO_POLY_CASE(64, 2, 8, 4, 16)
+        CHO_POLY_CASE(128, 4, 8, 8, 16)
+        CHO_POLY_CASE(256, 8, 8, 16, 16)
+        CHO_POLY_CASE(512, 8, 4, 16, 8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CHO_POLY_CASE
 }
 
 cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st)

@@ -511,6 +511,71 @@ def test_poly_form_matches_oracle(ctx, prec, tol, k):
     print(f"poly k={k} {prec}: x {ex:.3e} v {ev:.3e}")
 
 
+@pytest.mark.parametrize("s", [33, 64, 128, 256, 300])
+@pytest.mark.parametrize("prec,tol,k", [("fp64", TOL_FP64, 1), ("fp64", TOL_FP64, 25), ("fp32_kahan", TOL_FP32, 1),
+                                        ("fp32_kahan", TOL_FP32, 5)])
+def test_dense_poly_form_matches_oracle(ctx, s, prec, tol, k):
+    """Shared dense system, jumps x <- x + E_xx x + E_xv v, v <- v + E_vx x + E_xx v built from
+    P(hA)^k in FP64 on the host; 9 instances, 1000 steps against the stage-by-stage oracle."""
+    import torch
+
+    cfg = inputs.dense_group(s=s, n_inst=9, n_steps=1000)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                      1000, prec, 125, trajectory=True, poly_jump=k)
+        torch.cuda.synchronize()
+        out = {key: val.cpu().numpy() for key, val in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+    ref = oracle_run(cfg, ckpt_every=125)
+    ex, ev = check(out, ref, tol)
+    print(f"dense poly s={s} k={k} {prec}: x {ex:.3e} v {ev:.3e}")
+
+
+def test_dense_poly_form_needs_one_h(ctx):
+    cfg = inputs.dense_group(s=40, n_inst=3, n_steps=100)
+    h = cfg["h"].copy()
+    h[1] *= 0.5
+    sys_ = make_system(ctx, cfg)
+    try:
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], h, 100, "fp32_kahan", poly_jump=5)
+        assert ei.value.status == cho.CHO_EINVAL
+        own = inputs.dense_own(s=40, n_inst=2, n_steps=10)
+        s2 = make_system(ctx, own)
+        try:
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(ctx, s2, own["x0"], own["v0"], own["h"], 10, "fp32_kahan", poly_jump=5)
+            assert ei.value.status == cho.CHO_EINVAL
+        finally:
+            cho.cho_destroy_system(s2)
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+def test_dense_poly_form_full_size_sampled(ctx):
+    """8192 instances of s = 128, 5e3 steps, k = 5, sampled against the oracle."""
+    import torch
+
+    cfg = inputs.dense_group(s=128, n_inst=8192, n_steps=5000)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                      5000, "fp32_kahan", 625, trajectory=True, poly_jump=5)
+        torch.cuda.synchronize()
+        out = {key: val.cpu().numpy() for key, val in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+    idx = sample_indices(8192, 6)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=625)
+    check(out, ref, TOL_FP32, idx)
+
+
 @pytest.mark.parametrize("k", [1, 5, 25])
 def test_poly_form_full_size_sampled(ctx, k):
     """65,536 systems x 1e4 steps in the polynomial form on the balanced schedule, sampled
