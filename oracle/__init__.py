@@ -9,6 +9,7 @@ from .oracle import (  # noqa: F401
     build,
     load,
     rk4_chain,
+    rk4_chain_ext,
     rk4_dense,
     energy_chain,
     energy_dense,

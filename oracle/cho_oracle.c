@@ -19,7 +19,11 @@
  *     Runge-Kutta integration without the order; the classical scheme with
  *     weights 1/6, 1/3, 1/3, 1/6 at nodes 0, 1/2, 1/2, 1 is the reading used).
  *   - the mechanical energy 1/2 v^T M v + 1/2 x^T K x, which eq. 1 conserves for
- *     symmetric M and K.
+ *     symmetric M and K;
+ *   - beyond the paper (which treats the undamped case only): the chain with a
+ *     dashpot beside every spring and a harmonic force on every mass,
+ *     M x'' + D x' + K x = F cos(Om t + phi), integrated by the same RK4 with the
+ *     stage times t, t + h/2, t + h/2, t + h (oracle_rk4_chain_ext).
  *
  * Plain loops, FP64, single-threaded, built with -O2 -ffp-contract=off and no
  * fast-math so that every rounding is the one written here.
@@ -52,6 +56,9 @@ typedef struct {
     int s;
     const double* m;       /* chain: s masses */
     const double* C;       /* chain: s spring rates, C[0] is the wall spring */
+    const double* c;       /* chain, optional: s dashpot rates, dashpot i beside spring i */
+    const double* F;       /* chain, optional: s force amplitudes, f_i(t) = F_i cos(Om t + phi) */
+    double Om, phi;        /* forcing frequency (rad/s) and phase */
     const double* M;       /* dense: s*s row-major mass matrix */
     const double* K;       /* dense: s*s row-major stiffness matrix */
     double* L;             /* dense: Cholesky factor of M (lower, row-major), owned */
@@ -125,12 +132,41 @@ static void accel(const model_t* md, const double* x, double* a)
     else dense_accel(md, x, a);
 }
 
-/* First-order right-hand side of Section 3: y = (x, v), D(y) = (v, x''). */
-static void rhs(const model_t* md, const double* y, double* D)
+/* Beyond the paper (its undamped eq. 1-3): M x'' + D x' + K x = f(t) for the chain,
+ * a dashpot c_i beside every spring (same attachment) and a harmonic force on every
+ * mass.  Per mass:
+ *   m_i x_i'' = -C_i e_i + C_{i+1} e_{i+1} - c_i e_i' + c_{i+1} e_{i+1}' + F_i cos(Om t + phi),
+ * e_i = x_i - x_{i-1} (x_{-1} = 0), e_i' = v_i - v_{i-1}; nothing right of the last mass. */
+static void chain_accel_ext(const model_t* md, const double* x, const double* v, double t, double* a)
+{
+    const int s = md->s;
+    const double f = md->F ? cos(md->Om * t + md->phi) : 0.0;
+    for (int i = 0; i < s; ++i) {
+        double ext_left = (i == 0) ? x[0] : (x[i] - x[i - 1]);
+        double force = -md->C[i] * ext_left;
+        if (i + 1 < s) force += md->C[i + 1] * (x[i + 1] - x[i]);
+        if (md->c) {
+            double rate_left = (i == 0) ? v[0] : (v[i] - v[i - 1]);
+#if ORACLE_MUTANT == 4
+            force += md->c[i] * rate_left;                      /* wrong sign */
+#else
+            force -= md->c[i] * rate_left;
+#endif
+            if (i + 1 < s) force += md->c[i + 1] * (v[i + 1] - v[i]);
+        }
+        if (md->F) force += md->F[i] * f;
+        a[i] = force / md->m[i];
+    }
+}
+
+/* First-order right-hand side of Section 3: y = (x, v), D(y) = (v, x''); t is the
+ * stage time (used only by the forced model). */
+static void rhs(const model_t* md, const double* y, double t, double* D)
 {
     const int s = md->s;
     for (int i = 0; i < s; ++i) D[i] = y[s + i];            /* D(1), D(2): x' = v   */
-    accel(md, y, D + s);                                      /* D(3), D(4): v' = x'' */
+    if (md->kind == 0 && (md->c || md->F)) chain_accel_ext(md, y, y + s, t, D + s);
+    else accel(md, y, D + s);                                 /* D(3), D(4): v' = x'' */
 }
 
 /* ------------------------------------------------------------------------- */
@@ -155,17 +191,18 @@ static int rk4_run(const model_t* md, const double* x0, const double* v0, double
     for (int i = 0; i < s; ++i) { y[i] = x0[i]; y[s + i] = v0[i]; }
     long ck = 0;
     for (long step = 1; step <= n_steps; ++step) {
-        rhs(md, y, k1);
+        const double t = (double)(step - 1) * h;            /* stage times t, t + h/2, t + h/2, t + h */
+        rhs(md, y, t, k1);
         for (int i = 0; i < n; ++i) yt[i] = y[i] + (h / 2.0) * k1[i];
-        rhs(md, yt, k2);
+        rhs(md, yt, t + h / 2.0, k2);
         for (int i = 0; i < n; ++i) yt[i] = y[i] + (h / 2.0) * k2[i];
-        rhs(md, yt, k3);
+        rhs(md, yt, t + h / 2.0, k3);
 #if ORACLE_MUTANT == 2
         for (int i = 0; i < n; ++i) yt[i] = y[i] + (h / 2.0) * k3[i];   /* wrong node */
 #else
         for (int i = 0; i < n; ++i) yt[i] = y[i] + h * k3[i];
 #endif
-        rhs(md, yt, k4);
+        rhs(md, yt, t + h, k4);
         for (int i = 0; i < n; ++i) {
 #if ORACLE_MUTANT == 3
             y[i] = y[i] + (h / 6.0) * (k1[i] + 2.0 * k2[i] + k3[i] + k4[i]);  /* dropped weight */
@@ -218,6 +255,37 @@ int oracle_rk4_chain(int s, long n_inst, long n_sys, const double* masses, const
         md.s = s;
         md.m = masses + p * s;
         md.C = springs + p * s;
+        rc = rk4_run(&md, x0 + q * s, v0 + q * s, h[q], n_steps, ckpt_every,
+                     x_traj ? x_traj + q * n_ck * s : NULL, v_traj ? v_traj + q * n_ck * s : NULL,
+                     x_out ? x_out + q * s : NULL, v_out ? v_out + q * s : NULL);
+        if (rc) return rc;
+    }
+    return ORACLE_OK;
+}
+
+/* The damped and forced chain (chain_accel_ext); dampers and famp (n_sys, s) may be NULL,
+ * fomega and fphase (n_sys) are read only when famp is given. */
+int oracle_rk4_chain_ext(int s, long n_inst, long n_sys, const double* masses, const double* springs,
+                         const double* dampers, const double* famp, const double* fomega, const double* fphase,
+                         const double* x0, const double* v0, const double* h, long n_steps,
+                         long ckpt_every, double* x_traj, double* v_traj, double* x_out, double* v_out)
+{
+    int rc = check_common(s, n_inst, n_sys, n_steps, ckpt_every);
+    if (rc) return rc;
+    if (famp && (!fomega || !fphase)) return ORACLE_EINVAL;
+    long n_ck = ckpt_every > 0 ? n_steps / ckpt_every : 0;
+    for (long q = 0; q < n_inst; ++q) {
+        long p = (n_sys == 1) ? 0 : q;
+        model_t md;
+        memset(&md, 0, sizeof md);
+        md.kind = 0;
+        md.s = s;
+        md.m = masses + p * s;
+        md.C = springs + p * s;
+        md.c = dampers ? dampers + p * s : NULL;
+        md.F = famp ? famp + p * s : NULL;
+        md.Om = famp ? fomega[p] : 0.0;
+        md.phi = famp ? fphase[p] : 0.0;
         rc = rk4_run(&md, x0 + q * s, v0 + q * s, h[q], n_steps, ckpt_every,
                      x_traj ? x_traj + q * n_ck * s : NULL, v_traj ? v_traj + q * n_ck * s : NULL,
                      x_out ? x_out + q * s : NULL, v_out ? v_out + q * s : NULL);

@@ -61,6 +61,9 @@ def load(mutant: int = 0) -> ctypes.CDLL:
             f = getattr(lib, fn)
             f.restype = I
             f.argtypes = [I, L, L, _dp, _dp, _dp, _dp, _dp, L, L, _dp, _dp, _dp, _dp]
+        f = lib.oracle_rk4_chain_ext
+        f.restype = I
+        f.argtypes = [I, L, L, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, L, L, _dp, _dp, _dp, _dp]
         for fn in ("oracle_energy_chain", "oracle_energy_dense"):
             f = getattr(lib, fn)
             f.restype = I
@@ -132,6 +135,63 @@ def rk4_chain(masses, springs, x0, v0, h, n_steps, ckpt_every=0, threads=1, muta
     s = masses.shape[1]
     return _run_rk4("oracle_rk4_chain", s, masses, springs, x0, v0, h, n_steps, ckpt_every,
                     threads, mutant)
+
+
+def rk4_chain_ext(masses, springs, x0, v0, h, n_steps, ckpt_every=0, dampers=None, force_amp=None,
+                  force_omega=None, force_phase=None, threads=1, mutant=0):
+    """Classical RK4 on the chain with a dashpot beside every spring and a harmonic force
+    F_i cos(omega t + phase) on every mass: M x'' + D x' + K x = f(t) (beyond the paper's
+    undamped eqs. 1-3).  dampers, force_amp: (n_sys, s) or None; force_omega, force_phase:
+    (n_sys,) (phase defaults to 0).  t = 0 at the first step.  Other arguments as ``rk4_chain``."""
+    lib = load(mutant)
+    masses = _f64(np.atleast_2d(masses))
+    s = masses.shape[1]
+    springs = _f64(springs).reshape(-1, s)
+    n_sys = masses.shape[0]
+    x0 = _f64(x0).reshape(-1, s)
+    v0 = _f64(v0).reshape(-1, s)
+    n_inst = x0.shape[0]
+    if n_sys not in (1, n_inst):
+        raise ValueError("parameter sets must be 1 or one per instance")
+    h = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (n_inst,)))
+    damp = None if dampers is None else _f64(dampers).reshape(-1, s)
+    famp = None if force_amp is None else _f64(force_amp).reshape(-1, s)
+    fom = None if famp is None else _f64(np.broadcast_to(np.asarray(force_omega, dtype=np.float64), (n_sys,)))
+    fph = None if famp is None else _f64(np.broadcast_to(
+        np.asarray(0.0 if force_phase is None else force_phase, dtype=np.float64), (n_sys,)))
+    n_ck = n_steps // ckpt_every if ckpt_every else 0
+    x_out = np.empty((n_inst, s))
+    v_out = np.empty((n_inst, s))
+    x_tr = np.empty((n_inst, n_ck, s)) if n_ck else None
+    v_tr = np.empty((n_inst, n_ck, s)) if n_ck else None
+
+    def sl(a, lo, hi):
+        if a is None:
+            return None
+        return _ptr(a[0:1] if n_sys == 1 else a[lo:hi])
+
+    def part(lo, hi):
+        if hi <= lo:
+            return 0
+        nsys_part = 1 if n_sys == 1 else hi - lo
+        return lib.oracle_rk4_chain_ext(s, hi - lo, nsys_part, sl(masses, lo, hi), sl(springs, lo, hi),
+                                        sl(damp, lo, hi), sl(famp, lo, hi), sl(fom, lo, hi), sl(fph, lo, hi),
+                                        _ptr(x0[lo:hi]), _ptr(v0[lo:hi]), _ptr(h[lo:hi]), int(n_steps),
+                                        int(ckpt_every), _ptr(x_tr[lo:hi]) if n_ck else None,
+                                        _ptr(v_tr[lo:hi]) if n_ck else None, _ptr(x_out[lo:hi]),
+                                        _ptr(v_out[lo:hi]))
+
+    threads = max(1, min(int(threads), n_inst))
+    if threads == 1:
+        rcs = [part(0, n_inst)]
+    else:
+        bounds = np.linspace(0, n_inst, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(lambda i: part(bounds[i], bounds[i + 1]), range(threads)))
+    for rc in rcs:
+        if rc != 0:
+            raise RuntimeError(f"oracle_rk4_chain_ext failed with status {rc}")
+    return {"x": x_out, "v": v_out, "x_traj": x_tr, "v_traj": v_tr}
 
 
 def rk4_dense(M, K, x0, v0, h, n_steps, ckpt_every=0, threads=1, mutant=0):

@@ -534,3 +534,107 @@ def test_pins_catch_planted_mistakes(mutant):
     bad = oracle.rk4_chain(m[None], C[None], x0[None], np.zeros((1, s)), h, n, mutant=mutant)
     assert relmax(good["x"][0], y[:s]) < 1e-11
     assert relmax(bad["x"][0], y[:s]) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Damped and forced chain (beyond the paper's undamped model):
+#   M x'' + D x' + K x = F cos(Om t + phi),  D = E^T diag(c) E like K = E^T diag(C) E
+# --------------------------------------------------------------------------
+
+def damped_first_order_matrix(m, C, c):
+    s = len(m)
+    K = chain_K_from_energy(C)
+    Dm = chain_K_from_energy(c)          # dashpots attached like the springs
+    A = np.zeros((2 * s, 2 * s))
+    A[:s, s:] = np.eye(s)
+    A[s:, :s] = -K / np.asarray(m)[:, None]
+    A[s:, s:] = -Dm / np.asarray(m)[:, None]
+    return A
+
+
+def test_ext_without_damping_or_forcing_is_the_chain_oracle():
+    rng = np.random.default_rng(11)
+    m = rng.uniform(0.5, 2.0, (3, 6))
+    C = rng.uniform(1e2, 1e3, (3, 6))
+    x0 = rng.normal(size=(3, 6))
+    a = oracle.rk4_chain(m, C, x0, np.zeros((3, 6)), 1e-3, 400, 100)
+    b = oracle.rk4_chain_ext(m, C, x0, np.zeros((3, 6)), 1e-3, 400, 100)
+    for k in ("x", "v", "x_traj", "v_traj"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 6])
+def test_damped_chain_matches_matrix_power(s):
+    """Unforced damped chain: RK4 is y <- P(hA) y with A = [[0, I], [-M^-1 K, -M^-1 D]]."""
+    rng = np.random.default_rng(20 + s)
+    m = rng.uniform(0.5, 2.0, s)
+    C = rng.uniform(1e2, 1e3, s)
+    c = rng.uniform(0.5, 5.0, s)
+    x0 = rng.normal(size=s)
+    v0 = rng.normal(size=s)
+    A = damped_first_order_matrix(m, C, c)
+    h, n = 1e-3, 300
+    y = np.linalg.matrix_power(rk4_matrix(A, h), n) @ np.concatenate([x0, v0])
+    r = oracle.rk4_chain_ext(m[None], C[None], x0[None], v0[None], h, n, dampers=c[None])
+    assert relmax(r["x"][0], y[:s]) < 1e-12
+    assert relmax(r["v"][0], y[s:]) < 1e-12
+
+
+def forced_oscillator_exact(m, k, c, F, Om, phi, x0, v0, t):
+    """m x'' + c x' + k x = F cos(Om t + phi), underdamped: steady state plus transient."""
+    w = math.sqrt(k / m)
+    zeta = c / (2.0 * math.sqrt(k * m))
+    wd = w * math.sqrt(1.0 - zeta * zeta)
+    X = F / math.hypot(k - m * Om * Om, c * Om)
+    delta = math.atan2(c * Om, k - m * Om * Om)
+    xp = lambda tt: X * np.cos(Om * tt + phi - delta)                 # noqa: E731
+    vp = lambda tt: -X * Om * np.sin(Om * tt + phi - delta)           # noqa: E731
+    A = x0 - xp(0.0)
+    B = (v0 - vp(0.0) + zeta * w * A) / wd
+    env = np.exp(-zeta * w * t)
+    x = env * (A * np.cos(wd * t) + B * np.sin(wd * t)) + xp(t)
+    v = (env * (-zeta * w * (A * np.cos(wd * t) + B * np.sin(wd * t))
+                + wd * (-A * np.sin(wd * t) + B * np.cos(wd * t))) + vp(t))
+    return x, v
+
+
+def test_forced_damped_oscillator_closed_form_and_order():
+    """One mass on a spring and a dashpot, driven by F cos(Om t + phi): the RK4 result at
+    t = 2 s against the exact solution, and fourth-order convergence (halving h divides the
+    error by ~16: a stage taken at the wrong time would make it first or second order)."""
+    m, k, c, F, Om, phi = 1.5, 600.0, 3.0, 2.0, 13.0, 0.4
+    x0, v0, T = 0.3, -1.1, 2.0
+    xe, ve = forced_oscillator_exact(m, k, c, F, Om, phi, x0, v0, T)
+    errs = []
+    for n in (2000, 4000):
+        h = T / n
+        r = oracle.rk4_chain_ext([[m]], [[k]], [[x0]], [[v0]], h, n, dampers=[[c]], force_amp=[[F]],
+                                 force_omega=[Om], force_phase=[phi])
+        errs.append(max(abs(r["x"][0, 0] - xe), abs(r["v"][0, 0] - ve) / math.sqrt(k / m)))
+    assert errs[1] < 1e-9
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
+def test_damped_energy_decreases():
+    rng = np.random.default_rng(3)
+    s = 8
+    m = rng.uniform(0.5, 2.0, (1, s))
+    C = rng.uniform(1e2, 1e3, (1, s))
+    c = rng.uniform(0.1, 1.0, (1, s))
+    r = oracle.rk4_chain_ext(m, C, rng.normal(size=(1, s)), np.zeros((1, s)), 1e-3, 2000, 50, dampers=c)
+    E = oracle.energy_chain(m, C, r["x_traj"][0], r["v_traj"][0])
+    assert np.all(np.diff(E) < 0)
+
+
+def test_pin_catches_planted_damping_sign():
+    s = 3
+    rng = np.random.default_rng(9)
+    m = rng.uniform(0.5, 2.0, s)
+    C = rng.uniform(1e2, 1e3, s)
+    c = rng.uniform(0.5, 5.0, s)
+    x0 = rng.normal(size=s)
+    A = damped_first_order_matrix(m, C, c)
+    y = np.linalg.matrix_power(rk4_matrix(A, 1e-3), 300) @ np.concatenate([x0, np.zeros(s)])
+    bad = oracle.rk4_chain_ext(m[None], C[None], x0[None], np.zeros((1, s)), 1e-3, 300, dampers=c[None],
+                               mutant=4)
+    assert relmax(bad["x"][0], y[:s]) > 1e-6
