@@ -385,6 +385,37 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                                             "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak,
                                                          "unit": "TFLOP/s", "frac": ach / alu_peak}}
     cho.cho_destroy_system(s_)
+    # the same chains with a dashpot beside every spring (damping ratios of a few percent) and a
+    # harmonic force on every mass (beyond the paper's undamped model)
+    rng = np.random.default_rng(inputs.SEED_BASE + 6)
+    damp = 0.04 * np.sqrt(cfg["springs"] * cfg["masses"]) * rng.uniform(0.5, 2.0, cfg["springs"].shape)
+    famp = cfg["springs"] * rng.normal(0.0, 0.01, cfg["springs"].shape)
+    fom = cfg["omega_max"] * rng.uniform(0.05, 0.5, cfg["x0"].shape[0])
+    fph = rng.uniform(-np.pi, np.pi, cfg["x0"].shape[0])
+    s_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    cho.cho_system_set_damping(s_, damp)
+    cho.cho_system_set_forcing(s_, famp, fom, fph)
+    t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])
+    dof = cfg["x0"].size * cfg["n_steps"]
+    ach = dof * 68 / t / 1e12            # 34 FMA per DOF-step: 4 x (2 spring + 2 dashpot + 1 force), 14 combine/update
+    import oracle
+
+    idx = np.array([0, cfg["x0"].shape[0] - 1])
+    s2 = cho.cho_create_system(ctx, "chain", masses=cfg["masses"][idx], springs=cfg["springs"][idx])
+    cho.cho_system_set_damping(s2, damp[idx])
+    cho.cho_system_set_forcing(s2, famp[idx], fom[idx], fph[idx])
+    r = cho.cho_integrate_batch(ctx, s2, cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx], cfg["n_steps"], "fp32_kahan",
+                                625, trajectory=True)
+    cho.cho_destroy_system(s2)
+    ref = oracle.rk4_chain_ext(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx], cfg["v0"][idx],
+                               cfg["h"][idx], cfg["n_steps"], 625, dampers=damp[idx], force_amp=famp[idx],
+                               force_omega=fom[idx], force_phase=fph[idx], threads=2)
+    err = max(float(np.max(np.max(np.abs(r[k] - ref[k]), axis=(1, 2)) / np.max(np.abs(ref[k]), axis=(1, 2))))
+              for k in ("x_traj", "v_traj"))
+    res["chain_s1024_x4096_damped_forced_fp32_kahan"] = {
+        "value": dof / t, "unit": UNIT, "ms": 1e3 * t, "error_vs_oracle": {"max": err, "instances": 2},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak}}
+    cho.cho_destroy_system(s_)
     # dense systems with one (M, K) per instance: every stage streams the instance's own B^T
     # (hi and lo at stage 1, hi at stages 2-4); 8192 instances of s = 64 hold 268 MB of B,
     # more than L2, so each step must bring the instance's FP32 pair from HBM at least once:

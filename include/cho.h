@@ -200,6 +200,24 @@ const char* cho_last_error(void);
  * use; upload them to the device.  Errors: CHO_EINVAL, CHO_ENOTSPD, CHO_ENOMEM, CHO_ECUDA. */
 cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* desc, cho_system* out);
 
+/* Damping and forcing -- beyond the paper, whose eqs. 1-3 are undamped; its introduction
+ * motivates hardware-in-the-loop simulation, where both appear.  For TWO_DOF and CHAIN
+ * systems only, integrated by rk4_chain for any s <= 1024 in CHO_FP64 or CHO_FP32_KAHAN:
+ *   M x'' + D x' + K x = f(t),  m_i x_i'' = -C_i e_i + C_{i+1} e_{i+1} - c_i e_i' + c_{i+1} e_{i+1}'
+ *                                          + F_i cos(omega t + phase),  e_i = x_i - x_{i-1},
+ * classical RK4 with the stage times t, t + h/2, t + h/2, t + h; t = 0 at the first step of
+ * every batch (a resumed run carries its time in the phase).  Damped or forced systems are
+ * not accepted by cho_submit, the polynomial form, the plain form or the BF16 modes
+ * (CHO_EINVAL there).
+ *
+ * cho_system_set_damping: dampers (n_sys, s) host array in N s/m, finite and >= 0, dashpot i
+ * attached like spring i; NULL removes the damping.
+ * cho_system_set_forcing: amplitude (n_sys, s) in N (finite), omega and phase (n_sys) in rad/s
+ * and rad (finite; phase may be NULL for 0); NULL amplitude removes the forcing.
+ * Both replace earlier values and copy the arrays.  Errors: CHO_EINVAL, CHO_ENOMEM, CHO_ECUDA. */
+cho_status cho_system_set_damping(cho_system sys, const double* dampers);
+cho_status cho_system_set_forcing(cho_system sys, const double* amplitude, const double* omega, const double* phase);
+
 /* omega_max: the largest natural frequency over all parameter sets (rad/s). */
 cho_status cho_system_info(cho_system sys, double* omega_max, int32_t* s, int64_t* n_sys);
 

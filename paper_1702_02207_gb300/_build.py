@@ -23,6 +23,7 @@ SOURCES = [
     "serve.cpp",
     "rk4_small.cu",
     "rk4_chain.cu",
+    "rk4_chain_ext.cu",
     "rk4_dense.cu",
     "rk4_dense_tc.cu",
     "energy.cu",

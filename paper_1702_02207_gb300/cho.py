@@ -36,7 +36,8 @@ PRECS = {"fp64": CHO_FP64, "fp32_kahan": CHO_FP32_KAHAN, "bf16x3": CHO_DENSE_BF1
 
 EXPORTED = [
     "cho_init", "cho_shutdown", "cho_last_error", "cho_create_system", "cho_system_info",
-    "cho_system_omegas", "cho_system_status", "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
+    "cho_system_omegas", "cho_system_status", "cho_system_set_damping", "cho_system_set_forcing",
+    "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
 ]
@@ -105,6 +106,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_system_info": ([V, _dp, ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
             "cho_system_omegas": ([V, _dp], I32),
             "cho_system_status": ([V], I32),
+            "cho_system_set_damping": ([V, V], I32),
+            "cho_system_set_forcing": ([V, V, V, V], I32),
             "cho_destroy_system": ([V], None),
             "cho_integrate_batch": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
             "cho_integrate_plain": ([V, ctypes.POINTER(cho_batch_desc), V], I32),
@@ -232,6 +235,27 @@ def cho_system_omegas(system):
 def cho_system_status(system):
     """CHO_OK, or raises ChoError(CHO_ETIMEOUT) if a tensor-core run on the system gave up a wait."""
     return _check(load().cho_system_status(system))
+
+
+def cho_system_set_damping(system, dampers):
+    """A dashpot beside every spring: dampers (n_sys, s) in N s/m, or None to remove them."""
+    if dampers is None:
+        return _check(load().cho_system_set_damping(system, None))
+    d = _host_f64(dampers)
+    return _check(load().cho_system_set_damping(system, d.ctypes.data))
+
+
+def cho_system_set_forcing(system, amplitude, omega=None, phase=None):
+    """Harmonic force amplitude_i cos(omega t + phase) on every mass: amplitude (n_sys, s) in N,
+    omega and phase (n_sys) or scalars; amplitude None removes the forcing."""
+    if amplitude is None:
+        return _check(load().cho_system_set_forcing(system, None, None, None))
+    _, s, n = cho_system_info(system)
+    a = _host_f64(amplitude).reshape(-1)
+    w = _host_f64(np.broadcast_to(np.asarray(omega, dtype=np.float64), (n,)))
+    p = None if phase is None else _host_f64(np.broadcast_to(np.asarray(phase, dtype=np.float64), (n,)))
+    return _check(load().cho_system_set_forcing(system, a.ctypes.data, w.ctypes.data,
+                                                None if p is None else p.ctypes.data))
 
 
 def cho_destroy_system(system):

@@ -88,6 +88,11 @@ static void free_system_device(cho_system_impl* s)
         if (pb.d32) cudaFree(pb.d32);
     }
     s->poly.clear();
+    for (void* p : {(void*)s->d_ext64, (void*)s->d_ext32, (void*)s->d_force})
+        if (p) cudaFree(p);
+    s->d_ext64 = nullptr;
+    s->d_ext32 = nullptr;
+    s->d_force = nullptr;
     void* ptrs[] = {s->d_B64, s->d_B32, s->d_Bbf, s->d_masses, s->d_springs, s->d_M, s->d_K, s->d_plain, s->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -380,6 +385,105 @@ extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, 
     return CHO_OK;
 }
 
+// Coefficients of the damped / forced chain kernel from the system's masses, springs,
+// dashpots and force amplitudes (absent parts as zeros), FP64 and FP32 pairs, per set.
+static cho_status build_chain_ext(cho_system_impl* sys, const char* who)
+{
+    for (void* p : {(void*)sys->d_ext64, (void*)sys->d_ext32, (void*)sys->d_force})
+        if (p) cudaFree(p);
+    sys->d_ext64 = nullptr;
+    sys->d_ext32 = nullptr;
+    sys->d_force = nullptr;
+    if (!sys->damped() && !sys->forced()) return CHO_OK;
+    const int s = sys->s;
+    const int64_t n_sys = sys->n_sys;
+    std::vector<double> E64((size_t)n_sys * 5 * s, 0.0);
+    std::vector<float> E32((size_t)n_sys * 10 * s, 0.0f);
+    for (int64_t p = 0; p < n_sys; ++p) {
+        const double* m = &sys->h_masses[(size_t)p * s];
+        const double* C = &sys->h_springs[(size_t)p * s];
+        const double* c = sys->damped() ? &sys->h_dampers[(size_t)p * s] : nullptr;
+        const double* F = sys->forced() ? &sys->h_famp[(size_t)p * s] : nullptr;
+        double* e = &E64[(size_t)p * 5 * s];
+        for (int i = 0; i < s; ++i) {
+            e[i] = C[i] / m[i];
+            e[s + i] = i + 1 < s ? C[i + 1] / m[i] : 0.0;
+            e[2 * s + i] = c ? c[i] / m[i] : 0.0;
+            e[3 * s + i] = c && i + 1 < s ? c[i + 1] / m[i] : 0.0;
+            e[4 * s + i] = F ? F[i] / m[i] : 0.0;
+        }
+        float* f = &E32[(size_t)p * 10 * s];
+        for (int k = 0; k < 5 * s; ++k) split_pair(e[k], f[k], f[5 * s + k]);
+    }
+    cudaError_t err = upload(&sys->d_ext64, E64.data(), E64.size());
+    if (err == cudaSuccess) err = upload(&sys->d_ext32, E32.data(), E32.size());
+    if (err == cudaSuccess && sys->forced()) {
+        std::vector<double> fw((size_t)n_sys * 2);
+        for (int64_t p = 0; p < n_sys; ++p) {
+            fw[(size_t)p * 2] = sys->h_fomega[(size_t)p];
+            fw[(size_t)p * 2 + 1] = sys->h_fphase[(size_t)p];
+        }
+        err = upload(&sys->d_force, fw.data(), fw.size());
+    }
+    if (err != cudaSuccess)
+        return fail(err == cudaErrorMemoryAllocation ? CHO_ENOMEM : CHO_ECUDA, "%s: %s", who, cudaGetErrorString(err));
+    return CHO_OK;
+}
+
+static cho_status check_spring_system(cho_system sys, const char* who)
+{
+    if (!sys) return fail(CHO_EINVAL, "%s: NULL system", who);
+    if (sys->kind == CHO_DENSE) return fail(CHO_EINVAL, "%s: damping and forcing are built for spring systems", who);
+    if (sys->s > kChainExtMaxS) return fail(CHO_EINVAL, "%s: s = %d above %d", who, sys->s, kChainExtMaxS);
+    return CHO_OK;
+}
+
+extern "C" cho_status cho_system_set_damping(cho_system sys, const double* dampers)
+{
+    clear_error();
+    cho_status rc = check_spring_system(sys, "cho_system_set_damping");
+    if (rc != CHO_OK) return rc;
+    const size_t n = (size_t)sys->n_sys * sys->s;
+    if (dampers) {
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(dampers[i]) || dampers[i] < 0.0)
+                return fail(CHO_EINVAL, "cho_system_set_damping: damper %zu is not finite and >= 0", i);
+    }
+    DeviceGuard g(sys->ctx->device);
+    if (!g.ok()) return fail(CHO_ECUDA, "cho_system_set_damping: cudaSetDevice failed");
+    if (dampers) sys->h_dampers.assign(dampers, dampers + n);
+    else sys->h_dampers.clear();
+    return build_chain_ext(sys, "cho_system_set_damping");
+}
+
+extern "C" cho_status cho_system_set_forcing(cho_system sys, const double* amplitude, const double* omega,
+                                             const double* phase)
+{
+    clear_error();
+    cho_status rc = check_spring_system(sys, "cho_system_set_forcing");
+    if (rc != CHO_OK) return rc;
+    const size_t n = (size_t)sys->n_sys * sys->s;
+    const size_t ns = (size_t)sys->n_sys;
+    if (amplitude) {
+        if (!omega) return fail(CHO_EINVAL, "cho_system_set_forcing: omega required");
+        if (!all_finite(amplitude, n) || !all_finite(omega, ns) || (phase && !all_finite(phase, ns)))
+            return fail(CHO_EINVAL, "cho_system_set_forcing: non-finite amplitude, omega or phase");
+    }
+    DeviceGuard g(sys->ctx->device);
+    if (!g.ok()) return fail(CHO_ECUDA, "cho_system_set_forcing: cudaSetDevice failed");
+    if (amplitude) {
+        sys->h_famp.assign(amplitude, amplitude + n);
+        sys->h_fomega.assign(omega, omega + ns);
+        if (phase) sys->h_fphase.assign(phase, phase + ns);
+        else sys->h_fphase.assign(ns, 0.0);
+    } else {
+        sys->h_famp.clear();
+        sys->h_fomega.clear();
+        sys->h_fphase.clear();
+    }
+    return build_chain_ext(sys, "cho_system_set_forcing");
+}
+
 extern "C" cho_status cho_system_info(cho_system sys, double* omega_max, int32_t* s, int64_t* n_sys)
 {
     clear_error();
@@ -448,6 +552,12 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
         return fail(CHO_EINVAL, "%s: trajectories need ckpt_every > 0", who);
     const int p = b->prec;
     if (b->poly_jump < 0) return fail(CHO_EINVAL, "%s: poly_jump < 0", who);
+    if (sys->damped() || sys->forced()) {
+        if (plain_form || b->poly_jump != 0)
+            return fail(CHO_EINVAL, "%s: damped or forced systems run RK4 stage by stage in the batch kernels", who);
+        if (p != CHO_FP64 && p != CHO_FP32_KAHAN)
+            return fail(CHO_EINVAL, "%s: damped or forced systems run in CHO_FP64 or CHO_FP32_KAHAN", who);
+    }
     if (b->poly_jump > 0) {
         if (plain_form) return fail(CHO_EINVAL, "%s: the plain form runs RK4 stage by stage", who);
         const bool small2 = sys->path == PATH_SMALL && sys->s == 2;
@@ -564,7 +674,11 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     if (b->n_inst == 0) return CHO_OK;
     const bool fp64 = b->prec == CHO_FP64;
     cudaError_t e;
-    if (sys->path == PATH_SMALL) {
+    if (sys->damped() || sys->forced()) {
+        ChainExtSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_ext64, sys->d_ext32,
+                       sys->forced() ? sys->d_force : nullptr};
+        e = launch_rk4_chain_ext(cs, io, fp64, st);
+    } else if (sys->path == PATH_SMALL) {
         SmallSys ss{sys->s, sys->S, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32, sys->d_err};
         e = launch_rk4_small(ss, io, fp64, st);
     } else if (sys->path == PATH_CHAIN) {

@@ -102,6 +102,21 @@ struct ChainSys {
 
 int chain_dofs_per_thread(int s);
 cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
+
+// ---- rk4_chain_ext: the chain with dashpots and harmonic forcing -------------------
+// Per parameter set and DOF i (FP64 [n_sys][5][s], FP32 [n_sys][10][s]: the five hi
+// rows, then the five lo rows): g_i = C_i/m_i, u_i = C_{i+1}/m_i, y_i = c_i/m_i,
+// w_i = c_{i+1}/m_i, p_i = F_i/m_i (u, w = 0 at the free end).  Per set: omega, phase
+// (FP64 [n_sys][2]).
+struct ChainExtSys {
+    int32_t s;
+    int32_t per_inst_sys;
+    const double* E64;
+    const float* E32;
+    const double* force;    // [n_sys][2]: omega, phase (null: no forcing)
+};
+constexpr int kChainExtMaxS = 1024;
+cudaError_t launch_rk4_chain_ext(const ChainExtSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
 cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaStream_t st);
 
 // ---- rk4_dense (shared B, s > 32) ------------------------------------------------

@@ -76,6 +76,13 @@ struct cho_system_impl {
     };
     std::mutex poly_mu;
     std::vector<PolyBlocks> poly;
+    // spring kinds: dashpots and harmonic forcing (see cho_system_set_damping/_forcing)
+    std::vector<double> h_dampers, h_famp, h_fomega, h_fphase;
+    double* d_ext64 = nullptr;          // ChainExtSys coefficients
+    float* d_ext32 = nullptr;
+    double* d_force = nullptr;          // [n_sys][2] omega, phase
+    bool damped() const { return !h_dampers.empty(); }
+    bool forced() const { return !h_famp.empty(); }
 };
 
 struct cho_ctx {

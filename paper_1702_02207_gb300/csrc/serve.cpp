@@ -654,6 +654,8 @@ extern "C" cho_status cho_submit(cho_ctx* ctx, const cho_request* rq, uint64_t* 
     if (!rq->x0 || !rq->v0) return fail(CHO_EINVAL, "cho_submit: x0/v0 required");
     if (rq->n_steps < 0) return fail(CHO_EINVAL, "cho_submit: n_steps < 0");
     if (rq->priority < 0 || rq->priority > 2) return fail(CHO_EINVAL, "cho_submit: priority must be 0, 1 or 2");
+    if (sys->damped() || sys->forced())
+        return fail(CHO_EINVAL, "cho_submit: damped or forced systems run through cho_integrate_batch");
     const bool dense_simt = rq->prec == CHO_DENSE_FP32_SIMT && sys->kind == CHO_DENSE;
     const bool bf16 = rq->prec == CHO_DENSE_BF16X3 || rq->prec == CHO_DENSE_BF16X5 || rq->prec == CHO_DENSE_BF16X6;
     if (bf16 && (sys->path != PATH_DENSE || sys->s_tc == 0 || (rq->prec == CHO_DENSE_BF16X6 && sys->s_tc > 128)))

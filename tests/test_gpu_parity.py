@@ -484,6 +484,89 @@ def test_dense_per_instance_energy_and_errors(ctx):
         cho.cho_destroy_system(sys_)
 
 
+# ---- damped and forced spring systems (rk4_chain_ext) -------------------------------------------
+
+def _damped_forced_case(s, n_inst, n_steps, seed, damped, forced):
+    cfg = inputs.chain_batch(n_inst=n_inst, s=s, n_steps=n_steps, seed=seed)
+    if s == 2:
+        cfg["kind"] = "two_dof"
+    rng = np.random.default_rng(seed + 1)
+    m, C = cfg["masses"], cfg["springs"]
+    ext = {"dampers": None, "force_amp": None, "force_omega": None, "force_phase": None}
+    if damped:       # damping ratios of a few percent
+        ext["dampers"] = 0.04 * np.sqrt(C * m) * rng.uniform(0.5, 2.0, C.shape)
+    if forced:
+        ext["force_amp"] = C * rng.normal(0.0, 0.01, C.shape)
+        ext["force_omega"] = cfg["omega_max"] * rng.uniform(0.05, 0.5, n_inst)
+        ext["force_phase"] = rng.uniform(-np.pi, np.pi, n_inst)
+    return cfg, ext
+
+
+def _run_ext(ctx, cfg, ext, prec, every):
+    import torch
+
+    sys_ = cho.cho_create_system(ctx, cfg["kind"], masses=cfg["masses"], springs=cfg["springs"])
+    try:
+        if ext["dampers"] is not None:
+            cho.cho_system_set_damping(sys_, ext["dampers"])
+        if ext["force_amp"] is not None:
+            cho.cho_system_set_forcing(sys_, ext["force_amp"], ext["force_omega"], ext["force_phase"])
+        d = torch.device("cuda:0")
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                      cfg["n_steps"], prec, every, trajectory=True)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 64, 300, 1024])
+@pytest.mark.parametrize("mode", ["damped", "forced", "both"])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_damped_forced_chain_matches_oracle(ctx, s, mode, prec, tol):
+    import oracle
+
+    cfg, ext = _damped_forced_case(s, 5, 2000, 500 + s, mode != "forced", mode != "damped")
+    out = _run_ext(ctx, cfg, ext, prec, 125)
+    ref = oracle.rk4_chain_ext(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], 125,
+                               threads=5, **ext)
+    ex, ev = check(out, ref, tol)
+    print(f"{mode} s={s} {prec}: x {ex:.3e} v {ev:.3e}")
+
+
+def test_damping_and_forcing_api(ctx):
+    """Removing damping and forcing gives back the undamped kernels' bits; what the extended
+    model does not cover is refused with CHO_EINVAL."""
+    cfg, ext = _damped_forced_case(8, 3, 200, 77, True, True)
+    plain = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    sys_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    dn = inputs.dense_group(s=40, n_inst=1, n_steps=1)
+    dense = cho.cho_create_system(ctx, "dense", M=dn["M"], K=dn["K"])
+    try:
+        ref = cho.cho_integrate_batch(ctx, plain, cfg["x0"], cfg["v0"], cfg["h"], 200, "fp32_kahan")
+        cho.cho_system_set_damping(sys_, ext["dampers"])
+        cho.cho_system_set_forcing(sys_, ext["force_amp"], ext["force_omega"], ext["force_phase"])
+        moved = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 200, "fp32_kahan")
+        assert not np.array_equal(moved["x"], ref["x"])
+        for call in (lambda: cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 200, "fp32_kahan",
+                                                     poly_jump=1),
+                     lambda: cho.cho_submit(ctx, sys_, cfg["x0"][0], cfg["v0"][0], float(cfg["h"][0]), 10),
+                     lambda: cho.cho_system_set_damping(dense, np.ones((1, 40))),
+                     lambda: cho.cho_system_set_damping(sys_, -np.ones((3, 8))),
+                     lambda: cho.cho_system_set_forcing(sys_, np.full((3, 8), np.nan), 1.0)):
+            with pytest.raises(cho.ChoError) as ei:
+                call()
+            assert ei.value.status == cho.CHO_EINVAL
+        cho.cho_system_set_damping(sys_, None)
+        cho.cho_system_set_forcing(sys_, None)
+        back = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], 200, "fp32_kahan")
+        assert np.array_equal(back["x"], ref["x"]) and np.array_equal(back["v"], ref["v"])
+    finally:
+        for sy in (plain, sys_, dense):
+            cho.cho_destroy_system(sy)
+
+
 # ---- polynomial form (k RK4 steps per update with P(hA)^k) ---------------------------------------
 
 @pytest.mark.parametrize("prec,tol,k", [("fp32_kahan", TOL_FP32, 1), ("fp32_kahan", TOL_FP32, 5),
