@@ -17,6 +17,18 @@ enum Path : int32_t {
 constexpr int kSmallThreads = 64;    // threads per CTA of rk4_small (small CTAs balance the SMs)
 constexpr int kChainMaxThreads = 1024;
 
+#ifdef __CUDACC__
+#define CHO_HD __host__ __device__
+#else
+#define CHO_HD
+#endif
+
+// The FP32 small-system kernels carry the scaled velocity u = (h/6) v (exact step
+// constants 3 and 6 replace h/2 and h, and no h/6 multiply in the state update);
+// the batch kernels and the serving engine convert with these, identically.
+CHO_HD inline double scaled_velocity(double v, double h) { return v * (h / 6.0); }
+CHO_HD inline double unscaled_velocity(double u, double h) { return u * (6.0 / h); }
+
 // Host-side split of an FP64 value into an unevaluated FP32 pair hi + lo.
 inline void split_pair(double d, float& hi, float& lo)
 {

@@ -21,6 +21,27 @@ __device__ __forceinline__ void comp_update(float& x, float& e, float k, float h
     x = t;
 }
 
+// Compensated x += k in FP32 (the increment already scaled): the state is the
+// unevaluated sum x + e, as in comp_update.
+__device__ __forceinline__ void comp_add(float& x, float& e, float k)
+{
+    const float y = __fadd_rn(k, e);
+    const float t = __fadd_rn(x, y);
+    e = __fsub_rn(y, __fsub_rn(t, x));
+    x = t;
+}
+
+// FP32 small systems integrate the scaled velocity u = (h/6) v (scaled_velocity,
+// cho_internal.h) with the scaled iteration matrix B'' = (h^2/36) B, an FP32 pair
+// formed from B's pair in FP64: then h/2 v = 3 u and h v = 6 u, and the state update
+// adds the stage sums without a multiply.
+__host__ __device__ __forceinline__ void scaled_coef(float& hi, float& lo, double h)
+{
+    const double b = ((double)hi + (double)lo) * (h * h / 36.0);
+    hi = (float)b;
+    lo = (float)(b - (double)hi);
+}
+
 // Fused multiply-add in the precision of the operands.
 __device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }

@@ -58,16 +58,23 @@ struct BatchSrc {
             lo = b[S * S + row * S + j];
         }
     }
+    // FP32: v is held as the scaled velocity u = (h/6) v (see scaled_velocity)
     __device__ void load(int64_t q, int row, Real& x, Real& v, float& cx, float& cv) const
     {
         const int sz = sys.s;
         const double xd = row < sz ? io.x0[q * sz + row] : 0.0;
-        const double vd = row < sz ? io.v0[q * sz + row] : 0.0;
+        const double vd0 = row < sz ? io.v0[q * sz + row] : 0.0;
+        const double vd = F64 ? vd0 : scaled_velocity(vd0, h(q));
         x = (Real)xd;
         v = (Real)vd;
-        // Kahan convention: represented value = x - c
+        // the state is the unevaluated sum x + c
         cx = F64 ? 0.f : (float)(xd - (double)x);
         cv = F64 ? 0.f : (float)(vd - (double)v);
+    }
+    __device__ double vout(int64_t q, Real v, float cv) const
+    {
+        const double u = (double)v + (double)cv;
+        return F64 ? u : unscaled_velocity(u, h(q));
     }
     __device__ void checkpoint(int64_t q, int64_t ck, int row, Real x, Real v, float cx, float cv) const
     {
@@ -75,20 +82,22 @@ struct BatchSrc {
         if (row >= sz || io.x_traj == nullptr) return;
         const int64_t o = (q * io.n_ck + ck) * sz + row;
         io.x_traj[o] = (double)x + (double)cx;
-        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
+        if (io.v_traj) io.v_traj[o] = vout(q, v, cv);
     }
     __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool) const
     {
         const int sz = sys.s;
         if (row >= sz) return;
         io.x_out[q * sz + row] = (double)x + (double)cx;
-        io.v_out[q * sz + row] = (double)v + (double)cv;
+        io.v_out[q * sz + row] = vout(q, v, cv);
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
 };
 
 // Slot form (serving): resident state block [x(S), v(S), cx(S), cv(S)] in the
-// kernel's precision, coefficient block in the batch layout of one set.
+// kernel's precision (FP32: the scaled velocity u = (h/6) v in place of v, converted
+// by the serving engine at admission and retirement), coefficient block in the batch
+// layout of one set.
 template <bool F64, int S>
 struct SlotSrc {
     SlotIO io;
@@ -169,9 +178,14 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int j = 0; j < S; ++j) src.coef(q, g * R + r, j, bh[r][j], bl[r][j]);
+        for (int j = 0; j < S; ++j) {
+            src.coef(q, g * R + r, j, bh[r][j], bl[r][j]);
+            if constexpr (!F64) scaled_coef(bh[r][j], bl[r][j], src.h(q));   // B'' = h^2/36 B
+        }
 
     const StepSize<F64> hs(src.h(q));
+    // stage constants: FP64 h/2, h; FP32 (scaled velocity) 3, 6
+    const Real c_half = F64 ? hs.h2 : (Real)3, c_full = F64 ? hs.h : (Real)6;
     Real x[R], v[R];
     float cx[R], cv[R];
 #pragma unroll
@@ -238,32 +252,37 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
             for (int r = 0; r < R; ++r) {
                 kx[r] = v[r];
                 kv[r] = a[r];
-                xs[r] = fmar(hs.h2, v[r], x[r]);
-                vs[r] = fmar(hs.h2, a[r], v[r]);
+                xs[r] = fmar(c_half, v[r], x[r]);
+                vs[r] = fmar(c_half, a[r], v[r]);
             }
             accel(xs, a, false);                           // stage 2
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = fmar((Real)2, vs[r], kx[r]);
                 kv[r] = fmar((Real)2, a[r], kv[r]);
-                xs[r] = fmar(hs.h2, vs[r], x[r]);
-                vs[r] = fmar(hs.h2, a[r], v[r]);
+                xs[r] = fmar(c_half, vs[r], x[r]);
+                vs[r] = fmar(c_half, a[r], v[r]);
             }
             accel(xs, a, false);                           // stage 3
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = fmar((Real)2, vs[r], kx[r]);
                 kv[r] = fmar((Real)2, a[r], kv[r]);
-                xs[r] = fmar(hs.h, vs[r], x[r]);
-                vs[r] = fmar(hs.h, a[r], v[r]);
+                xs[r] = fmar(c_full, vs[r], x[r]);
+                vs[r] = fmar(c_full, a[r], v[r]);
             }
             accel(xs, a, false);                           // stage 4
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 kx[r] = addr(kx[r], vs[r]);
                 kv[r] = addr(kv[r], a[r]);
-                state_update<F64>(x[r], cx[r], kx[r], hs);
-                state_update<F64>(v[r], cv[r], kv[r], hs);
+                if constexpr (F64) {
+                    state_update<true>(x[r], cx[r], kx[r], hs);
+                    state_update<true>(v[r], cv[r], kv[r], hs);
+                } else {
+                    comp_add(x[r], cx[r], kx[r]);          // the scaled sums are the increments
+                    comp_add(v[r], cv[r], kv[r]);
+                }
             }
         });
         if (src.ckpt_every() > 0) {
@@ -317,22 +336,11 @@ cudaError_t dispatch(int S, bool fp64, int64_t n, cudaStream_t st, const Init& i
 // operation rounds each lane as the scalar intrinsic does), with lane 0 and
 // lane 1 of every float2 holding instances 2t and 2t+1.  Packing halves the
 // instructions issued per instance; the coefficients are stored negated so
-// that the packed accumulation yields a = -B x directly.
+// that the packed accumulation yields a = -B'' x directly.
 
 constexpr int kPairThreads = 32;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-
-__device__ __forceinline__ void pair_update(float2& x, float2& e, float2 k, float2 h6, float2 h6lo)
-{
-    const float2 m1 = f2(-1.f, -1.f);
-    float2 y = __ffma2_rn(h6lo, k, e);
-    y = __ffma2_rn(h6, k, y);
-    const float2 t = __fadd2_rn(x, y);
-    const float2 d = __ffma2_rn(x, m1, t);       // t - x
-    e = __ffma2_rn(d, m1, y);                    // y - (t - x)
-    x = t;
-}
 
 // Compensated x += k (the increment without a step-size factor).
 __device__ __forceinline__ void pair_add(float2& x, float2& e, float2 k)
@@ -403,12 +411,13 @@ struct Pair2State {
     }
 };
 
-// RK4 stage by stage (Section 3): the same step as rk4_small_kernel<2, false>.
+// RK4 stage by stage (Section 3): the same step as rk4_small_kernel<2, false>,
+// on the scaled velocity u = (h/6) v with B'' = (h^2/36) B (see scaled_velocity).
 // Shared by the one-launch kernel and the balanced kernel so that both issue
-// exactly the same operations.
+// exactly the same operations.  The v registers of the state hold u.
 struct Pair2 : Pair2State {
     float2 nbh[2][2], nbl[2][2];
-    float2 h, h2, h6, h6lo;
+    double hd0, hd1;
 
     __device__ __forceinline__ void init(const SmallSys& sys, const BatchIO& io, int64_t q)
     {
@@ -416,20 +425,58 @@ struct Pair2 : Pair2State {
         const int64_t s0 = sys.per_inst_sys ? q0 : 0, s1 = sys.per_inst_sys ? q1 : 0;
         const float* b0 = sys.B32 + s0 * 8;      // [hi 2x2][lo 2x2]
         const float* b1 = sys.B32 + s1 * 8;
+        hd0 = io.h[io.h_per_inst ? q0 : 0];
+        hd1 = io.h[io.h_per_inst ? q1 : 0];
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                nbh[r][j] = f2(-b0[r * 2 + j], -b1[r * 2 + j]);
-                nbl[r][j] = f2(-b0[4 + r * 2 + j], -b1[4 + r * 2 + j]);
+                float h0 = b0[r * 2 + j], l0 = b0[4 + r * 2 + j], h1 = b1[r * 2 + j], l1 = b1[4 + r * 2 + j];
+                scaled_coef(h0, l0, hd0);
+                scaled_coef(h1, l1, hd1);
+                nbh[r][j] = f2(-h0, -h1);
+                nbl[r][j] = f2(-l0, -l1);
             }
-        const StepSize<false> hs0(io.h[io.h_per_inst ? q0 : 0]), hs1(io.h[io.h_per_inst ? q1 : 0]);
-        h = f2(hs0.h, hs1.h);
-        h2 = f2(hs0.h2, hs1.h2);
-        h6 = f2(hs0.h6, hs1.h6);
-        h6lo = f2(hs0.h6lo, hs1.h6lo);
     }
     __device__ __forceinline__ int64_t quantum() const { return 1; }
+    __device__ __forceinline__ void load_initial(const BatchIO& io)
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const double xa = io.x0[q0 * 2 + r], xb = io.x0[q1 * 2 + r];
+            const double ua = scaled_velocity(io.v0[q0 * 2 + r], hd0), ub = scaled_velocity(io.v0[q1 * 2 + r], hd1);
+            x[r] = f2((float)xa, (float)xb);
+            v[r] = f2((float)ua, (float)ub);
+            ex[r] = f2((float)(xa - (double)x[r].x), (float)(xb - (double)x[r].y));
+            ev[r] = f2((float)(ua - (double)v[r].x), (float)(ub - (double)v[r].y));
+        }
+    }
+    __device__ __forceinline__ void store_ckpt(const BatchIO& io, int64_t ck) const
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            io.x_traj[(q0 * io.n_ck + ck) * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            if (io.v_traj)
+                io.v_traj[(q0 * io.n_ck + ck) * 2 + r] = unscaled_velocity((double)v[r].x + (double)ev[r].x, hd0);
+            if (has1) {
+                io.x_traj[(q1 * io.n_ck + ck) * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                if (io.v_traj)
+                    io.v_traj[(q1 * io.n_ck + ck) * 2 + r] = unscaled_velocity((double)v[r].y + (double)ev[r].y, hd1);
+            }
+        }
+    }
+    __device__ __forceinline__ void store_final(const BatchIO& io) const
+    {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            io.x_out[q0 * 2 + r] = (double)x[r].x + (double)ex[r].x;
+            io.v_out[q0 * 2 + r] = unscaled_velocity((double)v[r].x + (double)ev[r].x, hd0);
+            if (has1) {
+                io.x_out[q1 * 2 + r] = (double)x[r].y + (double)ex[r].y;
+                io.v_out[q1 * 2 + r] = unscaled_velocity((double)v[r].y + (double)ev[r].y, hd1);
+            }
+        }
+    }
     // Stage 1 forms the lo product and keeps it; stages 2-4 reuse it (frozen lo,
     // as rk4_small_kernel).
     __device__ __forceinline__ void accel(const float2 (&xs)[2], float2 (&a)[2], float2 (&lo)[2], bool first) const
@@ -446,39 +493,39 @@ struct Pair2 : Pair2State {
     }
     __device__ __forceinline__ void step()
     {
-        const float2 two = f2(2.f, 2.f);
+        const float2 two = f2(2.f, 2.f), three = f2(3.f, 3.f), six = f2(6.f, 6.f);
         float2 a[2], xs[2], kx[2], kv[2], vs[2], lo[2];
         accel(x, a, lo, true);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = v[r];
             kv[r] = a[r];
-            xs[r] = __ffma2_rn(h2, v[r], x[r]);
-            vs[r] = __ffma2_rn(h2, a[r], v[r]);
+            xs[r] = __ffma2_rn(three, v[r], x[r]);
+            vs[r] = __ffma2_rn(three, a[r], v[r]);
         }
         accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __ffma2_rn(two, vs[r], kx[r]);
             kv[r] = __ffma2_rn(two, a[r], kv[r]);
-            xs[r] = __ffma2_rn(h2, vs[r], x[r]);
-            vs[r] = __ffma2_rn(h2, a[r], v[r]);
+            xs[r] = __ffma2_rn(three, vs[r], x[r]);
+            vs[r] = __ffma2_rn(three, a[r], v[r]);
         }
         accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __ffma2_rn(two, vs[r], kx[r]);
             kv[r] = __ffma2_rn(two, a[r], kv[r]);
-            xs[r] = __ffma2_rn(h, vs[r], x[r]);
-            vs[r] = __ffma2_rn(h, a[r], v[r]);
+            xs[r] = __ffma2_rn(six, vs[r], x[r]);
+            vs[r] = __ffma2_rn(six, a[r], v[r]);
         }
         accel(xs, a, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             kx[r] = __fadd2_rn(kx[r], vs[r]);
             kv[r] = __fadd2_rn(kv[r], a[r]);
-            pair_update(x[r], ex[r], kx[r], h6, h6lo);
-            pair_update(v[r], ev[r], kv[r], h6, h6lo);
+            pair_add(x[r], ex[r], kx[r]);
+            pair_add(v[r], ev[r], kv[r]);
         }
     }
 };
@@ -802,93 +849,16 @@ rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSch
     }
 }
 
-// One 2-DOF instance per thread with the two DOFs packed in FP32x2 lanes: lane r
-// holds row r.  The off-diagonal products take the displacement with its lanes
-// swapped.  Same rounding as rk4_small_kernel<2, false>.
-constexpr int kTwoDofThreads = 64;
-
-__global__ void __launch_bounds__(kTwoDofThreads) rk4_two_dof_packed_kernel(const SmallSys sys, const BatchIO io)
-{
-    const int64_t q = (int64_t)blockIdx.x * kTwoDofThreads + threadIdx.x;
-    if (q >= io.n_inst) return;
-    const float* b = sys.B32 + (sys.per_inst_sys ? q : 0) * 8;      // [hi 2x2][lo 2x2]
-    const float2 dh = f2(-b[0], -b[3]), oh = f2(-b[1], -b[2]);      // -diag, -offdiag
-    const float2 dl = f2(-b[4], -b[7]), ol = f2(-b[5], -b[6]);
-    const StepSize<false> hs(io.h[io.h_per_inst ? q : 0]);
-    const float2 h = f2(hs.h, hs.h), h2 = f2(hs.h2, hs.h2), h6 = f2(hs.h6, hs.h6), h6lo = f2(hs.h6lo, hs.h6lo),
-                 two = f2(2.f, 2.f);
-    const double x0a = io.x0[q * 2], x0b = io.x0[q * 2 + 1], v0a = io.v0[q * 2], v0b = io.v0[q * 2 + 1];
-    float2 x = f2((float)x0a, (float)x0b), v = f2((float)v0a, (float)v0b);
-    float2 ex = f2((float)(x0a - (double)x.x), (float)(x0b - (double)x.y));
-    float2 ev = f2((float)(v0a - (double)v.x), (float)(v0b - (double)v.y));
-    float2 lo;                                   // frozen lo product, as rk4_small_kernel
-    auto accel = [&](float2 xs, bool first) {
-        const float2 xw = f2(xs.y, xs.x);
-        if (first) {
-            lo = __fmul2_rn(dl, xs);
-            lo = __ffma2_rn(ol, xw, lo);
-        }
-        const float2 acc = __ffma2_rn(dh, xs, lo);
-        return __ffma2_rn(oh, xw, acc);
-    };
-    auto step = [&]() {
-        float2 a = accel(x, true);
-        float2 kx = v, kv = a;
-        float2 xs = __ffma2_rn(h2, v, x), vs = __ffma2_rn(h2, a, v);
-        a = accel(xs, false);
-        kx = __ffma2_rn(two, vs, kx);
-        kv = __ffma2_rn(two, a, kv);
-        xs = __ffma2_rn(h2, vs, x);
-        vs = __ffma2_rn(h2, a, v);
-        a = accel(xs, false);
-        kx = __ffma2_rn(two, vs, kx);
-        kv = __ffma2_rn(two, a, kv);
-        xs = __ffma2_rn(h, vs, x);
-        vs = __ffma2_rn(h, a, v);
-        a = accel(xs, false);
-        kx = __fadd2_rn(kx, vs);
-        kv = __fadd2_rn(kv, a);
-        pair_update(x, ex, kx, h6, h6lo);
-        pair_update(v, ev, kv, h6, h6lo);
-    };
-    const int64_t n = io.n_steps;
-    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (n > 0 ? n : 1);
-    int64_t ck = 0;
-    for (int64_t done = 0; done < n; done += every) {
-        for (int64_t base = 0; base < every; base += 0x40000000LL) {
-            const int32_t m = (int32_t)(every - base < 0x40000000LL ? every - base : 0x40000000LL);
-#pragma unroll 2
-            for (int32_t it = 0; it < m; ++it) step();
-        }
-        if (io.ckpt_every > 0 && io.x_traj) {
-            const int64_t o = (q * io.n_ck + ck) * 2;
-            io.x_traj[o] = (double)x.x + (double)ex.x;
-            io.x_traj[o + 1] = (double)x.y + (double)ex.y;
-            if (io.v_traj) {
-                io.v_traj[o] = (double)v.x + (double)ev.x;
-                io.v_traj[o + 1] = (double)v.y + (double)ev.y;
-            }
-        }
-        ++ck;
-    }
-    io.x_out[q * 2] = (double)x.x + (double)ex.x;
-    io.x_out[q * 2 + 1] = (double)x.y + (double)ex.y;
-    io.v_out[q * 2] = (double)v.x + (double)ev.x;
-    io.v_out[q * 2 + 1] = (double)v.y + (double)ev.y;
-}
-
 // Which 2-DOF FP32 kernel runs: "balanced" (the default: two instances per
 // thread on the balanced schedule), "pair" (two instances per thread, one warp
-// per 64 instances), "packed" (one instance per thread, DOFs packed) or
-// "generic" (rk4_small_kernel<2>); all give the same bits.  CHO_TWO_DOF_KERNEL
-// overrides the default.
+// per 64 instances) or "generic" (rk4_small_kernel<2>); all give the same bits.
+// CHO_TWO_DOF_KERNEL overrides the default.
 int two_dof_variant()
 {
     static int v = -1;
     if (v < 0) {
         const char* e = std::getenv("CHO_TWO_DOF_KERNEL");
         v = 0;
-        if (e && std::strcmp(e, "packed") == 0) v = 1;
         if (e && std::strcmp(e, "generic") == 0) v = 2;
         if (e && std::strcmp(e, "pair") == 0) v = 3;
     }
@@ -990,13 +960,6 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
         return e != cudaSuccess ? e : ef;
     }
     const int variant = two_dof_variant();
-    if (sys.s == 2 && !fp64 && variant == 1) {
-        const int64_t blocks = (io.n_inst + kTwoDofThreads - 1) / kTwoDofThreads;
-        if (blocks <= 0) return cudaSuccess;
-        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-        rk4_two_dof_packed_kernel<<<(unsigned)blocks, kTwoDofThreads, 0, st>>>(sys, io);
-        return cudaGetLastError();
-    }
     // s = 1 is also padded to S = 2 but keeps the generic layout
     if (sys.s == 2 && !fp64 && variant == 3) return launch_pair2<Pair2>(sys, io, st);
     if (sys.s == 2 && !fp64 && variant == 0) return launch_pair2_balanced<Pair2>(sys, io, st);

@@ -339,9 +339,12 @@ cudaError_t ServeEngine::launch(Group* g)
                 d[n + i] = i < s ? r->v0[i] : 0.0;
             }
         } else {
+            // FP32 small systems hold the scaled velocity u = (h/6) v (rk4_small.cu)
+            const bool scaled = sys->path == PATH_SMALL;
             float* f = (float*)dst;
             for (int i = 0; i < n; ++i) {
-                const double xd = i < s ? r->x0[i] : 0.0, vd = i < s ? r->v0[i] : 0.0;
+                const double xd = i < s ? r->x0[i] : 0.0, v0 = i < s ? r->v0[i] : 0.0;
+                const double vd = scaled ? scaled_velocity(v0, r->h) : v0;
                 f[i] = (float)xd;
                 f[n + i] = (float)vd;
                 f[2 * n + i] = (float)(xd - (double)f[i]);          // compensation: x + e
@@ -457,9 +460,11 @@ void ServeEngine::retire(Group* g)
                 }
             } else {
                 const float* f = (const float*)src;
+                const bool scaled = sys->path == PATH_SMALL;
                 for (int k = 0; k < s; ++k) {
                     r->x[k] = (double)f[k] + (double)f[2 * n + k];
-                    r->v[k] = (double)f[n + k] + (double)f[3 * n + k];
+                    const double u = (double)f[n + k] + (double)f[3 * n + k];
+                    r->v[k] = scaled ? unscaled_velocity(u, r->h) : u;
                 }
             }
             r->status = CHO_OK;

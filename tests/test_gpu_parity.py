@@ -353,7 +353,7 @@ def test_dense_tensor_core(ctx, s, prec):
 
 
 def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
-    """The pair-packed, DOF-packed and generic 2-DOF FP32 kernels round identically."""
+    """The pair-packed and generic 2-DOF FP32 kernels round identically."""
     import subprocess
     import sys as _sys
 
@@ -371,12 +371,12 @@ def test_two_dof_kernel_variants_are_bitwise_equal(tmp_path):
         "np.savez(sys.argv[1], **{k: v.cpu().numpy() for k, v in o.items()})\n"
     ) % ROOT_DIR
     res = {}
-    for variant in ("pair", "packed", "generic"):
+    for variant in ("pair", "generic"):
         path = str(tmp_path / f"{variant}.npz")
         env = dict(os.environ, CHO_TWO_DOF_KERNEL=variant)
         subprocess.run([_sys.executable, "-c", code, path], check=True, env=env, timeout=300)
         res[variant] = np.load(path)
-    for variant in ("packed", "generic"):
+    for variant in ("generic",):
         for k in ("x", "v", "x_traj", "v_traj"):
             assert np.array_equal(res["pair"][k], res[variant][k]), (variant, k)
 
