@@ -39,31 +39,38 @@ struct ChainBatchSrc {
         if constexpr (F64) return sys.C64 + set * 2 * sys.s;
         else return sys.C32 + set * 4 * sys.s;
     }
+    // FP32: v is held as the scaled velocity u = (h/6) v (scaled_velocity)
     __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
     {
         const double xd = io.x0[q * sys.s + i];
-        const double vd = io.v0[q * sys.s + i];
+        const double vd = F64 ? io.v0[q * sys.s + i] : scaled_velocity(io.v0[q * sys.s + i], h(q));
         x = (Real)xd;
         v = (Real)vd;
         cx = F64 ? 0.f : (float)(xd - (double)x);
         cv = F64 ? 0.f : (float)(vd - (double)v);
+    }
+    __device__ double vout(int64_t q, Real v, float cv) const
+    {
+        const double u = (double)v + (double)cv;
+        return F64 ? u : unscaled_velocity(u, h(q));
     }
     __device__ void checkpoint(int64_t q, int64_t ck, int i, Real x, Real v, float cx, float cv) const
     {
         if (io.x_traj == nullptr) return;
         const int64_t o = (q * io.n_ck + ck) * sys.s + i;
         io.x_traj[o] = (double)x + (double)cx;
-        if (io.v_traj) io.v_traj[o] = (double)v + (double)cv;
+        if (io.v_traj) io.v_traj[o] = vout(q, v, cv);
     }
     __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
     {
         io.x_out[q * sys.s + i] = (double)x + (double)cx;
-        io.v_out[q * sys.s + i] = (double)v + (double)cv;
+        io.v_out[q * sys.s + i] = vout(q, v, cv);
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
 };
 
-// Slot form: state block [x(s), v(s), cx(s), cv(s)] in kernel precision.
+// Slot form: state block [x(s), v(s), cx(s), cv(s)] in kernel precision (FP32: the
+// scaled velocity in place of v, converted by the serving engine).
 template <bool F64>
 struct ChainSlotSrc {
     SlotIO io;
@@ -145,10 +152,14 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
             uh[p] = in ? c[s + i] : 0.f;
             gl[p] = in ? c[2 * s + i] : 0.f;
             ul[p] = in ? c[3 * s + i] : 0.f;
+            scaled_coef(gh[p], gl[p], src.h(q));     // g'' = h^2/36 g, u'' = h^2/36 u
+            scaled_coef(uh[p], ul[p], src.h(q));
         }
     }
 
     const StepSize<F64> hs(src.h(q));
+    // stage constants: FP64 h/2, h; FP32 (scaled velocity) 3, 6
+    const Real c_half = F64 ? hs.h2 : (Real)3, c_full = F64 ? hs.h : (Real)6;
     Real x[P], v[P];
     float cx[P], cv[P];
 #pragma unroll
@@ -213,32 +224,37 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
             for (int p = 0; p < P; ++p) {
                 kx[p] = v[p];
                 kv[p] = a[p];
-                xs[p] = fmar(hs.h2, v[p], x[p]);
-                vs[p] = fmar(hs.h2, a[p], v[p]);
+                xs[p] = fmar(c_half, v[p], x[p]);
+                vs[p] = fmar(c_half, a[p], v[p]);
             }
             accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = fmar((Real)2, vs[p], kx[p]);
                 kv[p] = fmar((Real)2, a[p], kv[p]);
-                xs[p] = fmar(hs.h2, vs[p], x[p]);
-                vs[p] = fmar(hs.h2, a[p], v[p]);
+                xs[p] = fmar(c_half, vs[p], x[p]);
+                vs[p] = fmar(c_half, a[p], v[p]);
             }
             accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = fmar((Real)2, vs[p], kx[p]);
                 kv[p] = fmar((Real)2, a[p], kv[p]);
-                xs[p] = fmar(hs.h, vs[p], x[p]);
-                vs[p] = fmar(hs.h, a[p], v[p]);
+                xs[p] = fmar(c_full, vs[p], x[p]);
+                vs[p] = fmar(c_full, a[p], v[p]);
             }
             accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 kx[p] = addr(kx[p], vs[p]);
                 kv[p] = addr(kv[p], a[p]);
-                state_update<F64>(x[p], cx[p], kx[p], hs);
-                state_update<F64>(v[p], cv[p], kv[p], hs);
+                if constexpr (F64) {
+                    state_update<true>(x[p], cx[p], kx[p], hs);
+                    state_update<true>(v[p], cv[p], kv[p], hs);
+                } else {
+                    comp_add(x[p], cx[p], kx[p]);
+                    comp_add(v[p], cv[p], kv[p]);
+                }
             }
         });
         if (src.ckpt_every() > 0) {

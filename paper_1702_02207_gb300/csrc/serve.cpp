@@ -339,8 +339,8 @@ cudaError_t ServeEngine::launch(Group* g)
                 d[n + i] = i < s ? r->v0[i] : 0.0;
             }
         } else {
-            // FP32 small systems hold the scaled velocity u = (h/6) v (rk4_small.cu)
-            const bool scaled = sys->path == PATH_SMALL;
+            // FP32 small systems and chains hold the scaled velocity u = (h/6) v
+            const bool scaled = sys->path == PATH_SMALL || sys->path == PATH_CHAIN;
             float* f = (float*)dst;
             for (int i = 0; i < n; ++i) {
                 const double xd = i < s ? r->x0[i] : 0.0, v0 = i < s ? r->v0[i] : 0.0;
@@ -460,7 +460,7 @@ void ServeEngine::retire(Group* g)
                 }
             } else {
                 const float* f = (const float*)src;
-                const bool scaled = sys->path == PATH_SMALL;
+                const bool scaled = sys->path == PATH_SMALL || sys->path == PATH_CHAIN;
                 for (int k = 0; k < s; ++k) {
                     r->x[k] = (double)f[k] + (double)f[2 * n + k];
                     const double u = (double)f[n + k] + (double)f[3 * n + k];
