@@ -586,7 +586,7 @@ def main():
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          # DRAM bytes per launch (read + write) measured by an ncu capture of this
                          # kernel on this workload
-                         "traffic": 4782080,
+                         "traffic": 4792576,
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
             "clocks": clocks,
             "e2e": {"value": DOF_STEPS / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
