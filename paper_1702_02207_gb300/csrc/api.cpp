@@ -596,16 +596,27 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
             if (sys->omega_max * hv > lim)
                 return fail(CHO_EUNSTABLE, "%s: omega_max*h = %g > 2 sqrt 2", who, sys->omega_max * hv);
         } else {
+            // one branch-free pass (it vectorises; a batch of 65,536 instances is checked in
+            // microseconds), then a second pass only to name the first offender
             const int64_t nh = b->h_per_inst ? b->n_inst : 1;
+            const bool per_set = sys->n_sys != 1 && b->h_per_inst;   // one h: check the largest omega
+            const double w0 = b->h_per_inst ? sys->omegas[0] : sys->omega_max;
+            const double* w = sys->omegas.data();
+            bool bad = false;
             for (int64_t i = 0; i < nh; ++i) {
                 const double hv = b->h[i];
-                if (!(hv > 0.0) || !std::isfinite(hv)) return fail(CHO_EINVAL, "%s: h[%lld] must be finite and > 0", who, (long long)i);
-                for (int64_t q = (b->h_per_inst ? i : 0); q < (b->h_per_inst ? i + 1 : b->n_inst); ++q) {
-                    const double w = sys->n_sys == 1 ? sys->omegas[0] : sys->omegas[(size_t)q];
-                    if (w * hv > lim)
+                const double wv = per_set ? w[i] : w0;
+                bad |= !(hv > 0.0) | !(hv < INFINITY) | (wv * hv > lim);
+            }
+            if (bad) {
+                for (int64_t i = 0; i < nh; ++i) {
+                    const double hv = b->h[i];
+                    if (!(hv > 0.0) || !std::isfinite(hv))
+                        return fail(CHO_EINVAL, "%s: h[%lld] must be finite and > 0", who, (long long)i);
+                    const double wv = per_set ? w[i] : w0;
+                    if (wv * hv > lim)
                         return fail(CHO_EUNSTABLE, "%s: instance %lld has omega_max*h = %g > 2 sqrt 2", who,
-                                    (long long)q, w * hv);
-                    if (sys->n_sys == 1) break;
+                                    (long long)i, wv * hv);
                 }
             }
         }

@@ -22,6 +22,7 @@
 #include "../../include/cho.h"
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include <cstdlib>
 #include <cstring>
@@ -865,6 +866,41 @@ int two_dof_variant()
     return v;
 }
 
+// Per-call device scratch (hand-over buffers, jump matrices) comes from a memory
+// pool of the library's own that keeps up to 256 MiB when freed: the default
+// pool returns freed memory to the driver at every synchronisation, and mapping it
+// again cost ~0.18 ms per synchronous call.  Stream-ordered, so concurrent calls on
+// other streams never share a block.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = (uint64_t)256 << 20;
+            e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 template <class T>
 cudaError_t launch_pair2(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
 {
@@ -914,7 +950,7 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
     sc.withhold = hook && hook[0] == '1' ? 1 : 0;
     const size_t xfer_bytes = (size_t)P * 8 * 32 * sizeof(float2);
     void* buf = nullptr;
-    e = cudaMallocAsync(&buf, xfer_bytes + (size_t)P * sizeof(unsigned), st);
+    e = scratch_alloc(&buf, xfer_bytes + (size_t)P * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     sc.xfer = (float2*)buf;
     sc.flag = (unsigned*)((char*)buf + xfer_bytes);
@@ -941,7 +977,7 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
         // the jump matrices live for this call only, in stream order
         void* buf = nullptr;
-        cudaError_t e = cudaMallocAsync(&buf, (size_t)io.n_inst * 16 * sizeof(double), st);
+        cudaError_t e = scratch_alloc(&buf, (size_t)io.n_inst * 16 * sizeof(double), st);
         if (e != cudaSuccess) return e;
         BatchIO pio = io;
         pio.poly_E = (const double*)buf;
