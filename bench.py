@@ -417,20 +417,21 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
         "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak}}
     cho.cho_destroy_system(s_)
     # dense systems with one (M, K) per instance: every stage streams the instance's own B^T
-    # (hi and lo at stage 1, hi at stages 2-4); 8192 instances of s = 64 hold 268 MB of B,
-    # more than L2, so each step must bring the instance's FP32 pair from HBM at least once:
-    # 8 s^2 bytes per instance-step (the re-reads of stages 2-4 are served by L2).
-    hbm_peak = peaks.get("hbm_gbs", 6788.0)
+    # through shared memory (hi and lo at stage 1, hi at stages 2-4: 20 s^2 bytes per
+    # instance-step).  A CTA keeps its instance for the whole horizon, so the B of the resident
+    # CTAs (~50 MB) stays in L2 and the stream is served by L2 (ncu: L2 throughput 80 % of
+    # peak, DRAM 4 %): the bound is L2 bandwidth, for which no measured peak is at hand.
     cfg = inputs.dense_own(s=64, n_inst=8192, n_steps=1000)
     s_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
     t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])
     dof = cfg["x0"].size * cfg["n_steps"]
-    ach = cfg["x0"].shape[0] * cfg["n_steps"] * 8 * 64 * 64 / t / 1e9
+    ach = cfg["x0"].shape[0] * cfg["n_steps"] * 20 * 64 * 64 / t / 1e9
     res["dense_own_s64_x8192_fp32_kahan"] = {
         "value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": cfg["n_steps"],
         "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan", every=125),
-        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                     "note": "algorithmic bytes: each instance's B^T pair once per step, 8 s^2 B per instance-step"}}
+        "roofline": {"bound": "l2", "achieved": ach, "peak": None, "unit": "GB/s", "frac": None,
+                     "note": "B^T streamed from L2, 20 s^2 B per instance-step; ncu (100-step case): "
+                             "lts__throughput 80 % of peak, DRAM throughput 4 %"}}
     cho.cho_destroy_system(s_)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     for s in (64, 128, 256):

@@ -9,6 +9,9 @@ Cases (each one cho_integrate_batch call, a few MB of device memory):
   dense_tc64 s = 64, 4096 instances, 500 steps, bf16x5      (rk4_dense_tc, two tiles stacked per CTA)
   dense_tc2 s = 256, 2048 instances, 200 steps, bf16x5       (rk4_dense_tc, 2-CTA clusters)
   dense_simt s = 256, 512 instances, 50 steps, fp32_simt     (rk4_dense_simt)
+  dense_own s = 64, 8192 instances with their own (M, K), 100 steps, fp32_kahan (rk4_dense_simt, one per CTA)
+  dense_poly s = 128, 2048 instances, 500 steps, fp32_kahan, k = 25 steps per update (rk4_dense_poly)
+  chain_ext 512 damped and forced chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain_ext)
 """
 from __future__ import annotations
 
@@ -22,6 +25,7 @@ def run(case: str) -> None:
 
     dev = torch.device("cuda:0")
     ctx = cho.cho_init(0)
+    poly = 0
     try:
         if case == "pair":
             cfg, prec, kind = inputs.two_dof_batch(), "fp32_kahan", "two_dof"
@@ -35,16 +39,32 @@ def run(case: str) -> None:
             cfg, prec, kind = inputs.dense_group(s=256, n_inst=2048, n_steps=200), "bf16x5", "dense"
         elif case == "dense_simt":
             cfg, prec, kind = inputs.dense_group(s=256, n_inst=512, n_steps=50), "fp32_simt", "dense"
+        elif case == "dense_own":
+            cfg, prec, kind = inputs.dense_own(s=64, n_inst=8192, n_steps=100), "fp32_kahan", "dense"
+        elif case == "dense_poly":
+            cfg, prec, kind = inputs.dense_group(s=128, n_inst=2048, n_steps=500), "fp32_kahan", "dense"
+            poly = 25
+        elif case == "chain_ext":
+            cfg, prec, kind = inputs.chain_batch(n_inst=512, n_steps=2000), "fp32_kahan", "chain"
         else:
             raise SystemExit(f"unknown case {case}")
         if kind == "dense":
             sys_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
         else:
             sys_ = cho.cho_create_system(ctx, kind, masses=cfg["masses"], springs=cfg["springs"])
+        if case == "chain_ext":
+            import numpy as np
+
+            rng = np.random.default_rng(inputs.SEED_BASE + 6)
+            C, m = cfg["springs"], cfg["masses"]
+            cho.cho_system_set_damping(sys_, 0.04 * np.sqrt(C * m) * rng.uniform(0.5, 2.0, C.shape))
+            cho.cho_system_set_forcing(sys_, C * rng.normal(0.0, 0.01, C.shape),
+                                       cfg["omega_max"] * rng.uniform(0.05, 0.5, C.shape[0]),
+                                       rng.uniform(-np.pi, np.pi, C.shape[0]))
         x0 = torch.as_tensor(cfg["x0"], device=dev)
         v0 = torch.as_tensor(cfg["v0"], device=dev)
         h = torch.as_tensor(cfg["h"], device=dev)
-        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec)
+        cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, poly_jump=poly)
         torch.cuda.synchronize()
         cho.cho_destroy_system(sys_)
     finally:
