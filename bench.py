@@ -136,7 +136,7 @@ def percentile(a, q):
 def run_periodic_mode(cho, inputs, seconds=5.0):
     """Fixed-priority periodic tasks (rate-monotonic classes, implicit deadlines) on their own
     context: a 2-DOF system every 20 ms, a 256-mass chain every 50 ms and a dense s = 128
-    system (bf16x5) every 100 ms, each job 1e4 / 1e4 / 2e3 RK4 steps."""
+    system every 100 ms, each job 1e4 / 1e4 / 2e3 RK4 steps in FP32 + compensation."""
     from paper_1702_02207_gb300 import periodic
 
     ctx = cho.cho_init(0, chunk_steps=2000)
@@ -151,7 +151,7 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
              periodic.PeriodicTask(systems[1], ch["x0"][0], ch["v0"][0], float(ch["h"][0]), 10000, 0.05,
                                    name="chain256_1e4_steps"),
              periodic.PeriodicTask(systems[2], dn["x0"][0], dn["v0"][0], float(dn["h"][0]), 2000, 0.1,
-                                   prec="bf16x5", name="dense128_2e3_steps_bf16x5")]
+                                   name="dense128_2e3_steps")]
     for t in tasks:                          # one job each before the clock starts (module loading)
         periodic.run_periodic(ctx, [periodic.PeriodicTask(**{**t.__dict__, "priority": 0})], 1e-3)
     res = periodic.run_periodic(ctx, tasks, seconds)
@@ -197,8 +197,10 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
         kind, s_ = int(st["kind"][i]), int(st["s"][i])
         sys_, hs = system_for(kind, s_)
         k = i % len(hs)
-        # dense groups with 32 < s <= 256 run on the tensor cores (bf16x5, error <= 1e-5)
-        prec = "bf16x5" if kind == 2 and 32 < s_ <= 256 else "fp32_kahan"
+        # FP32 + compensation throughout: with few requests of one dense system resident at a
+        # time, the few-instance kernels (one instance per CTA or cluster) serve them with a
+        # quarter to a fifth of the tensor-core kernel's time per step
+        prec = "fp32_kahan"
         reqs.append((sys_, k, rng.uniform(-1, 1, s_), np.zeros(s_), float(hs[k]), int(st["n_steps"][i]),
                      int(st["priority"][i]), s_, prec))
     work = np.array([r[7] * r[5] for r in reqs], dtype=np.float64)
@@ -254,7 +256,7 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
            "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
                          for c in range(3)},
            "mix": "s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5, "
-                  "classes 20/30/50 %, Poisson arrivals; FP32 + compensation, dense 32 < s <= 256 in bf16x5"}
+                  "classes 20/30/50 %, Poisson arrivals; FP32 + compensation"}
     return out
 
 
@@ -431,6 +433,20 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                      "note": "B operand bytes per instance-step (20 s^2) / time; B from registers and shared "
                              "memory, ncu: shared-memory pipe 95 % busy, FMA pipe 44 %"}}
     cho.cho_destroy_system(s_)
+    # one dense instance alone (a serving request, a real-time task): s = 128 on one CTA,
+    # s = 512 on a cluster of 8 CTAs (B's rows split over them, one cluster barrier per
+    # stage).  Latency bound: no throughput roofline applies; reported per RK4 step.
+    for s in (128, 512):
+        cfg = inputs.dense_group(s=s, n_inst=1, n_steps=2000)
+        s_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
+        t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])
+        res[f"dense_single_s{s}_fp32_kahan"] = {
+            "value": s * cfg["n_steps"] / t, "unit": UNIT, "ms": 1e3 * t, "us_per_step": 1e6 * t / cfg["n_steps"],
+            "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan", n_sample=1, every=500),
+            "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                         "note": "one instance: four dependent stages per step, each a B x product split over "
+                                 "the CTA (cluster) and one barrier"}}
+        cho.cho_destroy_system(s_)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     for s in (64, 128, 256):
         cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)

@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(NTHR) rk4_dense_simt_kernel(DenseSys sys, cons
     int buf = 0;
     // FP32: B = hi + lo.  The lo product is formed at stage 1 only, in its own
     // accumulator, and reused by stages 2-4 ("frozen lo", as rk4_small.cu): those
-    // stages stream and multiply the hi piece alone.
+    // stages stream and multiply the hi piece alone.  Both products are summed in
+    // blocks of kJC columns (a partial per block, the partials added in column
+    // order): every FP32 dense kernel (streaming, resident, cluster-split) keeps
+    // this order, so all of them give the same bits for the same instance.
     Real lo1[RI];
     auto accel = [&](const Real (&xs)[RI], Real (&acc)[RI], bool first) {
         Real* X = xsh + buf * SP * NT;
@@ -256,19 +259,22 @@ __global__ void __launch_bounds__(NTHR) rk4_dense_simt_kernel(DenseSys sys, cons
             const int jn = s - c * kJC < kJC ? s - c * kJC : kJC;   // columns beyond s are zero
             // blocked summation: the chunk's kJC terms go into a partial sum that is then
             // added to the total, so the rounding error grows with kJC + s / kJC, not with s
-            Real part[RI];
+            Real part[RI], lpart[RI];
 #pragma unroll
-            for (int k = 0; k < RI; ++k) part[k] = 0;
+            for (int k = 0; k < RI; ++k) part[k] = lpart[k] = 0;
             for (int jj = 0; jj < jn; ++jj) {
                 const Real xj = X[(c * kJC + jj) * NT + n];
                 const Real* col = bh + jj * SP + row0;
                 col_fma(col, xj, part);
                 if constexpr (!F64) {
-                    if (first) col_fma(col + CHUNK, xj, lo1);
+                    if (first) col_fma(col + CHUNK, xj, lpart);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < RI; ++k) t0[k] = addr(t0[k], part[k]);
+            for (int k = 0; k < RI; ++k) {
+                t0[k] = addr(t0[k], part[k]);
+                if (!F64 && first) lo1[k] = addr(lo1[k], lpart[k]);
+            }
             __syncthreads();                         // buffer c & 1 free for chunk c + 2
         }
 #pragma unroll
@@ -341,27 +347,25 @@ __global__ void __launch_bounds__(NTHR) rk4_dense_simt_kernel(DenseSys sys, cons
     if (live && r == 0) src.finish(q, my_steps, any_bad[n] != 0);
 }
 
-// One (M, K) per instance with B held in shared memory for the whole horizon
-// (FP32, s_pad <= 128): CTA = 1 instance, thread = 1 row.  B is stored row-major with
-// each row padded by 16 bytes, so that a thread reads its row with 16-byte vector
-// loads and the eight threads of a shared-memory phase fall in distinct banks.
-// The products keep the streaming kernel's order (columns in blocks of kJC into a
-// partial sum; the lo piece at stage 1 alone, column by column), so both give the
-// same bits; here B comes from shared memory instead of L2 every stage.
-// REG (FP32, s_pad = 64): the thread's row of B's hi piece lives in registers
-// (64 of them) and only the lo piece, used at stage 1, in shared memory: with B
-// read from shared memory every FMA needed 4 bytes from it, which held the FMA
-// pipe near a quarter of its rate.
-template <int SP, bool F64, class Src, bool REG = (!F64 && SP <= 64)>
-__global__ void __launch_bounds__(SP) rk4_dense_own_kernel(DenseSys sys, const Src src)
+// One instance per CTA, s_pad = 64, FP32 (systems with one (M, K) per instance, or a
+// few instances of a shared one): thread = 1 row, the thread's row of B's hi piece
+// in 64 registers for the whole horizon and the lo piece (used at stage 1) in shared
+// memory, row-major with each row padded by 16 bytes (the eight threads of a
+// shared-memory phase fall in distinct banks).  Streaming B from shared memory
+// instead needed 4 bytes of it per FMA, which held the FMA pipe near a quarter of
+// its rate.  The products keep the streaming kernel's order (blocks of kJC columns
+// into partials added in column order; the lo piece at stage 1 alone), so both give
+// the same bits.
+template <class Src>
+__global__ void __launch_bounds__(64) rk4_dense_own_kernel(DenseSys sys, const Src src)
 {
-    using Real = std::conditional_t<F64, double, float>;
-    constexpr int NB = F64 ? 1 : 2;
-    constexpr int VW = 16 / sizeof(Real);           // elements per 16-byte load
-    constexpr int LD = SP + VW;                     // padded row length
+    using Real = float;
+    constexpr bool F64 = false;
+    constexpr int SP = 64;
+    constexpr int LD = SP + 4;                      // padded row length
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* Bs = (Real*)smem_raw;                     // [NB][SP][LD]: B (hi, lo) row-major (REG: lo only)
-    Real* X = Bs + (size_t)(REG ? 1 : NB) * SP * LD;   // [2][SP]
+    float* Bs = (float*)smem_raw;                   // [SP][LD]: lo piece of B, row-major
+    float* X = Bs + (size_t)SP * LD;                // [2][SP]
     __shared__ int any_bad;
 
     const int t = threadIdx.x;
@@ -369,107 +373,55 @@ __global__ void __launch_bounds__(SP) rk4_dense_own_kernel(DenseSys sys, const S
     const int s = sys.s;
     const int64_t my_steps = src.steps(q);
     if (t == 0) any_bad = 0;
-    Real breg[REG ? SP : 1];
+    float breg[SP];
     {
-        const Real* Bt = (const Real*)src.bt(sys, q);   // [NB][SP][SP] = B^T
-        if constexpr (REG) {
+        const float* Bt = (const float*)src.bt(sys, q);   // [2][SP][SP] = B^T (hi, lo)
 #pragma unroll
-            for (int j = 0; j < SP; ++j) breg[j] = Bt[(size_t)j * SP + t];       // hi row t, coalesced
-            for (int e = t; e < SP * SP; e += SP) {
-                const int j = e / SP, i = e % SP;
-                Bs[(size_t)i * LD + j] = Bt[(size_t)SP * SP + e];              // lo piece
-            }
-        } else {
-            for (int pc = 0; pc < NB; ++pc)
-                for (int e = t; e < SP * SP; e += SP) {
-                    const int j = e / SP, i = e % SP;      // B^T[j][i] = B[i][j]
-                    Bs[((size_t)pc * SP + i) * LD + j] = Bt[(size_t)pc * SP * SP + e];
-                }
+        for (int j = 0; j < SP; ++j) breg[j] = Bt[(size_t)j * SP + t];       // hi row t, coalesced
+        for (int e = t; e < SP * SP; e += SP) {
+            const int j = e / SP, i = e % SP;
+            Bs[(size_t)i * LD + j] = Bt[(size_t)SP * SP + e];              // lo piece
         }
     }
-    const StepSize<F64> hs(src.h(q));
-    Real x = 0, v = 0;
-    float cx = 0.f, cv = 0.f;
+    const StepSize<false> hs(src.h(q));
+    float x = 0.f, v = 0.f, cx = 0.f, cv = 0.f;
     if (t < s) src.load(q, t, x, v, cx, cv);
     __syncthreads();
 
-    const Real* brow = Bs + (size_t)t * LD;
-    const Real* brow_lo = Bs + ((size_t)(REG ? 0 : SP) + t) * LD;
+    const float* brow_lo = Bs + (size_t)t * LD;
     int buf = 0;
-    Real lo1 = 0;
-    auto accel = [&](Real xs, bool first) -> Real {
-        Real* Xb = X + buf * SP;
+    float lo1 = 0.f;
+    auto accel = [&](float xs, bool first) -> float {
+        float* Xb = X + buf * SP;
         Xb[t] = xs;
         __syncthreads();
-        Real acc = 0;
-        if (!F64 && first) lo1 = 0;
-        if constexpr (REG) {
-            // every block full: columns beyond s hold zeros in B and X (adds of +0)
+        float acc = 0.f;
+        if (first) lo1 = 0.f;
+        // every block full: columns beyond s hold zeros in B and X (adds of +0)
 #pragma unroll
-            for (int c = 0; c < SP / kJC; ++c) {
-                Real part = 0;
+        for (int c = 0; c < SP / kJC; ++c) {
+            float part = 0.f, lpart = 0.f;
 #pragma unroll
-                for (int jj = 0; jj < kJC; jj += 4) {
-                    const int j = c * kJC + jj;
-                    const float4 xx = *(const float4*)(Xb + j);
-                    part = fmar(breg[j], xx.x, part);
-                    part = fmar(breg[j + 1], xx.y, part);
-                    part = fmar(breg[j + 2], xx.z, part);
-                    part = fmar(breg[j + 3], xx.w, part);
-                    if (first) {
-                        const float4 bl = *(const float4*)(brow_lo + j);
-                        lo1 = fmar(bl.x, xx.x, lo1);
-                        lo1 = fmar(bl.y, xx.y, lo1);
-                        lo1 = fmar(bl.z, xx.z, lo1);
-                        lo1 = fmar(bl.w, xx.w, lo1);
-                    }
-                }
-                acc = addr(acc, part);
-            }
-            buf ^= 1;
-            return -addr(acc, lo1);
-        }
-        for (int c = 0; c * kJC < s; ++c) {
-            Real part = 0;
-            const int jn = s - c * kJC < kJC ? s - c * kJC : kJC;
-            if (jn == kJC) {
-#pragma unroll
-                for (int jj = 0; jj < kJC; jj += VW) {
-                    const int j = c * kJC + jj;
-                    if constexpr (F64) {
-                        const double2 b = *(const double2*)(brow + j);
-                        const double2 xx = *(const double2*)(Xb + j);
-                        part = fmar(b.x, xx.x, part);
-                        part = fmar(b.y, xx.y, part);
-                    } else {
-                        const float4 b = *(const float4*)(brow + j);
-                        const float4 xx = *(const float4*)(Xb + j);
-                        part = fmar(b.x, xx.x, part);
-                        part = fmar(b.y, xx.y, part);
-                        part = fmar(b.z, xx.z, part);
-                        part = fmar(b.w, xx.w, part);
-                        if (first) {
-                            const float4 bl = *(const float4*)(brow_lo + j);
-                            lo1 = fmar(bl.x, xx.x, lo1);
-                            lo1 = fmar(bl.y, xx.y, lo1);
-                            lo1 = fmar(bl.z, xx.z, lo1);
-                            lo1 = fmar(bl.w, xx.w, lo1);
-                        }
-                    }
-                }
-            } else {
-                for (int jj = 0; jj < jn; ++jj) {
-                    const int j = c * kJC + jj;
-                    part = fmar(brow[j], Xb[j], part);
-                    if constexpr (!F64) {
-                        if (first) lo1 = fmar(brow_lo[j], Xb[j], lo1);
-                    }
+            for (int jj = 0; jj < kJC; jj += 4) {
+                const int j = c * kJC + jj;
+                const float4 xx = *(const float4*)(Xb + j);
+                part = fmar(breg[j], xx.x, part);
+                part = fmar(breg[j + 1], xx.y, part);
+                part = fmar(breg[j + 2], xx.z, part);
+                part = fmar(breg[j + 3], xx.w, part);
+                if (first) {
+                    const float4 bl = *(const float4*)(brow_lo + j);
+                    lpart = fmar(bl.x, xx.x, lpart);
+                    lpart = fmar(bl.y, xx.y, lpart);
+                    lpart = fmar(bl.z, xx.z, lpart);
+                    lpart = fmar(bl.w, xx.w, lpart);
                 }
             }
             acc = addr(acc, part);
+            if (first) lo1 = addr(lo1, lpart);
         }
         buf ^= 1;
-        return F64 ? -acc : -addr(acc, lo1);
+        return -addr(acc, lo1);
     };
 
     // the block's step count: every instance is alone in its CTA
@@ -515,16 +467,285 @@ __global__ void __launch_bounds__(SP) rk4_dense_own_kernel(DenseSys sys, const S
     if (t == 0) src.finish(q, my_steps, any_bad != 0);
 }
 
-template <int SP, bool F64, class Src>
+// ---- one instance spread over a cluster of CTAs (FP32, s_pad >= 128) ---------------
+//
+// With few instances (a serving request, a periodic real-time task) the kernels
+// above run each instance's stages one after the other on one SM while the other
+// SMs idle.  Here one instance spans a cluster of CS CTAs, each owning R = s_pad / CS
+// rows of B: the hi piece of its rows in registers (CPT consecutive blocks of kJC
+// columns per thread), the lo piece (stage 1 only) in shared memory.  A stage is:
+// every CTA forms the block partials of its rows (a thread per row and block
+// range), the owner thread of each row adds them in column order, completes the
+// row's stage values and writes its next stage displacement into every CTA's copy
+// of Xs (distributed shared memory, double-buffered), then one cluster barrier.
+// This is the paper's decomposition of one system's RK4 stage over parallel
+// workers with one synchronisation between stages (Section 3), at the scale of a
+// cluster of SMs.  The block partials and their order are those of the other FP32
+// dense kernels, so an instance gets the same bits whichever of them runs it.
+template <int SP, int R, int NTHR, class Src>
+__global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_kernel(DenseSys sys, const Src src)
+{
+    constexpr int CS = SP / R;                      // CTAs per cluster
+    constexpr int NCH = SP / kJC;                   // column blocks
+    constexpr int NRG = R / 32;                     // row groups (a warp's lanes are 32 rows)
+    constexpr int WPG = (NTHR / 32) / NRG;          // warps per row group
+    constexpr int CPT = NCH / WPG;                  // consecutive column blocks per thread
+    constexpr int LD = SP + 4;                      // padded row of the lo piece
+    constexpr int PLD = NCH + 4;                    // padded row of the partials
+    static_assert(R % 32 == 0 && (NTHR / 32) % NRG == 0 && NCH % WPG == 0 && R <= NTHR, "split shape");
+    static_assert(CPT % 4 == 0 && NCH % 4 == 0, "partials move as float4");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Lo = (float*)smem_raw;                   // [R][LD]: lo piece of this CTA's rows
+    float* X = Lo + (size_t)R * LD;                 // [2][SP]: stage displacements of all rows
+    float* Ph = X + 2 * SP;                         // [R][PLD]: block partials, hi piece
+    float* Pl = Ph + (size_t)R * PLD;               // [R][PLD]: block partials, lo piece (stage 1)
+    __shared__ int any_bad;
+
+    const int t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    const int lr = (w % NRG) * 32 + lane;           // local row of this thread's partials
+    const int c0 = (w / NRG) * CPT;                 // its blocks: c0 .. c0 + CPT - 1
+    const uint32_t rank = CS > 1 ? cluster_rank() : 0;
+    const int64_t q = blockIdx.x / CS;
+    const int s = sys.s;
+    // blocks at or past column s hold zero partials; a warp whose blocks all lie
+    // there never forms them (its partials keep the zeros written below)
+    const bool active = c0 * kJC < s;
+    const bool owner = t < R;                       // thread t < R owns local row t (its lr is t)
+    const int i = (int)rank * R + t;                // the owner's global row
+
+    const float* Bt = (const float*)src.bt(sys, q);   // [2][SP][SP]: B^T hi, then lo
+    float bh[CPT][kJC];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int jj = 0; jj < kJC; ++jj) bh[k][jj] = Bt[(size_t)((c0 + k) * kJC + jj) * SP + (int)rank * R + lr];
+    for (int e = t; e < R * SP; e += NTHR) {
+        const int j = e / R, r = e % R;             // B^T[j][rank R + r], coalesced over r
+        Lo[(size_t)r * LD + j] = Bt[(size_t)SP * SP + (size_t)j * SP + (int)rank * R + r];
+    }
+    for (int e = t; e < 2 * R * PLD; e += NTHR) Ph[e] = 0.f;   // Ph and Pl
+    const int64_t my_steps = src.steps(q);
+    const StepSize<false> hs(src.h(q));
+    float x = 0.f, v = 0.f, cx = 0.f, cv = 0.f;
+    if (owner && i < s) src.load(q, i, x, v, cx, cv);
+    if (t == 0) any_bad = 0;
+    // the owner's row of Xs (buffer 0); mapa gives its address in each CTA of the cluster
+    const uint32_t xloc = (uint32_t)__cvta_generic_to_shared(X) + 4u * (uint32_t)(owner ? i : 0);
+    // every CTA of the cluster is running and has initialised its shared memory
+    if (CS > 1) cluster_sync(); else __syncthreads();
+
+    int buf = 0;
+    float lo1 = 0.f;
+    auto accel = [&](float xs, bool first) -> float {
+        if (owner) {
+            const uint32_t off = (uint32_t)(buf * SP * 4);
+            if constexpr (CS > 1) {
+#pragma unroll
+                for (int c = 0; c < CS; ++c) st_cluster_f32(mapa(xloc + off, (uint32_t)c), xs);
+            } else {
+                X[buf * SP + i] = xs;
+            }
+        }
+        if (CS > 1) cluster_sync(); else __syncthreads();
+        if (active) {
+            const float* Xb = X + buf * SP + c0 * kJC;
+            const float* lrow = Lo + (size_t)lr * LD + c0 * kJC;
+            // each block's columns in order; the CPT blocks' chains are independent
+            float p[CPT], pl[CPT];
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const float4 x0 = *(const float4*)(Xb + k * kJC);
+                const float4 x1 = *(const float4*)(Xb + k * kJC + 4);
+                float u = 0.f;
+                u = fmar(bh[k][0], x0.x, u);
+                u = fmar(bh[k][1], x0.y, u);
+                u = fmar(bh[k][2], x0.z, u);
+                u = fmar(bh[k][3], x0.w, u);
+                u = fmar(bh[k][4], x1.x, u);
+                u = fmar(bh[k][5], x1.y, u);
+                u = fmar(bh[k][6], x1.z, u);
+                u = fmar(bh[k][7], x1.w, u);
+                p[k] = u;
+                if (first) {
+                    const float4 l0 = *(const float4*)(lrow + k * kJC);
+                    const float4 l1 = *(const float4*)(lrow + k * kJC + 4);
+                    float z = 0.f;
+                    z = fmar(l0.x, x0.x, z);
+                    z = fmar(l0.y, x0.y, z);
+                    z = fmar(l0.z, x0.z, z);
+                    z = fmar(l0.w, x0.w, z);
+                    z = fmar(l1.x, x1.x, z);
+                    z = fmar(l1.y, x1.y, z);
+                    z = fmar(l1.z, x1.z, z);
+                    z = fmar(l1.w, x1.w, z);
+                    pl[k] = z;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CPT; k += 4) {
+                *(float4*)(Ph + (size_t)lr * PLD + c0 + k) = make_float4(p[k], p[k + 1], p[k + 2], p[k + 3]);
+                if (first)
+                    *(float4*)(Pl + (size_t)lr * PLD + c0 + k) = make_float4(pl[k], pl[k + 1], pl[k + 2], pl[k + 3]);
+            }
+        }
+        __syncthreads();
+        float a = 0.f;
+        if (owner) {
+            // all NCH blocks in column order (the zero ones leave the sums unchanged)
+            float t0 = 0.f, l = 0.f;
+#pragma unroll
+            for (int c = 0; c < NCH; c += 4) {
+                const float4 u = *(const float4*)(Ph + (size_t)t * PLD + c);
+                t0 = addr(addr(addr(addr(t0, u.x), u.y), u.z), u.w);
+                if (first) {
+                    const float4 ul = *(const float4*)(Pl + (size_t)t * PLD + c);
+                    l = addr(addr(addr(addr(l, ul.x), ul.y), ul.z), ul.w);
+                }
+            }
+            if (first) lo1 = l;
+            a = -addr(t0, lo1);
+        }
+        buf ^= 1;
+        return a;
+    };
+
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (my_steps > 0 ? my_steps : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < my_steps; done += every) {
+        for (int64_t it = 0; it < every; ++it) {
+            float a, xs, kx, kv, vs;
+            a = accel(x, true);
+            kx = v;
+            kv = a;
+            xs = fmar(hs.h2, v, x);
+            vs = fmar(hs.h2, a, v);
+            a = accel(xs, false);
+            kx = fmar(2.f, vs, kx);
+            kv = fmar(2.f, a, kv);
+            xs = fmar(hs.h2, vs, x);
+            vs = fmar(hs.h2, a, v);
+            a = accel(xs, false);
+            kx = fmar(2.f, vs, kx);
+            kv = fmar(2.f, a, kv);
+            xs = fmar(hs.h, vs, x);
+            vs = fmar(hs.h, a, v);
+            a = accel(xs, false);
+            kx = addr(kx, vs);
+            kv = addr(kv, a);
+            state_update<false>(x, cx, kx, hs);
+            state_update<false>(v, cv, kv, hs);
+        }
+        if (src.ckpt_every() > 0) {
+            if (owner && i < s) src.checkpoint(q, ck, i, x, v, cx, cv);
+            ++ck;
+        }
+    }
+    bool bad = false;
+    if (owner && i < s) {
+        src.store(q, i, x, v, cx, cv);
+        bad = !(isfinite(x) && isfinite(v));
+    }
+    if (bad) {
+        if constexpr (CS > 1) st_cluster_u32(mapa((uint32_t)__cvta_generic_to_shared(&any_bad), 0u), 1u);
+        else any_bad = 1;
+    }
+    if (CS > 1) cluster_sync(); else __syncthreads();
+    if (rank == 0 && t == 0) src.finish(q, my_steps, any_bad != 0);
+}
+
+// Shapes of the split kernel: s_pad 128 -> one CTA of 256 threads (two per SM),
+// 256 -> 2 CTAs and 512 -> 8 CTAs of 512 threads; every thread holds 64 hi values.
+template <int SP> struct SplitShape;
+template <> struct SplitShape<128> { static constexpr int R = 128, NTHR = 256; };
+template <> struct SplitShape<256> { static constexpr int R = 128, NTHR = 512; };
+template <> struct SplitShape<512> { static constexpr int R = 64, NTHR = 512; };
+
+template <int SP>
+size_t split_smem()
+{
+    constexpr int R = SplitShape<SP>::R;
+    return sizeof(float) * ((size_t)R * (SP + 4) + 2 * (size_t)SP + 2 * (size_t)R * (SP / kJC + 4));
+}
+
+template <int SP, class Src>
+cudaLaunchConfig_t split_config(int64_t n_inst, cudaStream_t st, cudaLaunchAttribute* attr)
+{
+    constexpr int CS = SP / SplitShape<SP>::R;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_inst * CS), 1, 1);
+    cfg.blockDim = dim3(SplitShape<SP>::NTHR, 1, 1);
+    cfg.dynamicSmemBytes = split_smem<SP>();
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// How many clusters of the split kernel are resident at once on this device (asked
+// once per device and shape; 0 if none fits, and its callers keep the other kernels).
+template <int SP, class Src>
+int split_capacity()
+{
+    static int known[64];                           // cluster count + 1; 0 unknown
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (known[dev] == 0) {
+        auto kern = rk4_dense_split_kernel<SP, SplitShape<SP>::R, SplitShape<SP>::NTHR, Src>;
+        int n = 0;
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = split_config<SP, Src>(1, nullptr, attr);
+        bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem<SP>()) ==
+                  cudaSuccess;
+        ok = ok && cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            n = 0;
+        }
+        known[dev] = n + 1;
+    }
+    return known[dev] - 1;
+}
+
+template <int SP, class Src>
+cudaError_t launch_split(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+{
+    constexpr int CS = SP / SplitShape<SP>::R;
+    if (sys.s_pad != SP) return cudaErrorInvalidValue;
+    if (n_inst <= 0) return cudaSuccess;
+    if (n_inst > 0x7fffffffLL / CS) return cudaErrorInvalidValue;
+    auto kern = rk4_dense_split_kernel<SP, SplitShape<SP>::R, SplitShape<SP>::NTHR, Src>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem<SP>());
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = split_config<SP, Src>(n_inst, st, attr);
+    return cudaLaunchKernelEx(&cfg, kern, sys, src);
+}
+
+int device_sm_count()
+{
+    static int known[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (known[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        known[dev] = n;
+    }
+    return known[dev];
+}
+
+template <class Src>
 cudaError_t launch_own(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
-    using Real = std::conditional_t<F64, double, float>;
-    constexpr bool REG = !F64 && SP <= 64;
-    constexpr int NB = REG ? 1 : (F64 ? 1 : 2);
-    constexpr int LD = SP + 16 / (int)sizeof(Real);
+    constexpr int SP = 64;
     if (sys.s_pad != SP) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(Real) * ((size_t)NB * SP * LD + 2 * (size_t)SP);
-    auto kern = rk4_dense_own_kernel<SP, F64, Src>;
+    const size_t smem = sizeof(float) * ((size_t)SP * (SP + 4) + 2 * (size_t)SP);
+    auto kern = rk4_dense_own_kernel<Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (n_inst <= 0) return cudaSuccess;
@@ -561,17 +782,35 @@ cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaSt
     case SPV:                                                                                         \
         if (fp64) { SrcT<true> src; init(src); return launch_simt<RI, 1, true, SrcT<true>, SPV / RI>(sys, src, n_inst, st); } \
         else { SrcT<false> src; init(src); return launch_simt<RI, 1, false, SrcT<false>, SPV / RI>(sys, src, n_inst, st); }
-    if (sys.per_inst) {                             // one instance (and its own B) per CTA
+    // FP32 with one (M, K) per instance, or few instances of a shared one (up to eight
+    // waves of what fits at once): one instance per CTA (s_pad = 64, B resident) or per
+    // cluster (larger s, B split over the cluster).  All FP32 kernels give the same bits,
+    // so the choice may follow the instance count.
+    if (!fp64) {
+        SrcT<false> src;
+        init(src);
+        int cap = 0;
         switch (sys.s_pad) {
-            // FP32, s_pad <= 128: B resident in shared memory (1.7x / 1.45x the streaming form at
-            // s = 64 / 128); FP64 keeps the streaming form, which measured faster there
-            case 64:
-                if (fp64) { SrcT<true> src; init(src); return launch_simt<1, 1, true, SrcT<true>, 64>(sys, src, n_inst, st); }
-                else { SrcT<false> src; init(src); return launch_own<64, false>(sys, src, n_inst, st); }
-            case 128:
-                if (fp64) { SrcT<true> src; init(src); return launch_simt<2, 1, true, SrcT<true>, 64>(sys, src, n_inst, st); }
-                else { SrcT<false> src; init(src); return launch_own<128, false>(sys, src, n_inst, st); }
-            CHO_DENSE_OWN_CASE(256, 4)                  // B streamed through shared memory from L2
+            case 64: cap = device_sm_count(); break;
+            case 128: cap = split_capacity<128, SrcT<false>>(); break;
+            case 256: cap = split_capacity<256, SrcT<false>>(); break;
+            case 512: cap = split_capacity<512, SrcT<false>>(); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (cap > 0 && (sys.per_inst || n_inst <= 8 * (int64_t)cap)) {
+            switch (sys.s_pad) {
+                case 64: return launch_own(sys, src, n_inst, st);
+                case 128: return launch_split<128>(sys, src, n_inst, st);
+                case 256: return launch_split<256>(sys, src, n_inst, st);
+                default: return launch_split<512>(sys, src, n_inst, st);
+            }
+        }
+    }
+    if (sys.per_inst) {                             // one instance (and its own B) per CTA, streamed
+        switch (sys.s_pad) {
+            CHO_DENSE_OWN_CASE(64, 1)
+            CHO_DENSE_OWN_CASE(128, 2)
+            CHO_DENSE_OWN_CASE(256, 4)
             CHO_DENSE_OWN_CASE(512, 8)
             default: return cudaErrorInvalidValue;
         }

@@ -9,7 +9,9 @@ Cases (each one cho_integrate_batch call, a few MB of device memory):
   dense_tc64 s = 64, 4096 instances, 500 steps, bf16x5      (rk4_dense_tc, two tiles stacked per CTA)
   dense_tc2 s = 256, 2048 instances, 200 steps, bf16x5       (rk4_dense_tc, 2-CTA clusters)
   dense_simt s = 256, 512 instances, 50 steps, fp32_simt     (rk4_dense_simt)
-  dense_own s = 64, 8192 instances with their own (M, K), 100 steps, fp32_kahan (rk4_dense_simt, one per CTA)
+  dense_own s = 64, 8192 instances with their own (M, K), 100 steps, fp32_kahan (rk4_dense_own, one per CTA)
+  dense_split s = 512, 4 instances of one (M, K), 500 steps, fp32_kahan (rk4_dense_split, 8-CTA clusters)
+  dense_split128 s = 128, 608 instances with their own (M, K), 200 steps, fp32_kahan (rk4_dense_split, 1 CTA)
   dense_poly s = 128, 2048 instances, 500 steps, fp32_kahan, k = 25 steps per update (rk4_dense_poly)
   chain_ext 512 damped and forced chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain_ext)
 """
@@ -41,6 +43,10 @@ def run(case: str) -> None:
             cfg, prec, kind = inputs.dense_group(s=256, n_inst=512, n_steps=50), "fp32_simt", "dense"
         elif case == "dense_own":
             cfg, prec, kind = inputs.dense_own(s=64, n_inst=8192, n_steps=100), "fp32_kahan", "dense"
+        elif case == "dense_split":
+            cfg, prec, kind = inputs.dense_group(s=512, n_inst=4, n_steps=500), "fp32_kahan", "dense"
+        elif case == "dense_split128":
+            cfg, prec, kind = inputs.dense_own(s=128, n_inst=608, n_steps=200), "fp32_kahan", "dense"
         elif case == "dense_poly":
             cfg, prec, kind = inputs.dense_group(s=128, n_inst=2048, n_steps=500), "fp32_kahan", "dense"
             poly = 25

@@ -465,6 +465,59 @@ def test_dense_per_instance(ctx, s, prec, tol):
     print(f"dense own-K s={s} {prec}: x {ex:.3e} v {ev:.3e}")
 
 
+def _beyond_few(s, sms):
+    """An instance count above what the FP32 few-instance dense kernels take (eight waves of
+    one instance per CTA at s_pad = 64, one per SM; at 128, at most two per SM; per 2- or 8-CTA
+    cluster at 256 and 512), so that the streaming kernel runs it."""
+    sp = 64
+    while sp < s:
+        sp *= 2
+    return 8 * {64: sms, 128: 2 * sms, 256: sms // 2, 512: sms // 8}[sp] + 5
+
+
+@pytest.mark.parametrize("s", [64, 100, 200, 333, 512])
+def test_dense_few_instances_same_bits_as_many(ctx, s):
+    """A few instances of a shared dense system run one per CTA (s_pad = 64: B resident) or
+    one per cluster of CTAs (larger s: B's rows split over the cluster, stage displacements
+    exchanged through distributed shared memory); many instances run on the streaming
+    kernel.  All FP32 dense kernels sum the products in the same order, so the shared
+    instances agree bit for bit, trajectories included, and with the oracle."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    many = _beyond_few(s, sms)
+    cfg = inputs.dense_group(s=s, n_inst=many, n_steps=400)
+    few = dict(cfg, x0=cfg["x0"][:3], v0=cfg["v0"][:3], h=cfg["h"][:3])
+    out_few = run_gpu(ctx, few, "fp32_kahan", 100)
+    out_many = run_gpu(ctx, cfg, "fp32_kahan", 100)
+    for k in ("x", "v", "x_traj", "v_traj"):
+        assert np.array_equal(out_few[k], out_many[k][:3]), k
+    ref = oracle_run(few, ckpt_every=100)
+    ex, ev = check(out_few, ref, TOL_FP32)
+    print(f"dense few-instance s={s}: x {ex:.3e} v {ev:.3e}")
+
+
+@pytest.mark.parametrize("s", [100, 300])
+def test_dense_per_instance_same_bits_as_shared(ctx, s):
+    """Instance i of a system with one (M, K) per instance (cluster kernel) gives the bits of
+    the same instance in a large batch of a shared system built from its M and K (streaming
+    kernel)."""
+    import torch
+
+    cfg = inputs.dense_own(s=s, n_inst=3, n_steps=300)
+    out = run_gpu(ctx, cfg, "fp32_kahan", 100)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    many = _beyond_few(s, sms)
+    i = 1
+    shared = dict(kind="dense", s=s, M=cfg["M"][i:i + 1], K=cfg["K"][i:i + 1],
+                  x0=np.repeat(cfg["x0"][i:i + 1], many, 0), v0=np.repeat(cfg["v0"][i:i + 1], many, 0),
+                  h=np.full(many, cfg["h"][i]), n_steps=300)
+    out_sh = run_gpu(ctx, shared, "fp32_kahan", 100)
+    for k in ("x", "v", "x_traj", "v_traj"):
+        assert np.array_equal(out[k][i], out_sh[k][0]), k
+        assert np.array_equal(out_sh[k][0], out_sh[k][many - 1]), k
+
+
 def test_dense_per_instance_energy_and_errors(ctx):
     """FP64 energy per checkpoint from each instance's own M and K; BF16 modes are refused."""
     import oracle
