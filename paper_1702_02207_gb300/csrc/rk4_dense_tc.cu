@@ -23,19 +23,25 @@
 // Work split.  s <= 64: one CTA per 64 instances, two tiles of 32 stacked along
 // the 128 rows against the block-diagonal [B 0; 0 B] (the MMA shape is fixed at
 // 128 rows; a padded 64 x 64 B would leave half of every MMA idle).  64 < s <=
-// 128: one CTA per tile of 32 instances.  In both, B's BF16 pieces are written
-// once into tensor memory next to the accumulators and the MMAs read their A
-// operand from there.  128 < s <= 256: a cluster of two CTAs per tile; CTA r
-// owns rows [128 r, 128 r + 128) of B (resident in its shared memory for the
-// whole run, fetched once with bulk (TMA) copies) and the same rows of the
-// state, and writes its rows of each stage's Xs into both CTAs' shared memory,
-// so each CTA multiplies its 128 rows of B by the full Xs.
+// 128: one CTA per tile of 32 instances.  Both pair the stages (the products of
+// stages 1 and 2 go to the tensor cores together, then those of 3 and 4; see
+// rk4_dense_tc_pair_kernel) on two accumulator sets.  128 < s <= 256: a cluster
+// of two CTAs per tile, one stage at a time; CTA r owns rows [128 r, 128 r + 128)
+// of B and of the state and writes its rows of each stage's Xs into both CTAs'
+// shared memory, so each CTA multiplies its 128 rows of B by the full Xs.  B's
+// pieces are fetched once with bulk (TMA) copies and stay in shared memory.
 //
-// Measured cost (GB300, 128 x 32 x 16 BF16 MMAs): about 75 cycles per MMA
-// whether A comes from shared or tensor memory, plus about 1,100 cycles per
-// stage for publishing Xs, the barrier, the completion wait and the epilogue;
-// the MMA issue loop is unrolled with constant operand offsets (computing
-// descriptors per MMA cost another ~15 cycles each).
+// Measured cost (GB300, back-to-back tcgen05.mma of M = 128, K = 16 from one
+// thread): about 45 cycles per MMA for N <= 64 whether A comes from shared or
+// tensor memory, 64 at N = 128 and 128 at N = 256 (the full BF16 rate, about
+// 8,150 flop per cycle per SM); the issuing thread is held for about as long as
+// its MMAs run.  A stage here issues 40 MMAs of N = 32 (bf16x5), so the MMAs
+// alone cost about 1,800 cycles a stage at 36 % of the tensor rate, and the
+// epilogue (TMEM loads, FP32 sums, stage update, publishing Xs, barrier) about
+// as much again.  Wider tiles would need the state of 64 instances per SM,
+// which fits neither the register file nor tensor memory beside eight
+// accumulators; a warp that only issues MMAs would leave the others 96 registers
+// (the thread count rounds up to 640 for register allocation).
 //
 // Per CTA: 16 warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of its
 // 128-row block) and columns 8 (w / 4) .. +7 (instances); each thread keeps the
@@ -99,16 +105,21 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the phase with the given parity; false after kWaitNs.
+// Bounded wait for the phase with the given parity; false after kWaitNs.  The
+// suspend-time hint lets a waiting warp sleep until the phase completes (or the hint
+// runs out) instead of spinning: the warps that wait for the MMAs share the SM's
+// issue slots with the one that issues them.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
     const uint64_t t0 = globaltimer();
     while (true) {
         uint32_t done;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
         if (globaltimer() - t0 > kWaitNs) return false;
@@ -135,24 +146,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// The same MMA with the A operand (128 rows x 16 K, two BF16 per 32-bit column)
-// read from tensor memory.
-__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                            uint32_t accumulate)
-{
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, uint4 lo, uint4 hi)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(lo.x),
-                 "r"(lo.y), "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
-                 : "memory");
-}
-
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -170,21 +163,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Two accumulators' x8 column groups (kNT columns apart) with a single wait.
-__device__ __forceinline__ void tmem_ld8_x2(uint32_t taddr, float (&v)[2][8])
+// Four accumulators' x8 column groups (kNT columns apart) with a single wait.
+__device__ __forceinline__ void tmem_ld8_x4(uint32_t taddr, float (&v)[4][8])
 {
-    uint32_t r[2][8];
+    uint32_t r[4][8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
           "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
-          "=r"(r[1][6]), "=r"(r[1][7])
-        : "r"(taddr), "r"(taddr + (uint32_t)kNT)
+          "=r"(r[1][6]), "=r"(r[1][7]), "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[2][4]),
+          "=r"(r[2][5]), "=r"(r[2][6]), "=r"(r[2][7]), "=r"(r[3][0]), "=r"(r[3][1]), "=r"(r[3][2]), "=r"(r[3][3]),
+          "=r"(r[3][4]), "=r"(r[3][5]), "=r"(r[3][6]), "=r"(r[3][7])
+        : "r"(taddr), "r"(taddr + (uint32_t)kNT), "r"(taddr + (uint32_t)(2 * kNT)), "r"(taddr + (uint32_t)(3 * kNT))
         : "memory");
 #pragma unroll
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < 4; ++g)
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[g][i] = __uint_as_float(r[g][i]);
 }
@@ -273,33 +270,20 @@ struct TcSlotSrc {
     __device__ void book(int64_t q, int64_t ran) const { io.slots[io.slot_ids[q]].remaining -= ran; }
 };
 
-// One CTA per tile (s <= 128): the B pieces live in tensor memory next to the
-// accumulators and the MMAs read A from there, so that shared memory serves only
-// the narrow Xs operand (an MMA of 128 x 32 x 16 reads 4 KB of A and 1 KB of Xs;
-// from shared memory the A reads set its pace).  Clusters (s <= 256) keep B in
-// shared memory: their 16 accumulators and B pieces would not fit 512 columns.
-constexpr bool tc_a_in_tmem(int CS) { return CS == 1; }
 constexpr uint32_t tc_pow2(uint32_t n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512))); }
-constexpr uint32_t tc_tmem_cols(int PA, int CS, int NACC)
-{
-    return tc_pow2((uint32_t)(NACC * kNT + (tc_a_in_tmem(CS) ? PA * 8 * CS * 8 : 0)));
-}
 
-// PA pieces of B, PB pieces of Xs, CS CTAs per cluster, NACC accumulators, PK
-// tiles stacked along the rows (PK = 2 for s <= 64: rows 64 h + i hold DOF i of
-// the tile's half h, against the block-diagonal [B 0; 0 B]).
-template <int PA, int PB, int CS, int NACC, int PK, class Src>
+// A cluster of CS CTAs per tile (128 < s <= 256): PA pieces of B, PB pieces of Xs,
+// NACC accumulators; one stage at a time (two accumulator sets of 16 would not fit
+// the 512 TMEM columns).
+template <int PA, int PB, int CS, int NACC, class Src>
 __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
 {
-    static_assert(PK == 1 || CS == 1, "stacked tiles use one CTA");
-    constexpr int NI = kNT * PK;                     // instances per CTA
+    static_assert(CS > 1, "one CTA per tile: rk4_dense_tc_pair_kernel");
+    constexpr int NI = kNT;                          // instances per tile
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
-    constexpr bool ATM = tc_a_in_tmem(CS);           // B pieces in tensor memory (else shared)
-    constexpr int A_BYTES = ATM ? 0 : PA * KC * kAChunk;
-    constexpr int X_BYTES = PB * KC * kXChunk;
+    constexpr int A_BYTES = PA * KC * kAChunk;
     constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
-    constexpr int ACOL = NACC * kNT;                 // first TMEM column of the B pieces
-    constexpr uint32_t TCOLS = tc_tmem_cols(PA, CS, NACC);
+    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(NACC * kNT));
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces (shared-memory form)
     unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
@@ -315,14 +299,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const uint32_t rank = CS > 1 ? cluster_rank() : 0;
+    const uint32_t rank = cluster_rank();
     const int64_t tile = blockIdx.x / CS;
     const int quad = warp & 3;
     const int colgrp = warp >> 2;
     const int row = 32 * quad + lane;                // row of this CTA's block
     const int k = 128 * (int)rank + row;             // K index of the MMA (row of Xs)
-    const int kio = PK == 2 ? (row & 63) : k;        // DOF
-    const int ib = PK == 2 ? (row >> 6) * kNT : 0;   // first instance slot of this row's tile half
+    const int kio = k;                               // DOF
+    const int ib = 0;
     const int s = sys.s;
     const bool live_row = kio < s;
     const int n0 = colgrp * kCPT;                    // first instance column of this thread
@@ -355,38 +339,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    if (CS > 1) cluster_sync();   // the peer's shared memory is initialised before any remote write
+    cluster_sync();               // the peer's shared memory is initialised before any remote write
 
     // Cluster-wide agreement on a local outcome: a failing thread flags its own CTA and
     // the peer, then every thread passes the same barrier and reads the same flags.
     auto agree = [&](bool mine) -> bool {
         if (!mine) {
             atomicExch(&abort_flag[0], 1);
-            if (CS > 1) {
-                const uint32_t peer = mapa(smem_u32(&abort_flag[1]), rank ^ 1u);
-                asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
-            }
+            const uint32_t peer = mapa(smem_u32(&abort_flag[1]), rank ^ 1u);
+            asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer), "r"(1) : "memory");
         }
-        if (CS > 1) cluster_sync(); else __syncthreads();
+        cluster_sync();
         return abort_flag[0] == 0 && abort_flag[1] == 0;
     };
     bool ok = true;
-    if constexpr (ATM) {
-        // Row `row` of each 16-wide chunk of each piece into this warp's TMEM lanes:
-        // the chunk's two 16-byte core-matrix rows (K 0-7, K 8-15) are its 8 columns.
-        const unsigned char* img = (const unsigned char*)sys.Bbf;
-        const uint32_t roff = (uint32_t)((row / 8) * 256 + (row % 8) * 16);
-        for (int idx = colgrp; idx < PA * KC; idx += 4) {
-            const unsigned char* chunk = img + (size_t)idx * kAChunk;   // piece idx / KC, chunk idx % KC
-            const uint4 lo = *(const uint4*)(chunk + roff);
-            const uint4 hi = *(const uint4*)(chunk + roff + 128);
-            tmem_st8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(ACOL + idx * 8), lo, hi);
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = agree(true);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    } else {
+    {
         if (tid == 0) {
             const unsigned char* src = (const unsigned char*)sys.Bbf + (size_t)rank * kBPieces * KC * kAChunk;
             mbar_expect_tx(&bar_load, A_BYTES);
@@ -421,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
     uint32_t xdst[CS];
 #pragma unroll
-    for (int c = 0; c < CS; ++c) xdst[c] = CS > 1 ? mapa(smem_u32(sX) + xoff, (uint32_t)c) : smem_u32(sX) + xoff;
+    for (int c = 0; c < CS; ++c) xdst[c] = mapa(smem_u32(sX) + xoff, (uint32_t)c);
 
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
@@ -431,7 +398,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const uint64_t bdesc0 = smem_desc(smem_u32(sX), 512, 128);
     const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
     uint32_t phase = 0;
-    bool prev_done = true;                           // one CTA: the last wait not yet agreed on
 
     // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
     auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
@@ -452,20 +418,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
                 for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
             }
         }
+        // the Xs stores (this CTA's and the peer's) visible to the tensor cores (the async proxy)
         asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        // One CTA: this barrier also settles the previous stage's wait (a thread
-        // past its wait knows the MMAs that read Xs and wrote TMEM are complete,
-        // and every thread reaches here after its TMEM loads).  Clusters keep a
-        // barrier at the end of the stage: the peer writes into this CTA's Xs.
-        bool go = true;
-        if (CS > 1) cluster_sync(); else go = agree(prev_done);
+        cluster_sync();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!go) {
-#pragma unroll
-            for (int j = 0; j < kCPT; ++j) a[j] = 0.f;
-            return false;
-        }
         if (tid == 0 && !sys.stall_mma) {
             uint32_t started = 0;                    // accumulators already written this stage
 #pragma unroll
@@ -473,23 +430,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
                 constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
                 const int ia = prod_a(TBL, pr);
                 const int ib = prod_b(TBL, pr);
-                // descriptor address fields count 16-byte units; clusters (16 chunks) unroll
-                // by 4 only: fully unrolled, the offsets held in registers spill
+                // descriptor address fields count 16-byte units; 16 chunks unroll by 4
+                // only: fully unrolled, the offsets held in registers spill
                 uint64_t bd = bdesc0 + (uint64_t)((ib * KC * kXChunk) >> 4);
                 uint64_t ad = adesc0 + (uint64_t)((ia * KC * kAChunk) >> 4);
-                uint32_t at = tmem + (uint32_t)(ACOL + ia * KC * 8);
-#pragma unroll(CS == 1 ? KC : 4)
+#pragma unroll 4
                 for (int c = 0; c < KC; ++c) {
                     const int slot = c % NACC;
-                    if constexpr (ATM) {
-                        mma_bf16_ta(tmem + (uint32_t)(slot * kNT), at, bd, idesc, (started >> slot) & 1u);
-                    } else {
-                        mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
-                    }
+                    mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
                     started |= 1u << slot;
                     bd += kXChunk >> 4;
                     ad += kAChunk >> 4;
-                    at += 8;
                 }
             }
             mma_commit(&bar_mma);
@@ -503,15 +454,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             if constexpr (NACC == 1) {
                 tmem_ld8(taddr, acc);
             } else {
-                static_assert(NACC % 2 == 0, "accumulators are read two at a time");
+                static_assert(NACC % 4 == 0, "accumulators are read four at a time");
 #pragma unroll
-                for (int g2 = 0; g2 < NACC / 2; ++g2) {
-                    float part[2][kCPT];
-                    tmem_ld8_x2(taddr + (uint32_t)(2 * g2 * kNT), part);
+                for (int g4 = 0; g4 < NACC / 4; ++g4) {
+                    float part[4][kCPT];
+                    tmem_ld8_x4(taddr + (uint32_t)(4 * g4 * kNT), part);
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
+                    for (int g = 0; g < 4; ++g) {
 #pragma unroll
-                        for (int j = 0; j < kCPT; ++j) acc[j] = (g2 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
+                        for (int j = 0; j < kCPT; ++j) acc[j] = (g4 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
                     }
                 }
             }
@@ -519,10 +470,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        // clusters: every CTA has its MMA done (so Xs may be rewritten) and agrees on aborts
-        if (CS > 1) return agree(done);
-        prev_done = done;
-        return true;
+        // every CTA has its MMA done (so Xs may be rewritten) and agrees on aborts
+        return agree(done);
     };
 
     const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
@@ -581,7 +530,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             ++ck;
         }
     }
-    if (CS == 1 && ok) ok = agree(prev_done);
     if (live_row) {
 #pragma unroll
         for (int j = 0; j < kCPT; ++j) {
@@ -604,19 +552,339 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
-    if (CS > 1) cluster_sync();   // the peer may still write into this CTA's shared memory until here
+    cluster_sync();               // the peer may still write into this CTA's shared memory until here
 }
 
-template <int PA, int PB, int CS, int NACC, int PK, class Src>
-cudaError_t launch_tc_n(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+// One CTA per tile (s <= 128), stages paired.  For x'' = -B x the RK4 stage
+// displacements are x, x + h/2 v, x + h/2 v2 and x + h v3 with v2 = v + h/2 a1 and
+// v3 = v + h/2 a2: the third needs only the first product and the fourth only the
+// second.  So the products of stages 1 and 2 go to the tensor cores together,
+// each into its own set of accumulators and from its own Xs buffers; the epilogue
+// of stage 1 (which yields stage 3's Xs) runs while stage 2's MMAs execute, and
+// that of stage 2 (stage 4's Xs) while stage 3's do.  The tensor cores then
+// wait only for the step's final update.  Every value is formed by the same
+// operations as in rk4_dense_tc_kernel, so both give the same bits.  B's pieces
+// stay in shared memory: two accumulator sets fill the 512 TMEM columns, and an
+// MMA this narrow costs the same with A from shared memory.
+template <int PA, int PB, int NACC, int PK, class Src>
+__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseSys sys, const Src src)
 {
-    constexpr int KC = 8 * CS;
-    static_assert(tc_tmem_cols(PA, CS, NACC) <= 512, "tensor memory holds 512 columns");
-    const size_t smem = (tc_a_in_tmem(CS) ? 0 : (size_t)PA * KC * kAChunk) + (size_t)PB * KC * kXChunk;
-    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, PK, Src>;
+    constexpr int NI = kNT * PK;                     // instances per CTA
+    constexpr int KC = 8;                            // 16-wide K chunks (K = 128)
+    constexpr int A_BYTES = PA * KC * kAChunk;
+    constexpr int X_BYTES = PB * KC * kXChunk;       // one Xs buffer set
+    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
+    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(2 * NACC * kNT));
+    static_assert(2 * NACC * kNT <= 512, "two accumulator sets fit tensor memory");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                        // B, PA pieces
+    unsigned char* sX = smem + A_BYTES;              // two Xs buffer sets of PB pieces
+    __shared__ __align__(8) uint64_t bar_load;
+    __shared__ __align__(8) uint64_t bar_mma[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float sh_h[NI][4];                    // h, h/2, h/6 hi, h/6 lo of each instance
+    __shared__ long long sh_steps[NI];               // steps of each instance in this launch
+    __shared__ long long sh_max_steps;
+    __shared__ int sh_bad[NI];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int64_t tile = blockIdx.x;
+    const int quad = warp & 3;
+    const int colgrp = warp >> 2;
+    const int row = 32 * quad + lane;                // row of the 128-row block = K index of the MMA
+    const int kio = PK == 2 ? (row & 63) : row;      // DOF
+    const int ib = PK == 2 ? (row >> 6) * kNT : 0;   // first instance slot of this row's tile half
+    const int s = sys.s;
+    const bool live_row = kio < s;
+    const int n0 = colgrp * kCPT;                    // first instance column of this thread
+
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < NI) {
+        const int64_t q = tile * NI + tid;
+        const bool live = q < src.count();
+        const double hd = live ? src.h(q) : 1.0;
+        sh_steps[tid] = live ? (long long)src.steps(q) : 0;
+        sh_bad[tid] = 0;
+        const double h6 = hd / 6.0;
+        sh_h[tid][0] = (float)hd;
+        sh_h[tid][1] = (float)(0.5 * hd);
+        sh_h[tid][2] = (float)h6;
+        sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // agreement on a local outcome: every thread passes the barrier and reads the flag
+    auto agree = [&](bool mine) -> bool {
+        if (!mine) atomicExch(&abort_flag, 1);
+        __syncthreads();
+        return abort_flag == 0;
+    };
+    if (tid == 0) {
+        const unsigned char* img = (const unsigned char*)sys.Bbf;
+        mbar_expect_tx(&bar_load, A_BYTES);
+        for (int off = 0; off < A_BYTES; off += 16384) {
+            const int n = A_BYTES - off < 16384 ? A_BYTES - off : 16384;
+            bulk_g2s(sA + off, img + off, (uint32_t)n, &bar_load);
+        }
+    }
+    bool ok = agree(mbar_wait(&bar_load, 0));
+
+    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+#pragma unroll
+    for (int j = 0; j < kCPT; ++j) {
+        const int64_t q = tile * NI + ib + n0 + j;
+        if (live_row && q < src.count()) {
+            src.load(q, kio, x[j], v[j], cx[j], cv[j]);
+        } else {
+            x[j] = v[j] = cx[j] = cv[j] = 0.f;
+        }
+    }
+    if (tid == 0) {
+        long long m = 0;
+        for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+        sh_max_steps = m;
+    }
+    __syncthreads();
+
+    const int kc = row / 16, kk = row % 16;
+    const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
+    const uint32_t xdst = smem_u32(sX) + xoff;      // this thread's cells in buffer set 0
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t tlane = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
+    const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
+    uint32_t phase[2] = {0u, 0u};
+    bool inflight[2] = {false, false};               // a commit not yet waited for (same in every thread)
+
+    // Xs pieces of xs into buffer set b
+    auto publish = [&](int b, const float (&xs)[kCPT]) {
+        float r[kCPT];
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) r[j] = xs[j];
+#pragma unroll
+        for (int p = 0; p < PB; ++p) {
+            uint4 w;
+            w.x = pack_bf16(r[0], r[1]);
+            w.y = pack_bf16(r[2], r[3]);
+            w.z = pack_bf16(r[4], r[5]);
+            w.w = pack_bf16(r[6], r[7]);
+            st_cluster_v4(xdst + (uint32_t)(b * X_BYTES + p * KC * kXChunk), w);
+            if (p + 1 < PB) {
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
+            }
+        }
+    };
+    // every thread's Xs stores visible to the tensor cores and its TMEM loads done; agree
+    auto sync = [&](bool mine) -> bool {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        const bool go = agree(mine);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return go;
+    };
+    // thread 0: the stage's products from buffer set b into accumulator set b
+    auto issue = [&](int b) {
+        if (tid == 0 && !sys.stall_mma) {
+            uint32_t started = 0;
+            const uint64_t bdesc0 = smem_desc(smem_u32(sX + b * X_BYTES), 512, 128);
+            const uint32_t dcol = tmem + (uint32_t)(b * NACC * kNT);
+#pragma unroll
+            for (int pr = 0; pr < NPROD; ++pr) {
+                constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
+                const int ia = prod_a(TBL, pr);
+                const int ibx = prod_b(TBL, pr);
+                uint64_t bd = bdesc0 + (uint64_t)((ibx * KC * kXChunk) >> 4);
+                uint64_t ad = adesc0 + (uint64_t)((ia * KC * kAChunk) >> 4);
+#pragma unroll
+                for (int c = 0; c < KC; ++c) {
+                    const int slot = c % NACC;
+                    mma_bf16(dcol + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
+                    started |= 1u << slot;
+                    bd += kXChunk >> 4;
+                    ad += kAChunk >> 4;
+                }
+            }
+            mma_commit(&bar_mma[b]);
+        }
+        inflight[b] = !sys.stall_mma;
+    };
+    // wait for accumulator set b and return a = -(B Xs) for this thread's cells
+    auto collect = [&](int b, float (&a)[kCPT]) -> bool {
+        const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma[b], phase[b]));
+        if (done) {
+            phase[b] ^= 1u;
+            inflight[b] = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc[kCPT];
+        if (done) {
+            const uint32_t taddr = tlane + (uint32_t)(b * NACC * kNT);
+            if constexpr (NACC == 1) {
+                tmem_ld8(taddr, acc);
+            } else {
+                static_assert(NACC % 4 == 0, "accumulators are read four at a time");
+#pragma unroll
+                for (int g4 = 0; g4 < NACC / 4; ++g4) {
+                    float part[4][kCPT];
+                    tmem_ld8_x4(taddr + (uint32_t)(4 * g4 * kNT), part);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+#pragma unroll
+                        for (int j = 0; j < kCPT; ++j) acc[j] = (g4 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
+        return done;
+    };
+
+    const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
+    int64_t ck = 0, step = 0;
+    for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
+        for (int64_t it = 0; it < every && ok; ++it, ++step) {
+            float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vm[kCPT];
+            // stages 1 and 2 together: Xs = x and x + h/2 v
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) xs[j] = __fmaf_rn(sh_h[ib + n0 + j][1], v[j], x[j]);
+            publish(0, x);
+            publish(1, xs);
+            if (!(ok = sync(true))) break;
+            issue(0);
+            issue(1);
+            // stage 1 result: a1; stage 3's Xs = x + h/2 v2 with v2 = v + h/2 a1
+            bool good = collect(0, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h2 = sh_h[ib + n0 + j][1];
+                kx[j] = v[j];
+                kv[j] = a[j];
+                vm[j] = __fmaf_rn(h2, a[j], v[j]);     // v2
+                xs[j] = __fmaf_rn(h2, vm[j], x[j]);    // x3
+            }
+            publish(0, xs);
+            if (!(ok = sync(good))) break;
+            issue(0);
+            // stage 2 result: a2; stage 4's Xs = x + h v3 with v3 = v + h/2 a2
+            good = collect(1, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h2 = sh_h[ib + n0 + j][1], h = sh_h[ib + n0 + j][0];
+                kx[j] = __fmaf_rn(2.f, vm[j], kx[j]);
+                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
+                vm[j] = __fmaf_rn(h2, a[j], v[j]);     // v3
+                xs[j] = __fmaf_rn(h, vm[j], x[j]);     // x4
+            }
+            publish(1, xs);
+            if (!(ok = sync(good))) break;
+            issue(1);
+            // stage 3 result: a3; v4 = v + h a3
+            good = collect(0, a);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const float h = sh_h[ib + n0 + j][0];
+                kx[j] = __fmaf_rn(2.f, vm[j], kx[j]);
+                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
+                vm[j] = __fmaf_rn(h, a[j], v[j]);      // v4
+            }
+            // stage 4 result: a4, then the step's update
+            if (good) good = collect(1, a);
+            if (!(ok = agree(good))) break;
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                if (step < sh_steps[ib + n0 + j]) {       // instances past their count hold still
+                    const float h6 = sh_h[ib + n0 + j][2], h6l = sh_h[ib + n0 + j][3];
+                    kx[j] = addr(kx[j], vm[j]);
+                    kv[j] = addr(kv[j], a[j]);
+                    comp_update(x[j], cx[j], kx[j], h6, h6l);
+                    comp_update(v[j], cv[j], kv[j], h6, h6l);
+                }
+            }
+        }
+        if (src.ckpt_every() > 0 && ok) {
+            if (live_row) {
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) {
+                    const int64_t q = tile * NI + ib + n0 + j;
+                    if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                }
+            }
+            ++ck;
+        }
+    }
+    // after a failed wait: wait once more (bounded) for what is still in flight
+    // before the accumulators are freed
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+        if (inflight[b]) (void)mbar_wait(&bar_mma[b], phase[b]);
+    if (live_row) {
+#pragma unroll
+        for (int j = 0; j < kCPT; ++j) {
+            const int64_t q = tile * NI + ib + n0 + j;
+            if (q < src.count()) {
+                src.store(q, kio, x[j], v[j], cx[j], cv[j]);
+                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
+            }
+        }
+    }
+    if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid < NI) {
+        const int64_t q = tile * NI + tid;
+        if (q < src.count()) {
+            if (!ok) src.flag(q, CHO_ETIMEOUT);
+            else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
+            src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
+        }
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+}
+
+template <int PA, int PB, int NACC, int PK, class Src>
+cudaError_t launch_tc_pair(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+{
+    const size_t smem = (size_t)PA * 8 * kAChunk + 2 * (size_t)PB * 8 * kXChunk;
+    auto kern = rk4_dense_tc_pair_kernel<PA, PB, NACC, PK, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n_inst + kNT * PK - 1) / (kNT * PK);
+    if (tiles <= 0) return cudaSuccess;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)tiles, kTcThreads, smem, st>>>(sys, src);
+    return cudaGetLastError();
+}
+
+template <int PA, int PB, int CS, class Src>
+cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
+{
+    constexpr int KC = 8 * CS;
+    constexpr int NACC = PA == 2 ? 1 : KC;           // bf16x3: one accumulator; x5/x6: one per K chunk
+    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (n_inst + kNT - 1) / kNT;
     if (tiles <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(tiles * CS), 1, 1);
@@ -633,32 +901,24 @@ cudaError_t launch_tc_n(const DenseSys& sys, const Src& src, int64_t n_inst, cud
     return cudaLaunchKernelEx(&cfg, kern, sys, src);
 }
 
-// bf16x3 accumulates in one TMEM accumulator, bf16x5/x6 in one per K chunk.
-template <int PA, int PB, int CS, int PK = 1, class Src>
-cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
-{
-    constexpr int NACC = PA == 2 ? 1 : 8 * CS;
-    return launch_tc_n<PA, PB, CS, NACC, PK>(sys, src, n_inst, st);
-}
-
-
 template <class Src>
 cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int prec, cudaStream_t st)
 {
     if (n_inst == 0) return cudaSuccess;
     if (!sys.Bbf || sys.s_tc == 0) return cudaErrorNotSupported;
+    // one CTA per tile (s <= 128): stages paired on two accumulator sets; 2-CTA clusters
+    // (s <= 256): one stage at a time
     const bool two = sys.s_tc == 256, pack = sys.s_tc == 64;
     switch (prec) {
         case CHO_DENSE_BF16X3:
-            if (pack) return launch_tc<2, 2, 1, 2>(sys, src, n_inst, st);
-            return two ? launch_tc<2, 2, 2>(sys, src, n_inst, st) : launch_tc<2, 2, 1>(sys, src, n_inst, st);
+            if (two) return launch_tc<2, 2, 2>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<2, 2, 1, 2>(sys, src, n_inst, st) : launch_tc_pair<2, 2, 1, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X5:
-            if (pack) return launch_tc<3, 2, 1, 2>(sys, src, n_inst, st);
-            return two ? launch_tc<3, 2, 2>(sys, src, n_inst, st) : launch_tc<3, 2, 1>(sys, src, n_inst, st);
+            if (two) return launch_tc<3, 2, 2>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 2, 8, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 2, 8, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
             if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
-            if (pack) return launch_tc<3, 3, 1, 2>(sys, src, n_inst, st);
-            return launch_tc<3, 3, 1>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 3, 8, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 3, 8, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
 }
