@@ -363,6 +363,30 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
         return a.elapsed_time(b) / 1e3
 
     alu_peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+    # eq. 3 alone, the paper's own example: one instance, FP64, h = 1e-4, 1e5 steps (t = 10 s).
+    # Latency bound: one thread runs the step.  The FP64 pipe takes about 64 cycles per warp
+    # instruction whatever the number of active lanes (measured: dependent FMA 64 cycles,
+    # batch throughput one warp instruction per 64 cycles per sub-partition), so a step costs
+    # its FP64 instruction count x 64 cycles: 44 in the stage form, 16 in the polynomial form
+    # (y <- P(hA) y, the same map).
+    cfg = inputs.eq3_single()
+    s_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
+    # x after 1e5 steps from the discrete modal closed form of RK4 for eq. 3 (pinned in the oracle tests)
+    x_exact = np.array([0.5919944669044028, -0.55303750830408224])
+    for k in (0, 1, 10):
+        t = timed(s_, cfg, "fp64", cfg["n_steps"], poly=k)
+        r = cho.cho_integrate_batch(ctx, s_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], "fp64", poly_jump=k)
+        n_ops = 44 if k == 0 else 16 / k
+        res["eq3_single_fp64" + (f"_poly_k{k}" if k else "")] = {
+            "value": 2 * cfg["n_steps"] / t, "unit": UNIT, "ms": 1e3 * t, "ns_per_step": 1e9 * t / cfg["n_steps"],
+            "error_vs_closed_form": float(np.max(np.abs(np.asarray(r["x"])[0] - x_exact)) / np.max(np.abs(x_exact))),
+            "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                         "fp64_instructions_per_step": n_ops,
+                         "bound_ns_per_step": n_ops * 64 / (max_mhz * 1e-3),
+                         "note": "one instance, one thread: FP64 instructions per step x 64 cycles"},
+            "paper_context": "D(1)/D(2) and D(3)/D(4) evaluations of 4.12e-7 / 5.24e-7 s each on a 4-core "
+                             "i5-2400 (Section 4), not a like-for-like measure"}
+    cho.cho_destroy_system(s_)
     # The polynomial form of the headline workload: the same RK4 map, k steps per update
     # y <- y + (P(hA)^k - I) y; its own work is 36 flop per instance-update (16 FMA + 4 adds).
     cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS)

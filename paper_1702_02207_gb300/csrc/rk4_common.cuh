@@ -124,6 +124,53 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ---- mbarriers with transaction counts (distributed shared memory transfers) ------
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbarrier_init_one(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+
+// The barrier's single arrival, expecting `bytes` of transfers for the current phase.
+__device__ __forceinline__ void mbarrier_arm(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Wait for the phase of the given parity; false after about `limit_ns`.
+__device__ __forceinline__ bool mbarrier_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint64_t t0 = global_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 4-byte store into (possibly another CTA's) shared memory that completes 4 bytes on
+// that CTA's mbarrier `bar` (both addresses from mapa).
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+
 // Run f() n times with a 32-bit inner counter (64-bit compares cost extra
 // instructions and a branch every step).
 template <class F>

@@ -74,6 +74,7 @@ struct DenseBatchSrc {
         io.v_out[q * s + i] = (double)v + (double)cv;
     }
     __device__ void finish(int64_t, int64_t, bool) const {}
+    __device__ void timed_out(int64_t) const {}     // reported through the system's error word
     // B^T (FP64) or its FP32 pair of instance q's parameter set
     __device__ const void* bt(const DenseSys& sys, int64_t q) const
     {
@@ -125,6 +126,7 @@ struct DenseSlotSrc {
         io.slots[slot].remaining -= ran;
         if (bad) io.status[slot] = CHO_ENONFINITE;
     }
+    __device__ void timed_out(int64_t q) const { io.status[io.slot_ids[q]] = CHO_ETIMEOUT; }
     // the slot's coefficient block (its parameter set's B^T) or the shared one
     __device__ const void* bt(const DenseSys& sys, int64_t q) const
     {
@@ -476,11 +478,13 @@ __global__ void __launch_bounds__(64) rk4_dense_own_kernel(DenseSys sys, const S
 // columns per thread), the lo piece (stage 1 only) in shared memory.  A stage is:
 // every CTA forms the block partials of its rows (a thread per row and block
 // range), the owner thread of each row adds them in column order, completes the
-// row's stage values and writes its next stage displacement into every CTA's copy
-// of Xs (distributed shared memory, double-buffered), then one cluster barrier.
-// This is the paper's decomposition of one system's RK4 stage over parallel
-// workers with one synchronisation between stages (Section 3), at the scale of a
-// cluster of SMs.  The block partials and their order are those of the other FP32
+// row's stage values and sends its next stage displacement to every CTA's copy of
+// Xs (st.async into distributed shared memory, double-buffered); each CTA waits on
+// its own mbarrier until the stage's s_pad values have arrived.  This is the
+// paper's decomposition of one system's RK4 stage over parallel workers with one
+// synchronisation between stages (Section 3), at the scale of a cluster of SMs.
+// (A cluster barrier per stage, whose release waits for the remote stores to be
+// acknowledged before the barrier itself, cost about 60 % of the warps' time.)  The block partials and their order are those of the other FP32
 // dense kernels, so an instance gets the same bits whichever of them runs it.
 template <int SP, int R, int NTHR, class Src>
 __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_kernel(DenseSys sys, const Src src)
@@ -500,6 +504,7 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
     float* Ph = X + 2 * SP;                         // [R][PLD]: block partials, hi piece
     float* Pl = Ph + (size_t)R * PLD;               // [R][PLD]: block partials, lo piece (stage 1)
     __shared__ int any_bad;
+    __shared__ __align__(8) uint64_t xbar[2];       // Xs buffer b complete (clusters)
 
     const int t = threadIdx.x;
     const int lane = t & 31, w = t >> 5;
@@ -529,9 +534,22 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
     const StepSize<false> hs(src.h(q));
     float x = 0.f, v = 0.f, cx = 0.f, cv = 0.f;
     if (owner && i < s) src.load(q, i, x, v, cx, cv);
-    if (t == 0) any_bad = 0;
-    // the owner's row of Xs (buffer 0); mapa gives its address in each CTA of the cluster
+    if (t == 0) {
+        any_bad = 0;
+        if constexpr (CS > 1) {
+            mbarrier_init_one(&xbar[0]);
+            mbarrier_init_one(&xbar[1]);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbarrier_arm(&xbar[0], 4u * SP);        // each stage brings all s_pad rows of Xs
+            mbarrier_arm(&xbar[1], 4u * SP);
+        }
+    }
+    // the owner's row of Xs (buffer 0) and the buffers' mbarriers; mapa gives their
+    // addresses in each CTA of the cluster
     const uint32_t xloc = (uint32_t)__cvta_generic_to_shared(X) + 4u * (uint32_t)(owner ? i : 0);
+    const uint32_t bloc = (uint32_t)__cvta_generic_to_shared(&xbar[0]);
+    uint32_t xphase[2] = {0u, 0u};
+    bool ok = true;
     // every CTA of the cluster is running and has initialised its shared memory
     if (CS > 1) cluster_sync(); else __syncthreads();
 
@@ -542,12 +560,23 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
             const uint32_t off = (uint32_t)(buf * SP * 4);
             if constexpr (CS > 1) {
 #pragma unroll
-                for (int c = 0; c < CS; ++c) st_cluster_f32(mapa(xloc + off, (uint32_t)c), xs);
+                for (int c = 0; c < CS; ++c)
+                    st_async_f32(mapa(xloc + off, (uint32_t)c), xs, mapa(bloc + 8u * (uint32_t)buf, (uint32_t)c));
             } else {
                 X[buf * SP + i] = xs;
             }
         }
-        if (CS > 1) cluster_sync(); else __syncthreads();
+        if constexpr (CS > 1) {
+            // all rows of this stage's Xs have arrived (bounded wait, agreed by the CTA)
+            ok = __syncthreads_and(mbarrier_wait_bounded(&xbar[buf], xphase[buf], 1000000000ull));
+            if (!ok) return 0.f;
+            xphase[buf] ^= 1u;
+            // the buffer's next use is two stages on; its data can only be sent after
+            // this CTA's next stage values, so arming it here precedes every transfer
+            if (t == 0) mbarrier_arm(&xbar[buf], 4u * SP);
+        } else {
+            __syncthreads();
+        }
         if (active) {
             const float* Xb = X + buf * SP + c0 * kJC;
             const float* lrow = Lo + (size_t)lr * LD + c0 * kJC;
@@ -612,35 +641,39 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
 
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (my_steps > 0 ? my_steps : 1);
     int64_t ck = 0;
-    for (int64_t done = 0; done < my_steps; done += every) {
-        for (int64_t it = 0; it < every; ++it) {
+    for (int64_t done = 0; done < my_steps && ok; done += every) {
+        for (int64_t it = 0; it < every && ok; ++it) {
             float a, xs, kx, kv, vs;
             a = accel(x, true);
             kx = v;
             kv = a;
             xs = fmar(hs.h2, v, x);
             vs = fmar(hs.h2, a, v);
-            a = accel(xs, false);
+            if (ok) a = accel(xs, false);
             kx = fmar(2.f, vs, kx);
             kv = fmar(2.f, a, kv);
             xs = fmar(hs.h2, vs, x);
             vs = fmar(hs.h2, a, v);
-            a = accel(xs, false);
+            if (ok) a = accel(xs, false);
             kx = fmar(2.f, vs, kx);
             kv = fmar(2.f, a, kv);
             xs = fmar(hs.h, vs, x);
             vs = fmar(hs.h, a, v);
-            a = accel(xs, false);
+            if (ok) a = accel(xs, false);
+            if (!ok) break;
             kx = addr(kx, vs);
             kv = addr(kv, a);
             state_update<false>(x, cx, kx, hs);
             state_update<false>(v, cv, kv, hs);
         }
-        if (src.ckpt_every() > 0) {
+        if (src.ckpt_every() > 0 && ok) {
             if (owner && i < s) src.checkpoint(q, ck, i, x, v, cx, cv);
             ++ck;
         }
     }
+    // a wait that gave up: the peers give up on this CTA's values in turn; all meet
+    // at the cluster barrier below, after which no transfer is in flight
+    if (!ok && t == 0 && sys.err) atomicExch(sys.err, 1);
     bool bad = false;
     if (owner && i < s) {
         src.store(q, i, x, v, cx, cv);
@@ -651,7 +684,8 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
         else any_bad = 1;
     }
     if (CS > 1) cluster_sync(); else __syncthreads();
-    if (rank == 0 && t == 0) src.finish(q, my_steps, any_bad != 0);
+    if (!ok && t == 0) src.timed_out(q);
+    if (rank == 0 && t == 0) src.finish(q, ok ? my_steps : 0, any_bad != 0);
 }
 
 // Shapes of the split kernel: s_pad 128 -> one CTA of 256 threads (two per SM),
