@@ -67,6 +67,10 @@ def measured_peaks():
         return {}
 
 
+# kernels of the 2-DOF FP32 variants the tuner chooses among
+KERNEL_OF_VARIANT = {"balanced": "rk4_pair2_balanced", "pair": "rk4_pair2", "lane_group": "rk4_small<2>"}
+
+
 def fp32_alu_peak_tflops(sm_count, mhz):
     """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -162,7 +166,7 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
     return res
 
 
-def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
+def run_serving(cho, inputs, device, n_req, load=0.8, stream_seconds=20.0, chunk_us=2000):
     """Mixed request stream through cho_submit / cho_poll (continuous batching).
 
     Requests follow the mixed-load recipe of request_stream: Poisson arrivals, s
@@ -170,10 +174,12 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
     log-uniform 1e3..1e5 steps, three priority classes 20/30/50 %, FP32 + Kahan.
     A saturated burst of n_req // 10 requests first measures the service rate; the
     stream then arrives at `load` times that rate.  Returns throughput and the
-    p50/p99 submit-to-done latency per class.
+    p50/p99 submit-to-done latency per class.  The engine runs on its own context whose
+    kernel groups tune their chunk length to about `chunk_us` of device time each.
     """
     import time as _t
 
+    ctx = cho.cho_init(device, chunk_us=chunk_us)
     st = inputs.request_stream(n_req=n_req, rate_per_s=1.0)
     systems = {}
 
@@ -250,7 +256,9 @@ def run_serving(cho, inputs, ctx, n_req, load=0.8, stream_seconds=20.0):
     log(f"serving: stream took {t_run:.1f} s")
     for sys_, _ in systems.values():
         cho.cho_destroy_system(sys_)
+    cho.cho_shutdown(ctx)
     out = {"requests": int(n_cal + n_stream), "burst_requests": int(n_cal), "saturated_dof_steps_per_s": rate_dof,
+           "chunking": f"each kernel group's chunk length tuned to about {chunk_us} us of device time",
            "offered_load": load, "arrival_rate_per_s": lam,
            "stream_dof_steps_per_s": work[idx].sum() / t_run, "stream_seconds": t_run,
            "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
@@ -536,6 +544,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # choose among the same-bits kernels of this shape (off the timed region)
+    tune = cho.cho_autotune(ctx, sys_, N_INST, "fp32_kahan")
+    log(f"autotune: {tune['chosen']} of {[(n, round(us, 5)) for n, _, us in tune['variants']]} us per step")
 
     def step(prec):
         cho.cho_integrate_batch(ctx, sys_, x0, v0, h, N_STEPS, prec, out=out, stream=stream)
@@ -621,16 +632,19 @@ def main():
                        "prec": "fp32_kahan", "l2": "flushed between timed iterations (512 MiB write)",
                        "parallelism": f"instances sharded over {world} GPU(s)"},
             "error_vs_oracle": err32,
-            "roofline": {"bound": "alu", "kernel": "rk4_pair2_balanced (2-DOF, FP32 + compensated state)", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": KERNEL_OF_VARIANT.get(tune["chosen"], tune["chosen"]) +
+                         " (2-DOF, FP32 + compensated state)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         # DRAM bytes per launch (read + write) measured by an ncu capture of this
-                         # kernel on this workload
-                         "traffic": 4792576,
+                         # DRAM bytes per launch (read + write) measured by an ncu capture of the
+                         # balanced kernel on this workload
+                         "traffic": 4792576 if tune["chosen"] == "balanced" else None,
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
             "clocks": clocks,
             "e2e": {"value": DOF_STEPS / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e},
             "gpu_launches": args.steps,
+            "autotune": {"chosen": tune["chosen"], "sample_steps": tune["sample_steps"],
+                         "us_per_step": {n: us for n, _, us in tune["variants"]}},
         }
         if not args.no_extras:
             # FP64 mode of the same workload (fewer steps: FP64 runs far below FP32 on this part)
@@ -660,7 +674,7 @@ def main():
             log("other configurations")
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks)
             if args.serve_requests > 0:
-                line["serving"] = run_serving(cho, inputs, ctx, args.serve_requests)
+                line["serving"] = run_serving(cho, inputs, local_rank, args.serve_requests)
                 log("periodic mode")
                 line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:

@@ -100,7 +100,11 @@ typedef struct cho_config {
     int64_t budget_bytes;   /* serving: device bytes for resident request state (default 40 GiB) */
     int32_t chunk_steps;    /* serving: RK4 steps per chunk between scheduling points (default 1000) */
     int32_t max_slots;      /* serving: maximum resident requests (default 1 << 20)       */
-    int32_t reserved[4];
+    int32_t chunk_us;       /* serving: > 0 tunes each kernel group's chunk length while it runs so
+                               that a chunk takes about this many microseconds of device time
+                               (chunk_steps is the first guess); 0 keeps chunk_steps.  Results do
+                               not depend on the chunk length. */
+    int32_t reserved[3];
 } cho_config;
 
 /* Description of one system kind and size, with n_sys parameter sets.
@@ -276,6 +280,43 @@ cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_desc* batch
  * mem selects host or device pointers as in cho_batch_desc.  Errors: CHO_EINVAL, CHO_ECUDA. */
 cho_status cho_energy(cho_ctx* ctx, cho_system sys, const double* x, const double* v,
                       int64_t n_inst, int64_t n_per, int32_t mem, double* E, void* stream);
+
+/* ---- autotuning of the batch kernels ------------------------------------------------- */
+
+/* For some batch shapes several kernels compute the same bits: FP32 TWO_DOF systems
+ * (balanced schedule, pair form, lane-group form), CHAIN systems (1, 2, 4 or 8 DOFs per
+ * thread), FP32 DENSE systems (one instance per CTA or cluster of CTAs, or the streaming
+ * kernel).  cho_autotune runs each candidate for the shape (system, n_inst, prec,
+ * poly_jump) on seeded inputs on the context's device, keeps those whose final states
+ * equal the first candidate's bit for bit, times them with CUDA events (best of three
+ * runs of about 3 ms after a warm-up) and records the fastest in the context's tune
+ * table.  Later cho_integrate_batch calls of the same shape use it; the instance count
+ * is matched by floor(log2(n_inst)).  Shapes with a single kernel report one variant
+ * and record nothing.  A system with one parameter set per instance needs n_inst equal
+ * to its set count.  Synchronous; allocates 7 n_inst s doubles of device memory for the
+ * call.  Errors: CHO_EINVAL (as cho_integrate_batch for the shape), CHO_ENOMEM, CHO_ECUDA. */
+typedef struct cho_tune_result {
+    int32_t n_variants;         /* candidates timed (1: the shape has a single kernel)           */
+    int32_t chosen;             /* index of the fastest eligible candidate                        */
+    int32_t code[8];            /* variant code as stored in the tune table (-1: default kernel)  */
+    double us_per_step[8];      /* device time per RK4 step of the whole batch; < 0: its bits
+                                   differed from the first candidate's, so it was not eligible  */
+    char name[8][24];           /* candidate names                                                */
+    int64_t sample_steps;       /* RK4 steps per timed run                                        */
+} cho_tune_result;
+
+cho_status cho_autotune(cho_ctx* ctx, cho_system sys, int64_t n_inst, int32_t prec, int32_t poly_jump,
+                        cho_tune_result* out);
+
+/* The variant code recorded for a shape (-1: none; the default rules apply). */
+cho_status cho_tune_query(cho_ctx* ctx, cho_system sys, int64_t n_inst, int32_t prec, int32_t poly_jump,
+                          int32_t* code);
+
+/* Write the tune table to a text file ("cho-tune 1", then one tab-separated entry per line
+ * led by the device name), or read one and add the entries recorded for this context's
+ * device (n_loaded may be NULL).  Errors: CHO_EINVAL (cannot open, or not a tune file). */
+cho_status cho_tune_save(cho_ctx* ctx, const char* path);
+cho_status cho_tune_load(cho_ctx* ctx, const char* path, int32_t* n_loaded);
 
 /* ---- serving: continuous batching of single-instance requests --------------------- */
 

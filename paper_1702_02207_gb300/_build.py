@@ -21,6 +21,7 @@ SOURCES = [
     "api.cpp",
     "linalg.cpp",
     "serve.cpp",
+    "tune.cpp",
     "rk4_small.cu",
     "rk4_chain.cu",
     "rk4_chain_ext.cu",

@@ -40,6 +40,7 @@ EXPORTED = [
     "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
+    "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -47,7 +48,13 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class cho_config(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("chunk_steps", ctypes.c_int32),
-                ("max_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("max_slots", ctypes.c_int32), ("chunk_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class cho_tune_result(ctypes.Structure):
+    _fields_ = [("n_variants", ctypes.c_int32), ("chosen", ctypes.c_int32), ("code", ctypes.c_int32 * 8),
+                ("us_per_step", ctypes.c_double * 8), ("name", (ctypes.c_char * 24) * 8),
+                ("sample_steps", ctypes.c_int64)]
 
 
 class cho_system_desc(ctypes.Structure):
@@ -117,6 +124,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_poll": ([V, ctypes.c_uint64, ctypes.POINTER(cho_result)], I32),
             "cho_cancel": ([V, ctypes.c_uint64], I32),
             "cho_serve_stats": ([V] + [ctypes.POINTER(I64)] * 4, I32),
+            "cho_autotune": ([V, V, I64, I32, I32, ctypes.POINTER(cho_tune_result)], I32),
+            "cho_tune_query": ([V, V, I64, I32, I32, ctypes.POINTER(I32)], I32),
+            "cho_tune_save": ([V, ctypes.c_char_p], I32),
+            "cho_tune_load": ([V, ctypes.c_char_p, ctypes.POINTER(I32)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -174,10 +185,10 @@ def _stream_ptr(stream):
 
 # ---- context -----------------------------------------------------------------------
 
-def cho_init(device=0, budget_bytes=0, chunk_steps=0, max_slots=0):
+def cho_init(device=0, budget_bytes=0, chunk_steps=0, max_slots=0, chunk_us=0):
     lib = load()
     ctx = ctypes.c_void_p()
-    cfg = cho_config(int(budget_bytes), int(chunk_steps), int(max_slots))
+    cfg = cho_config(int(budget_bytes), int(chunk_steps), int(max_slots), int(chunk_us))
     _check(lib.cho_init(ctypes.byref(ctx), int(device), ctypes.byref(cfg)))
     return ctx
 
@@ -402,3 +413,36 @@ def cho_serve_stats(ctx):
     vals = [ctypes.c_int64() for _ in range(4)]
     _check(load().cho_serve_stats(ctx, *[ctypes.byref(v) for v in vals]))
     return dict(zip(("queued", "resident", "completed", "resident_bytes"), (v.value for v in vals)))
+
+
+# ---- autotuning ------------------------------------------------------------------------
+
+def cho_autotune(ctx, system, n_inst, prec=CHO_FP32_KAHAN, poly_jump=0):
+    """Time the same-bits kernel variants of a batch shape and record the fastest (see
+    include/cho.h).  Returns a dict: variants [(name, code, us_per_step)], chosen (name),
+    code and sample_steps."""
+    r = cho_tune_result()
+    _check(load().cho_autotune(ctx, system, int(n_inst), int(PRECS.get(prec, prec)), int(poly_jump),
+                               ctypes.byref(r)))
+    variants = [(bytes(r.name[k]).split(b"\0")[0].decode(), int(r.code[k]), float(r.us_per_step[k]))
+                for k in range(r.n_variants)]
+    return {"variants": variants, "chosen": variants[r.chosen][0], "code": variants[r.chosen][1],
+            "sample_steps": int(r.sample_steps)}
+
+
+def cho_tune_query(ctx, system, n_inst, prec=CHO_FP32_KAHAN, poly_jump=0):
+    """The variant code recorded for a batch shape, or -1."""
+    code = ctypes.c_int32()
+    _check(load().cho_tune_query(ctx, system, int(n_inst), int(PRECS.get(prec, prec)), int(poly_jump),
+                                 ctypes.byref(code)))
+    return code.value
+
+
+def cho_tune_save(ctx, path):
+    _check(load().cho_tune_save(ctx, os.fsencode(path)))
+
+
+def cho_tune_load(ctx, path):
+    n = ctypes.c_int32()
+    _check(load().cho_tune_load(ctx, os.fsencode(path), ctypes.byref(n)))
+    return n.value

@@ -164,6 +164,7 @@ extern "C" cho_status cho_init(cho_ctx** out, int device, const cho_config* cfg)
         if (cfg->budget_bytes > 0) c->cfg.budget_bytes = cfg->budget_bytes;
         if (cfg->chunk_steps > 0) c->cfg.chunk_steps = cfg->chunk_steps;
         if (cfg->max_slots > 0) c->cfg.max_slots = cfg->max_slots;
+        if (cfg->chunk_us > 0) c->cfg.chunk_us = cfg->chunk_us;
     }
     {
         DeviceGuard g(device);
@@ -178,6 +179,7 @@ extern "C" cho_status cho_init(cho_ctx** out, int device, const cho_config* cfg)
             return fail(CHO_ECUDA, "cho_init: cudaGetDeviceProperties: %s", cudaGetErrorString(e));
         }
         c->sm_count = prop.multiProcessorCount;
+        std::snprintf(c->device_name, sizeof(c->device_name), "%s", prop.name);
         c->cc_major = prop.major;
         c->cc_minor = prop.minor;
     }
@@ -664,10 +666,47 @@ static cho_status dense_poly_blocks(cho_system_impl* sys, double h, int k, bool 
     return CHO_OK;
 }
 
+bool tune_key(const cho_system_impl* sys, int64_t n_inst, int32_t prec, int32_t poly_jump, TuneKey* key)
+{
+    if (sys->damped() || sys->forced() || n_inst <= 0) return false;
+    int bucket = 0;
+    while (bucket < 62 && ((int64_t)1 << (bucket + 1)) <= n_inst) ++bucket;
+    const int32_t per = sys->n_sys != 1 ? 1 : 0;
+    const bool fp32 = prec == CHO_FP32_KAHAN || prec == CHO_DENSE_FP32_SIMT;
+    if (sys->path == PATH_SMALL && sys->s == 2 && prec == CHO_FP32_KAHAN) {
+        *key = {PATH_SMALL, sys->S, prec, per, bucket + (poly_jump > 0 ? 64 : 0)};
+        return true;
+    }
+    if (sys->path == PATH_CHAIN && poly_jump == 0) {
+        *key = {PATH_CHAIN, sys->s, prec, per, bucket};
+        return true;
+    }
+    if (sys->path == PATH_DENSE && fp32 && poly_jump == 0) {
+        *key = {PATH_DENSE, sys->s_pad, prec, per, bucket};
+        return true;
+    }
+    return false;
+}
+
 // Run one batch whose arrays are all device pointers.
-static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st)
+cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st, const KernelChoice* force)
 {
     cho_system_impl* sys = b->system;
+    KernelChoice kc;
+    if (force) {
+        kc = *force;
+    } else {
+        TuneKey key;
+        if (tune_key(sys, b->n_inst, b->prec, b->poly_jump, &key)) {
+            std::lock_guard<std::mutex> lk(ctx->tune_mu);
+            auto it = ctx->tune.find(key);
+            if (it != ctx->tune.end()) {
+                if (sys->path == PATH_SMALL) kc.small_variant = it->second;
+                if (sys->path == PATH_CHAIN) kc.chain_dofs = it->second;
+                if (sys->path == PATH_DENSE) kc.dense_few = it->second;
+            }
+        }
+    }
     BatchIO io{};
     io.n_inst = b->n_inst;
     io.x0 = b->x0;
@@ -691,9 +730,11 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
         e = launch_rk4_chain_ext(cs, io, fp64, st);
     } else if (sys->path == PATH_SMALL) {
         SmallSys ss{sys->s, sys->S, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32, sys->d_err};
+        ss.variant = kc.small_variant;
         e = launch_rk4_small(ss, io, fp64, st);
     } else if (sys->path == PATH_CHAIN) {
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
+        cs.dofs_per_thread = kc.chain_dofs;
         e = launch_rk4_chain(cs, io, fp64, st);
     } else if (b->poly_jump > 0) {
         // polynomial form of a shared dense system: one h for the whole batch
@@ -712,6 +753,7 @@ static cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
     } else {
         DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
                     sys->n_sys != 1 ? 1 : 0};
+        ds.few = kc.dense_few;
         e = launch_rk4_dense(ds, io, b->prec, st);
     }
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: kernel launch: %s", cudaGetErrorString(e));
@@ -821,6 +863,11 @@ static cho_status run_plain_device(cho_ctx* ctx, const cho_batch_desc* b, cudaSt
 
 }  // namespace cho
 
+cho_status cho::validate_batch(const cho_batch_desc* b, const char* who, cudaStream_t st)
+{
+    return check_batch(b, who, false, st);
+}
+
 extern "C" cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* b, void* stream)
 {
     clear_error();
@@ -830,8 +877,8 @@ extern "C" cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* b,
     cudaStream_t st = (cudaStream_t)stream;
     cho_status rc = check_batch(b, "cho_integrate_batch", false, st);
     if (rc != CHO_OK) return rc;
-    if (b->mem == CHO_MEM_DEVICE) return run_device_batch(ctx, b, st);
-    return run_staged(ctx, b, st, [&](const cho_batch_desc* d) { return run_device_batch(ctx, d, st); });
+    if (b->mem == CHO_MEM_DEVICE) return run_device_batch(ctx, b, st, nullptr);
+    return run_staged(ctx, b, st, [&](const cho_batch_desc* d) { return run_device_batch(ctx, d, st, nullptr); });
 }
 
 extern "C" cho_status cho_integrate_plain(cho_ctx* ctx, const cho_batch_desc* b, void* stream)

@@ -97,6 +97,7 @@ struct SmallSys {
     const double* B64;      // [n_sys][S][S]
     const float* B32;       // [n_sys][2][S][S] (hi then lo)
     int* err;               // device error word: set when a bounded wait gives up (may be null)
+    int32_t variant = -1;   // FP32 s = 2 kernel: -1 default, 0 balanced, 2 lane-group form, 3 pair form
 };
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
@@ -110,9 +111,13 @@ struct ChainSys {
     int32_t per_inst_sys;
     const double* C64;      // [n_sys][2][s]
     const float* C32;       // [n_sys][4][s]
+    int32_t dofs_per_thread = 0;   // 1, 2, 4 or 8 (chain_dofs_valid); 0: chain_dofs_per_thread(s)
 };
 
 int chain_dofs_per_thread(int s);
+// Whether P DOFs per thread fit the chain kernel for s DOFs (P < 8: at most 256
+// threads; P = 8: at most 1024).
+bool chain_dofs_valid(int s, int P);
 cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
 
 // ---- rk4_chain_ext: the chain with dashpots and harmonic forcing -------------------
@@ -142,7 +147,11 @@ struct DenseSys {
     int* err;               // device error word of the tensor-core kernel (bounded waits)
     int32_t stall_mma;      // test hook: issue no MMA, so the bounded wait on it runs out
     int32_t per_inst;       // 1: one (M, K) per instance, B64/B32 hold n_sys matrices back to back
+    int32_t few = -1;       // FP32: 1 one instance per CTA or cluster, 0 the streaming kernel, -1 by count
 };
+
+// Whether the FP32 one-instance-per-CTA-or-cluster kernels can run this system here.
+bool dense_few_capable(const DenseSys& sys);
 
 // Test hook for the bounded device waits: CHO_TEST_STALL_MMA=1 in the environment makes
 // the tensor-core kernel skip its MMAs, so its wait on their completion gives up after

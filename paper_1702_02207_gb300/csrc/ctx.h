@@ -4,7 +4,9 @@
 #include "../../include/cho.h"
 #include "cho_internal.h"
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <set>
 #include <vector>
@@ -85,10 +87,25 @@ struct cho_system_impl {
     bool forced() const { return !h_famp.empty(); }
 };
 
+namespace cho {
+// Kernel variants that give the same bits for a batch, chosen by the tuner or forced.
+struct KernelChoice {
+    int32_t small_variant = -1;     // SmallSys::variant
+    int32_t chain_dofs = 0;         // ChainSys::dofs_per_thread
+    int32_t dense_few = -1;         // DenseSys::few
+};
+// Tune table key: kernel family, its size (S, s or s_pad), precision, one (M, K) per
+// instance, floor(log2(n_inst)).
+using TuneKey = std::array<int32_t, 5>;
+}  // namespace cho
+
 struct cho_ctx {
     int device = 0;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
+    char device_name[256] = {};
+    std::mutex tune_mu;                 // guards `tune`
+    std::map<cho::TuneKey, int32_t> tune;   // chosen variant per batch shape (tuner's code)
     cho_config cfg{};
     std::mutex mu;                      // guards `systems`
     std::set<cho_system_impl*> systems;
@@ -107,4 +124,10 @@ cudaError_t build_dense_device(cho_system_impl* sys, const double* B);
 cudaError_t build_dense_tc_device(cho_system_impl* sys, const double* B);
 // Stops the serving thread of a context, if any.
 void serve_stop(cho_ctx* ctx);
+// The argument checks of cho_integrate_batch.
+cho_status validate_batch(const cho_batch_desc* b, const char* who, cudaStream_t st);
+// One batch with device arrays (validated by the caller); `force` overrides the tune table.
+cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st, const KernelChoice* force);
+// Tune key of a batch shape; false for shapes with a single variant.
+bool tune_key(const cho_system_impl* sys, int64_t n_inst, int32_t prec, int32_t poly_jump, TuneKey* key);
 }  // namespace cho

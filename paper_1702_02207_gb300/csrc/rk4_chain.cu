@@ -296,9 +296,10 @@ cudaError_t launch_p(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
 }
 
 template <bool F64, class Src>
-cudaError_t launch_any(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
+cudaError_t launch_any(const Src& src, int64_t n_inst, int s_max, cudaStream_t st, int P = 0)
 {
-    switch (chain_dofs_per_thread(s_max)) {
+    if (P == 0 || !chain_dofs_valid(s_max, P)) P = chain_dofs_per_thread(s_max);
+    switch (P) {
         case 1: return launch_p<1, F64>(src, n_inst, s_max, st);
         case 2: return launch_p<2, F64>(src, n_inst, s_max, st);
         case 4: return launch_p<4, F64>(src, n_inst, s_max, st);
@@ -322,14 +323,21 @@ int chain_dofs_per_thread(int s)
     return 8;
 }
 
+bool chain_dofs_valid(int s, int P)
+{
+    if (P != 1 && P != 2 && P != 4 && P != 8) return false;
+    const int threads = (((s + P - 1) / P + 31) / 32) * 32;
+    return threads <= (P == 8 ? kChainMaxThreads : 256);
+}
+
 cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
     if (fp64) {
         ChainBatchSrc<true> s{sys, io};
-        return launch_any<true>(s, io.n_inst, sys.s, st);
+        return launch_any<true>(s, io.n_inst, sys.s, st, sys.dofs_per_thread);
     }
     ChainBatchSrc<false> s{sys, io};
-    return launch_any<false>(s, io.n_inst, sys.s, st);
+    return launch_any<false>(s, io.n_inst, sys.s, st, sys.dofs_per_thread);
 }
 
 cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaStream_t st)

@@ -831,7 +831,8 @@ cudaError_t dispatch_simt(const DenseSys& sys, bool fp64, int64_t n_inst, cudaSt
             case 512: cap = split_capacity<512, SrcT<false>>(); break;
             default: return cudaErrorInvalidValue;
         }
-        if (cap > 0 && (sys.per_inst || n_inst <= 8 * (int64_t)cap)) {
+        const bool few = sys.few == 1 || (sys.few < 0 && (sys.per_inst || n_inst <= 8 * (int64_t)cap));
+        if (cap > 0 && few) {
             switch (sys.s_pad) {
                 case 64: return launch_own(sys, src, n_inst, st);
                 case 128: return launch_split<128>(sys, src, n_inst, st);
@@ -1041,6 +1042,17 @@ cudaError_t launch_poly(const DenseSys& sys, const void* E, const BatchIO& io, c
 }
 
 }  // namespace
+
+bool dense_few_capable(const DenseSys& sys)
+{
+    switch (sys.s_pad) {
+        case 64: return true;
+        case 128: return split_capacity<128, DenseBatchSrc<false>>() > 0;
+        case 256: return split_capacity<256, DenseBatchSrc<false>>() > 0;
+        case 512: return split_capacity<512, DenseBatchSrc<false>>() > 0;
+        default: return false;
+    }
+}
 
 // s_pad: next power of two >= max(s, 64); the SIMT kernels cover s_pad <= 512.
 int dense_pad(int s)

@@ -854,12 +854,13 @@ rk4_pair2_balanced_kernel(const SmallSys sys, const BatchIO io, const BalanceSch
 // thread on the balanced schedule), "pair" (two instances per thread, one warp
 // per 64 instances) or "generic" (rk4_small_kernel<2>); all give the same bits.
 // CHO_TWO_DOF_KERNEL overrides the default.
-int two_dof_variant()
+// FP32 s = 2 kernel forced by CHO_TWO_DOF_KERNEL (test hook: "generic", "pair"), else -1.
+int two_dof_env_variant()
 {
-    static int v = -1;
-    if (v < 0) {
+    static int v = -2;
+    if (v == -2) {
         const char* e = std::getenv("CHO_TWO_DOF_KERNEL");
-        v = 0;
+        v = -1;
         if (e && std::strcmp(e, "generic") == 0) v = 2;
         if (e && std::strcmp(e, "pair") == 0) v = 3;
     }
@@ -988,14 +989,15 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
                 rk4_poly64_kernel<<<(unsigned)blocks, 64, 0, st>>>(sys, pio);
                 e = cudaGetLastError();
             } else {
-                e = two_dof_variant() == 3 ? launch_pair2<Pair2Poly>(sys, pio, st)
-                                           : launch_pair2_balanced<Pair2Poly>(sys, pio, st);
+                const int pv = two_dof_env_variant() >= 0 ? two_dof_env_variant() : sys.variant;
+                e = pv == 3 ? launch_pair2<Pair2Poly>(sys, pio, st) : launch_pair2_balanced<Pair2Poly>(sys, pio, st);
             }
         }
         const cudaError_t ef = cudaFreeAsync(buf, st);
         return e != cudaSuccess ? e : ef;
     }
-    const int variant = two_dof_variant();
+    // the test hook, else the caller's (tuned) choice, else the balanced kernel
+    const int variant = two_dof_env_variant() >= 0 ? two_dof_env_variant() : (sys.variant >= 0 ? sys.variant : 0);
     // s = 1 is also padded to S = 2 but keeps the generic layout
     if (sys.s == 2 && !fp64 && variant == 3) return launch_pair2<Pair2>(sys, io, st);
     if (sys.s == 2 && !fp64 && variant == 0) return launch_pair2_balanced<Pair2>(sys, io, st);

@@ -204,6 +204,8 @@ struct Group {
     cudaEvent_t ev = nullptr;
     bool busy = false;
     int64_t chunk = 0;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;   // around the kernel of a launch (chunk tuning only)
+    int64_t max_run = 0;            // most steps a member runs in the launch in flight
     std::vector<Req*> members;      // resident
     std::vector<Req*> incoming;     // admitted, state not uploaded yet
     std::vector<Req*> launched;     // advanced by the launch in flight
@@ -306,6 +308,10 @@ Group* ServeEngine::group_for(Req* r, cudaError_t* e)
     g->chunk = group_chunk(ctx);
     *e = cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking);
     if (*e == cudaSuccess) *e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (*e == cudaSuccess && ctx->cfg.chunk_us > 0) {
+        *e = cudaEventCreate(&g->k0);
+        if (*e == cudaSuccess) *e = cudaEventCreate(&g->k1);
+    }
     if (*e != cudaSuccess) {
         if (g->st) cudaStreamDestroy(g->st);
         delete g;
@@ -392,6 +398,10 @@ cudaError_t ServeEngine::launch(Group* g)
     const int path = std::get<0>(g->key), size = std::get<1>(g->key), prec = std::get<2>(g->key);
     const bool f64 = fp64_prec(prec);
     SlotIO io{(int64_t)n_ids, g->d_ids.ptr(), d_slots.ptr(), d_status.ptr(), L};
+    g->max_run = 0;
+    for (Req* r : g->launched) g->max_run = std::max(g->max_run, std::min(L, r->remaining));
+    if (g->k0) e = cudaEventRecord(g->k0, g->st);
+    if (e != cudaSuccess) return e;
     if (path == PATH_SMALL) {
         e = launch_rk4_small_slots(size, io, f64, g->st);
     } else if (path == PATH_CHAIN) {
@@ -407,6 +417,7 @@ cudaError_t ServeEngine::launch(Group* g)
         else
             e = launch_rk4_dense_slots(ds, io, f64, g->st);
     }
+    if (e == cudaSuccess && g->k1) e = cudaEventRecord(g->k1, g->st);
     if (e == cudaSuccess) e = launch_gather_status(g->d_ids.ptr(), d_status.ptr(), g->d_st.ptr(), (int64_t)n_ids, g->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hst, g->d_st.ptr(), n_ids * sizeof(int32_t), cudaMemcpyDeviceToHost, g->st);
@@ -484,6 +495,15 @@ void ServeEngine::retire(Group* g)
     g->members.erase(it, g->members.end());
     g->launched.clear();
     g->busy = false;
+    // chunk-length tuning: from the kernel's device time per step in this launch, the
+    // chunk that would take chunk_us, moving at most a factor of two per launch
+    float ms = 0.f;
+    if (g->k0 && g->max_run > 0 && cudaEventElapsedTime(&ms, g->k0, g->k1) == cudaSuccess && ms > 0.f) {
+        const double per_step_us = 1e3 * (double)ms / (double)g->max_run;
+        double target = (double)ctx->cfg.chunk_us / per_step_us;
+        target = std::min(std::max(target, 0.5 * (double)L), 2.0 * (double)L);
+        g->chunk = std::min<int64_t>(std::max<int64_t>(std::llround(target), 16), (int64_t)1 << 22);
+    }
 }
 
 void ServeEngine::run()
@@ -632,6 +652,8 @@ void serve_stop(cho_ctx* ctx)
             Group* gr = kv.second;
             cudaStreamSynchronize(gr->st);
             cudaEventDestroy(gr->ev);
+            if (gr->k0) cudaEventDestroy(gr->k0);
+            if (gr->k1) cudaEventDestroy(gr->k1);
             cudaStreamDestroy(gr->st);
             delete gr;
         }

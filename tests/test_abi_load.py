@@ -51,6 +51,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     structs = {
         "cho_config": cho.cho_config, "cho_system_desc": cho.cho_system_desc,
         "cho_batch_desc": cho.cho_batch_desc, "cho_request": cho.cho_request, "cho_result": cho.cho_result,
+        "cho_tune_result": cho.cho_tune_result,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cho.h"', "int main(void) {"]
     for name, cls in structs.items():

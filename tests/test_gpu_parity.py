@@ -896,3 +896,62 @@ def test_tensor_core_wait_gives_up_and_reports(ctx):
         assert rel_err(out["x"][:, None], ref["x"][:, None]).max() < TOL_FP32
     finally:
         cho.cho_destroy_system(sys_)
+
+
+# ---- autotuning among kernels that give the same bits ----------------------------------------
+
+def _device_run(ctx, sys_, cfg, prec, n_steps):
+    import torch
+
+    dev = torch.device("cuda:0")
+    out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=dev),
+                                  torch.as_tensor(cfg["v0"], device=dev), torch.as_tensor(cfg["h"], device=dev),
+                                  n_steps, prec)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("case", ["two_dof", "chain_fp32", "chain_fp64", "dense_fp32"])
+def test_autotune_chooses_among_same_bit_kernels(tmp_path, case):
+    """cho_autotune times every candidate kernel of the shape; all give the bits of the first,
+    the fastest is recorded, later batches of the shape use it (same bits as an untuned
+    context), and the table survives a save / load into another context."""
+    if case == "two_dof":
+        cfg, prec, n_cand = inputs.two_dof_batch(n_inst=4096, n_steps=300), "fp32_kahan", 3
+    elif case.startswith("chain"):
+        cfg = inputs.chain_batch(n_inst=64, s=300, n_steps=200)
+        prec, n_cand = ("fp32_kahan" if case == "chain_fp32" else "fp64"), 3     # 8 (default), 2, 4 DOFs per thread
+    else:
+        cfg, prec, n_cand = inputs.dense_group(s=200, n_inst=12, n_steps=200), "fp32_kahan", 2
+    n_inst = cfg["x0"].shape[0]
+    ctx, ctx2 = cho.cho_init(0), cho.cho_init(0)
+    try:
+        sys1, sys2 = make_system(ctx, cfg), make_system(ctx2, cfg)
+        assert cho.cho_tune_query(ctx, sys1, n_inst, prec) == -1
+        r = cho.cho_autotune(ctx, sys1, n_inst, prec)
+        print(case, r)
+        assert len(r["variants"]) == n_cand
+        times = [us for _, _, us in r["variants"]]
+        assert all(us > 0 for us in times), "a candidate gave different bits"
+        assert r["chosen"] == r["variants"][int(np.argmin(times))][0]
+        assert cho.cho_tune_query(ctx, sys1, n_inst, prec) == r["code"]
+        tuned = _device_run(ctx, sys1, cfg, prec, cfg["n_steps"])
+        default = _device_run(ctx2, sys2, cfg, prec, cfg["n_steps"])
+        assert np.array_equal(tuned["x"], default["x"]) and np.array_equal(tuned["v"], default["v"])
+        path = tmp_path / "tune.txt"
+        cho.cho_tune_save(ctx, str(path))
+        assert cho.cho_tune_load(ctx2, str(path)) >= 1
+        assert cho.cho_tune_query(ctx2, sys2, n_inst, prec) == r["code"]
+        # one kernel only (FP64 dense, or the tensor cores): nothing to choose, nothing recorded
+        if case == "dense_fp32":
+            r64 = cho.cho_autotune(ctx, sys1, n_inst, "fp64")
+            assert len(r64["variants"]) == 1 and cho.cho_tune_query(ctx, sys1, n_inst, "fp64") == -1
+        bad = tmp_path / "bad.txt"
+        bad.write_text("not a tune file\n")
+        with pytest.raises(cho.ChoError):
+            cho.cho_tune_load(ctx2, str(bad))
+        cho.cho_destroy_system(sys1)
+        cho.cho_destroy_system(sys2)
+    finally:
+        cho.cho_shutdown(ctx)
+        cho.cho_shutdown(ctx2)

@@ -170,6 +170,23 @@ def test_same_result_alone_and_in_the_mix_and_any_chunk():
             cho.cho_shutdown(ctx)
 
 
+def test_tuned_chunk_length_keeps_results():
+    """With chunk_us set, each kernel group retunes its chunk length from the measured
+    device time of its launches; results stay those of the batch API, bit for bit."""
+    ctx = cho.cho_init(0, chunk_steps=64, chunk_us=300)
+    mix = Mix(ctx, seed=4)
+    try:
+        reqs = [mix.request(k, n_steps=3000) for k in range(len(mix.systems))]
+        tickets = [mix.submit(r, priority=k % 3) for k, r in enumerate(reqs)]
+        res = wait_all(ctx, tickets, [r["s"] for r in reqs])
+        for t, r in zip(tickets, reqs):
+            b = batch_result(ctx, r)
+            assert np.array_equal(res[t]["x"], b["x"][0]) and np.array_equal(res[t]["v"], b["v"][0]), r["kind"]
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
+
+
 def test_mixed_stream_against_oracle():
     ctx = cho.cho_init(0, chunk_steps=1000)
     mix = Mix(ctx, seed=3)
