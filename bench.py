@@ -479,6 +479,78 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                          "note": "one instance: four dependent stages per step, each a B x product split over "
                                  "the CTA (cluster) and one barrier"}}
         cho.cho_destroy_system(s_)
+    # one period of a real-time loop over uneven batches (2-DOF, a chain, few dense instances,
+    # dense on the tensor cores), issued by direct calls or replayed from a CUDA graph
+    # captured once; wall time per period including the synchronisation
+    import time as _time
+
+    cases = [(inputs.two_dof_batch(n_inst=4096, n_steps=1), "fp32_kahan", 200),
+             (inputs.chain_batch(n_inst=16, s=300, n_steps=1), "fp32_kahan", 100),
+             (inputs.dense_group(s=200, n_inst=3, n_steps=1), "fp32_kahan", 100),
+             (inputs.dense_group(s=128, n_inst=40, n_steps=1), "bf16x5", 100)]
+    gb = []
+    for cfg, prec, n in cases:
+        if cfg["kind"] == "dense":
+            sy = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
+        else:
+            sy = cho.cho_create_system(ctx, cfg["kind"], masses=cfg["masses"], springs=cfg["springs"])
+        tt = {k: torch.as_tensor(cfg[k], device=dev) for k in ("x0", "v0", "h")}
+        gb.append((sy, tt, {"x": torch.empty_like(tt["x0"]), "v": torch.empty_like(tt["v0"])}, prec, n))
+    gs = torch.cuda.Stream()
+
+    def period():
+        for sy, tt, oo, prec, n in gb:
+            cho.cho_integrate_batch(ctx, sy, tt["x0"], tt["v0"], tt["h"], n, prec, out=oo, stream=gs)
+
+    side = [torch.cuda.Stream() for _ in gb]
+
+    def period_concurrent():
+        # one stream per batch, forked from and joined back to gs
+        fork = torch.cuda.Event()
+        fork.record(gs)
+        joins = []
+        for (sy, tt, oo, prec, n), st in zip(gb, side):
+            st.wait_event(fork)
+            cho.cho_integrate_batch(ctx, sy, tt["x0"], tt["v0"], tt["h"], n, prec, out=oo, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+            joins.append(ev)
+        for ev in joins:
+            gs.wait_event(ev)
+
+    with torch.cuda.stream(gs):
+        period()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs, capture_error_mode="thread_local"):
+        period()
+    graph_c = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_c, stream=gs, capture_error_mode="thread_local"):
+        period_concurrent()
+
+    def wall(fn, reps=50):
+        fn()
+        torch.cuda.synchronize()
+        t0 = _time.perf_counter()
+        for _ in range(reps):
+            fn()
+            gs.synchronize()
+        return (_time.perf_counter() - t0) / reps
+
+    t_direct = wall(period)
+    t_direct_c = wall(period_concurrent)
+    t_graph = wall(graph.replay)
+    t_graph_c = wall(graph_c.replay)
+    res["uneven_batches_period"] = {
+        "batches": ["2-DOF x4096 x200 steps fp32", "chain 16x300 x100 fp32", "dense 3x200 x100 fp32 (clusters)",
+                    "dense 40x128 x100 bf16x5"],
+        "us_per_period_direct": 1e6 * t_direct, "us_per_period_direct_4_streams": 1e6 * t_direct_c,
+        "us_per_period_graph": 1e6 * t_graph, "us_per_period_graph_4_streams": 1e6 * t_graph_c,
+        "note": "wall time per period with synchronisation; the graphs replay the captured calls (one stream, or "
+                "one stream per batch forked and joined) with the bits of direct calls"}
+    del graph, graph_c
+    for sy, _, _, _, _ in gb:
+        cho.cho_destroy_system(sy)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     for s in (64, 128, 256):
         cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)

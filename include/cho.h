@@ -250,6 +250,14 @@ void cho_destroy_system(cho_system sys);
  * CHO_ECUDA, CHO_ENOMEM.  CHO_MEM_DEVICE: asynchronous on `stream`. */
 cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
 
+/* CUDA graphs.  With device arrays and h_per_inst = 1 (and not the dense polynomial form,
+ * which reads h on the host), cho_integrate_batch neither synchronises nor allocates outside
+ * stream-ordered memory pools, so a sequence of calls -- batches of different systems, sizes
+ * and precisions -- can be captured on a stream into a CUDA graph and replayed: each replay
+ * runs the captured batches on the current contents of their arrays, with the bits of direct
+ * calls.  Make one call of each shape before capturing (first calls set kernel attributes
+ * and query cluster occupancy). */
+
 /* The same integration in the plain form: one system at a time, one kernel launch per
  * RK stage and one per update, FP64 state kept in device memory between launches.
  * This is the un-batched baseline the batched kernels are measured against.  Only

@@ -955,3 +955,59 @@ def test_autotune_chooses_among_same_bit_kernels(tmp_path, case):
     finally:
         cho.cho_shutdown(ctx)
         cho.cho_shutdown(ctx2)
+
+
+def test_uneven_batches_replay_from_a_cuda_graph():
+    """A period's worth of uneven batches (2-DOF FP32, a chain, few dense instances on a
+    cluster, dense on the tensor cores) captured on one stream into a CUDA graph: each
+    replay gives the bits of direct calls, also after the inputs are rewritten in place."""
+    import torch
+
+    dev = torch.device("cuda:0")
+    ctx = cho.cho_init(0)
+    cases = [(inputs.two_dof_batch(n_inst=4096, n_steps=1), "fp32_kahan", 200),
+             (inputs.chain_batch(n_inst=16, s=300, n_steps=1), "fp32_kahan", 100),
+             (inputs.dense_group(s=200, n_inst=3, n_steps=1), "fp32_kahan", 100),
+             (inputs.dense_group(s=128, n_inst=40, n_steps=1), "bf16x5", 100)]
+    try:
+        batches = []
+        for cfg, prec, n in cases:
+            sys_ = make_system(ctx, cfg)
+            t = {k: torch.as_tensor(cfg[k], device=dev).clone() for k in ("x0", "v0", "h")}
+            out = {"x": torch.empty_like(t["x0"]), "v": torch.empty_like(t["v0"])}
+            batches.append((sys_, t, out, prec, n))
+        s = torch.cuda.Stream()
+
+        def run_all():
+            for sys_, t, out, prec, n in batches:
+                cho.cho_integrate_batch(ctx, sys_, t["x0"], t["v0"], t["h"], n, prec, out=out, stream=s)
+
+        with torch.cuda.stream(s):
+            run_all()                                  # first calls outside the capture
+        torch.cuda.synchronize()
+        direct = [(out["x"].clone(), out["v"].clone()) for _, _, out, _, _ in batches]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            run_all()
+        for _, _, out, _, _ in batches:
+            out["x"].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for (_, _, out, _, _), (x, v) in zip(batches, direct):
+            assert torch.equal(out["x"], x) and torch.equal(out["v"], v)
+        # new initial states in place: the replay follows them
+        for _, t, _, _, _ in batches:
+            t["x0"].mul_(0.5)
+        g.replay()
+        torch.cuda.synchronize()
+        replayed = [(out["x"].clone(), out["v"].clone()) for _, _, out, _, _ in batches]
+        with torch.cuda.stream(s):
+            run_all()
+        torch.cuda.synchronize()
+        for (_, _, out, _, _), (x, v) in zip(batches, replayed):
+            assert torch.equal(out["x"], x) and torch.equal(out["v"], v)
+        del g
+        for sys_, _, _, _, _ in batches:
+            cho.cho_destroy_system(sys_)
+    finally:
+        cho.cho_shutdown(ctx)
