@@ -529,12 +529,13 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
         period_concurrent()
 
     def wall(fn, reps=50):
+        # graph replays run on the current stream, direct calls on gs: wait for the device
         fn()
         torch.cuda.synchronize()
         t0 = _time.perf_counter()
         for _ in range(reps):
             fn()
-            gs.synchronize()
+            torch.cuda.synchronize()
         return (_time.perf_counter() - t0) / reps
 
     t_direct = wall(period)
