@@ -411,10 +411,13 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
     cho.cho_destroy_system(s_)
     cfg = inputs.chain_batch()
     s_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    chain_tune = cho.cho_autotune(ctx, s_, cfg["x0"].shape[0], "fp32_kahan")   # same-bits variants
     t = timed(s_, cfg, "fp32_kahan", cfg["n_steps"])
     dof = cfg["x0"].size * cfg["n_steps"]
     ach = dof * 52 / t / 1e12            # 26 FMA per DOF-step (4 x 3-point stencil, 6 combine, 6 sums, 2 update)
     res["chain_s1024_x4096_fp32_kahan"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                            "kernel": chain_tune["chosen"],
+                                            "autotune_us_per_step": {n: us for n, _, us in chain_tune["variants"]},
                                             "error_vs_oracle": sampled_err(s_, cfg, "fp32_kahan"),
                                             "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak,
                                                          "unit": "TFLOP/s", "frac": ach / alu_peak}}
