@@ -381,6 +381,14 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
     s_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
     # x after 1e5 steps from the discrete modal closed form of RK4 for eq. 3 (pinned in the oracle tests)
     x_exact = np.array([0.5919944669044028, -0.55303750830408224])
+    # the same in double-FP32 (CHO_FP32X2): FP64-class accuracy on the FP32 pipe
+    t = timed(s_, cfg, "fp32x2", cfg["n_steps"])
+    r = cho.cho_integrate_batch(ctx, s_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], "fp32x2")
+    res["eq3_single_fp32x2"] = {
+        "value": 2 * cfg["n_steps"] / t, "unit": UNIT, "ms": 1e3 * t, "ns_per_step": 1e9 * t / cfg["n_steps"],
+        "error_vs_closed_form": float(np.max(np.abs(np.asarray(r["x"])[0] - x_exact)) / np.max(np.abs(x_exact))),
+        "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                     "note": "one instance, one thread: dependent FP32 operations of the pair arithmetic"}}
     for k in (0, 1, 10):
         t = timed(s_, cfg, "fp64", cfg["n_steps"], poly=k)
         r = cho.cho_integrate_batch(ctx, s_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], "fp64", poly_jump=k)
@@ -394,6 +402,15 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                          "note": "one instance, one thread: FP64 instructions per step x 64 cycles"},
             "paper_context": "D(1)/D(2) and D(3)/D(4) evaluations of 4.12e-7 / 5.24e-7 s each on a 4-core "
                              "i5-2400 (Section 4), not a like-for-like measure"}
+    cho.cho_destroy_system(s_)
+    # the headline workload in double-FP32: FP64-class accuracy at FP32-pipe rates
+    cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS)
+    s_ = cho.cho_create_system(ctx, "two_dof", masses=cfg["masses"], springs=cfg["springs"])
+    t = timed(s_, cfg, "fp32x2", cfg["n_steps"])
+    dof = cfg["x0"].size * cfg["n_steps"]
+    res["two_dof_x65536_fp32x2"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
+                                    "error_vs_oracle": sampled_err(s_, cfg, "fp32x2", n_sample=8, every=1000),
+                                    "vs_fp64_mode": "see modes.fp64 (same workload)"}
     cho.cho_destroy_system(s_)
     # The polynomial form of the headline workload: the same RK4 map, k steps per update
     # y <- y + (P(hA)^k - I) y; its own work is 36 flop per instance-update (16 FMA + 4 adds).

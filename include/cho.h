@@ -75,14 +75,22 @@ typedef enum cho_kind {
  *                        x5: 5 products, M^{-1}K to 24 bits, X to 16; x6: 6 products,
  *                        both to 24 bits (s <= 128).  x5/x6 keep each 16-wide K chunk
  *                        in its own accumulator and add the chunks in FP32 (<= 1e-5
- *                        over 5e3 steps at h = T_min/100).                          */
+ *                        over 5e3 steps at h = T_min/100).
+ *   CHO_FP32X2           s = 2 systems (TWO_DOF, CHAIN with s = 2): state, coefficients
+ *                        and every operation as unevaluated pairs of FP32 numbers
+ *                        (about 48 significant bits; error-free TwoSum / TwoProd on the
+ *                        FP32 pipe), the stage form of CHO_FP64.  Within the FP64 mode's
+ *                        tolerance of the FP64 oracle on this GPU's much faster FP32 pipe.
+ *                        Batch calls only (not the polynomial form, serving or the
+ *                        plain form).                                               */
 typedef enum cho_prec {
     CHO_FP64 = 0,
     CHO_FP32_KAHAN = 1,
     CHO_DENSE_BF16X3 = 2,
     CHO_DENSE_BF16X5 = 3,
     CHO_DENSE_BF16X6 = 4,
-    CHO_DENSE_FP32_SIMT = 5
+    CHO_DENSE_FP32_SIMT = 5,
+    CHO_FP32X2 = 6
 } cho_prec;
 
 /* Where the state arrays of a batch live. */

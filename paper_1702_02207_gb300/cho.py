@@ -28,11 +28,13 @@ STATUS_NAMES = {
 }
 CHO_TWO_DOF, CHO_CHAIN, CHO_DENSE = 0, 1, 2
 CHO_FP64, CHO_FP32_KAHAN, CHO_DENSE_BF16X3, CHO_DENSE_BF16X5, CHO_DENSE_BF16X6, CHO_DENSE_FP32_SIMT = 0, 1, 2, 3, 4, 5
+CHO_FP32X2 = 6
 CHO_MEM_DEVICE, CHO_MEM_HOST = 0, 1
 
 KINDS = {"two_dof": CHO_TWO_DOF, "chain": CHO_CHAIN, "dense": CHO_DENSE}
 PRECS = {"fp64": CHO_FP64, "fp32_kahan": CHO_FP32_KAHAN, "bf16x3": CHO_DENSE_BF16X3,
-         "bf16x5": CHO_DENSE_BF16X5, "bf16x6": CHO_DENSE_BF16X6, "fp32_simt": CHO_DENSE_FP32_SIMT}
+         "bf16x5": CHO_DENSE_BF16X5, "bf16x6": CHO_DENSE_BF16X6, "fp32_simt": CHO_DENSE_FP32_SIMT,
+         "fp32x2": CHO_FP32X2}
 
 EXPORTED = [
     "cho_init", "cho_shutdown", "cho_last_error", "cho_create_system", "cho_system_info",

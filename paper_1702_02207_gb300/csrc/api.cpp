@@ -575,6 +575,9 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
         if (p != CHO_FP64) return fail(CHO_EINVAL, "%s: the plain form is FP64 only", who);
         if (b->x_traj || b->v_traj || b->energy) return fail(CHO_EINVAL, "%s: no checkpoints in the plain form", who);
     } else if (p == CHO_FP64 || p == CHO_FP32_KAHAN) {
+    } else if (p == CHO_FP32X2) {
+        if (sys->path != PATH_SMALL || sys->s != 2)
+            return fail(CHO_EINVAL, "%s: CHO_FP32X2 integrates s = 2 systems", who);
     } else if (p == CHO_DENSE_FP32_SIMT || p == CHO_DENSE_BF16X3 || p == CHO_DENSE_BF16X5 || p == CHO_DENSE_BF16X6) {
         if (sys->kind != CHO_DENSE) return fail(CHO_EINVAL, "%s: precision %d is for dense systems", who, p);
         if ((p != CHO_DENSE_FP32_SIMT) && (sys->path != PATH_DENSE || sys->s_tc == 0))
@@ -731,7 +734,7 @@ cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t 
     } else if (sys->path == PATH_SMALL) {
         SmallSys ss{sys->s, sys->S, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32, sys->d_err};
         ss.variant = kc.small_variant;
-        e = launch_rk4_small(ss, io, fp64, st);
+        e = b->prec == CHO_FP32X2 ? launch_rk4_small_dw(ss, io, st) : launch_rk4_small(ss, io, fp64, st);
     } else if (sys->path == PATH_CHAIN) {
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         cs.dofs_per_thread = kc.chain_dofs;

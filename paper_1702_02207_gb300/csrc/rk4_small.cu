@@ -967,6 +967,138 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
     return e != cudaSuccess ? e : ef;
 }
 
+
+// ---- double-FP32: s = 2 systems with about 48 significant bits on the FP32 pipe ------
+//
+// GB300 runs FP64 at about 1/64 of the FP32 rate (a dependent FP64 FMA takes 64
+// cycles), so FP64-class accuracy is cheaper as unevaluated pairs hi + lo of FP32
+// numbers ("double-word" arithmetic).  The pieces are the classical error-free
+// transformations: Knuth's TwoSum, FastTwoSum (|a| >= |b|) and the FMA form of
+// TwoProd (a b = p + e exactly with e = fma(a, b, -p)).  Sums use one TwoSum of the
+// high parts plus the low parts ("sloppy" double-word addition: its error is a few
+// units of 2^-48 of the larger operand); products use TwoProd of the high parts and
+// the two cross terms.  The step is the FP64 mode's stage form, operation for
+// operation, in this arithmetic; coefficients, h, h/2 and h/6 are split from FP64.
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_split(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double dw_value(dw a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dw fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y)
+{
+    const dw s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dw dw_fma(dw a, dw b, dw c) { return dw_add(dw_mul(a, b), c); }
+__device__ __forceinline__ dw dw_neg(dw a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dw dw_twice(dw a) { return {2.f * a.hi, 2.f * a.lo}; }
+
+__global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const BatchIO io)
+{
+    const int64_t q = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (q >= io.n_inst) return;
+    const int64_t set = sys.per_inst_sys ? q : 0;
+    const double* Bq = sys.B64 + set * 4;           // [2][2] of the padded S = 2 block
+    dw b[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b[r][j] = dw_split(Bq[r * 2 + j]);
+    const double hd = io.h[io.h_per_inst ? q : 0];
+    const dw h = dw_split(hd), h2 = dw_split(0.5 * hd), h6 = dw_split(hd / 6.0);
+    const int s = sys.s;
+    dw x[2], v[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        x[r] = dw_split(r < s ? io.x0[q * s + r] : 0.0);
+        v[r] = dw_split(r < s ? io.v0[q * s + r] : 0.0);
+    }
+    // a = -(B xs), each row from its diagonal, as the FP64 mode
+    auto accel = [&](const dw (&xs)[2], dw (&a)[2]) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) a[r] = dw_neg(dw_fma(b[r][1 - r], xs[1 - r], dw_mul(b[r][r], xs[r])));
+    };
+    const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (io.n_steps > 0 ? io.n_steps : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < io.n_steps; done += every) {
+        repeat_steps(every, [&]() {
+            dw a[2], xs[2], kx[2], kv[2], vs[2];
+            accel(x, a);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                kx[r] = v[r];
+                kv[r] = a[r];
+                xs[r] = dw_fma(h2, v[r], x[r]);
+                vs[r] = dw_fma(h2, a[r], v[r]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                kx[r] = dw_add(dw_twice(vs[r]), kx[r]);
+                kv[r] = dw_add(dw_twice(a[r]), kv[r]);
+                xs[r] = dw_fma(h2, vs[r], x[r]);
+                vs[r] = dw_fma(h2, a[r], v[r]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                kx[r] = dw_add(dw_twice(vs[r]), kx[r]);
+                kv[r] = dw_add(dw_twice(a[r]), kv[r]);
+                xs[r] = dw_fma(h, vs[r], x[r]);
+                vs[r] = dw_fma(h, a[r], v[r]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                kx[r] = dw_add(kx[r], vs[r]);
+                kv[r] = dw_add(kv[r], a[r]);
+                x[r] = dw_fma(h6, kx[r], x[r]);
+                v[r] = dw_fma(h6, kv[r], v[r]);
+            }
+        });
+        if (io.ckpt_every > 0 && io.x_traj) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (r >= s) continue;
+                const int64_t o = (q * io.n_ck + ck) * s + r;
+                io.x_traj[o] = dw_value(x[r]);
+                if (io.v_traj) io.v_traj[o] = dw_value(v[r]);
+            }
+        }
+        ++ck;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r >= s) continue;
+        io.x_out[q * s + r] = dw_value(x[r]);
+        io.v_out[q * s + r] = dw_value(v[r]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
@@ -1005,6 +1137,16 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
         s.sys = sys;
         s.io = io;
     });
+}
+
+cudaError_t launch_rk4_small_dw(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    if (sys.S != 2 || !sys.B64) return cudaErrorInvalidValue;
+    const int64_t blocks = (io.n_inst + 127) / 128;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rk4_dw2_kernel<<<(unsigned)blocks, 128, 0, st>>>(sys, io);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st)

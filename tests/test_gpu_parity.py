@@ -1011,3 +1011,53 @@ def test_uneven_batches_replay_from_a_cuda_graph():
             cho.cho_destroy_system(sys_)
     finally:
         cho.cho_shutdown(ctx)
+
+
+# ---- double-FP32 (CHO_FP32X2): FP64-class accuracy on the FP32 pipe -----------------------------
+
+def test_fp32x2_eq3_full_horizon():
+    """Eq. 3 for 1e5 steps in double-FP32: within the FP64 mode's bar of the oracle and of the
+    discrete closed form."""
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.eq3_single()
+        out = run_gpu(c, cfg, "fp32x2", 1000)
+        ref = oracle_run(cfg, ckpt_every=1000)
+        ex, ev = check(out, ref, TOL_FP64)
+        print(f"fp32x2 eq3: x {ex:.3e} v {ev:.3e}")
+        assert np.allclose(out["x"][0], [0.5919944669044028, -0.55303750830408224], atol=1e-10)
+    finally:
+        cho.cho_shutdown(c)
+
+
+@pytest.mark.parametrize("n_inst", [1, 37, 1000])
+def test_fp32x2_two_dof_batch(n_inst):
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.two_dof_batch(n_inst=n_inst, n_steps=2000)
+        out = run_gpu(c, cfg, "fp32x2", 250)
+        ref = oracle_run(cfg, ckpt_every=250)
+        ex, ev = check(out, ref, TOL_FP64)
+        print(f"fp32x2 two_dof x{n_inst}: x {ex:.3e} v {ev:.3e}")
+    finally:
+        cho.cho_shutdown(c)
+
+
+def test_fp32x2_is_refused_outside_its_scope():
+    c = cho.cho_init(0)
+    try:
+        ch = inputs.chain_batch(n_inst=2, s=40, n_steps=10)
+        sys_ = make_system(c, ch)
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_integrate_batch(c, sys_, ch["x0"], ch["v0"], ch["h"], 10, "fp32x2")
+        assert ei.value.status == cho.CHO_EINVAL
+        cho.cho_destroy_system(sys_)
+        two = inputs.two_dof_batch(n_inst=2, n_steps=10)
+        sys2 = make_system(c, two)
+        with pytest.raises(cho.ChoError):
+            cho.cho_integrate_batch(c, sys2, two["x0"], two["v0"], two["h"], 10, "fp32x2", poly_jump=5)
+        with pytest.raises(cho.ChoError):
+            cho.cho_submit(c, sys2, two["x0"][0], two["v0"][0], float(two["h"][0]), 10, "fp32x2", 0, 0)
+        cho.cho_destroy_system(sys2)
+    finally:
+        cho.cho_shutdown(c)
