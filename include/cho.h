@@ -306,7 +306,8 @@ cho_status cho_energy(cho_ctx* ctx, cho_system sys, const double* x, const doubl
  * poly_jump) on seeded inputs on the context's device, keeps those whose final states
  * equal the first candidate's bit for bit, times them with CUDA events (best of three
  * runs of about 3 ms after a warm-up) and records the fastest in the context's tune
- * table.  Later cho_integrate_batch calls of the same shape use it; the instance count
+ * table; the first candidate is the kernel the default rules pick, and it is kept unless
+ * another is at least 3 % faster.  Later cho_integrate_batch calls of the same shape use it; the instance count
  * is matched by floor(log2(n_inst)).  Shapes with a single kernel report one variant
  * and record nothing.  A system with one parameter set per instance needs n_inst equal
  * to its set count.  Synchronous; allocates 7 n_inst s doubles of device memory for the

@@ -152,8 +152,10 @@ struct DenseSys {
     int32_t few = -1;       // FP32: 1 one instance per CTA or cluster, 0 the streaming kernel, -1 by count
 };
 
-// Whether the FP32 one-instance-per-CTA-or-cluster kernels can run this system here.
+// Whether the FP32 one-instance-per-CTA-or-cluster kernels can run this system here,
+// and whether the default rule picks them for n_inst instances.
 bool dense_few_capable(const DenseSys& sys);
+bool dense_few_default(const DenseSys& sys, int64_t n_inst);
 
 // Test hook for the bounded device waits: CHO_TEST_STALL_MMA=1 in the environment makes
 // the tensor-core kernel skip its MMAs, so its wait on their completion gives up after

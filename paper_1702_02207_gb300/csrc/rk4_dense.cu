@@ -1043,6 +1043,19 @@ cudaError_t launch_poly(const DenseSys& sys, const void* E, const BatchIO& io, c
 
 }  // namespace
 
+bool dense_few_default(const DenseSys& sys, int64_t n_inst)
+{
+    int cap = 0;
+    switch (sys.s_pad) {
+        case 64: cap = device_sm_count(); break;
+        case 128: cap = split_capacity<128, DenseBatchSrc<false>>(); break;
+        case 256: cap = split_capacity<256, DenseBatchSrc<false>>(); break;
+        case 512: cap = split_capacity<512, DenseBatchSrc<false>>(); break;
+        default: return false;
+    }
+    return cap > 0 && (sys.per_inst || n_inst <= 8 * (int64_t)cap);
+}
+
 bool dense_few_capable(const DenseSys& sys)
 {
     switch (sys.s_pad) {

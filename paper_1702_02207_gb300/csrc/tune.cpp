@@ -28,7 +28,8 @@ struct Candidate {
     char name[24];
 };
 
-std::vector<Candidate> candidates(const cho_system_impl* sys, int32_t prec, int32_t poly_jump)
+// The first candidate is the kernel the default rules pick for the shape.
+std::vector<Candidate> candidates(const cho_system_impl* sys, int64_t n_inst, int32_t prec, int32_t poly_jump)
 {
     std::vector<Candidate> c;
     auto add = [&](int32_t code, const char* name) {
@@ -53,9 +54,14 @@ std::vector<Candidate> candidates(const cho_system_impl* sys, int32_t prec, int3
     } else if (sys->path == PATH_DENSE) {
         DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
                     sys->n_sys != 1 ? 1 : 0};
-        add(1, "one_per_cta_or_cluster");
-        if (!dense_few_capable(ds)) c.clear();
-        add(0, "streaming");
+        const bool few_ok = dense_few_capable(ds);
+        if (few_ok && dense_few_default(ds, n_inst)) {
+            add(1, "one_per_cta_or_cluster");
+            add(0, "streaming");
+        } else {
+            add(0, "streaming");
+            if (few_ok) add(1, "one_per_cta_or_cluster");
+        }
     }
     (void)prec;
     return c;
@@ -95,7 +101,7 @@ extern "C" cho_status cho_autotune(cho_ctx* ctx, cho_system sys, int64_t n_inst,
     std::memset(&res, 0, sizeof(res));
     TuneKey key;
     std::vector<Candidate> cand;
-    if (tune_key(sys, n_inst, prec, poly_jump, &key)) cand = candidates(sys, prec, poly_jump);
+    if (tune_key(sys, n_inst, prec, poly_jump, &key)) cand = candidates(sys, n_inst, prec, poly_jump);
     if (cand.size() > 8) cand.resize(8);
 
     // seeded inputs of the shape: x0 in [-1, 1), v0 = 0, h = T_min / 32 of each set
@@ -209,9 +215,15 @@ extern "C" cho_status cho_autotune(cho_ctx* ctx, cho_system sys, int64_t n_inst,
     if (rc != CHO_OK) return rc;
     res.n_variants = (int32_t)cand.size();
     res.sample_steps = b.n_steps;
+    // the default kernel (candidate 0) stays unless another is at least 3 % faster, so that
+    // timing noise between near-equal kernels does not flip the choice
     res.chosen = 0;
+    double best = res.us_per_step[0] * 0.97;
     for (int k = 1; k < res.n_variants; ++k)
-        if (res.us_per_step[k] > 0 && res.us_per_step[k] < res.us_per_step[res.chosen]) res.chosen = k;
+        if (res.us_per_step[k] > 0 && res.us_per_step[k] < best) {
+            res.chosen = k;
+            best = res.us_per_step[k];
+        }
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         ctx->tune[key] = res.code[res.chosen];

@@ -933,7 +933,9 @@ def test_autotune_chooses_among_same_bit_kernels(tmp_path, case):
         assert len(r["variants"]) == n_cand
         times = [us for _, _, us in r["variants"]]
         assert all(us > 0 for us in times), "a candidate gave different bits"
-        assert r["chosen"] == r["variants"][int(np.argmin(times))][0]
+        best = int(np.argmin(times))
+        expect = best if times[best] < 0.97 * times[0] else 0          # the default stays unless 3 % slower
+        assert r["chosen"] == r["variants"][expect][0]
         assert cho.cho_tune_query(ctx, sys1, n_inst, prec) == r["code"]
         tuned = _device_run(ctx, sys1, cfg, prec, cfg["n_steps"])
         default = _device_run(ctx2, sys2, cfg, prec, cfg["n_steps"])
