@@ -14,12 +14,16 @@
 // chunk overlaps the products of the current one; each thread reads its rows
 // of a column with vector shared-memory loads.
 //
-// One (M, K) per instance: the same kernel with one instance per CTA (NT = 1)
-// and the CTA's own B^T streamed through the chunk buffers; B is read from L2 or
-// HBM every stage (hi and lo at stage 1, hi alone at stages 2-4: 20 s^2 bytes per
-// instance-step in FP32), so this form is bound by memory bandwidth.
+// One (M, K) per instance, FP64: the same kernel with one instance per CTA (NT = 1)
+// and the CTA's own B^T streamed through the chunk buffers (read from L2 or HBM
+// every stage, so this form is bound by memory bandwidth).  In FP32, instances with
+// their own (M, K), and batches of few instances, run on rk4_dense_own_kernel
+// (s_pad = 64: one CTA per instance, B held in registers and shared memory) or
+// rk4_dense_split_kernel (s_pad >= 128: one CTA or cluster of CTAs per instance,
+// B's rows split over it); every FP32 kernel here forms the products in the same
+// order, so the choice between them never changes a result's bits.
 //
-// The tensor-core split-BF16 variant lives in rk4_dense_tc.cu.
+// The tensor-core split-BF16 variants live in rk4_dense_tc.cu.
 #include "cho_internal.h"
 #include "ctx.h"
 #include "rk4_common.cuh"
