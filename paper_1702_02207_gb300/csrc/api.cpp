@@ -204,6 +204,7 @@ extern "C" void cho_shutdown(cho_ctx* ctx)
     }
     ctx->ws.release();
     ctx->plain_ws.release();
+    if (ctx->err_host) cudaFreeHost(ctx->err_host);
     delete ctx;
 }
 
@@ -824,9 +825,22 @@ static cho_status run_staged(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t
     if (b->v_traj) CHO_STAGE(b->v_traj, d.v_traj, ntr * 8, cudaMemcpyDeviceToHost);
     if (b->energy) CHO_STAGE(b->energy, d.energy, (size_t)n * n_ck * 8, cudaMemcpyDeviceToHost);
 #undef CHO_STAGE
+    // the system's device error word comes back with the results (one synchronisation);
+    // it is reset only in the rare case that a bounded wait gave up
+    cho_system_impl* sys = b->system;
+    const bool err_async = sys->d_err && (ctx->err_host || cudaHostAlloc((void**)&ctx->err_host, sizeof(int),
+                                                                         cudaHostAllocDefault) == cudaSuccess);
+    if (err_async) {
+        e = cudaMemcpyAsync(ctx->err_host, sys->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: %s", cudaGetErrorString(e));
+    }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: %s", cudaGetErrorString(e));
-    return take_device_error(b->system, "integrate");
+    if (!err_async) return take_device_error(sys, "integrate");
+    if (*ctx->err_host == 0) return CHO_OK;
+    e = cudaMemset(sys->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(CHO_ECUDA, "integrate: resetting the device error word: %s", cudaGetErrorString(e));
+    return fail(CHO_ETIMEOUT, "integrate: a bounded device wait gave up after its time limit; results are invalid");
 }
 
 static cho_status run_plain_device(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t st)

@@ -109,8 +109,9 @@ struct cho_ctx {
     cho_config cfg{};
     std::mutex mu;                      // guards `systems`
     std::set<cho_system_impl*> systems;
-    std::mutex ws_mu;                   // guards `ws`
+    std::mutex ws_mu;                   // guards `ws` and `err_host`
     cho::Workspace ws;                  // host-memory batch staging
+    int* err_host = nullptr;            // pinned word: a system's device error word, read in stream order
     std::mutex plain_mu;
     cho::Workspace plain_ws;            // plain-form state and stage buffers
     cho::ServeEngine* serve = nullptr;
