@@ -479,17 +479,22 @@ __global__ void __launch_bounds__(64) rk4_dense_own_kernel(DenseSys sys, const S
 // above run each instance's stages one after the other on one SM while the other
 // SMs idle.  Here one instance spans a cluster of CS CTAs, each owning R = s_pad / CS
 // rows of B: the hi piece of its rows in registers (CPT consecutive blocks of kJC
-// columns per thread), the lo piece (stage 1 only) in shared memory.  A stage is:
-// every CTA forms the block partials of its rows (a thread per row and block
-// range), the owner thread of each row adds them in column order, completes the
-// row's stage values and sends its next stage displacement to every CTA's copy of
-// Xs (st.async into distributed shared memory, double-buffered); each CTA waits on
-// its own mbarrier until the stage's s_pad values have arrived.  This is the
-// paper's decomposition of one system's RK4 stage over parallel workers with one
-// synchronisation between stages (Section 3), at the scale of a cluster of SMs.
-// (A cluster barrier per stage, whose release waits for the remote stores to be
-// acknowledged before the barrier itself, cost about 60 % of the warps' time.)  The block partials and their order are those of the other FP32
-// dense kernels, so an instance gets the same bits whichever of them runs it.
+// columns per thread), the lo piece (stage 1 only) in shared memory.  For x'' = -B x
+// the displacement of stage 3, x + h/2 v2, needs only stage 1's product and that of
+// stage 4, x + h v3, only stage 2's, so the kernel forms the products of two stages
+// per round (stages 1 and 2, then 3 and 4): every CTA forms the block partials of
+// its rows for both displacements (a thread per row and block range, B read once
+// for the two), the owner thread of each row adds them in column order, completes
+// the row's stage values and sends the round's next two displacements to every CTA's
+// copy of Xs (st.async into distributed shared memory, double-buffered); each CTA
+// waits on its own mbarrier until the round's 2 s_pad values have arrived.  Two
+// exchanges per step instead of four.  This is the paper's decomposition of one
+// system's RK4 step over parallel workers with a synchronisation between stages
+// (Section 3), at the scale of a cluster of SMs.  The block partials and their
+// order, and every stage value, are those of the other FP32 dense kernels, so an
+// instance gets the same bits whichever of them runs it.  (A cluster barrier per
+// stage, whose release waits for the remote stores to be acknowledged before the
+// barrier itself, cost about 60 % of the warps' time.)
 template <int SP, int R, int NTHR, class Src>
 __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_kernel(DenseSys sys, const Src src)
 {
@@ -504,11 +509,11 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
     static_assert(CPT % 4 == 0 && NCH % 4 == 0, "partials move as float4");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Lo = (float*)smem_raw;                   // [R][LD]: lo piece of this CTA's rows
-    float* X = Lo + (size_t)R * LD;                 // [2][SP]: stage displacements of all rows
-    float* Ph = X + 2 * SP;                         // [R][PLD]: block partials, hi piece
-    float* Pl = Ph + (size_t)R * PLD;               // [R][PLD]: block partials, lo piece (stage 1)
+    float* X = Lo + (size_t)R * LD;                 // [2 rounds][2 displacements][SP], all rows
+    float* Ph = X + 4 * SP;                         // [2][R][PLD]: block partials of the two displacements
+    float* Pl = Ph + 2 * (size_t)R * PLD;           // [R][PLD]: block partials, lo piece (stage 1)
     __shared__ int any_bad;
-    __shared__ __align__(8) uint64_t xbar[2];       // Xs buffer b complete (clusters)
+    __shared__ __align__(8) uint64_t xbar[2];       // Xs buffer set b complete (clusters)
 
     const int t = threadIdx.x;
     const int lane = t & 31, w = t >> 5;
@@ -533,7 +538,7 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
         const int j = e / R, r = e % R;             // B^T[j][rank R + r], coalesced over r
         Lo[(size_t)r * LD + j] = Bt[(size_t)SP * SP + (size_t)j * SP + (int)rank * R + r];
     }
-    for (int e = t; e < 2 * R * PLD; e += NTHR) Ph[e] = 0.f;   // Ph and Pl
+    for (int e = t; e < 3 * R * PLD; e += NTHR) Ph[e] = 0.f;   // Ph (both) and Pl
     const int64_t my_steps = src.steps(q);
     const StepSize<false> hs(src.h(q));
     float x = 0.f, v = 0.f, cx = 0.f, cv = 0.f;
@@ -544,12 +549,12 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
             mbarrier_init_one(&xbar[0]);
             mbarrier_init_one(&xbar[1]);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            mbarrier_arm(&xbar[0], 4u * SP);        // each stage brings all s_pad rows of Xs
-            mbarrier_arm(&xbar[1], 4u * SP);
+            mbarrier_arm(&xbar[0], 8u * SP);        // each round brings two displacements of s_pad rows
+            mbarrier_arm(&xbar[1], 8u * SP);
         }
     }
-    // the owner's row of Xs (buffer 0) and the buffers' mbarriers; mapa gives their
-    // addresses in each CTA of the cluster
+    // the owner's row of Xs (set 0, first displacement) and the sets' mbarriers; mapa
+    // gives their addresses in each CTA of the cluster
     const uint32_t xloc = (uint32_t)__cvta_generic_to_shared(X) + 4u * (uint32_t)(owner ? i : 0);
     const uint32_t bloc = (uint32_t)__cvta_generic_to_shared(&xbar[0]);
     uint32_t xphase[2] = {0u, 0u};
@@ -557,116 +562,139 @@ __global__ void __launch_bounds__(NTHR, NTHR >= 512 ? 1 : 2) rk4_dense_split_ker
     // every CTA of the cluster is running and has initialised its shared memory
     if (CS > 1) cluster_sync(); else __syncthreads();
 
-    int buf = 0;
+    int set = 0;
     float lo1 = 0.f;
-    auto accel = [&](float xs, bool first) -> float {
+    // One round: aa = -(B xa), ab = -(B xb) for this thread's row (owners); the first
+    // round of a step also forms the lo product of xa (= x), reused by every stage.
+    auto round = [&](float xa, float xb, bool first, float& aa, float& ab) {
         if (owner) {
-            const uint32_t off = (uint32_t)(buf * SP * 4);
+            const uint32_t off = (uint32_t)(set * 2 * SP * 4);
             if constexpr (CS > 1) {
 #pragma unroll
-                for (int c = 0; c < CS; ++c)
-                    st_async_f32(mapa(xloc + off, (uint32_t)c), xs, mapa(bloc + 8u * (uint32_t)buf, (uint32_t)c));
+                for (int c = 0; c < CS; ++c) {
+                    const uint32_t bar = mapa(bloc + 8u * (uint32_t)set, (uint32_t)c);
+                    st_async_f32(mapa(xloc + off, (uint32_t)c), xa, bar);
+                    st_async_f32(mapa(xloc + off + 4u * SP, (uint32_t)c), xb, bar);
+                }
             } else {
-                X[buf * SP + i] = xs;
+                X[set * 2 * SP + i] = xa;
+                X[(set * 2 + 1) * SP + i] = xb;
             }
         }
         if constexpr (CS > 1) {
-            // all rows of this stage's Xs have arrived (bounded wait, agreed by the CTA)
-            ok = __syncthreads_and(mbarrier_wait_bounded(&xbar[buf], xphase[buf], 1000000000ull));
-            if (!ok) return 0.f;
-            xphase[buf] ^= 1u;
-            // the buffer's next use is two stages on; its data can only be sent after
-            // this CTA's next stage values, so arming it here precedes every transfer
-            if (t == 0) mbarrier_arm(&xbar[buf], 4u * SP);
+            // both displacements of every row have arrived (bounded wait, agreed by the CTA)
+            ok = __syncthreads_and(mbarrier_wait_bounded(&xbar[set], xphase[set], 1000000000ull));
+            if (!ok) {
+                aa = ab = 0.f;
+                return;
+            }
+            xphase[set] ^= 1u;
+            // the set's next use is two rounds on; its data can only be sent after this
+            // CTA's next round of values, so arming it here precedes every transfer
+            if (t == 0) mbarrier_arm(&xbar[set], 8u * SP);
         } else {
             __syncthreads();
         }
         if (active) {
-            const float* Xb = X + buf * SP + c0 * kJC;
+            const float* Xa = X + set * 2 * SP + c0 * kJC;
+            const float* Xb = Xa + SP;
             const float* lrow = Lo + (size_t)lr * LD + c0 * kJC;
-            // each block's columns in order; the CPT blocks' chains are independent
-            float p[CPT], pl[CPT];
+            // each block's columns in order, for both displacements; four blocks at a time
 #pragma unroll
-            for (int k = 0; k < CPT; ++k) {
-                const float4 x0 = *(const float4*)(Xb + k * kJC);
-                const float4 x1 = *(const float4*)(Xb + k * kJC + 4);
-                float u = 0.f;
-                u = fmar(bh[k][0], x0.x, u);
-                u = fmar(bh[k][1], x0.y, u);
-                u = fmar(bh[k][2], x0.z, u);
-                u = fmar(bh[k][3], x0.w, u);
-                u = fmar(bh[k][4], x1.x, u);
-                u = fmar(bh[k][5], x1.y, u);
-                u = fmar(bh[k][6], x1.z, u);
-                u = fmar(bh[k][7], x1.w, u);
-                p[k] = u;
-                if (first) {
-                    const float4 l0 = *(const float4*)(lrow + k * kJC);
-                    const float4 l1 = *(const float4*)(lrow + k * kJC + 4);
-                    float z = 0.f;
-                    z = fmar(l0.x, x0.x, z);
-                    z = fmar(l0.y, x0.y, z);
-                    z = fmar(l0.z, x0.z, z);
-                    z = fmar(l0.w, x0.w, z);
-                    z = fmar(l1.x, x1.x, z);
-                    z = fmar(l1.y, x1.y, z);
-                    z = fmar(l1.z, x1.z, z);
-                    z = fmar(l1.w, x1.w, z);
-                    pl[k] = z;
+            for (int k4 = 0; k4 < CPT; k4 += 4) {
+                float pa[4], pb[4], pl[4];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int k = k4 + kk;
+                    const float4 a0 = *(const float4*)(Xa + k * kJC);
+                    const float4 a1 = *(const float4*)(Xa + k * kJC + 4);
+                    const float4 b0 = *(const float4*)(Xb + k * kJC);
+                    const float4 b1 = *(const float4*)(Xb + k * kJC + 4);
+                    float u = 0.f, z = 0.f;
+                    u = fmar(bh[k][0], a0.x, u);
+                    z = fmar(bh[k][0], b0.x, z);
+                    u = fmar(bh[k][1], a0.y, u);
+                    z = fmar(bh[k][1], b0.y, z);
+                    u = fmar(bh[k][2], a0.z, u);
+                    z = fmar(bh[k][2], b0.z, z);
+                    u = fmar(bh[k][3], a0.w, u);
+                    z = fmar(bh[k][3], b0.w, z);
+                    u = fmar(bh[k][4], a1.x, u);
+                    z = fmar(bh[k][4], b1.x, z);
+                    u = fmar(bh[k][5], a1.y, u);
+                    z = fmar(bh[k][5], b1.y, z);
+                    u = fmar(bh[k][6], a1.z, u);
+                    z = fmar(bh[k][6], b1.z, z);
+                    u = fmar(bh[k][7], a1.w, u);
+                    z = fmar(bh[k][7], b1.w, z);
+                    pa[kk] = u;
+                    pb[kk] = z;
+                    if (first) {
+                        const float4 l0 = *(const float4*)(lrow + k * kJC);
+                        const float4 l1 = *(const float4*)(lrow + k * kJC + 4);
+                        float y = 0.f;
+                        y = fmar(l0.x, a0.x, y);
+                        y = fmar(l0.y, a0.y, y);
+                        y = fmar(l0.z, a0.z, y);
+                        y = fmar(l0.w, a0.w, y);
+                        y = fmar(l1.x, a1.x, y);
+                        y = fmar(l1.y, a1.y, y);
+                        y = fmar(l1.z, a1.z, y);
+                        y = fmar(l1.w, a1.w, y);
+                        pl[kk] = y;
+                    }
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < CPT; k += 4) {
-                *(float4*)(Ph + (size_t)lr * PLD + c0 + k) = make_float4(p[k], p[k + 1], p[k + 2], p[k + 3]);
-                if (first)
-                    *(float4*)(Pl + (size_t)lr * PLD + c0 + k) = make_float4(pl[k], pl[k + 1], pl[k + 2], pl[k + 3]);
+                *(float4*)(Ph + (size_t)lr * PLD + c0 + k4) = make_float4(pa[0], pa[1], pa[2], pa[3]);
+                *(float4*)(Ph + ((size_t)R + lr) * PLD + c0 + k4) = make_float4(pb[0], pb[1], pb[2], pb[3]);
+                if (first) *(float4*)(Pl + (size_t)lr * PLD + c0 + k4) = make_float4(pl[0], pl[1], pl[2], pl[3]);
             }
         }
         __syncthreads();
-        float a = 0.f;
         if (owner) {
             // all NCH blocks in column order (the zero ones leave the sums unchanged)
-            float t0 = 0.f, l = 0.f;
+            float ta = 0.f, tb = 0.f, l = 0.f;
 #pragma unroll
             for (int c = 0; c < NCH; c += 4) {
-                const float4 u = *(const float4*)(Ph + (size_t)t * PLD + c);
-                t0 = addr(addr(addr(addr(t0, u.x), u.y), u.z), u.w);
+                const float4 ua = *(const float4*)(Ph + (size_t)t * PLD + c);
+                const float4 ub = *(const float4*)(Ph + ((size_t)R + t) * PLD + c);
+                ta = addr(addr(addr(addr(ta, ua.x), ua.y), ua.z), ua.w);
+                tb = addr(addr(addr(addr(tb, ub.x), ub.y), ub.z), ub.w);
                 if (first) {
                     const float4 ul = *(const float4*)(Pl + (size_t)t * PLD + c);
                     l = addr(addr(addr(addr(l, ul.x), ul.y), ul.z), ul.w);
                 }
             }
             if (first) lo1 = l;
-            a = -addr(t0, lo1);
+            aa = -addr(ta, lo1);
+            ab = -addr(tb, lo1);
         }
-        buf ^= 1;
-        return a;
+        set ^= 1;
     };
 
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (my_steps > 0 ? my_steps : 1);
     int64_t ck = 0;
     for (int64_t done = 0; done < my_steps && ok; done += every) {
         for (int64_t it = 0; it < every && ok; ++it) {
-            float a, xs, kx, kv, vs;
-            a = accel(x, true);
-            kx = v;
-            kv = a;
-            xs = fmar(hs.h2, v, x);
-            vs = fmar(hs.h2, a, v);
-            if (ok) a = accel(xs, false);
-            kx = fmar(2.f, vs, kx);
-            kv = fmar(2.f, a, kv);
-            xs = fmar(hs.h2, vs, x);
-            vs = fmar(hs.h2, a, v);
-            if (ok) a = accel(xs, false);
-            kx = fmar(2.f, vs, kx);
-            kv = fmar(2.f, a, kv);
-            xs = fmar(hs.h, vs, x);
-            vs = fmar(hs.h, a, v);
-            if (ok) a = accel(xs, false);
+            // stages 1 and 2: x and x2 = x + h/2 v
+            float a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+            const float x2 = fmar(hs.h2, v, x);
+            round(x, x2, true, a1, a2);
             if (!ok) break;
-            kx = addr(kx, vs);
-            kv = addr(kv, a);
+            float kx = v, kv = a1;
+            const float v2 = fmar(hs.h2, a1, v);
+            kx = fmar(2.f, v2, kx);
+            kv = fmar(2.f, a2, kv);
+            const float x3 = fmar(hs.h2, v2, x);
+            const float v3 = fmar(hs.h2, a2, v);
+            const float x4 = fmar(hs.h, v3, x);
+            // stages 3 and 4: x3 = x + h/2 v2 and x4 = x + h v3
+            round(x3, x4, false, a3, a4);
+            if (!ok) break;
+            kx = fmar(2.f, v3, kx);
+            kv = fmar(2.f, a3, kv);
+            const float v4 = fmar(hs.h, a3, v);
+            kx = addr(kx, v4);
+            kv = addr(kv, a4);
             state_update<false>(x, cx, kx, hs);
             state_update<false>(v, cv, kv, hs);
         }
@@ -703,7 +731,7 @@ template <int SP>
 size_t split_smem()
 {
     constexpr int R = SplitShape<SP>::R;
-    return sizeof(float) * ((size_t)R * (SP + 4) + 2 * (size_t)SP + 2 * (size_t)R * (SP / kJC + 4));
+    return sizeof(float) * ((size_t)R * (SP + 4) + 4 * (size_t)SP + 3 * (size_t)R * (SP / kJC + 4));
 }
 
 template <int SP, class Src>
