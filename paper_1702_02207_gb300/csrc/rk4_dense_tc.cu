@@ -15,10 +15,12 @@
 // Accumulation.  Summing all K/16 chunk products of a stage into one TMEM
 // accumulator lets the tensor core's accumulation rounding build up a bias that
 // acts like a frequency shift, so the error grew with the horizon (bf16x5 at
-// s = 256: 2.4e-5 after 5e3 steps).  bf16x5 and bf16x6 therefore give each
-// 16-wide K chunk its own accumulator (K/16 x 32 TMEM columns) and add the
-// chunk sums on the CUDA cores in FP32 round-to-nearest (s = 256: 5.9e-6, for
-// 10 % more time); bf16x3, whose truncation error dominates, keeps one.
+// s = 256: 2.4e-5 after 5e3 steps).  bf16x5 and bf16x6 therefore spread the chunk
+// products over several accumulators and add those on the CUDA cores in FP32
+// round-to-nearest: one per 16-wide K chunk in the 2-CTA clusters (s = 256: 5.9e-6
+// after 5e3 steps), one per two chunks in the one-CTA kernel (s = 128: 6.4e-6
+// against 5.6e-6 with one per chunk, 5.5 % faster); bf16x3, whose truncation
+// error dominates, keeps one.
 
 // Work split.  s <= 64: one CTA per 64 instances, two tiles of 32 stacked along
 // the 128 rows against the block-diagonal [B 0; 0 B] (the MMA shape is fixed at
@@ -915,10 +917,10 @@ cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int
             return pack ? launch_tc_pair<2, 2, 1, 2>(sys, src, n_inst, st) : launch_tc_pair<2, 2, 1, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X5:
             if (two) return launch_tc<3, 2, 2>(sys, src, n_inst, st);
-            return pack ? launch_tc_pair<3, 2, 8, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 2, 8, 1>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 2, 4, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 2, 4, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
             if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
-            return pack ? launch_tc_pair<3, 3, 8, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 3, 8, 1>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 3, 4, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 3, 4, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
 }
