@@ -881,7 +881,9 @@ template <int PA, int PB, int CS, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
-    constexpr int NACC = PA == 2 ? 1 : KC;           // bf16x3: one accumulator; x5/x6: one per K chunk
+    // bf16x3: one accumulator; x5/x6: one per K chunk (one per two chunks measured slower
+    // here, 366 against 356 ms at s = 256, and less accurate, 7.5e-6 against 5.9e-6)
+    constexpr int NACC = PA == 2 ? 1 : KC;
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
     auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
