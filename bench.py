@@ -441,6 +441,15 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
                                             "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak,
                                                          "unit": "TFLOP/s", "frac": ach / alu_peak}}
     cho.cho_destroy_system(s_)
+    # the same chains, 1e3 steps, in FP64 and in double-FP32 (FP64-class accuracy on the FP32 pipe)
+    cfg_l = dict(cfg, n_steps=1000)
+    s_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+    for prec in ("fp64", "fp32x2"):
+        t = timed(s_, cfg_l, prec, cfg_l["n_steps"])
+        dof = cfg_l["x0"].size * cfg_l["n_steps"]
+        res[f"chain_s1024_x4096_{prec}"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": 1000,
+                                            "error_vs_oracle": sampled_err(s_, cfg_l, prec, every=250)}
+    cho.cho_destroy_system(s_)
     # the same chains with a dashpot beside every spring (damping ratios of a few percent) and a
     # harmonic force on every mass (beyond the paper's undamped model)
     rng = np.random.default_rng(inputs.SEED_BASE + 6)

@@ -577,8 +577,10 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
         if (b->x_traj || b->v_traj || b->energy) return fail(CHO_EINVAL, "%s: no checkpoints in the plain form", who);
     } else if (p == CHO_FP64 || p == CHO_FP32_KAHAN) {
     } else if (p == CHO_FP32X2) {
-        if (sys->path != PATH_SMALL || sys->s != 2)
-            return fail(CHO_EINVAL, "%s: CHO_FP32X2 integrates s = 2 systems", who);
+        const bool two = sys->path == PATH_SMALL && sys->s == 2;
+        const bool chain = sys->path == PATH_CHAIN && sys->s <= 1024;
+        if (!two && !chain)
+            return fail(CHO_EINVAL, "%s: CHO_FP32X2 integrates s = 2 systems and spring chains of 32 < s <= 1024", who);
     } else if (p == CHO_DENSE_FP32_SIMT || p == CHO_DENSE_BF16X3 || p == CHO_DENSE_BF16X5 || p == CHO_DENSE_BF16X6) {
         if (sys->kind != CHO_DENSE) return fail(CHO_EINVAL, "%s: precision %d is for dense systems", who, p);
         if ((p != CHO_DENSE_FP32_SIMT) && (sys->path != PATH_DENSE || sys->s_tc == 0))
@@ -739,7 +741,7 @@ cho_status run_device_batch(cho_ctx* ctx, const cho_batch_desc* b, cudaStream_t 
     } else if (sys->path == PATH_CHAIN) {
         ChainSys cs{sys->s, sys->n_sys != 1 ? 1 : 0, sys->d_B64, sys->d_B32};
         cs.dofs_per_thread = kc.chain_dofs;
-        e = launch_rk4_chain(cs, io, fp64, st);
+        e = b->prec == CHO_FP32X2 ? launch_rk4_chain_dw(cs, io, st) : launch_rk4_chain(cs, io, fp64, st);
     } else if (b->poly_jump > 0) {
         // polynomial form of a shared dense system: one h for the whole batch
         const size_t nh = b->h_per_inst ? (size_t)b->n_inst : 1;

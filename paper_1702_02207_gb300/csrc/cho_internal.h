@@ -121,6 +121,8 @@ int chain_dofs_per_thread(int s);
 // threads; P = 8: at most 1024).
 bool chain_dofs_valid(int s, int P);
 cudaError_t launch_rk4_chain(const ChainSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
+// Double-FP32 (CHO_FP32X2) for chains of s <= 1024, 4 DOFs per thread, batch form.
+cudaError_t launch_rk4_chain_dw(const ChainSys& sys, const BatchIO& io, cudaStream_t st);
 
 // ---- rk4_chain_ext: the chain with dashpots and harmonic forcing -------------------
 // Per parameter set and DOF i (FP64 [n_sys][5][s], FP32 [n_sys][10][s]: the five hi

@@ -277,6 +277,127 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     if (t == 0) src.finish(q, n, any_bad != 0);
 }
 
+// Double-FP32 (CHO_FP32X2): the FP64 form of rk4_chain_kernel, operation for
+// operation, in the pair arithmetic of rk4_common.cuh (dw).  P = 4 DOFs per thread
+// (a pair state takes twice the registers of FP32).  The spring extensions
+// e_i = x_i - x_{i-1} start with an exact TwoSum of the high parts, so close
+// neighbours keep their difference to about 2^-48 of the displacement.
+template <int P>
+__global__ void __launch_bounds__(256) rk4_chain_dw_kernel(const ChainBatchSrc<true> src)
+{
+    __shared__ float2 edge_last[2][8][32];   // last DOF of every thread (hi, lo), [buffer][warp][lane]
+    __shared__ float2 edge_first[2][8][32];  // first DOF of every thread
+    const int64_t q = blockIdx.x;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const int s = src.s(q);
+    const int i0 = t * P;
+
+    dw g[P], u[P];
+    {
+        const double* c = (const double*)src.coef(q);   // [2][s]: g, u
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int i = i0 + p;
+            g[p] = dw_split(i < s ? c[i] : 0.0);
+            u[p] = dw_split(i < s ? c[s + i] : 0.0);
+        }
+    }
+    const double hd = src.h(q);
+    const dw h = dw_split(hd), h2 = dw_split(0.5 * hd), h6 = dw_split(hd / 6.0);
+    dw x[P], v[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        double xd = 0.0, vd = 0.0;
+        float e0, e1;
+        if (i0 + p < s) src.load(q, i0 + p, xd, vd, e0, e1);
+        x[p] = dw_split(xd);
+        v[p] = dw_split(vd);
+    }
+
+    int buf = 0;
+    const int wl = warp > 0 ? warp - 1 : 0;
+    const int wr = warp + 1 < nwarp ? warp + 1 : warp;
+    const bool has_left = warp > 0, has_right = warp + 1 < nwarp;
+    auto shfl = [&](dw a, int d, bool up) -> dw {
+        return up ? dw{__shfl_up_sync(0xffffffffu, a.hi, d), __shfl_up_sync(0xffffffffu, a.lo, d)}
+                  : dw{__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
+    };
+    // a_i = u_i e_{i+1} - g_i e_i, as the FP64 form's fma(u, e_{i+1}, -g e_i)
+    auto accel = [&](const dw (&xs)[P], dw (&acc)[P]) {
+        const dw up = shfl(xs[P - 1], 1, true);
+        const dw dn = shfl(xs[0], 1, false);
+        edge_last[buf][warp][lane] = make_float2(xs[P - 1].hi, xs[P - 1].lo);
+        edge_first[buf][warp][lane] = make_float2(xs[0].hi, xs[0].lo);
+        __syncthreads();
+        const float2 el2 = edge_last[buf][wl][31], ef2 = edge_first[buf][wr][0];
+        const dw el = has_left ? dw{el2.x, el2.y} : dw{0.f, 0.f};
+        const dw ef = has_right ? dw{ef2.x, ef2.y} : dw{0.f, 0.f};
+        const dw left = lane == 0 ? el : up;
+        const dw right = lane == 31 ? ef : dn;
+        buf ^= 1;
+        dw e[P + 1];
+        e[0] = dw_add(xs[0], dw_neg(left));
+#pragma unroll
+        for (int p = 1; p < P; ++p) e[p] = dw_add(xs[p], dw_neg(xs[p - 1]));
+        e[P] = dw_add(right, dw_neg(xs[P - 1]));
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p] = dw_fma(u[p], e[p + 1], dw_neg(dw_mul(g[p], e[p])));
+    };
+
+    const int64_t n = src.steps(q);
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        repeat_steps(every, [&]() {
+            dw a[P], xs[P], kx[P], kv[P], vs[P];
+            accel(x, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = v[p];
+                kv[p] = a[p];
+                xs[p] = dw_fma(h2, v[p], x[p]);
+                vs[p] = dw_fma(h2, a[p], v[p]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = dw_add(dw_twice(vs[p]), kx[p]);
+                kv[p] = dw_add(dw_twice(a[p]), kv[p]);
+                xs[p] = dw_fma(h2, vs[p], x[p]);
+                vs[p] = dw_fma(h2, a[p], v[p]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = dw_add(dw_twice(vs[p]), kx[p]);
+                kv[p] = dw_add(dw_twice(a[p]), kv[p]);
+                xs[p] = dw_fma(h, vs[p], x[p]);
+                vs[p] = dw_fma(h, a[p], v[p]);
+            }
+            accel(xs, a);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                kx[p] = dw_add(kx[p], vs[p]);
+                kv[p] = dw_add(kv[p], a[p]);
+                x[p] = dw_fma(h6, kx[p], x[p]);
+                v[p] = dw_fma(h6, kv[p], v[p]);
+            }
+        });
+        if (src.ckpt_every() > 0) {
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (i0 + p < s) src.checkpoint(q, ck, i0 + p, dw_value(x[p]), dw_value(v[p]), 0.f, 0.f);
+            ++ck;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (i0 + p < s) src.store(q, i0 + p, dw_value(x[p]), dw_value(v[p]), 0.f, 0.f);
+}
+
 template <int P, bool F64, class Src>
 cudaError_t launch_p(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
 {
@@ -348,6 +469,19 @@ cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaS
     }
     ChainSlotSrc<false> s{io};
     return launch_any<false>(s, io.n_inst, s_max, st);
+}
+
+cudaError_t launch_rk4_chain_dw(const ChainSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    constexpr int P = 4;
+    int threads = (sys.s + P - 1) / P;
+    threads = ((threads + 31) / 32) * 32;
+    if (threads > 256 || !sys.C64) return cudaErrorInvalidValue;
+    if (io.n_inst <= 0) return cudaSuccess;
+    if (io.n_inst > 0x7fffffffLL) return cudaErrorInvalidValue;
+    ChainBatchSrc<true> src{sys, io};
+    rk4_chain_dw_kernel<P><<<(unsigned)io.n_inst, threads, 0, st>>>(src);
+    return cudaGetLastError();
 }
 
 }  // namespace cho

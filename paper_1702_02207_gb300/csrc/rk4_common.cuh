@@ -85,6 +85,54 @@ __device__ __forceinline__ void state_update(std::conditional_t<F64, double, flo
     }
 }
 
+// ---- double-FP32 ("double-word") arithmetic -----------------------------------------
+//
+// GB300 runs FP64 at about 1/64 of the FP32 rate (a dependent FP64 FMA takes 64
+// cycles), so FP64-class accuracy is cheaper as unevaluated pairs hi + lo of FP32
+// numbers.  The pieces are the classical error-free transformations: Knuth's TwoSum,
+// FastTwoSum (|a| >= |b|) and the FMA form of TwoProd (a b = p + e exactly with
+// e = fma(a, b, -p)).  Sums use one TwoSum of the high parts plus the low parts
+// ("sloppy" double-word addition: its error is a few units of 2^-48 of the larger
+// operand); products use TwoProd of the high parts and the two cross terms.
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_split(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double dw_value(dw a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dw fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y)
+{
+    const dw s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dw dw_fma(dw a, dw b, dw c) { return dw_add(dw_mul(a, b), c); }
+__device__ __forceinline__ dw dw_neg(dw a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dw dw_twice(dw a) { return {2.f * a.hi, 2.f * a.lo}; }
+
+
 // ---- thread-block clusters ------------------------------------------------------
 __device__ __forceinline__ uint32_t cluster_rank()
 {

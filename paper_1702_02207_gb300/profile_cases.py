@@ -6,6 +6,7 @@ Cases (each one cho_integrate_batch call, a few MB of device memory):
   pair      65,536 two-DOF systems, 1e4 steps, fp32_kahan   (rk4_pair2_balanced, the benchmark launch)
   pair_dw   65,536 two-DOF systems, 2000 steps, fp32x2      (rk4_dw2, double-FP32)
   chain     512 chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain<8>)
+  chain_dw  512 chains of 1024 masses, 500 steps, fp32x2    (rk4_chain_dw<4>, double-FP32)
   dense_tc  s = 128, 2048 instances, 500 steps, bf16x5       (rk4_dense_tc, one CTA per SM)
   dense_tc64 s = 64, 4096 instances, 500 steps, bf16x5      (rk4_dense_tc, two tiles stacked per CTA)
   dense_tc2 s = 256, 2048 instances, 200 steps, bf16x5       (rk4_dense_tc, 2-CTA clusters)
@@ -36,6 +37,8 @@ def run(case: str) -> None:
             cfg, prec, kind = inputs.two_dof_batch(n_steps=2000), "fp32x2", "two_dof"
         elif case == "chain":
             cfg, prec, kind = inputs.chain_batch(n_inst=512, n_steps=2000), "fp32_kahan", "chain"
+        elif case == "chain_dw":
+            cfg, prec, kind = inputs.chain_batch(n_inst=512, n_steps=500), "fp32x2", "chain"
         elif case == "dense_tc":
             cfg, prec, kind = inputs.dense_group(s=128, n_inst=2048, n_steps=500), "bf16x5", "dense"
         elif case == "dense_tc64":

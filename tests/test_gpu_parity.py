@@ -1045,15 +1045,63 @@ def test_fp32x2_two_dof_batch(n_inst):
         cho.cho_shutdown(c)
 
 
+@pytest.mark.parametrize("s", [33, 64, 127, 128, 129, 255, 256, 500, 1023, 1024])
+def test_fp32x2_chains(s):
+    """Spring chains in double-FP32 (four DOFs per thread, one CTA per chain; s not a
+    multiple of 4 or of 128 leaves ragged threads and warps): within the FP64 mode's bar."""
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.chain_batch(n_inst=5, s=s, n_steps=2000, seed=1900 + s)
+        out = run_gpu(c, cfg, "fp32x2", 250)
+        ref = oracle_run(cfg, ckpt_every=250)
+        ex, ev = check(out, ref, TOL_FP64)
+        print(f"fp32x2 chain s={s}: x {ex:.3e} v {ev:.3e}")
+    finally:
+        cho.cho_shutdown(c)
+
+
+def test_fp32x2_chain_shared_parameters_and_host_arrays():
+    """One (masses, springs) set for the whole batch, per-instance h, host arrays."""
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.chain_batch(n_inst=9, s=300, n_steps=1000, seed=77)
+        cfg = dict(cfg, masses=cfg["masses"][:1], springs=cfg["springs"][:1])
+        out = run_gpu(c, cfg, "fp32x2", 125, device=False)
+        ref = oracle_run(cfg, ckpt_every=125)
+        check(out, ref, TOL_FP64)
+    finally:
+        cho.cho_shutdown(c)
+
+
+def test_fp32x2_chain_full_size_sampled():
+    """4096 chains of 1024 masses x 1e4 steps in double-FP32, sampled against the oracle."""
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.chain_batch()
+        out = run_gpu(c, cfg, "fp32x2", 625)
+        idx = sample_indices(cfg["x0"].shape[0], 6)
+        ref = oracle_run(cfg, idx=idx, ckpt_every=625)
+        ex, ev = check(out, ref, TOL_FP64, idx)
+        print(f"fp32x2 chain 4096 x 1024 sampled: x {ex:.3e} v {ev:.3e}")
+    finally:
+        cho.cho_shutdown(c)
+
+
 def test_fp32x2_is_refused_outside_its_scope():
     c = cho.cho_init(0)
     try:
-        ch = inputs.chain_batch(n_inst=2, s=40, n_steps=10)
-        sys_ = make_system(c, ch)
-        with pytest.raises(cho.ChoError) as ei:
-            cho.cho_integrate_batch(c, sys_, ch["x0"], ch["v0"], ch["h"], 10, "fp32x2")
-        assert ei.value.status == cho.CHO_EINVAL
-        cho.cho_destroy_system(sys_)
+        for s in (5, 1040):      # small chains other than s = 2; chains beyond 1024 DOFs
+            ch = inputs.chain_batch(n_inst=2, s=s, n_steps=10)
+            sys_ = make_system(c, ch)
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(c, sys_, ch["x0"], ch["v0"], ch["h"], 10, "fp32x2")
+            assert ei.value.status == cho.CHO_EINVAL
+            cho.cho_destroy_system(sys_)
+        dn = inputs.dense_group(s=64, n_inst=2, n_steps=10)
+        sysd = cho.cho_create_system(c, "dense", M=dn["M"], K=dn["K"])
+        with pytest.raises(cho.ChoError):
+            cho.cho_integrate_batch(c, sysd, dn["x0"], dn["v0"], dn["h"], 10, "fp32x2")
+        cho.cho_destroy_system(sysd)
         two = inputs.two_dof_batch(n_inst=2, n_steps=10)
         sys2 = make_system(c, two)
         with pytest.raises(cho.ChoError):
