@@ -76,8 +76,8 @@ typedef enum cho_kind {
  *                        both to 24 bits (s <= 128).  x5/x6 keep each 16-wide K chunk
  *                        in its own accumulator and add the chunks in FP32 (<= 1e-5
  *                        over 5e3 steps at h = T_min/100).
- *   CHO_FP32X2           s = 2 systems (TWO_DOF, CHAIN with s = 2) and spring chains of
- *                        32 < s <= 1024: state, coefficients
+ *   CHO_FP32X2           systems of s <= 32 (any kind) and spring chains of s <= 1024:
+ *                        state, coefficients
  *                        and every operation as unevaluated pairs of FP32 numbers
  *                        (about 48 significant bits; error-free TwoSum / TwoProd on the
  *                        FP32 pipe), the stage form of CHO_FP64.  Within the FP64 mode's

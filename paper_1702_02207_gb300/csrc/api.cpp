@@ -577,10 +577,10 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
         if (b->x_traj || b->v_traj || b->energy) return fail(CHO_EINVAL, "%s: no checkpoints in the plain form", who);
     } else if (p == CHO_FP64 || p == CHO_FP32_KAHAN) {
     } else if (p == CHO_FP32X2) {
-        const bool two = sys->path == PATH_SMALL && sys->s == 2;
+        const bool small = sys->path == PATH_SMALL;
         const bool chain = sys->path == PATH_CHAIN && sys->s <= 1024;
-        if (!two && !chain)
-            return fail(CHO_EINVAL, "%s: CHO_FP32X2 integrates s = 2 systems and spring chains of 32 < s <= 1024", who);
+        if (!small && !chain)
+            return fail(CHO_EINVAL, "%s: CHO_FP32X2 integrates systems of s <= 32 and spring chains of s <= 1024", who);
     } else if (p == CHO_DENSE_FP32_SIMT || p == CHO_DENSE_BF16X3 || p == CHO_DENSE_BF16X5 || p == CHO_DENSE_BF16X6) {
         if (sys->kind != CHO_DENSE) return fail(CHO_EINVAL, "%s: precision %d is for dense systems", who, p);
         if ((p != CHO_DENSE_FP32_SIMT) && (sys->path != PATH_DENSE || sys->s_tc == 0))

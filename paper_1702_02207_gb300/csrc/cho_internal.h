@@ -101,7 +101,7 @@ struct SmallSys {
 };
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
-// Double-FP32 (CHO_FP32X2) for S = 2 systems, one thread per instance.
+// Double-FP32 (CHO_FP32X2) for s <= 32 systems (padded S = 2 .. 32), the lanes of rk4_small.
 cudaError_t launch_rk4_small_dw(const SmallSys& sys, const BatchIO& io, cudaStream_t st);
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st);
 

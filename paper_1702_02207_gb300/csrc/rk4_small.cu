@@ -31,6 +31,7 @@ namespace cho {
 namespace {
 
 constexpr int rows_per_lane(int S) { return S <= 4 ? S : (S == 8 ? 2 : 1); }
+constexpr int kDwThreads = 128;   // threads per CTA of the double-FP32 kernel
 
 // ---- instance sources ----------------------------------------------------------
 
@@ -968,43 +969,83 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
 }
 
 
-// ---- double-FP32: s = 2 systems with about 48 significant bits on the FP32 pipe ------
+// ---- double-FP32: s <= 32 systems with about 48 significant bits on the FP32 pipe ----
 //
-// The step is the FP64 mode's stage form, operation for operation, in the pair
-// arithmetic of rk4_common.cuh (dw); coefficients, h, h/2 and h/6 are split from FP64.
-__global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const BatchIO io)
+// The step is the FP64 mode's stage form (rk4_small_kernel<S, true>), operation for
+// operation, in the pair arithmetic of rk4_common.cuh (dw): the same lanes per instance
+// and rows per lane, the same column order of B x (from the diagonal for S <= 4, from
+// column 0 with the shared-memory exchange above), B, h, h/2 and h/6 split from FP64.
+// Batch form only.
+template <int S>
+__global__ void __launch_bounds__(kDwThreads) rk4_dw_small_kernel(const SmallSys sys, const BatchIO io)
 {
-    const int64_t q = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    if (q >= io.n_inst) return;
+    constexpr int R = rows_per_lane(S);
+    constexpr int G = S / R;                      // lanes per instance
+    constexpr int GPB = kDwThreads / G;           // groups per block
+    __shared__ float2 xch[G > 1 ? 2 : 1][G > 1 ? GPB : 1][G > 1 ? S : 1];
+
+    const int64_t tid = (int64_t)blockIdx.x * kDwThreads + threadIdx.x;
+    const int64_t q = tid / G;
+    const int g = (int)(tid % G);
+    const int grp = threadIdx.x / G;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+    if (q >= io.n_inst) return;                   // whole groups leave together
+
     const int64_t set = sys.per_inst_sys ? q : 0;
-    const double* Bq = sys.B64 + set * 4;           // [2][2] of the padded S = 2 block
-    dw b[2][2];
+    const double* Bq = sys.B64 + set * S * S;     // padded [S][S]
+    dw b[R][S];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) b[r][j] = dw_split(Bq[r * 2 + j]);
+        for (int j = 0; j < S; ++j) b[r][j] = dw_split(Bq[(g * R + r) * S + j]);
     const double hd = io.h[io.h_per_inst ? q : 0];
     const dw h = dw_split(hd), h2 = dw_split(0.5 * hd), h6 = dw_split(hd / 6.0);
     const int s = sys.s;
-    dw x[2], v[2];
+    dw x[R], v[R];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        x[r] = dw_split(r < s ? io.x0[q * s + r] : 0.0);
-        v[r] = dw_split(r < s ? io.v0[q * s + r] : 0.0);
+    for (int r = 0; r < R; ++r) {
+        const int row = g * R + r;
+        x[r] = dw_split(row < s ? io.x0[q * s + row] : 0.0);
+        v[r] = dw_split(row < s ? io.v0[q * s + row] : 0.0);
     }
-    // a = -(B xs), each row from its diagonal, as the FP64 mode
-    auto accel = [&](const dw (&xs)[2], dw (&a)[2]) {
+    int buf = 0;
+    // a = -(B xs): the first product rounded (the FP64 mode's fma onto zero), then fmas
+    auto accel = [&](const dw (&xs)[R], dw (&a)[R]) {
+        if constexpr (G == 1) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) a[r] = dw_neg(dw_fma(b[r][1 - r], xs[1 - r], dw_mul(b[r][r], xs[r])));
+            for (int r = 0; r < R; ++r) {
+                dw t = dw_mul(b[r][r], xs[r]);
+#pragma unroll
+                for (int jj = 1; jj < S; ++jj) t = dw_fma(b[r][(r + jj) % S], xs[(r + jj) % S], t);
+                a[r] = dw_neg(t);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) xch[buf][grp][g * R + r] = make_float2(xs[r].hi, xs[r].lo);
+            __syncwarp(gmask);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 c = xch[buf][grp][0];
+                dw t = dw_mul(b[r][0], dw{c.x, c.y});
+#pragma unroll
+                for (int j = 1; j < S; ++j) {
+                    c = xch[buf][grp][j];
+                    t = dw_fma(b[r][j], dw{c.x, c.y}, t);
+                }
+                a[r] = dw_neg(t);
+            }
+            buf ^= 1;
+        }
     };
     const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (io.n_steps > 0 ? io.n_steps : 1);
     int64_t ck = 0;
     for (int64_t done = 0; done < io.n_steps; done += every) {
         repeat_steps(every, [&]() {
-            dw a[2], xs[2], kx[2], kv[2], vs[2];
+            dw a[R], xs[R], kx[R], kv[R], vs[R];
             accel(x, a);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < R; ++r) {
                 kx[r] = v[r];
                 kv[r] = a[r];
                 xs[r] = dw_fma(h2, v[r], x[r]);
@@ -1012,7 +1053,7 @@ __global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const 
             }
             accel(xs, a);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < R; ++r) {
                 kx[r] = dw_add(dw_twice(vs[r]), kx[r]);
                 kv[r] = dw_add(dw_twice(a[r]), kv[r]);
                 xs[r] = dw_fma(h2, vs[r], x[r]);
@@ -1020,7 +1061,7 @@ __global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const 
             }
             accel(xs, a);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < R; ++r) {
                 kx[r] = dw_add(dw_twice(vs[r]), kx[r]);
                 kv[r] = dw_add(dw_twice(a[r]), kv[r]);
                 xs[r] = dw_fma(h, vs[r], x[r]);
@@ -1028,7 +1069,7 @@ __global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const 
             }
             accel(xs, a);
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < R; ++r) {
                 kx[r] = dw_add(kx[r], vs[r]);
                 kv[r] = dw_add(kv[r], a[r]);
                 x[r] = dw_fma(h6, kx[r], x[r]);
@@ -1037,9 +1078,10 @@ __global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const 
         });
         if (io.ckpt_every > 0 && io.x_traj) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                if (r >= s) continue;
-                const int64_t o = (q * io.n_ck + ck) * s + r;
+            for (int r = 0; r < R; ++r) {
+                const int row = g * R + r;
+                if (row >= s) continue;
+                const int64_t o = (q * io.n_ck + ck) * s + row;
                 io.x_traj[o] = dw_value(x[r]);
                 if (io.v_traj) io.v_traj[o] = dw_value(v[r]);
             }
@@ -1047,11 +1089,23 @@ __global__ void __launch_bounds__(128) rk4_dw2_kernel(const SmallSys sys, const 
         ++ck;
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        if (r >= s) continue;
-        io.x_out[q * s + r] = dw_value(x[r]);
-        io.v_out[q * s + r] = dw_value(v[r]);
+    for (int r = 0; r < R; ++r) {
+        const int row = g * R + r;
+        if (row >= s) continue;
+        io.x_out[q * s + row] = dw_value(x[r]);
+        io.v_out[q * s + row] = dw_value(v[r]);
     }
+}
+
+template <int S>
+cudaError_t launch_dw_one(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
+{
+    constexpr int G = S / rows_per_lane(S);
+    const int64_t blocks = (io.n_inst * G + kDwThreads - 1) / kDwThreads;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    rk4_dw_small_kernel<S><<<(unsigned)blocks, kDwThreads, 0, st>>>(sys, io);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -1096,12 +1150,15 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
 
 cudaError_t launch_rk4_small_dw(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
 {
-    if (sys.S != 2 || !sys.B64) return cudaErrorInvalidValue;
-    const int64_t blocks = (io.n_inst + 127) / 128;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    rk4_dw2_kernel<<<(unsigned)blocks, 128, 0, st>>>(sys, io);
-    return cudaGetLastError();
+    if (!sys.B64) return cudaErrorInvalidValue;
+    switch (sys.S) {
+        case 2: return launch_dw_one<2>(sys, io, st);
+        case 4: return launch_dw_one<4>(sys, io, st);
+        case 8: return launch_dw_one<8>(sys, io, st);
+        case 16: return launch_dw_one<16>(sys, io, st);
+        case 32: return launch_dw_one<32>(sys, io, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st)

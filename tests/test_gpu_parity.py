@@ -1045,6 +1045,39 @@ def test_fp32x2_two_dof_batch(n_inst):
         cho.cho_shutdown(c)
 
 
+@pytest.mark.parametrize("s", [1, 3, 4, 5, 8, 9, 13, 16, 17, 31, 32])
+def test_fp32x2_small_chains(s):
+    """Chains of s <= 32 in double-FP32 on the small-system lanes (padded S = 2 .. 32: one
+    lane holds S <= 4 rows, S = 8 two rows per lane, S >= 16 one): within the FP64 mode's bar."""
+    c = cho.cho_init(0)
+    try:
+        cfg = inputs.chain_batch(n_inst=67, s=s, n_steps=2000, seed=2900 + s)
+        # checkpoints every 125 steps: at 100 steps per period of the fastest mode a 250-step
+        # stride meets s = 1 (one mode) at v = 0 every time
+        out = run_gpu(c, cfg, "fp32x2", 125)
+        ref = oracle_run(cfg, ckpt_every=125)
+        ex, ev = check(out, ref, TOL_FP64)
+        print(f"fp32x2 small chain s={s}: x {ex:.3e} v {ev:.3e}")
+    finally:
+        cho.cho_shutdown(c)
+
+
+@pytest.mark.parametrize("s", [3, 6, 8, 13, 32])
+def test_fp32x2_small_dense(s):
+    """Dense (M, K) of s <= 32 in double-FP32: one (M, K) per instance, and one shared."""
+    c = cho.cho_init(0)
+    try:
+        cfg = dense_per_instance(s, 21, 40 + s)
+        out = run_gpu(c, cfg, "fp32x2", 125)
+        check(out, oracle_run(cfg, ckpt_every=125), TOL_FP64)
+        cfg = inputs.dense_group(s=s, n_inst=37, n_steps=1000)
+        out = run_gpu(c, cfg, "fp32x2", 125)
+        ex, ev = check(out, oracle_run(cfg, ckpt_every=125), TOL_FP64)
+        print(f"fp32x2 small dense s={s}: x {ex:.3e} v {ev:.3e}")
+    finally:
+        cho.cho_shutdown(c)
+
+
 @pytest.mark.parametrize("s", [33, 64, 127, 128, 129, 255, 256, 500, 1023, 1024])
 def test_fp32x2_chains(s):
     """Spring chains in double-FP32 (four DOFs per thread, one CTA per chain; s not a
@@ -1090,13 +1123,12 @@ def test_fp32x2_chain_full_size_sampled():
 def test_fp32x2_is_refused_outside_its_scope():
     c = cho.cho_init(0)
     try:
-        for s in (5, 1040):      # small chains other than s = 2; chains beyond 1024 DOFs
-            ch = inputs.chain_batch(n_inst=2, s=s, n_steps=10)
-            sys_ = make_system(c, ch)
-            with pytest.raises(cho.ChoError) as ei:
-                cho.cho_integrate_batch(c, sys_, ch["x0"], ch["v0"], ch["h"], 10, "fp32x2")
-            assert ei.value.status == cho.CHO_EINVAL
-            cho.cho_destroy_system(sys_)
+        ch = inputs.chain_batch(n_inst=2, s=1040, n_steps=10)      # chains beyond 1024 DOFs
+        sys_ = make_system(c, ch)
+        with pytest.raises(cho.ChoError) as ei:
+            cho.cho_integrate_batch(c, sys_, ch["x0"], ch["v0"], ch["h"], 10, "fp32x2")
+        assert ei.value.status == cho.CHO_EINVAL
+        cho.cho_destroy_system(sys_)
         dn = inputs.dense_group(s=64, n_inst=2, n_steps=10)
         sysd = cho.cho_create_system(c, "dense", M=dn["M"], K=dn["K"])
         with pytest.raises(cho.ChoError):
