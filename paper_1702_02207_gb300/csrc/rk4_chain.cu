@@ -277,6 +277,178 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     if (t == 0) src.finish(q, n, any_bad != 0);
 }
 
+// FP32 with P >= 2 DOFs per thread in packed FP32x2 arithmetic: the step of
+// rk4_chain_kernel<P, false>, every packed operation rounding each lane as the scalar
+// one does (the same bits), with DOF p of the thread in lane .x and DOF p + P/2 in
+// lane .y of pair p.  That pairing keeps the spring extensions on aligned pairs,
+// E_k = (e_k, e_{k+P/2}) = X_k - X_{k-1}, and leaves two pairs per stage to assemble
+// from scalars: (left neighbour, x_{P/2-1}) for E_0 and (x_{P/2}, right neighbour)
+// for E_{P/2}.  Packing halves the FP32 instructions the stage issues.
+template <int P, int MAXT, class Src>
+__global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
+{
+    static_assert(P >= 2 && P % 2 == 0, "pairs of DOFs");
+    constexpr int H = P / 2;
+    __shared__ float edge_last[2][32][32];   // last DOF of every thread, [buffer][warp][lane]
+    __shared__ float edge_first[2][32][32];  // first DOF of every thread
+    __shared__ int any_bad;
+
+    const int64_t q = blockIdx.x;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const int s = src.s(q);
+    const int i0 = t * P;
+    if (t == 0) any_bad = 0;
+    __syncthreads();
+
+    // coefficients, negated g (zero beyond s: padded DOFs stay at rest)
+    float2 ngh[H], uh[H], ngl[H], ul[H];
+    {
+        const float* c = (const float*)src.coef(q);
+        float gh_[P], uh_[P], gl_[P], ul_[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int i = i0 + p;
+            const bool in = i < s;
+            gh_[p] = in ? c[i] : 0.f;
+            uh_[p] = in ? c[s + i] : 0.f;
+            gl_[p] = in ? c[2 * s + i] : 0.f;
+            ul_[p] = in ? c[3 * s + i] : 0.f;
+            scaled_coef(gh_[p], gl_[p], src.h(q));     // g'' = h^2/36 g, u'' = h^2/36 u
+            scaled_coef(uh_[p], ul_[p], src.h(q));
+        }
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            ngh[k] = make_float2(-gh_[k], -gh_[k + H]);
+            uh[k] = make_float2(uh_[k], uh_[k + H]);
+            ngl[k] = make_float2(-gl_[k], -gl_[k + H]);
+            ul[k] = make_float2(ul_[k], ul_[k + H]);
+        }
+    }
+    const float2 m1 = make_float2(-1.f, -1.f), two = make_float2(2.f, 2.f);
+    const float2 three = make_float2(3.f, 3.f), six = make_float2(6.f, 6.f);
+    float2 x[H], v[H], cx[H], cv[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        float a[2], b[2], ca[2], cb[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int i = i0 + k + l * H;
+            if (i < s) {
+                src.load(q, i, a[l], b[l], ca[l], cb[l]);
+            } else {
+                a[l] = b[l] = ca[l] = cb[l] = 0.f;
+            }
+        }
+        x[k] = make_float2(a[0], a[1]);
+        v[k] = make_float2(b[0], b[1]);
+        cx[k] = make_float2(ca[0], ca[1]);
+        cv[k] = make_float2(cb[0], cb[1]);
+    }
+
+    int buf = 0;
+    const int wl = warp > 0 ? warp - 1 : 0;
+    const int wr = warp + 1 < nwarp ? warp + 1 : warp;
+    const float has_left = warp > 0 ? 1.f : 0.f;
+    const float has_right = warp + 1 < nwarp ? 1.f : 0.f;
+    float2 lo1[H];   // lo parts of g and u times the stage-1 extensions (frozen lo)
+    auto accel = [&](const float2 (&xs)[H], float2 (&acc)[H], bool first) {
+        const float up = __shfl_up_sync(0xffffffffu, xs[H - 1].y, 1);
+        const float dn = __shfl_down_sync(0xffffffffu, xs[0].x, 1);
+        edge_last[buf][warp][lane] = xs[H - 1].y;
+        edge_first[buf][warp][lane] = xs[0].x;
+        __syncthreads();
+        const float el = edge_last[buf][wl][31] * has_left;
+        const float ef = edge_first[buf][wr][0] * has_right;
+        const float left = lane == 0 ? el : up;
+        const float right = lane == 31 ? ef : dn;
+        buf ^= 1;
+        float2 e[H + 1];                     // e[k] = (e_k, e_{k+H}); e[H] = (e_H, e_P)
+        e[0] = __ffma2_rn(make_float2(left, xs[H - 1].x), m1, xs[0]);
+#pragma unroll
+        for (int k = 1; k < H; ++k) e[k] = __ffma2_rn(xs[k - 1], m1, xs[k]);
+        e[H] = __ffma2_rn(xs[H - 1], m1, make_float2(xs[0].y, right));
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            if (first) lo1[k] = __ffma2_rn(ul[k], e[k + 1], __fmul2_rn(ngl[k], e[k]));
+            acc[k] = __ffma2_rn(uh[k], e[k + 1], __ffma2_rn(ngh[k], e[k], lo1[k]));
+        }
+    };
+    // compensated x += k
+    auto comp_add2 = [&](float2& xx, float2& ee, float2 kk) {
+        const float2 y = __fadd2_rn(kk, ee);
+        const float2 tt = __fadd2_rn(xx, y);
+        ee = __ffma2_rn(__ffma2_rn(xx, m1, tt), m1, y);     // y - (t - x)
+        xx = tt;
+    };
+
+    const int64_t n = src.steps(q);
+    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
+    int64_t ck = 0;
+    for (int64_t done = 0; done < n; done += every) {
+        repeat_steps(every, [&]() {
+            float2 a[H], xs[H], kx[H], kv[H], vs[H];
+            accel(x, a, true);
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                kx[k] = v[k];
+                kv[k] = a[k];
+                xs[k] = __ffma2_rn(three, v[k], x[k]);
+                vs[k] = __ffma2_rn(three, a[k], v[k]);
+            }
+            accel(xs, a, false);
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                kx[k] = __ffma2_rn(two, vs[k], kx[k]);
+                kv[k] = __ffma2_rn(two, a[k], kv[k]);
+                xs[k] = __ffma2_rn(three, vs[k], x[k]);
+                vs[k] = __ffma2_rn(three, a[k], v[k]);
+            }
+            accel(xs, a, false);
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                kx[k] = __ffma2_rn(two, vs[k], kx[k]);
+                kv[k] = __ffma2_rn(two, a[k], kv[k]);
+                xs[k] = __ffma2_rn(six, vs[k], x[k]);
+                vs[k] = __ffma2_rn(six, a[k], v[k]);
+            }
+            accel(xs, a, false);
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                kx[k] = __fadd2_rn(kx[k], vs[k]);
+                kv[k] = __fadd2_rn(kv[k], a[k]);
+                comp_add2(x[k], cx[k], kx[k]);
+                comp_add2(v[k], cv[k], kv[k]);
+            }
+        });
+        if (src.ckpt_every() > 0) {
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                if (i0 + k < s) src.checkpoint(q, ck, i0 + k, x[k].x, v[k].x, cx[k].x, cv[k].x);
+                if (i0 + k + H < s) src.checkpoint(q, ck, i0 + k + H, x[k].y, v[k].y, cx[k].y, cv[k].y);
+            }
+            ++ck;
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        if (i0 + k < s) {
+            src.store(q, i0 + k, x[k].x, v[k].x, cx[k].x, cv[k].x);
+            bad |= !(isfinite(x[k].x) && isfinite(v[k].x));
+        }
+        if (i0 + k + H < s) {
+            src.store(q, i0 + k + H, x[k].y, v[k].y, cx[k].y, cv[k].y);
+            bad |= !(isfinite(x[k].y) && isfinite(v[k].y));
+        }
+    }
+    if (bad) any_bad = 1;
+    __syncthreads();
+    if (t == 0) src.finish(q, n, any_bad != 0);
+}
+
 // Double-FP32 (CHO_FP32X2): the FP64 form of rk4_chain_kernel, operation for
 // operation, in the pair arithmetic of rk4_common.cuh (dw).  P = 4 DOFs per thread
 // (a pair state takes twice the registers of FP32).  The spring extensions
@@ -408,11 +580,13 @@ cudaError_t launch_p(const Src& src, int64_t n_inst, int s_max, cudaStream_t st)
     if (n_inst > 0x7fffffffLL) return cudaErrorInvalidValue;
     if constexpr (P == 8) {
         if (threads > 256) {   // s > 2048: wide CTAs, 64 registers per thread
-            rk4_chain_kernel<P, F64, kChainMaxThreads, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+            if constexpr (F64) rk4_chain_kernel<P, F64, kChainMaxThreads, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+            else rk4_chain_pk_kernel<P, kChainMaxThreads, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
             return cudaGetLastError();
         }
     }
-    rk4_chain_kernel<P, F64, 256, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+    if constexpr (!F64 && P >= 2) rk4_chain_pk_kernel<P, 256, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
+    else rk4_chain_kernel<P, F64, 256, Src><<<(unsigned)n_inst, threads, 0, st>>>(src);
     return cudaGetLastError();
 }
 
