@@ -574,7 +574,7 @@ def _run_ext(ctx, cfg, ext, prec, every):
         cho.cho_destroy_system(sys_)
 
 
-@pytest.mark.parametrize("s", [1, 2, 3, 64, 300, 1024])
+@pytest.mark.parametrize("s", [1, 2, 3, 64, 300, 513, 1024])
 @pytest.mark.parametrize("mode", ["damped", "forced", "both"])
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
 def test_damped_forced_chain_matches_oracle(ctx, s, mode, prec, tol):
