@@ -15,6 +15,10 @@
 // thread: inside a warp these come by shuffle, across warps through a
 // double-buffered shared-memory edge array, so each stage costs a single
 // __syncthreads.  Stage order and the state update are those of rk4_small.cu.
+//
+// Kernels: rk4_chain_kernel (FP64 at every P; FP32 at P = 1), rk4_chain_pk_kernel
+// (FP32 at P >= 2: the same operations on packed pairs of DOFs, the same bits) and
+// rk4_chain_dw_kernel (double-FP32, CHO_FP32X2).
 #include "cho_internal.h"
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
