@@ -450,6 +450,17 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
         res[f"chain_s1024_x4096_{prec}"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": 1000,
                                             "error_vs_oracle": sampled_err(s_, cfg_l, prec, every=250)}
     cho.cho_destroy_system(s_)
+    # small chains (the lane-group kernels, s <= 32): 131,072 DOFs, 1e3 steps, FP64 against double-FP32
+    for sv in (4, 8, 16, 32):
+        cfg_s = inputs.chain_batch(n_inst=131072 // sv, s=sv, n_steps=1000)
+        s_ = cho.cho_create_system(ctx, "chain", masses=cfg_s["masses"], springs=cfg_s["springs"])
+        for prec in ("fp64", "fp32x2"):
+            t = timed(s_, cfg_s, prec, cfg_s["n_steps"])
+            dof = cfg_s["x0"].size * cfg_s["n_steps"]
+            res[f"chain_s{sv}_x{131072 // sv}_{prec}"] = {
+                "value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": 1000,
+                "error_vs_oracle": sampled_err(s_, cfg_s, prec, every=125)}
+        cho.cho_destroy_system(s_)
     # the same chains with a dashpot beside every spring (damping ratios of a few percent) and a
     # harmonic force on every mass (beyond the paper's undamped model)
     rng = np.random.default_rng(inputs.SEED_BASE + 6)
