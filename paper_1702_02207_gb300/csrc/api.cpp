@@ -683,7 +683,7 @@ bool tune_key(const cho_system_impl* sys, int64_t n_inst, int32_t prec, int32_t 
         *key = {PATH_SMALL, sys->S, prec, per, bucket + (poly_jump > 0 ? 64 : 0)};
         return true;
     }
-    if (sys->path == PATH_CHAIN && poly_jump == 0) {
+    if (sys->path == PATH_CHAIN && poly_jump == 0 && prec != CHO_FP32X2) {   // double-FP32: one kernel
         *key = {PATH_CHAIN, sys->s, prec, per, bucket};
         return true;
     }

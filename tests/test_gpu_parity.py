@@ -1105,6 +1105,11 @@ def test_fp32x2_chain_shared_parameters_and_host_arrays():
         out = run_gpu(c, cfg, "fp32x2", 125, device=False)
         ref = oracle_run(cfg, ckpt_every=125)
         check(out, ref, TOL_FP64)
+        # one double-FP32 chain kernel: nothing for the tuner to choose or record
+        sys_ = make_system(c, cfg)
+        r = cho.cho_autotune(c, sys_, 9, "fp32x2")
+        assert len(r["variants"]) == 1 and cho.cho_tune_query(c, sys_, 9, "fp32x2") == -1
+        cho.cho_destroy_system(sys_)
     finally:
         cho.cho_shutdown(c)
 
