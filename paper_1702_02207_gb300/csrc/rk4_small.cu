@@ -973,9 +973,10 @@ cudaError_t launch_pair2_balanced(const SmallSys& sys, const BatchIO& io, cudaSt
 //
 // The step is the FP64 mode's stage form (rk4_small_kernel<S, true>), operation for
 // operation, in the pair arithmetic of rk4_common.cuh (dw): the same lanes per instance
-// and rows per lane, the same column order of B x (from the diagonal for S <= 4, from
-// column 0 with the shared-memory exchange above), B, h, h/2 and h/6 split from FP64.
-// Batch form only.
+// and rows per lane, and the same column order of B x (S <= 4: one lane per instance,
+// each row from its diagonal onwards; S >= 8: lane groups that exchange x as (hi, lo)
+// through shared memory, each row from column 0).  B, h, h/2 and h/6 are split from
+// FP64.  Batch form only.
 template <int S>
 __global__ void __launch_bounds__(kDwThreads) rk4_dw_small_kernel(const SmallSys sys, const BatchIO io)
 {
