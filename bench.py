@@ -68,8 +68,31 @@ def measured_peaks():
 
 
 def fp32_alu_peak_tflops(sm_count, mhz):
-    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    """FP32 FMA peak derived from unit counts: SMs x 128 FP32 lanes x 2 flops x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measure_alu_peaks(cho, ctx, index):
+    """Measured FMA throughput of the CUDA cores (cho_measure_fma_peak: independent FMA chains
+    on a full-occupancy grid, CUDA events), with the SM clock sampled while it runs.  The FP32
+    peak is the larger of the scalar and packed-pair rates."""
+    sampler = ClockSampler(index)
+    sampler.start()
+    out = {}
+    for kind, iters in (("fp32", 40000), ("fp32x2", 20000), ("fp64", 800)):
+        best, sec = 0.0, 0.0
+        for _ in range(3):
+            f, t = cho.cho_measure_fma_peak(ctx, kind, iters)
+            if f > best:
+                best, sec = f, t
+        out[kind] = {"tflops": best / 1e12, "launch_s": sec}
+    clk = sampler.stop()
+    out["fp32_peak_tflops"] = max(out["fp32"]["tflops"], out["fp32x2"]["tflops"])
+    out["fp64_peak_tflops"] = out["fp64"]["tflops"]
+    out["clocks"] = clk
+    out["how"] = ("cho_measure_fma_peak: 8 independent FMA chains per thread, full-occupancy grid, best of 3 "
+                  "CUDA-event-timed launches after a warm-up")
+    return out
 
 
 class ClockSampler:
@@ -131,6 +154,35 @@ def log(msg):
 
 def percentile(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def host_cores():
+    """Host cores this process may use."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_periodic_mode(cho, inputs, seconds=5.0):
@@ -277,23 +329,25 @@ def oracle_sample_rate(cfg, n_sample, threads=1):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on this host's cores, a bounded sample per step."""
+    """Reference arm: the FP64 oracle on all of this host's cores (instances partitioned over
+    threads, the same single-threaded C function on each slice), a bounded sample per step."""
     rank, _, world = dist_env()
     if world > 1 and rank != 0:
         return
     from paper_1702_02207_gb300 import inputs
 
+    cores = host_cores()
     cfg = inputs.two_dof_batch(n_inst=N_INST, n_steps=N_STEPS)
     oracle_sample_rate(cfg, 16)  # build the oracle
-    _, t_cal = oracle_sample_rate(cfg, 64)
+    _, t_cal = oracle_sample_rate(cfg, 64 * cores, threads=cores)
     # per-step sample sized so that warm-up plus timed steps take about two minutes
     per_step_s = 120.0 / max(1, args.steps + args.warmup)
-    n_sample = int(max(16, min(N_INST, per_step_s / (t_cal / 64))))
+    n_sample = int(max(16 * cores, min(N_INST, per_step_s / (t_cal / (64 * cores)))))
     for _ in range(args.warmup):
-        oracle_sample_rate(cfg, n_sample)
+        oracle_sample_rate(cfg, n_sample, threads=cores)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_sample_rate(cfg, n_sample)
+        _, dt = oracle_sample_rate(cfg, n_sample, threads=cores)
         times.append(dt)
     total = sum(times)
     value = args.steps * n_sample * S * N_STEPS / total
@@ -303,47 +357,55 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "two_dof_eq2_batch", "n_inst": N_INST, "s": S, "n_steps": N_STEPS,
                    "sample_per_step": n_sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_sample} of the {N_INST} systems, {N_STEPS} steps, per bench step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"first {n_sample} of the {N_INST} systems, {N_STEPS} steps, per bench step, "
+                                   f"instances partitioned over {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
+def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_peak):
     """The chain (s = 1024 x 4096, 1e4 steps) and dense (s = 64/128/256 x 8192, 5e3 steps)
     workloads, one timed run each after a warm-up, with their roofline fractions."""
     import torch
 
     res = {}
 
+    ref_cache = {}
+
     def sampled_err(sys_, cfg, prec, n_sample=2, every=625, poly=0):
-        """max relative error of a few instances against the oracle (x and v, over checkpoints)."""
+        """max relative error of a few instances against the oracle (x and v, over checkpoints).
+        Oracle runs are kept per (workload, instances, checkpoint stride) for the other modes."""
         import oracle
 
         k = cfg["x0"].shape[0]
         idx = np.array([0, k - 1][:n_sample]) if n_sample <= 2 else np.linspace(0, k - 1, n_sample).astype(int)
+        key = (id(cfg["x0"]), cfg["n_steps"], every, tuple(idx.tolist()))
+        cached = ref_cache.get(key)
         x0 = torch.as_tensor(cfg["x0"][idx], device=dev)
         v0 = torch.as_tensor(cfg["v0"][idx], device=dev)
         h = torch.as_tensor(cfg["h"][idx], device=dev)
+        nt = min(n_sample, host_cores())
         if cfg["kind"] == "dense" and cfg["M"].shape[0] > 1:          # one (M, K) per instance
             s2 = cho.cho_create_system(ctx, "dense", M=cfg["M"][idx], K=cfg["K"][idx])
             r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
             cho.cho_destroy_system(s2)
-            ref = oracle.rk4_dense(cfg["M"][idx], cfg["K"][idx], cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx],
-                                   cfg["n_steps"], every, threads=n_sample)
+            ref = cached or oracle.rk4_dense(cfg["M"][idx], cfg["K"][idx], cfg["x0"][idx], cfg["v0"][idx],
+                                             cfg["h"][idx], cfg["n_steps"], every, threads=nt)
         elif cfg["kind"] == "dense":
             r = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
                                         poly_jump=poly)
-            ref = oracle.rk4_dense(cfg["M"][0], cfg["K"][0], cfg["x0"][idx], cfg["v0"][idx], cfg["h"][idx],
-                                   cfg["n_steps"], every, threads=n_sample)
+            ref = cached or oracle.rk4_dense(cfg["M"][0], cfg["K"][0], cfg["x0"][idx], cfg["v0"][idx],
+                                             cfg["h"][idx], cfg["n_steps"], every, threads=nt)
         else:
             s2 = cho.cho_create_system(ctx, "chain", masses=cfg["masses"][idx], springs=cfg["springs"][idx])
             r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
                                         poly_jump=poly)
             cho.cho_destroy_system(s2)
-            ref = oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx], cfg["v0"][idx],
-                                   cfg["h"][idx], cfg["n_steps"], every, threads=n_sample)
+            ref = cached or oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx],
+                                             cfg["v0"][idx], cfg["h"][idx], cfg["n_steps"], every, threads=nt)
+        ref_cache[key] = ref
         torch.cuda.synchronize()
         e = 0.0
         for key in ("x_traj", "v_traj"):
@@ -366,7 +428,7 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3
 
-    alu_peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+    # alu_peak: the measured FP32 FMA throughput (TFLOP/s)
     # eq. 3 alone, the paper's own example: one instance, FP64, h = 1e-4, 1e5 steps (t = 10 s).
     # Latency bound: one thread runs the step.  The FP64 pipe takes about 64 cycles per warp
     # instruction whatever the number of active lanes (measured: dependent FMA 64 cycles,
@@ -594,18 +656,24 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks):
     del graph, graph_c
     for sy, _, _, _, _ in gb:
         cho.cho_destroy_system(sy)
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
     for s in (64, 128, 256):
         cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
         s_ = cho.cho_create_system(ctx, "dense", M=cfg["M"], K=cfg["K"])
-        for prec in ("bf16x5", "bf16x3"):
+        for prec in ("bf16x5", "bf16x3", "fp32_simt", "fp64"):
             t = timed(s_, cfg, prec, cfg["n_steps"])
             dof = cfg["x0"].size * cfg["n_steps"]
             ach = dof * 8 * s / t / 1e12     # four B x products of 2 s flops per DOF per step
-            res[f"dense_s{s}_x8192_{prec}"] = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t,
-                                               "error_vs_oracle": sampled_err(s_, cfg, prec),
-                                               "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
-                                                            "unit": "TFLOP/s", "frac": ach / bf16_peak}}
+            line_ = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": cfg["n_steps"],
+                     "error_vs_oracle": sampled_err(s_, cfg, prec, n_sample=16)}
+            if prec.startswith("bf16"):
+                line_["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                                     "frac": ach / bf16_peak,
+                                     "note": "algorithmic flops (8 s per DOF-step) against the sustained BF16 peak"}
+            elif prec == "fp32_simt":
+                line_["roofline"] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                                     "frac": ach / alu_peak}
+            res[f"dense_s{s}_x8192_{prec}"] = line_
         if s == 128:
             # the polynomial form with k-step jumps on the CUDA cores (FP32 pairs): three
             # s x s jump blocks, four products per k steps; flops of the form itself
@@ -685,6 +753,9 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms
 
+    alu = measure_alu_peaks(cho, ctx, local_rank)
+    log(f"measured FMA peaks: FP32 {alu['fp32']['tflops']:.1f} / packed {alu['fp32x2']['tflops']:.1f} / "
+        f"FP64 {alu['fp64']['tflops']:.2f} TFLOP/s at {alu['clocks'].get('sm_mhz')} MHz")
     log("set-up done; headline run")
     # ---- headline: FP32 + Kahan ----
     sampler = ClockSampler(local_rank)
@@ -742,7 +813,8 @@ def main():
 
         peaks = measured_peaks()
         max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        peak = fp32_alu_peak_tflops(sm_count, max_mhz)
+        peak_derived = fp32_alu_peak_tflops(sm_count, max_mhz)
+        peak = alu["fp32_peak_tflops"]
         achieved = N_INST * N_STEPS * FLOPS_PER_INSTANCE_STEP / avg_kernel_s / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -758,7 +830,11 @@ def main():
                          # DRAM bytes per launch (read + write) measured by an ncu capture of the
                          # balanced kernel on this workload
                          "traffic": 4792576,
-                         "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz"},
+                         "peak_note": "measured FP32 FMA throughput (cho_measure_fma_peak, in this run); "
+                                      f"derived from unit counts {sm_count} SMs x 128 lanes x 2 flops x "
+                                      f"{max_mhz:.0f} MHz = {peak_derived:.1f}",
+                         "peak_derived": peak_derived, "frac_of_derived": achieved / peak_derived},
+            "alu_peaks_measured": alu,
             "clocks": clocks,
             "e2e": {"value": DOF_STEPS / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e},
@@ -793,18 +869,25 @@ def main():
                                   "batched_over_plain": value / world / plain_rate}
         if not args.no_extras:
             log("other configurations")
-            line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks)
+            line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks,
+                                                  alu["fp32_peak_tflops"])
             if args.serve_requests > 0:
                 line["serving"] = run_serving(cho, inputs, local_rank, args.serve_requests)
                 log("periodic mode")
                 line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:
             log("CPU baseline (oracle)")
-            n_cpu = 16384
-            rate, dt = oracle_sample_rate(cfg, n_cpu)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"first {n_cpu} of the {N_INST} systems x {N_STEPS} steps, "
-                                              f"single-threaded FP64 C oracle ({dt:.1f} s)"}
+            cores = host_cores()
+            n_all = N_INST                 # about 25 s of CPU work over all cores
+            rate_all, dt_all = oracle_sample_rate(cfg, n_all, threads=cores)
+            n_one = 8192
+            rate_one, dt_one = oracle_sample_rate(cfg, n_one)
+            line["cpu_baseline"] = {
+                "value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                "sample": f"all {n_all} systems x {N_STEPS} steps, FP64 C oracle, instances partitioned over "
+                          f"{cores} threads ({dt_all:.1f} s)",
+                "single_core": {"value": rate_one, "unit": UNIT, "cores": 1,
+                                "sample": f"first {n_one} systems x {N_STEPS} steps, one thread ({dt_one:.1f} s)"}}
         print(json.dumps(line), flush=True)
     cho.cho_destroy_system(sys_)
     cho.cho_shutdown(ctx)

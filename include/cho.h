@@ -30,6 +30,17 @@
  *   - all floating-point inputs and outputs are IEEE binary64, row-major;
  *   - device pointers must be CUDA device memory of the context's device (or
  *     managed memory); "stream" is a cudaStream_t (NULL = legacy default stream).
+ *
+ * Test-only environment switches.  Three variables exist only so that the test suite
+ * can reach code paths that normal inputs never take; applications must leave them
+ * unset, and no result depends on them except as stated:
+ *   CHO_TWO_DOF_KERNEL=generic|pair         forces the lane-group or the pair form of the
+ *       FP32 s = 2 batch kernels instead of the default choice (all give the same bits;
+ *       read once, at the first such launch of the process);
+ *   CHO_TEST_STALL_MMA=1                    the tensor-core dense kernel issues no MMA,
+ *       so its bounded wait runs out and the call reports CHO_ETIMEOUT (read per launch);
+ *   CHO_TEST_WITHHOLD_HANDOVER=1            the balanced s = 2 kernel publishes no
+ *       hand-over flag, so every hand-over wait runs out (CHO_ETIMEOUT, NaN states).
  */
 #ifndef CHO_H
 #define CHO_H
@@ -286,10 +297,16 @@ cho_status cho_integrate_plain(cho_ctx* ctx, const cho_batch_desc* batch, void* 
  * caller (same stream, or synchronised streams).  Each call rewrites all scratch it
  * reads, so nothing in it has to start at zero.
  * The first call on a device looks up the array's device address (this loads it onto
- * that device); make that first call before any stream capture.
- * Arrays: device pointers only (batch->mem == CHO_MEM_DEVICE), prec == CHO_FP64, h read
- * on the device, no checkpoints or energy.  Asynchronous on `stream`; no allocation, host
- * or device, at any call.  Errors: CHO_EINVAL, CHO_ECUDA. */
+ * that device) and keeps it for the life of the process; make that first call before any
+ * stream capture.  The kept address does not survive cudaDeviceReset (or any other
+ * teardown of the device's primary context): do not call this entry point after one.
+ * Arrays: device pointers only (batch->mem == CHO_MEM_DEVICE), prec == CHO_FP64, no
+ * checkpoints or energy, no damped or forced systems.  h is read on the device only, so
+ * the host cannot check it: an h that is not finite and > 0, or with omega_max * h >
+ * 2 sqrt 2 for the instance's parameter set, yields NaN in that instance's x_out and
+ * v_out (where cho_integrate_plain returns CHO_EINVAL or CHO_EUNSTABLE) once at least
+ * one step runs.  Asynchronous on `stream`; no allocation, host or device, at any call.
+ * Errors: CHO_EINVAL, CHO_ECUDA. */
 cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
 
 /* FP64 energy 1/2 v^T M v + 1/2 x^T K x of states x, v (n_inst, n_per, s); state (i, c)
@@ -335,6 +352,17 @@ cho_status cho_tune_query(cho_ctx* ctx, cho_system sys, int64_t n_inst, int32_t 
  * device (n_loaded may be NULL).  Errors: CHO_EINVAL (cannot open, or not a tune file). */
 cho_status cho_tune_save(cho_ctx* ctx, const char* path);
 cho_status cho_tune_load(cho_ctx* ctx, const char* path, int32_t* n_loaded);
+
+/* ---- measurement ---------------------------------------------------------------------- */
+
+/* Measured arithmetic peak of the CUDA cores on the context's device: every thread of a
+ * full-occupancy grid runs 8 independent fused multiply-add chains for iters x 16 rounds
+ * (kind 0: scalar FP32 fma.rn.f32; 1: packed FP32 pairs fma.rn.f32x2; 2: FP64 fma.rn.f64),
+ * timed with CUDA events after one warm-up launch.  *flops_per_s = 2 x FMAs / time, the
+ * denominator of the batched kernels' "alu" roofline fractions; *seconds (may be NULL) is
+ * the timed launch's duration.  Not part of the paper's method: the hardware's own rate.
+ * Synchronous; allocates no device memory.  Errors: CHO_EINVAL, CHO_ECUDA. */
+cho_status cho_measure_fma_peak(cho_ctx* ctx, int32_t kind, int32_t iters, double* flops_per_s, double* seconds);
 
 /* ---- serving: continuous batching of single-instance requests --------------------- */
 

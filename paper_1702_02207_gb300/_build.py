@@ -31,6 +31,7 @@ SOURCES = [
     "plain.cu",
     "plain_noalloc.cu",
     "serve_kernels.cu",
+    "peaks.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -42,7 +42,7 @@ EXPORTED = [
     "cho_destroy_system", "cho_integrate_batch", "cho_integrate_plain",
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
-    "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load",
+    "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load", "cho_measure_fma_peak",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -130,6 +130,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_tune_query": ([V, V, I64, I32, I32, ctypes.POINTER(I32)], I32),
             "cho_tune_save": ([V, ctypes.c_char_p], I32),
             "cho_tune_load": ([V, ctypes.c_char_p, ctypes.POINTER(I32)], I32),
+            "cho_measure_fma_peak": ([V, I32, I32, _dp, _dp], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -448,3 +449,17 @@ def cho_tune_load(ctx, path):
     n = ctypes.c_int32()
     _check(load().cho_tune_load(ctx, os.fsencode(path), ctypes.byref(n)))
     return n.value
+
+
+# ---- measurement -----------------------------------------------------------------------
+
+FMA_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def cho_measure_fma_peak(ctx, kind="fp32", iters=20000):
+    """Measured FMA throughput of the CUDA cores (see include/cho.h): returns
+    (flop/s, seconds of the timed launch)."""
+    f, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().cho_measure_fma_peak(ctx, int(FMA_KINDS.get(kind, kind)), int(iters), ctypes.byref(f),
+                                       ctypes.byref(t)))
+    return f.value, t.value

@@ -16,9 +16,17 @@
 // Each call overwrites all of the scratch it reads before reading it (the
 // state from x0/v0, each stage buffer before the next stage uses it), so no
 // part of it has to start at zero.
+//
+// The step size stays on the device (reading it on the host would need a
+// synchronisation), so the host cannot reject a bad one.  The stage kernel
+// checks it instead: an h that is not finite and > 0, or that puts the
+// instance's fastest mode outside RK4's stability interval on the imaginary
+// axis (omega_max h > 2 sqrt 2), makes every stage value NaN, and the call
+// returns NaN states for that instance where cho_integrate_plain would return
+// CHO_EINVAL or CHO_EUNSTABLE.
 #include "../../include/cho.h"
-#include "cho_internal.h"
 #include "ctx.h"
+#include "plain_common.cuh"
 
 #include <mutex>
 
@@ -49,36 +57,17 @@ cudaError_t scratch_ptr(int dev, double** out)
     return cudaSuccess;
 }
 
-__device__ __forceinline__ double stage_x(const double* y, const double* kp, double c, int j)
-{
-    return kp ? y[j] + c * kp[j] : y[j];
-}
-
-// Stage j of the plain form for instance q, with c = factor * h read on the device.
+// Stage j of the plain form for one instance, with c = factor * h and h read on the
+// device; omega is the fastest angular frequency of the instance's parameter set.
 __global__ void plain_stage_dh_kernel(PlainSys sys, const double* __restrict__ y, const double* __restrict__ kprev,
-                                      double factor, const double* __restrict__ h, double* __restrict__ kout)
+                                      double factor, const double* __restrict__ h, double omega,
+                                      double* __restrict__ kout)
 {
-    const int s = sys.s;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 2 * s) return;
-    const double c = factor * h[0];
-    if (i < s) {
-        kout[i] = kprev ? y[s + i] + c * kprev[s + i] : y[s + i];
-        return;
-    }
-    const int r = i - s;
-    double a;
-    if (sys.dense) {
-        const double* B = sys.coef + (int64_t)r * s;
-        a = 0.0;
-        for (int j = 0; j < s; ++j) a = fma(B[j], stage_x(y, kprev, c, j), a);
-    } else {
-        const double* C = sys.coef;
-        a = C[s + r] * stage_x(y, kprev, c, r);
-        if (r > 0) a = fma(C[r], stage_x(y, kprev, c, r - 1), a);
-        if (r + 1 < s) a = fma(C[2 * s + r], stage_x(y, kprev, c, r + 1), a);
-    }
-    kout[i] = -a;
+    if (i >= 2 * sys.s) return;
+    const double hv = h[0];
+    const bool h_ok = hv > 0.0 && hv < INFINITY && omega * hv <= 2.0 * 1.4142135623730951;
+    kout[i] = h_ok ? plain_stage_elem(sys, y, kprev, factor * hv, i) : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 __global__ void plain_update_dh_kernel(int n, double* __restrict__ y, const double* __restrict__ k,
@@ -86,8 +75,7 @@ __global__ void plain_update_dh_kernel(int n, double* __restrict__ y, const doub
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double h6 = h[0] / 6.0;
-    y[i] = y[i] + h6 * (k[i] + 2.0 * k[n + i] + 2.0 * k[2 * n + i] + k[3 * n + i]);
+    y[i] = plain_update_elem(y[i], k, n, i, h[0] / 6.0);
 }
 
 }  // namespace
@@ -106,6 +94,8 @@ extern "C" cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_
     if (b->prec != CHO_FP64) return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: the plain form is FP64 only");
     if (b->poly_jump != 0)
         return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: the plain form runs RK4 stage by stage");
+    if (sys->damped() || sys->forced())
+        return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: damped or forced systems run in the batch kernels");
     if (sys->s > kNoAllocMaxS)
         return fail(CHO_EINVAL, "cho_integrate_plain_noalloc: s = %d exceeds the fixed scratch limit of %d DOF",
                     sys->s, kNoAllocMaxS);
@@ -133,12 +123,13 @@ extern "C" cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_
         const int64_t set = sys->n_sys == 1 ? 0 : q;
         PlainSys ps{s, dense ? 1 : 0, sys->d_plain + set * (dense ? (int64_t)s * s : 3 * (int64_t)s)};
         const double* hq = b->h + (b->h_per_inst ? q : 0);
+        const double omega = sys->omegas[(size_t)set];
         e = cudaMemcpyAsync(y, b->x0 + q * s, sizeof(double) * s, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(y + s, b->v0 + q * s, sizeof(double) * s, cudaMemcpyDeviceToDevice, st);
         for (int64_t step = 0; step < b->n_steps && e == cudaSuccess; ++step) {
             for (int j = 0; j < 4; ++j)
                 plain_stage_dh_kernel<<<blocks, threads, 0, st>>>(ps, y, j ? k + (j - 1) * n : nullptr, factor[j], hq,
-                                                                  k + j * n);
+                                                                  omega, k + j * n);
             plain_update_dh_kernel<<<blocks, threads, 0, st>>>(n, y, k, hq);
             e = cudaGetLastError();
         }

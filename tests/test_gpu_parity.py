@@ -796,9 +796,23 @@ def test_dense_full_size_sampled(ctx, s, prec):
     """8192 instances sharing one (M, K), 5e3 steps on the tensor cores (the benchmark launch)."""
     cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
     out = run_gpu(ctx, cfg, prec, 625)
-    idx = sample_indices(8192, 6)
+    idx = sample_indices(8192, 16)
     ref = oracle_run(cfg, idx=idx, ckpt_every=625)
     ex, ev = check(out, ref, TOL_BF16_FULL[prec], idx)
+    print(f"dense s={s} 8192 x 5000 {prec} sampled: x {ex:.3e} v {ev:.3e}")
+
+
+@pytest.mark.parametrize("s", [64, 128, 256])
+@pytest.mark.parametrize("prec,tol", [("fp32_simt", TOL_FP32), ("fp64", TOL_FP64)])
+def test_dense_full_horizon_cuda_cores(ctx, s, prec, tol):
+    """The dense workload at its full size and horizon (8192 instances sharing one (M, K),
+    5e3 steps) on the CUDA cores, FP32 + compensation and FP64, sampled against the oracle
+    on 16 instances (first, last and a seeded sample)."""
+    cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)
+    out = run_gpu(ctx, cfg, prec, 625)
+    idx = sample_indices(8192, 16)
+    ref = oracle_run(cfg, idx=idx, ckpt_every=625)
+    ex, ev = check(out, ref, tol, idx)
     print(f"dense s={s} 8192 x 5000 {prec} sampled: x {ex:.3e} v {ev:.3e}")
 
 
