@@ -447,7 +447,13 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
         "error_vs_closed_form": float(np.max(np.abs(np.asarray(r["x"])[0] - x_exact)) / np.max(np.abs(x_exact))),
         "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
                      "note": "one instance, one thread: dependent FP32 operations of the pair arithmetic"}}
-    for k in (0, 1, 10):
+    # the oracle on one host core for the same instance: the GPU's single instance against it
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.rk4_chain(cfg["masses"], cfg["springs"], cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], 0)
+    cpu_ns = 1e9 * (time.perf_counter() - t0) / cfg["n_steps"]
+    for k in (0, 1, 10, 25, 125, 1000):
         t = timed(s_, cfg, "fp64", cfg["n_steps"], poly=k)
         r = cho.cho_integrate_batch(ctx, s_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], "fp64", poly_jump=k)
         n_ops = 44 if k == 0 else 16 / k
@@ -458,6 +464,7 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
                          "fp64_instructions_per_step": n_ops,
                          "bound_ns_per_step": n_ops * 64 / (max_mhz * 1e-3),
                          "note": "one instance, one thread: FP64 instructions per step x 64 cycles"},
+            "oracle_one_core_ns_per_step": cpu_ns,
             "paper_context": "D(1)/D(2) and D(3)/D(4) evaluations of 4.12e-7 / 5.24e-7 s each on a 4-core "
                              "i5-2400 (Section 4), not a like-for-like measure"}
     cho.cho_destroy_system(s_)

@@ -159,8 +159,17 @@ typedef struct cho_system_desc {
  * (the four stages of Section 3 composed).  The library forms E = P(hA)^k - I per instance in
  * FP64 and advances y <- y + E y (FP32: E as FP32 pairs, compensated state), k steps per
  * update: the same result up to rounding with fewer dependent operations.  Supported for
- * s = 2 systems (TWO_DOF, or CHAIN with s = 2) in CHO_FP64 and CHO_FP32_KAHAN; k must divide
- * n_steps and ckpt_every.  Errors: CHO_EINVAL otherwise. */
+ *   - every system of s <= 32 (any kind; one parameter set or one per instance) in CHO_FP64
+ *     and CHO_FP32_KAHAN.  s = 2: E (4 x 4) per instance in registers.  Other s: E is
+ *     2 S x 2 S (S = s padded to 2, 4, 8, 16 or 32), formed per instance by a set-up kernel
+ *     (one matrix for the batch when the system has one parameter set and h_per_inst == 0)
+ *     and kept in shared memory by the integration kernel; device scratch of
+ *     (matrices) x 4 S^2 doubles for the call, from the library's stream-ordered pool;
+ *   - DENSE systems with one shared (M, K) and one h for the whole batch: the blocks of
+ *     P(hA)^k formed in FP64 on the host and cached per (h, k), in CHO_FP64, CHO_FP32_KAHAN
+ *     or CHO_DENSE_FP32_SIMT on the CUDA cores (reading h synchronises the stream).
+ * k must divide n_steps and ckpt_every.  In FP32, k omega_max h <= 1 keeps the rounding of
+ * the increments within the FP32 tolerance.  Errors: CHO_EINVAL otherwise. */
 typedef struct cho_batch_desc {
     cho_system system;
     int64_t n_inst;

@@ -563,10 +563,11 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
     }
     if (b->poly_jump > 0) {
         if (plain_form) return fail(CHO_EINVAL, "%s: the plain form runs RK4 stage by stage", who);
-        const bool small2 = sys->path == PATH_SMALL && sys->s == 2;
+        const bool small = sys->path == PATH_SMALL;
         const bool dense1 = sys->path == PATH_DENSE && sys->n_sys == 1;
-        if (!small2 && !dense1)
-            return fail(CHO_EINVAL, "%s: the polynomial form is built for s = 2 systems and shared dense systems", who);
+        if (!small && !dense1)
+            return fail(CHO_EINVAL, "%s: the polynomial form is built for systems of s <= 32 and shared dense systems",
+                        who);
         if (p != CHO_FP64 && p != CHO_FP32_KAHAN && !(dense1 && p == CHO_DENSE_FP32_SIMT))
             return fail(CHO_EINVAL, "%s: the polynomial form runs in CHO_FP64 or FP32 (compensated)", who);
         if (b->n_steps % b->poly_jump != 0 || (b->ckpt_every > 0 && b->ckpt_every % b->poly_jump != 0))

@@ -735,6 +735,222 @@ __global__ void __launch_bounds__(64) rk4_poly64_kernel(const SmallSys sys, cons
     io.v_out[q * 2 + 1] = y[3];
 }
 
+// ---- polynomial form for every system of the small family (s <= 32) ---------------
+//
+// The same map for S = 2 .. 32 (s padded to S with zero rows and columns of B, so the
+// padded coordinates keep E's zero rows and never move): y = (x, v) of 2S rows,
+// E = P(hA)^k - I of 2S x 2S.  Set-up: one CTA per matrix forms E in FP64 in shared
+// memory (hA from B, Horner for P, binary powers for the k-th power, the s = 2 set-up's
+// order of operations).  Integration: one thread per row of y; a CTA holds NI = 128/2S
+// instances, their E transposed in shared memory (FP64, or FP32 hi and lo pieces), and
+// exchanges y through shared memory once per update: thread i forms (E y)_i (FP32: the
+// lo products first) and adds it to its row (compensated in FP32).  One E serves every
+// instance when they share B and h.
+
+constexpr int kPolySetupThreads = 256;
+constexpr int kPolyThreads = 128;
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+
+// C = A B for n x n row-major FP64 matrices in shared memory; every thread of the CTA
+// takes part, and C is complete (and A, B free) when it returns.
+__device__ void smem_matmul(const double* A, const double* B, double* C, int n)
+{
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double t = 0.0;
+        for (int l = 0; l < n; ++l) t = __fma_rn(A[i * n + l], B[l * n + j], t);
+        C[e] = t;
+    }
+    __syncthreads();
+}
+
+// E (n_E matrices of 2S x 2S, row-major) for instance blockIdx.x (or the shared one).
+template <int S>
+__global__ void __launch_bounds__(kPolySetupThreads) small_poly_setup_kernel(const SmallSys sys, const BatchIO io,
+                                                                              bool fp64, double* E)
+{
+    constexpr int n = 2 * S;
+    extern __shared__ __align__(16) double pm[];
+    double* hA = pm;
+    double* base = pm + n * n;
+    double* R = pm + 2 * n * n;
+    double* T = pm + 3 * n * n;
+    const int64_t q = blockIdx.x;
+    const int64_t set = sys.per_inst_sys ? q : 0;
+    const double h = io.h[io.h_per_inst ? q : 0];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double a = 0.0;
+        if (i < S) {
+            a = (j == S + i) ? h : 0.0;                          // x' = v
+        } else if (j < S) {
+            const int r = i - S;                                // v' = -B x
+            const double b = fp64 ? sys.B64[(set * S + r) * S + j]
+                                  : (double)sys.B32[set * 2 * S * S + r * S + j] +
+                                        (double)sys.B32[set * 2 * S * S + S * S + r * S + j];
+            a = -h * b;
+        }
+        hA[e] = a;
+        base[e] = (i == j) ? 1.0 : 0.0;                           // P starts at I
+        R[e] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // P = I + hA (I + hA/2 (I + hA/3 (I + hA/4)))
+    for (int d = 4; d >= 1; --d) {
+        smem_matmul(hA, base, T, n);
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+            base[e] = ((e / n == e % n) ? 1.0 : 0.0) + T[e] / (double)d;
+        __syncthreads();
+    }
+    // R = P^k by binary powers (T is scratch; hA is free now)
+    double* tmp = hA;
+    for (int kk = io.poly_jump; kk > 0; kk >>= 1) {
+        if (kk & 1) {
+            smem_matmul(R, base, T, n);
+            double* sw = R;
+            R = T;
+            T = sw;
+        }
+        if (kk > 1) {
+            smem_matmul(base, base, tmp, n);
+            double* sw = base;
+            base = tmp;
+            tmp = sw;
+        }
+    }
+    double* out = E + (size_t)q * n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) out[e] = R[e] - ((e / n == e % n) ? 1.0 : 0.0);
+}
+
+template <int S, bool F64>
+__global__ void __launch_bounds__(kPolyThreads) rk4_small_poly_kernel(const SmallSys sys, const BatchIO io,
+                                                                      const double* __restrict__ E, int shared_E)
+{
+    using Real = std::conditional_t<F64, double, float>;
+    constexpr int n = 2 * S;                     // rows of y per instance
+    constexpr int NI = kPolyThreads / n;         // instances per CTA
+    extern __shared__ __align__(16) unsigned char poly_sm[];
+    const int nmat = shared_E ? 1 : NI;
+    // E^T per instance slot: FP64 [nmat][n][n], FP32 hi [nmat][n][n] then lo
+    Real* Eh = (Real*)poly_sm;
+    float* El = (float*)(Eh + (size_t)nmat * n * n);
+    Real* ybuf = F64 ? (Real*)(Eh + (size_t)nmat * n * n) : (Real*)(El + (size_t)nmat * n * n);   // [2][NI][n]
+
+    const int li = threadIdx.x / n;
+    const int i = threadIdx.x % n;
+    const int64_t q0 = (int64_t)blockIdx.x * NI;
+    const int64_t q = q0 + li;
+    const bool live = q < io.n_inst;
+    const int s = sys.s;
+    // E of the CTA's instances into shared memory, transposed: Et[m][j][r] = E_m[r][j]
+    for (int e = threadIdx.x; e < nmat * n * n; e += kPolyThreads) {
+        const int m = e / (n * n), r = (e / n) % n, j = e % n;
+        const int64_t src = shared_E ? 0 : q0 + m;
+        double d = 0.0;
+        if (src < io.n_inst) d = E[(size_t)src * n * n + (size_t)r * n + j];
+        const size_t o = (size_t)m * n * n + (size_t)j * n + r;
+        if constexpr (F64) {
+            Eh[o] = d;
+        } else {
+            const float hi = (float)d;
+            Eh[o] = hi;
+            El[o] = (float)(d - (double)hi);
+        }
+    }
+    // row i of this instance's y: x_i (i < S) or v_{i-S}
+    const int dof = i < S ? i : i - S;
+    Real y = 0;
+    float c = 0.f;
+    if (live && dof < s) {
+        const double d = i < S ? io.x0[q * s + dof] : io.v0[q * s + dof];
+        y = (Real)d;
+        c = F64 ? 0.f : (float)(d - (double)y);
+    }
+    __syncthreads();
+    const int m = shared_E ? 0 : li;
+    const Real* eh = Eh + (size_t)m * n * n + i;
+    const float* el = El + (size_t)m * n * n + i;
+    int b = 0;
+    auto jumps = [&](int64_t count) {
+        for (int64_t it = 0; it < count; ++it) {
+            Real* yb = ybuf + (size_t)(b * NI + li) * n;
+            yb[i] = y;
+            __syncthreads();
+            Real z;
+            if constexpr (F64) {
+                z = 0.0;
+#pragma unroll 8
+                for (int j = 0; j < n; ++j) z = __fma_rn(eh[(size_t)j * n], yb[j], z);
+                y = __dadd_rn(y, z);
+            } else {
+                z = 0.f;
+#pragma unroll 8
+                for (int j = 0; j < n; ++j) z = __fmaf_rn(el[(size_t)j * n], yb[j], z);
+#pragma unroll 8
+                for (int j = 0; j < n; ++j) z = __fmaf_rn(eh[(size_t)j * n], yb[j], z);
+                comp_add(y, c, z);
+            }
+            b ^= 1;
+        }
+    };
+    const int64_t k = io.poly_jump;
+    auto put = [&](double* xo, double* vo, int64_t off) {
+        if (!live || dof >= s) return;
+        const double val = (double)y + (double)c;
+        if (i < S) xo[off + dof] = val;
+        else if (vo) vo[off + dof] = val;
+    };
+    if (io.ckpt_every > 0 && io.x_traj) {
+        for (int64_t done = 0; done < io.n_steps; done += io.ckpt_every) {
+            jumps(io.ckpt_every / k);
+            put(io.x_traj, io.v_traj, (q * io.n_ck + done / io.ckpt_every) * s);
+        }
+    } else {
+        jumps(io.n_steps / k);
+    }
+    put(io.x_out, io.v_out, q * s);
+}
+
+template <int S>
+cudaError_t launch_small_poly(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
+{
+    constexpr int n = 2 * S;
+    constexpr int NI = kPolyThreads / n;
+    const bool shared_E = !sys.per_inst_sys && !io.h_per_inst;
+    const int64_t n_E = shared_E ? 1 : io.n_inst;
+    void* buf = nullptr;
+    cudaError_t e = scratch_alloc(&buf, (size_t)n_E * n * n * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const size_t setup_smem = 4 * (size_t)n * n * sizeof(double);
+    e = cudaFuncSetAttribute(small_poly_setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)setup_smem);
+    if (e == cudaSuccess) {
+        small_poly_setup_kernel<S><<<(unsigned)n_E, kPolySetupThreads, setup_smem, st>>>(sys, io, fp64, (double*)buf);
+        e = cudaGetLastError();
+    }
+    const int nmat = shared_E ? 1 : NI;
+    const size_t esz = fp64 ? sizeof(double) : 2 * sizeof(float);
+    const size_t smem = (size_t)nmat * n * n * esz + 2 * (size_t)NI * n * (fp64 ? sizeof(double) : sizeof(float));
+    const int64_t blocks = (io.n_inst + NI - 1) / NI;
+    if (e == cudaSuccess && blocks > 0x7fffffffLL) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) {
+        if (fp64) {
+            e = cudaFuncSetAttribute(rk4_small_poly_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                rk4_small_poly_kernel<S, true><<<(unsigned)blocks, kPolyThreads, smem, st>>>(sys, io, (const double*)buf,
+                                                                                             shared_E ? 1 : 0);
+        } else {
+            e = cudaFuncSetAttribute(rk4_small_poly_kernel<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                rk4_small_poly_kernel<S, false><<<(unsigned)blocks, kPolyThreads, smem, st>>>(sys, io, (const double*)buf,
+                                                                                              shared_E ? 1 : 0);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return e != cudaSuccess ? e : ef;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kPairThreads) rk4_pair2_kernel(const SmallSys sys, const BatchIO io)
 {
@@ -1113,8 +1329,18 @@ cudaError_t launch_dw_one(const SmallSys& sys, const BatchIO& io, cudaStream_t s
 
 cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, cudaStream_t st)
 {
-    if (io.poly_jump > 0) {                      // polynomial form (s = 2, checked by the caller)
-        if (sys.s != 2) return cudaErrorInvalidValue;
+    if (io.poly_jump > 0 && sys.s != 2) {        // polynomial form, any other s <= 32
+        if (io.n_inst == 0) return cudaSuccess;
+        switch (sys.S) {
+            case 2: return launch_small_poly<2>(sys, io, fp64, st);
+            case 4: return launch_small_poly<4>(sys, io, fp64, st);
+            case 8: return launch_small_poly<8>(sys, io, fp64, st);
+            case 16: return launch_small_poly<16>(sys, io, fp64, st);
+            case 32: return launch_small_poly<32>(sys, io, fp64, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (io.poly_jump > 0) {                      // polynomial form, s = 2
         const int64_t blocks = (io.n_inst + 63) / 64;
         if (blocks <= 0) return cudaSuccess;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;

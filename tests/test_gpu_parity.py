@@ -647,6 +647,43 @@ def test_poly_form_matches_oracle(ctx, prec, tol, k):
     print(f"poly k={k} {prec}: x {ex:.3e} v {ev:.3e}")
 
 
+@pytest.mark.parametrize("s", [1, 3, 8, 17, 32])
+@pytest.mark.parametrize("kind", ["chain", "dense_own", "dense_shared"])
+@pytest.mark.parametrize("prec,tol,k", [("fp64", TOL_FP64, 1), ("fp64", TOL_FP64, 25), ("fp64", TOL_FP64, 125),
+                                        ("fp32_kahan", TOL_FP32, 1), ("fp32_kahan", TOL_FP32, 5)])
+def test_poly_form_small_systems(ctx, s, kind, prec, tol, k):
+    """Systems of s <= 32 other than s = 2 in the polynomial form: a 2S x 2S jump matrix per
+    instance (chains and dense systems with their own parameters and h) or one for the batch
+    (a shared dense system with one h), 21 instances x 1000 steps against the stage-by-stage
+    oracle, checkpoints every 125 steps (a stride of 250 = 2.5 periods of the fastest mode
+    samples a single-mode velocity only at its zeros).  FP32: k omega h <= 0.32 at h = T_min/100."""
+    import torch
+
+    n_steps = 1000
+    if kind == "chain":
+        cfg = inputs.chain_batch(n_inst=21, s=s, n_steps=n_steps, seed=700 + s)
+    elif kind == "dense_own":
+        cfg = inputs.dense_own(s=s, n_inst=21, n_steps=n_steps, seed=7000 + s)
+    else:
+        cfg = inputs.dense_group(s=s, n_inst=21, n_steps=n_steps, seed=8000 + s)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    h = cfg["h"] if kind != "dense_shared" else cfg["h"][:1]
+    try:
+        out = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(h, device=d),
+                                      n_steps, prec, 125, trajectory=True, poly_jump=k)
+        torch.cuda.synchronize()
+        out = {key: val.cpu().numpy() for key, val in out.items()}
+    finally:
+        cho.cho_destroy_system(sys_)
+    if kind == "dense_shared":
+        cfg = dict(cfg, h=np.full(21, cfg["h"][0]))
+    ref = oracle_run(cfg, ckpt_every=125)
+    ex, ev = check(out, ref, tol)
+    print(f"small poly s={s} {kind} k={k} {prec}: x {ex:.3e} v {ev:.3e}")
+
+
 @pytest.mark.parametrize("s", [33, 64, 128, 256, 300])
 @pytest.mark.parametrize("prec,tol,k", [("fp64", TOL_FP64, 1), ("fp64", TOL_FP64, 25), ("fp32_kahan", TOL_FP32, 1),
                                         ("fp32_kahan", TOL_FP32, 5)])
@@ -768,8 +805,8 @@ def test_poly_form_rejects_what_it_does_not_cover(ctx):
                                             trajectory=True, poly_jump=20),     # 20 does not divide 50
             lambda: cho.cho_integrate_batch(ctx, two, cfg["x0"], cfg["v0"], cfg["h"], 100, "fp32_kahan",
                                             poly_jump=-1),
-            lambda: cho.cho_integrate_batch(ctx, chain, ch["x0"], ch["v0"], ch["h"], 100, "fp32_kahan",
-                                            poly_jump=1),                       # s = 5
+            lambda: cho.cho_integrate_batch(ctx, chain, ch["x0"], ch["v0"], ch["h"], 100, "fp32x2",
+                                            poly_jump=1),                       # not in double-FP32
         ]
         for call in bad:
             with pytest.raises(cho.ChoError) as ei:
