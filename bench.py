@@ -663,6 +663,50 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
     del graph, graph_c
     for sy, _, _, _, _ in gb:
         cho.cho_destroy_system(sy)
+    # uneven sizes packed into one launch per kernel family and size class (cho_integrate_packed)
+    # against one launch per batch, on one stream or one stream per batch; 1e3 steps, FP32
+    pk_cfgs = ([inputs.chain_batch(n_inst=400, s=sv, n_steps=1, seed=9000 + sv) for sv in (33, 40, 47, 55, 63)] +
+               [inputs.chain_batch(n_inst=4000, s=sv, n_steps=1, seed=9100 + sv) for sv in (5, 6, 7, 8)] +
+               [inputs.chain_batch(n_inst=8000, s=sv, n_steps=1, seed=9200 + sv) for sv in (3, 4)])
+    pk = []
+    for cfg in pk_cfgs:
+        sy = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"])
+        tt = {k: torch.as_tensor(cfg[k], device=dev) for k in ("x0", "v0", "h")}
+        pk.append({"system": sy, "x0": tt["x0"], "v0": tt["v0"], "h": tt["h"], "n_steps": 1000, "prec": "fp32_kahan",
+                   "out": {"x": torch.empty_like(tt["x0"]), "v": torch.empty_like(tt["v0"])}})
+    pk_side = [torch.cuda.Stream() for _ in pk]
+
+    def run_packed():
+        with torch.cuda.stream(gs):
+            cho.cho_integrate_packed(ctx, pk, stream=gs)
+
+    def run_separate():
+        for b in pk:
+            cho.cho_integrate_batch(ctx, b["system"], b["x0"], b["v0"], b["h"], 1000, "fp32_kahan", out=b["out"],
+                                    stream=gs)
+
+    def run_streams():
+        fork = torch.cuda.Event()
+        fork.record(gs)
+        for b, st in zip(pk, pk_side):
+            st.wait_event(fork)
+            cho.cho_integrate_batch(ctx, b["system"], b["x0"], b["v0"], b["h"], 1000, "fp32_kahan", out=b["out"],
+                                    stream=st)
+        for st in pk_side:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            gs.wait_event(ev)
+
+    t_pk, t_sep, t_str = wall(run_packed, 20), wall(run_separate, 20), wall(run_streams, 20)
+    pk_dof = sum(b["x0"].numel() for b in pk) * 1000
+    res["uneven_sizes_packed"] = {
+        "batches": "chains s = 33, 40, 47, 55, 63 x 400; s = 5..8 x 4000; s = 3, 4 x 8000; 1e3 steps each, FP32",
+        "launch_groups": 3, "batches_n": len(pk),
+        "ms_packed": 1e3 * t_pk, "ms_one_stream": 1e3 * t_sep, "ms_one_stream_per_batch": 1e3 * t_str,
+        "value_packed": pk_dof / t_pk, "unit": UNIT,
+        "note": "wall time per call with synchronisation; packed results are bitwise those of separate calls"}
+    for b in pk:
+        cho.cho_destroy_system(b["system"])
     bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
     for s in (64, 128, 256):
         cfg = inputs.dense_group(s=s, n_inst=8192, n_steps=5000)

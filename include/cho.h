@@ -318,6 +318,25 @@ cho_status cho_integrate_plain(cho_ctx* ctx, const cho_batch_desc* batch, void* 
  * Errors: CHO_EINVAL, CHO_ECUDA. */
 cho_status cho_integrate_plain_noalloc(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
 
+/* Several batches packed into as few kernel launches as possible.  Batches whose systems fall
+ * into one kernel family and size class run in ONE launch over a device work table with one
+ * entry per instance (its parameter set's coefficients, its state, h, its step count and its
+ * own s): rk4_small by padded size S (any kind of s <= 32 together: 2-DOF systems, chains of
+ * 3 and 4 masses and dense systems of s = 4 share S = 4), rk4_chain by DOFs per thread (s < 64,
+ * < 128, < 256, >= 256; the CTA is sized for the group's largest chain) and rk4_dense by
+ * system.  Each batch's x_out, v_out are bitwise equal to a separate cho_integrate_batch call
+ * of that batch (every family computes an instance with the same operations in both forms).
+ * Eq. 1 and eq. 2 with uneven sizes and horizons in one launch: the instance, not the batch,
+ * is the unit of work.
+ * Every batch: device arrays (mem == CHO_MEM_DEVICE), poly_jump == 0, no checkpoints or energy,
+ * not damped or forced, prec CHO_FP64, CHO_FP32_KAHAN, CHO_DENSE_FP32_SIMT or (one shared dense
+ * system) CHO_DENSE_BF16X3/X5/X6; each batch is otherwise checked as cho_integrate_batch checks
+ * it (a batch with one h on the device is read synchronously for the stability check).
+ * Asynchronous on `stream`; the work table and state blocks come from the library's
+ * stream-ordered scratch pool for the call.  Errors: CHO_EINVAL, CHO_EUNSTABLE, CHO_ENOMEM,
+ * CHO_ECUDA. */
+cho_status cho_integrate_packed(cho_ctx* ctx, const cho_batch_desc* batches, int32_t n_batches, void* stream);
+
 /* FP64 energy 1/2 v^T M v + 1/2 x^T K x of states x, v (n_inst, n_per, s); state (i, c)
  * uses parameter set i (or 0 when the system has one set).  E is (n_inst, n_per).
  * mem selects host or device pointers as in cho_batch_desc.  Errors: CHO_EINVAL, CHO_ECUDA. */

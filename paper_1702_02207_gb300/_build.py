@@ -32,6 +32,7 @@ SOURCES = [
     "plain_noalloc.cu",
     "serve_kernels.cu",
     "peaks.cu",
+    "packed.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

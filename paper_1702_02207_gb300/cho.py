@@ -43,6 +43,7 @@ EXPORTED = [
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
     "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load", "cho_measure_fma_peak",
+    "cho_integrate_packed",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -131,6 +132,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_tune_save": ([V, ctypes.c_char_p], I32),
             "cho_tune_load": ([V, ctypes.c_char_p, ctypes.POINTER(I32)], I32),
             "cho_measure_fma_peak": ([V, I32, I32, _dp, _dp], I32),
+            "cho_integrate_packed": ([V, ctypes.POINTER(cho_batch_desc), I32, V], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -355,6 +357,49 @@ def cho_integrate_plain_noalloc(ctx, system, x0, v0, h, n_steps, out=None, strea
         raise ValueError("cho_integrate_plain_noalloc takes device arrays")
     return _batch("cho_integrate_plain_noalloc", ctx, system, x0, v0, h, n_steps, CHO_FP64, 0, False, False,
                   out, stream)
+
+
+def cho_integrate_packed(ctx, batches, stream=None):
+    """Several batches in as few launches as possible (see include/cho.h).  ``batches`` is a
+    list of dicts with keys system, x0, v0, h (CUDA tensors; h of 1 or n_inst values),
+    n_steps, prec and optionally out ({"x", "v"} tensors).  Returns one {"x", "v"} dict per
+    batch."""
+    import torch
+
+    descs = (cho_batch_desc * max(1, len(batches)))()
+    results, keep = [], []
+    for k, bt in enumerate(batches):
+        _, s, _ = cho_system_info(bt["system"])
+        x0 = _cuda_f64(bt["x0"])
+        v0 = _cuda_f64(bt["v0"])
+        h = bt["h"]
+        if not _is_cuda(h):
+            h = torch.as_tensor(np.asarray(h, dtype=np.float64).reshape(-1), device=x0.device)
+        h = _cuda_f64(h)
+        n_inst = x0.shape[0] if x0.dim() > 1 else 1
+        if h.shape[0] not in (1, n_inst):
+            raise ValueError("h must have 1 or n_inst values")
+        res = dict(bt.get("out") or {})
+        for key in ("x", "v"):
+            if key not in res:
+                res[key] = torch.empty((n_inst, s), dtype=torch.float64, device=x0.device)
+        d = descs[k]
+        d.system = bt["system"]
+        d.n_inst = n_inst
+        d.prec = PRECS.get(bt.get("prec", CHO_FP64), bt.get("prec", CHO_FP64))
+        d.mem = CHO_MEM_DEVICE
+        d.x0, d.v0, d.h = _ptr(x0), _ptr(v0), _ptr(h)
+        d.h_per_inst = int(h.shape[0] != 1 or n_inst == 1)
+        d.poly_jump = 0
+        d.n_steps = int(bt["n_steps"])
+        d.ckpt_every = 0
+        d.x_out, d.v_out = _ptr(res["x"]), _ptr(res["v"])
+        d.x_traj = d.v_traj = d.energy = None
+        keep += [x0, v0, h]
+        results.append(res)
+    st = _stream_ptr(stream)
+    _check(load().cho_integrate_packed(ctx, descs, len(batches), st))
+    return results
 
 
 def cho_energy(ctx, system, x, v, stream=None):

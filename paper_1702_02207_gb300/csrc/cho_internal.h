@@ -85,6 +85,10 @@ struct SlotIO {
     int64_t chunk;          // each slot runs min(chunk, remaining) steps
 };
 
+// Stream-ordered per-call device scratch from the library's own memory pool (rk4_small.cu);
+// release it with cudaFreeAsync on the same stream.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+
 cudaError_t launch_gather_status(const int32_t* ids, const int32_t* status, int32_t* out, int64_t n,
                                  cudaStream_t st);
 

@@ -750,8 +750,6 @@ __global__ void __launch_bounds__(64) rk4_poly64_kernel(const SmallSys sys, cons
 constexpr int kPolySetupThreads = 256;
 constexpr int kPolyThreads = 128;
 
-cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
-
 // C = A B for n x n row-major FP64 matrices in shared memory; every thread of the CTA
 // takes part, and C is complete (and A, B free) when it returns.
 __device__ void smem_matmul(const double* A, const double* B, double* C, int n)
@@ -1084,11 +1082,13 @@ int two_dof_env_variant()
     return v;
 }
 
-// Per-call device scratch (hand-over buffers, jump matrices) comes from a memory
-// pool of the library's own that keeps up to 256 MiB when freed: the default
-// pool returns freed memory to the driver at every synchronisation, and mapping it
-// again cost ~0.18 ms per synchronous call.  Stream-ordered, so concurrent calls on
-// other streams never share a block.
+}  // namespace
+
+// Per-call device scratch (hand-over buffers, jump matrices, packed work tables) comes
+// from a memory pool of the library's own that keeps up to 256 MiB when freed: the
+// default pool returns freed memory to the driver at every synchronisation, and
+// mapping it again cost ~0.18 ms per synchronous call.  Stream-ordered, so concurrent
+// calls on other streams never share a block.
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st)
 {
     static std::mutex mu;
@@ -1118,6 +1118,8 @@ cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st)
     }
     return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
+
+namespace {
 
 template <class T>
 cudaError_t launch_pair2(const SmallSys& sys, const BatchIO& io, cudaStream_t st)
