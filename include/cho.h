@@ -40,7 +40,10 @@
  *   CHO_TEST_STALL_MMA=1                    the tensor-core dense kernel issues no MMA,
  *       so its bounded wait runs out and the call reports CHO_ETIMEOUT (read per launch);
  *   CHO_TEST_WITHHOLD_HANDOVER=1            the balanced s = 2 kernel publishes no
- *       hand-over flag, so every hand-over wait runs out (CHO_ETIMEOUT, NaN states).
+ *       hand-over flag, so every hand-over wait runs out (CHO_ETIMEOUT, NaN states);
+ *   CHO_TEST_WITHHOLD_DOORBELL=1            persistent serving never rings its kernels'
+ *       doorbell, so their bounded waits run out (requests end with CHO_ETIMEOUT; read when
+ *       a context's serving engine starts).
  */
 #ifndef CHO_H
 #define CHO_H
@@ -124,7 +127,11 @@ typedef struct cho_config {
                                that a chunk takes about this many microseconds of device time
                                (chunk_steps is the first guess); 0 keeps chunk_steps.  Results do
                                not depend on the chunk length. */
-    int32_t reserved[3];
+    int32_t persistent;     /* serving: 1 serves rk4_small groups and chain groups (s <= 2048) with
+                               resident kernels driven through pinned mapped memory (doorbell per
+                               chunk, completion ring; see cho_submit), 0 launches every chunk.
+                               Results are bitwise the same. */
+    int32_t reserved[2];
 } cho_config;
 
 /* Description of one system kind and size, with n_sys parameter sets.
@@ -393,6 +400,20 @@ cho_status cho_tune_load(cho_ctx* ctx, const char* path, int32_t* n_loaded);
 cho_status cho_measure_fma_peak(cho_ctx* ctx, int32_t kind, int32_t iters, double* flops_per_s, double* seconds);
 
 /* ---- serving: continuous batching of single-instance requests --------------------- */
+
+/* Persistent serving (cho_config.persistent = 1).  rk4_small groups (any kind of s <= 32) and
+ * chain groups (s <= 2048) are served by a kernel that stays resident on the group's stream
+ * and runs one chunk per generation instead of one launch per chunk (Section 5's real-time
+ * use: no launch on the per-chunk path).  The slot table, the status words, each group's
+ * slot-id list and completion ring are pinned host memory mapped into the device; the
+ * serving thread writes a generation's slot ids and rings a doorbell, the kernel's CTAs
+ * advance their share, append finished slots to the ring and count the generation done.
+ * Every doorbell wait on the device is bounded (about a second): a kernel left without a
+ * doorbell stops, reports CHO_ETIMEOUT, and the requests of its pending generation end
+ * with CHO_ETIMEOUT; the context stays usable.  Resident kernels together hold at most half
+ * the SMs' worth of CTAs and 60 % of the registers, so at least half the SMs stay whole for
+ * launched kernels; a group beyond that, and every dense group, is launched per chunk as in
+ * the default mode.  A group with no resident request releases its kernel. */
 
 /* Queue one request.  Inputs are copied; returns at once with a ticket.
  * Errors: CHO_EINVAL, CHO_EUNSTABLE, CHO_EBUDGET (the request alone exceeds the budget). */

@@ -165,6 +165,7 @@ extern "C" cho_status cho_init(cho_ctx** out, int device, const cho_config* cfg)
         if (cfg->chunk_steps > 0) c->cfg.chunk_steps = cfg->chunk_steps;
         if (cfg->max_slots > 0) c->cfg.max_slots = cfg->max_slots;
         if (cfg->chunk_us > 0) c->cfg.chunk_us = cfg->chunk_us;
+        c->cfg.persistent = cfg->persistent != 0 ? 1 : 0;
     }
     {
         DeviceGuard g(device);

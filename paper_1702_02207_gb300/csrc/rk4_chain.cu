@@ -20,6 +20,7 @@
 // (FP32 at P >= 2: the same operations on packed pairs of DOFs, the same bits) and
 // rk4_chain_dw_kernel (double-FP32, CHO_FP32X2).
 #include "cho_internal.h"
+#include "persist.cuh"
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
 
@@ -74,36 +75,73 @@ struct ChainBatchSrc {
 };
 
 // Slot form: state block [x(s), v(s), cx(s), cv(s)] in kernel precision (FP32: the
-// scaled velocity in place of v, converted by the serving engine).
-template <bool F64>
+// scaled velocity in place of v, converted by the serving engine).  FRESH (persistent
+// kernels): table and ids in mapped host memory read with volatile loads, state blocks
+// through L2 only, finished slots to the completion ring (as SlotSrc in rk4_small.cu).
+template <bool F64, bool FRESH = false>
 struct ChainSlotSrc {
     SlotIO io;
+    const PersistIO* pio = nullptr;
     using Real = std::conditional_t<F64, double, float>;
 
+    __device__ int32_t id(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile int32_t*)io.slot_ids)[q];
+        else return io.slot_ids[q];
+    }
     __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
-    __device__ int s(int64_t q) const { return d(q).s; }
-    __device__ double h(int64_t q) const { return d(q).h; }
-    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
+    __device__ const volatile SlotDesc& vd(int64_t q) const { return ((const volatile SlotDesc*)io.slots)[id(q)]; }
+    __device__ int s(int64_t q) const
+    {
+        if constexpr (FRESH) return vd(q).s;
+        else return d(q).s;
+    }
+    __device__ double h(int64_t q) const
+    {
+        if constexpr (FRESH) return vd(q).h;
+        else return d(q).h;
+    }
+    __device__ int64_t steps(int64_t q) const
+    {
+        int64_t rem;
+        if constexpr (FRESH) rem = vd(q).remaining;
+        else rem = d(q).remaining;
+        return rem < io.chunk ? rem : io.chunk;
+    }
     __device__ int64_t ckpt_every() const { return 0; }
-    __device__ const void* coef(int64_t q) const { return d(q).coef; }
+    __device__ const void* coef(int64_t q) const
+    {
+        if constexpr (FRESH) return vd(q).coef;
+        else return d(q).coef;
+    }
+    __device__ Real* state(int64_t q) const
+    {
+        if constexpr (FRESH) return (Real*)vd(q).state;
+        else return (Real*)d(q).state;
+    }
+    __device__ Real ld(const Real* p) const
+    {
+        if constexpr (FRESH) return __ldcg(p);
+        else return *p;
+    }
     __device__ void load(int64_t q, int i, Real& x, Real& v, float& cx, float& cv) const
     {
-        const int sz = d(q).s;
-        const Real* st = (const Real*)d(q).state;
-        x = st[i];
-        v = st[sz + i];
+        const int sz = s(q);
+        const Real* st = state(q);
+        x = ld(st + i);
+        v = ld(st + sz + i);
         if constexpr (F64) {
             cx = cv = 0.f;
         } else {
-            cx = st[2 * sz + i];
-            cv = st[3 * sz + i];
+            cx = ld(st + 2 * sz + i);
+            cv = ld(st + 3 * sz + i);
         }
     }
     __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
     __device__ void store(int64_t q, int i, Real x, Real v, float cx, float cv) const
     {
-        const int sz = d(q).s;
-        Real* st = (Real*)d(q).state;
+        const int sz = s(q);
+        Real* st = state(q);
         st[i] = x;
         st[sz + i] = v;
         if constexpr (!F64) {
@@ -113,21 +151,30 @@ struct ChainSlotSrc {
     }
     __device__ void finish(int64_t q, int64_t ran, bool bad) const
     {
-        const int32_t slot = io.slot_ids[q];
-        io.slots[slot].remaining -= ran;
-        if (bad) io.status[slot] = CHO_ENONFINITE;
+        const int32_t slot = id(q);
+        if constexpr (FRESH) {
+            volatile SlotDesc* sd = (volatile SlotDesc*)io.slots + slot;
+            const int64_t left = sd->remaining - ran;
+            sd->remaining = left;
+            if (bad) ((volatile int32_t*)io.status)[slot] = CHO_ENONFINITE;
+            if (left == 0 || bad) persist_complete(*pio, slot);
+        } else {
+            io.slots[slot].remaining -= ran;
+            if (bad) io.status[slot] = CHO_ENONFINITE;
+        }
     }
 };
 
-template <int P, bool F64, int MAXT, class Src>
-__global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
+// One instance per CTA: the work of instance q (the kernel's CTA blockIdx.x, or an item
+// of a persistent kernel's generation).
+template <int P, bool F64, class Src>
+__device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
 {
     using Real = std::conditional_t<F64, double, float>;
     __shared__ Real edge_last[2][32][32];   // last DOF of every thread, [buffer][warp][lane]
     __shared__ Real edge_first[2][32][32];  // first DOF of every thread
     __shared__ int any_bad;
 
-    const int64_t q = blockIdx.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
@@ -281,6 +328,12 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
     if (t == 0) src.finish(q, n, any_bad != 0);
 }
 
+template <int P, bool F64, int MAXT, class Src>
+__global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
+{
+    rk4_chain_body<P, F64>(src, blockIdx.x);
+}
+
 // FP32 with P >= 2 DOFs per thread in packed FP32x2 arithmetic: the step of
 // rk4_chain_kernel<P, false>, every packed operation rounding each lane as the scalar
 // one does (the same bits), with DOF p of the thread in lane .x and DOF p + P/2 in
@@ -288,8 +341,8 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
 // E_k = (e_k, e_{k+P/2}) = X_k - X_{k-1}, and leaves two pairs per stage to assemble
 // from scalars: (left neighbour, x_{P/2-1}) for E_0 and (x_{P/2}, right neighbour)
 // for E_{P/2}.  Packing halves the FP32 instructions the stage issues.
-template <int P, int MAXT, class Src>
-__global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
+template <int P, class Src>
+__device__ __forceinline__ void rk4_chain_pk_body(const Src& src, int64_t q)
 {
     static_assert(P >= 2 && P % 2 == 0, "pairs of DOFs");
     constexpr int H = P / 2;
@@ -297,7 +350,6 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
     __shared__ float edge_first[2][32][32];  // first DOF of every thread
     __shared__ int any_bad;
 
-    const int64_t q = blockIdx.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
@@ -451,6 +503,30 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
     if (bad) any_bad = 1;
     __syncthreads();
     if (t == 0) src.finish(q, n, any_bad != 0);
+}
+
+template <int P, int MAXT, class Src>
+__global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
+{
+    rk4_chain_pk_body<P>(src, blockIdx.x);
+}
+
+// Persistent form for the serving engine: the generation loop of persist.cuh around the
+// body of rk4_chain_kernel (FP64, or FP32 at P = 1) or rk4_chain_pk_kernel (FP32, P >= 2),
+// one generation item per CTA in turn.  The CTA has the thread count of the size class
+// (64 threads for P = 1, 2, 4: s < 256; 256 for P = 8: s <= 2048).
+template <int P, bool F64, int MAXT>
+__global__ void __launch_bounds__(MAXT) rk4_chain_persist_kernel(const PersistIO pio)
+{
+    persist_loop(pio, [&](int64_t n, int64_t chunk) {
+        ChainSlotSrc<F64, true> src;
+        src.io = SlotIO{n, pio.slot_ids, pio.slots, pio.status, chunk};
+        src.pio = &pio;
+        for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
+            if constexpr (!F64 && P >= 2) rk4_chain_pk_body<P>(src, q);
+            else rk4_chain_body<P, F64>(src, q);
+        }
+    });
 }
 
 // Double-FP32 (CHO_FP32X2): the FP64 form of rk4_chain_kernel, operation for
@@ -647,6 +723,34 @@ cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaS
     }
     ChainSlotSrc<false> s{io};
     return launch_any<false>(s, io.n_inst, s_max, st);
+}
+
+int chain_persist_threads(int P) { return P == 8 ? 256 : 64; }
+
+cudaError_t launch_rk4_chain_persist(int P, const PersistIO& pio, bool fp64, int grid, cudaStream_t st)
+{
+    if (grid <= 0) return cudaErrorInvalidValue;
+    const int th = chain_persist_threads(P);
+    switch (P) {
+        case 1:
+            if (fp64) rk4_chain_persist_kernel<1, true, 64><<<grid, th, 0, st>>>(pio);
+            else rk4_chain_persist_kernel<1, false, 64><<<grid, th, 0, st>>>(pio);
+            break;
+        case 2:
+            if (fp64) rk4_chain_persist_kernel<2, true, 64><<<grid, th, 0, st>>>(pio);
+            else rk4_chain_persist_kernel<2, false, 64><<<grid, th, 0, st>>>(pio);
+            break;
+        case 4:
+            if (fp64) rk4_chain_persist_kernel<4, true, 64><<<grid, th, 0, st>>>(pio);
+            else rk4_chain_persist_kernel<4, false, 64><<<grid, th, 0, st>>>(pio);
+            break;
+        case 8:
+            if (fp64) rk4_chain_persist_kernel<8, true, 256><<<grid, th, 0, st>>>(pio);
+            else rk4_chain_persist_kernel<8, false, 256><<<grid, th, 0, st>>>(pio);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rk4_chain_dw(const ChainSys& sys, const BatchIO& io, cudaStream_t st)

@@ -18,6 +18,7 @@
 // The whole horizon runs with the state in registers; only checkpoints and
 // the final state are written to memory.
 #include "cho_internal.h"
+#include "persist.cuh"
 #include "rk4_common.cuh"
 #include "../../include/cho.h"
 
@@ -99,46 +100,84 @@ struct BatchSrc {
 // Slot form (serving): resident state block [x(S), v(S), cx(S), cv(S)] in the
 // kernel's precision (FP32: the scaled velocity u = (h/6) v in place of v, converted
 // by the serving engine at admission and retirement), coefficient block in the batch
-// layout of one set.
-template <bool F64, int S>
+// layout of one set.  FRESH (persistent kernels): the slot table and ids live in mapped
+// host memory and change between generations, so they are read with volatile loads and
+// the state blocks through L2 only (a block may hold another request's state than the
+// last time this SM's L1 saw it); finished slots go to the completion ring.
+template <bool F64, int S, bool FRESH = false>
 struct SlotSrc {
     SlotIO io;
+    const PersistIO* pio = nullptr;
     using Real = std::conditional_t<F64, double, float>;
 
+    __device__ int32_t id(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile int32_t*)io.slot_ids)[q];
+        else return io.slot_ids[q];
+    }
     __device__ const SlotDesc& d(int64_t q) const { return io.slots[io.slot_ids[q]]; }
+    __device__ const void* f_coef(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile SlotDesc*)io.slots)[id(q)].coef;
+        else return d(q).coef;
+    }
+    __device__ void* f_state(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile SlotDesc*)io.slots)[id(q)].state;
+        else return d(q).state;
+    }
     __device__ int64_t count() const { return io.n_inst; }
-    __device__ int s(int64_t q) const { return d(q).s; }
-    __device__ double h(int64_t q) const { return d(q).h; }
-    __device__ int64_t steps(int64_t q) const { return d(q).remaining < io.chunk ? d(q).remaining : io.chunk; }
+    __device__ int s(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile SlotDesc*)io.slots)[id(q)].s;
+        else return d(q).s;
+    }
+    __device__ double h(int64_t q) const
+    {
+        if constexpr (FRESH) return ((const volatile SlotDesc*)io.slots)[id(q)].h;
+        else return d(q).h;
+    }
+    __device__ int64_t steps(int64_t q) const
+    {
+        int64_t rem;
+        if constexpr (FRESH) rem = ((const volatile SlotDesc*)io.slots)[id(q)].remaining;
+        else rem = d(q).remaining;
+        return rem < io.chunk ? rem : io.chunk;
+    }
     __device__ int64_t ckpt_every() const { return 0; }
 
     __device__ void coef(int64_t q, int row, int j, Real& hi, float& lo) const
     {
         if constexpr (F64) {
-            hi = ((const double*)d(q).coef)[row * S + j];
+            hi = ((const double*)f_coef(q))[row * S + j];
             lo = 0.f;
         } else {
-            const float* b = (const float*)d(q).coef;
+            const float* b = (const float*)f_coef(q);
             hi = b[row * S + j];
             lo = b[S * S + row * S + j];
         }
     }
+    __device__ Real ld(const Real* p) const
+    {
+        if constexpr (FRESH) return __ldcg(p);
+        else return *p;
+    }
     __device__ void load(int64_t q, int row, Real& x, Real& v, float& cx, float& cv) const
     {
-        const Real* st = (const Real*)d(q).state;
-        x = st[row];
-        v = st[S + row];
+        const Real* st = (const Real*)f_state(q);
+        x = ld(st + row);
+        v = ld(st + S + row);
         if constexpr (F64) {
             cx = cv = 0.f;
         } else {
-            cx = st[2 * S + row];
-            cv = st[3 * S + row];
+            cx = ld(st + 2 * S + row);
+            cv = ld(st + 3 * S + row);
         }
     }
     __device__ void checkpoint(int64_t, int64_t, int, Real, Real, float, float) const {}
     __device__ void store(int64_t q, int row, Real x, Real v, float cx, float cv, bool) const
     {
-        Real* st = (Real*)d(q).state;
+        Real* st = (Real*)f_state(q);
         st[row] = x;
         st[S + row] = v;
         if constexpr (!F64) {
@@ -149,16 +188,26 @@ struct SlotSrc {
     // once per instance, after every lane has stored: book the steps run, flag a bad state
     __device__ void finish(int64_t q, int64_t ran, bool bad) const
     {
-        const int32_t slot = io.slot_ids[q];
-        io.slots[slot].remaining -= ran;
-        if (bad) io.status[slot] = CHO_ENONFINITE;
+        const int32_t slot = id(q);
+        if constexpr (FRESH) {
+            volatile SlotDesc* sd = (volatile SlotDesc*)io.slots + slot;
+            const int64_t left = sd->remaining - ran;
+            sd->remaining = left;
+            if (bad) ((volatile int32_t*)io.status)[slot] = CHO_ENONFINITE;
+            if (left == 0 || bad) persist_complete(*pio, slot);
+        } else {
+            io.slots[slot].remaining -= ran;
+            if (bad) io.status[slot] = CHO_ENONFINITE;
+        }
     }
 };
 
 // ---- the kernel ------------------------------------------------------------------
 
+// The work of CTA `cta` of a launch (the kernel below; the persistent kernel calls it
+// for every CTA-sized share of a generation).
 template <int S, bool F64, class Src>
-__global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
+__device__ __forceinline__ void rk4_small_body(const Src& src, int64_t cta)
 {
     using Real = std::conditional_t<F64, double, float>;
     constexpr int R = rows_per_lane(S);
@@ -166,7 +215,7 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     constexpr int GPB = kSmallThreads / G;        // groups per block
     __shared__ Real xch[G > 1 ? 2 : 1][G > 1 ? GPB : 1][G > 1 ? S : 1];
 
-    const int64_t tid = (int64_t)blockIdx.x * kSmallThreads + threadIdx.x;
+    const int64_t tid = cta * kSmallThreads + threadIdx.x;
     const int64_t q = tid / G;
     const int g = (int)(tid % G);
     const int grp = threadIdx.x / G;
@@ -300,6 +349,27 @@ __global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
     for (int r = 0; r < R; ++r) src.store(q, g * R + r, x[r], v[r], cx[r], cv[r], bad);
     if constexpr (G > 1) bad = __any_sync(gmask, bad);
     if (g == 0) src.finish(q, n, bad);
+}
+
+template <int S, bool F64, class Src>
+__global__ void __launch_bounds__(kSmallThreads) rk4_small_kernel(const Src src)
+{
+    rk4_small_body<S, F64>(src, blockIdx.x);
+}
+
+// Persistent form for the serving engine: the generation loop of persist.cuh around
+// the same body, over the generation's slot ids.
+template <int S, bool F64>
+__global__ void __launch_bounds__(kSmallThreads) rk4_small_persist_kernel(const PersistIO pio)
+{
+    constexpr int G = S / rows_per_lane(S);
+    persist_loop(pio, [&](int64_t n, int64_t chunk) {
+        SlotSrc<F64, S, true> src;
+        src.io = SlotIO{n, pio.slot_ids, pio.slots, pio.status, chunk};
+        src.pio = &pio;
+        const int64_t ctas = (n * G + kSmallThreads - 1) / kSmallThreads;
+        for (int64_t c = blockIdx.x; c < ctas; c += gridDim.x) rk4_small_body<S, F64>(src, c);
+    });
 }
 
 template <int S, bool F64, class Src>
@@ -1393,6 +1463,25 @@ cudaError_t launch_rk4_small_dw(const SmallSys& sys, const BatchIO& io, cudaStre
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st)
 {
     return dispatch<SlotSrc>(S, fp64, io.n_inst, st, [&](auto& s) { s.io = io; });
+}
+
+cudaError_t launch_rk4_small_persist(int S, const PersistIO& pio, bool fp64, int grid, cudaStream_t st)
+{
+#define CHO_PERSIST_CASE(SV)                                                                            \
+    case SV:                                                                                            \
+        if (fp64) rk4_small_persist_kernel<SV, true><<<grid, kSmallThreads, 0, st>>>(pio);             \
+        else rk4_small_persist_kernel<SV, false><<<grid, kSmallThreads, 0, st>>>(pio);                 \
+        return cudaGetLastError();
+    if (grid <= 0) return cudaErrorInvalidValue;
+    switch (S) {
+        CHO_PERSIST_CASE(2)
+        CHO_PERSIST_CASE(4)
+        CHO_PERSIST_CASE(8)
+        CHO_PERSIST_CASE(16)
+        CHO_PERSIST_CASE(32)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CHO_PERSIST_CASE
 }
 
 }  // namespace cho

@@ -18,12 +18,28 @@
 // how its horizon is cut into chunks or on which requests share its launches.
 // This follows the paper's use of the model as a fixed-priority real-time
 // workload (Section 5) with the GPU as the executor.
+//
+// Persistent mode (cho_config.persistent): rk4_small groups and chain groups (s <= 2048)
+// are served by a kernel that stays resident on the group's stream and runs one chunk
+// per generation (persist.h): the slot table, the status words, each group's slot-id
+// list and its completion ring live in pinned host memory mapped into the device, the
+// host rings a doorbell instead of launching, and the kernel appends finished slots to
+// the ring.  State blocks are copied on a second stream of the group while its kernel
+// holds the first.  The resident kernels together hold at most half the SMs' worth of
+// CTAs (each CTA on one SM at most) and 60 % of the register file, so they stay
+// co-resident with each other and at least half the SMs stay whole for the relaunched
+// kernels (dense groups, which allocate clusters and tensor memory per launch, and any
+// group beyond the cap, which falls back to relaunching); a group with no resident
+// request tells its kernel to quit.  Results are bitwise those of the relaunch mode.
 #include "../../include/cho.h"
 #include "cho_internal.h"
 #include "ctx.h"
+#include "persist.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
@@ -36,6 +52,13 @@
 #include <vector>
 
 namespace cho {
+
+// Called by the serving buffers before they allocate.  An allocation of device or
+// page-locked host memory serialises all streams; a resident serving kernel waits for the
+// serving thread's next doorbell, so on the serving thread every resident kernel is first
+// told to quit (it finishes any generation in flight without the host, then leaves) and is
+// started again at its group's next generation.
+void serving_before_alloc();
 
 static double now_s()
 {
@@ -81,7 +104,9 @@ size_t round_class(size_t b)
     return c;
 }
 
-// Device blocks of power-of-two size classes carved from 64 MiB arenas.
+// Device blocks of power-of-two size classes carved from 64 MiB arenas.  Arenas come from
+// stream-ordered allocation on the pool's own stream (no wait for other streams, where
+// resident serving kernels may be waiting for the serving thread) and are freed at release.
 class BlockPool {
 public:
     BlockPool() = default;
@@ -97,9 +122,18 @@ public:
             fl.pop_back();
             return p;
         }
+        if (!st_) {
+            *err = cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking);
+            if (*err != cudaSuccess) {
+                st_ = nullptr;
+                return nullptr;
+            }
+        }
         const size_t arena = std::max<size_t>((size_t)64 << 20, cls);
         void* base = nullptr;
-        *err = cudaMalloc(&base, arena);
+        serving_before_alloc();
+        *err = cudaMallocAsync(&base, arena, st_);
+        if (*err == cudaSuccess) *err = cudaStreamSynchronize(st_);
         if (*err != cudaSuccess) return nullptr;
         arenas_.push_back(base);
         for (size_t off = cls; off + cls <= arena; off += cls) fl.push_back((char*)base + off);
@@ -108,7 +142,12 @@ public:
     void put(size_t cls, void* p) { free_[cls].push_back(p); }
     void release()
     {
-        for (void* a : arenas_) cudaFree(a);
+        for (void* a : arenas_) cudaFreeAsync(a, st_);
+        if (st_) {
+            cudaStreamSynchronize(st_);
+            cudaStreamDestroy(st_);
+        }
+        st_ = nullptr;
         arenas_.clear();
         free_.clear();
     }
@@ -116,8 +155,13 @@ public:
 private:
     std::map<size_t, std::vector<void*>> free_;
     std::vector<void*> arenas_;
+    cudaStream_t st_ = nullptr;
 };
 
+// Growth of the serving loop's buffers never frees: cudaFree and cudaFreeHost wait for
+// the whole device, and a resident (persistent) kernel is waiting for the serving thread's
+// next doorbell, so a free there would stall both until the kernel's wait runs out.  A
+// buffer that grows (at least doubling) keeps its old allocations until release().
 template <class T>
 class PinnedBuf {
 public:
@@ -129,13 +173,13 @@ public:
     {
         *err = cudaSuccess;
         if (n <= cap_) return p_;
-        release();
-        size_t want = std::max(n, (size_t)4096);
-        *err = cudaHostAlloc((void**)&p_, want * sizeof(T), cudaHostAllocDefault);
-        if (*err != cudaSuccess) {
-            p_ = nullptr;
-            return nullptr;
-        }
+        size_t want = std::max(std::max(n, (size_t)4096), 2 * cap_);
+        T* p = nullptr;
+        serving_before_alloc();
+        *err = cudaHostAlloc((void**)&p, want * sizeof(T), cudaHostAllocDefault);
+        if (*err != cudaSuccess) return nullptr;
+        if (p_) old_.push_back(p_);
+        p_ = p;
         cap_ = want;
         return p_;
     }
@@ -143,6 +187,8 @@ public:
     void release()
     {
         if (p_) cudaFreeHost(p_);
+        for (T* o : old_) cudaFreeHost(o);
+        old_.clear();
         p_ = nullptr;
         cap_ = 0;
     }
@@ -150,6 +196,7 @@ public:
 private:
     T* p_ = nullptr;
     size_t cap_ = 0;
+    std::vector<T*> old_;
 };
 
 template <class T>
@@ -163,26 +210,23 @@ public:
     {
         *err = cudaSuccess;
         if (n <= cap_) return p_;
-        release();
-        size_t want = std::max(n, (size_t)1024);
-        *err = cudaMalloc((void**)&p_, want * sizeof(T));
-        if (*err != cudaSuccess) {
-            p_ = nullptr;
-            return nullptr;
-        }
+        size_t want = std::max(std::max(n, (size_t)1024), 2 * cap_);
+        T* p = nullptr;
+        serving_before_alloc();
+        *err = cudaMalloc((void**)&p, want * sizeof(T));
+        if (*err != cudaSuccess) return nullptr;
+        if (p_) old_.push_back(p_);            // kept until release(): see PinnedBuf
+        p_ = p;
         cap_ = want;
         return p_;
     }
     T* ptr() const { return p_; }
     size_t cap() const { return cap_; }
-    void swap(DevBuf& o)
-    {
-        std::swap(p_, o.p_);
-        std::swap(cap_, o.cap_);
-    }
     void release()
     {
         if (p_) cudaFree(p_);
+        for (T* o : old_) cudaFree(o);
+        old_.clear();
         p_ = nullptr;
         cap_ = 0;
     }
@@ -190,7 +234,48 @@ public:
 private:
     T* p_ = nullptr;
     size_t cap_ = 0;
+    std::vector<T*> old_;
 };
+
+// Pinned host memory mapped into the device (host and device pointer).
+template <class T>
+class Mapped {
+public:
+    Mapped() = default;
+    Mapped(const Mapped&) = delete;
+    Mapped& operator=(const Mapped&) = delete;
+    ~Mapped() { release(); }
+    cudaError_t alloc(size_t n)
+    {
+        release();
+        serving_before_alloc();
+        cudaError_t e = cudaHostAlloc((void**)&h, std::max<size_t>(n, 1) * sizeof(T), cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            h = nullptr;
+            return e;
+        }
+        std::memset((void*)h, 0, std::max<size_t>(n, 1) * sizeof(T));
+        e = cudaHostGetDevicePointer((void**)&d, (void*)h, 0);
+        n_ = n;
+        return e;
+    }
+    void release()
+    {
+        if (h) cudaFreeHost((void*)h);
+        h = nullptr;
+        d = nullptr;
+        n_ = 0;
+    }
+    size_t size() const { return n_; }
+    T* h = nullptr;
+    T* d = nullptr;
+
+private:
+    size_t n_ = 0;
+};
+
+// Lanes per instance of rk4_small at padded size S (rows_per_lane of rk4_small.cu).
+int small_lanes(int S) { return S <= 4 ? 1 : (S == 8 ? 4 : S); }
 
 }  // namespace
 
@@ -216,6 +301,21 @@ struct Group {
     PinnedBuf<unsigned char> h_up;
     PinnedBuf<unsigned char> h_down;
     PinnedBuf<SlotDesc> h_desc;
+    // persistent mode
+    bool persist = false;           // the group can be served by a resident kernel
+    bool running = false;           // its kernel takes doorbells (launched, not told to quit)
+    bool resident = false;          // its kernel may still be on `st` (until synchronised)
+    bool inflight = false;          // a generation rung on the resident kernel, not yet retired
+    int grid = 0;
+    int64_t footprint = 0;          // registers the resident kernel holds
+    uint64_t gen = 0;               // last generation rung
+    unsigned long long ring_tail = 0;
+    double t_ring = 0.0;
+    double t_last = 0.0;            // last start or completed generation of the resident kernel
+    cudaStream_t cst = nullptr;     // state copies while the kernel holds `st`
+    Mapped<PersistCtl> ctl;
+    Mapped<int32_t> ids;
+    Mapped<int32_t> ring;
 };
 
 struct ServeEngine {
@@ -239,11 +339,26 @@ struct ServeEngine {
     DevBuf<int32_t> d_status;
     BlockPool pool;
     std::map<GroupKey, Group*> groups;
+    // persistent mode: slot table and status words in mapped host memory
+    bool persistent = false;
+    bool withhold_doorbell = false;  // test hook (CHO_TEST_WITHHOLD_DOORBELL=1)
+    Mapped<SlotDesc> m_slots;
+    Mapped<int32_t> m_status;
+    int64_t persist_regs = 0, persist_cap = 0;     // registers held by resident kernels, and the cap
+    int64_t persist_ctas = 0, persist_cta_cap = 0; // their CTAs, and the cap (half the SMs)
+    SlotDesc* slots_d() { return persistent ? m_slots.d : d_slots.ptr(); }
+    int32_t* status_d() { return persistent ? m_status.d : d_status.ptr(); }
 
     void run();
     Group* group_for(Req* r, cudaError_t* e);
+    cudaError_t upload(Group* g, cudaStream_t copy_st);
     cudaError_t launch(Group* g);
+    cudaError_t launch_persist(Group* g, bool* fell_back);
     void retire(Group* g);          // caller holds mu
+    void retire_persist(Group* g);  // caller holds mu
+    void timed_out(Group* g);       // caller holds mu
+    void quit(Group* g);
+    void park();                    // quit every resident kernel (before an allocation)
     void fail_all(cho_status st_code);
     void release(Req* r);           // caller holds mu
 };
@@ -255,6 +370,7 @@ void ServeEngine::fail_all(cho_status code)
     const double t = now_s();
     for (auto& kv : groups) {
         Group* g = kv.second;
+        quit(g);
         for (auto* list : {&g->members, &g->incoming})
             for (Req* r : *list) {
                 r->state = RQ_DONE;
@@ -295,7 +411,11 @@ Group* ServeEngine::group_for(Req* r, cudaError_t* e)
 {
     *e = cudaSuccess;
     const cho_system_impl* sys = r->sys;
-    const int size = sys->path == PATH_SMALL ? sys->S : (sys->path == PATH_CHAIN ? chain_dofs_per_thread(sys->s) : sys->s);
+    // chains of more than 2048 masses need wider CTAs than the persistent chain kernel's
+    const bool wide_chain = sys->path == PATH_CHAIN && sys->s > 2048;
+    const int size = sys->path == PATH_SMALL
+                         ? sys->S
+                         : (sys->path == PATH_CHAIN ? (wide_chain ? 16 : chain_dofs_per_thread(sys->s)) : sys->s);
     GroupKey key(sys->path, size, r->prec, sys->path == PATH_DENSE ? r->sys : nullptr);
     auto it = groups.find(key);
     if (it != groups.end()) return it->second;
@@ -312,8 +432,16 @@ Group* ServeEngine::group_for(Req* r, cudaError_t* e)
         *e = cudaEventCreate(&g->k0);
         if (*e == cudaSuccess) *e = cudaEventCreate(&g->k1);
     }
+    g->persist = persistent && (sys->path == PATH_SMALL || (sys->path == PATH_CHAIN && !wide_chain));
+    if (*e == cudaSuccess && g->persist) {
+        *e = cudaStreamCreateWithFlags(&g->cst, cudaStreamNonBlocking);
+        if (*e == cudaSuccess) *e = g->ctl.alloc(1);
+        if (*e == cudaSuccess) *e = g->ids.alloc((size_t)slot_cap);
+        if (*e == cudaSuccess) *e = g->ring.alloc((size_t)slot_cap);
+    }
     if (*e != cudaSuccess) {
         if (g->st) cudaStreamDestroy(g->st);
+        if (g->cst) cudaStreamDestroy(g->cst);
         delete g;
         return nullptr;
     }
@@ -321,12 +449,12 @@ Group* ServeEngine::group_for(Req* r, cudaError_t* e)
     return g;
 }
 
-// Upload the group's new requests, advance every member by one chunk, and queue the
-// read-back of status words and of the states that finish in this chunk.
-cudaError_t ServeEngine::launch(Group* g)
+// Upload the group's new requests (state blocks on copy_st, table entries and status
+// words: mapped host memory in persistent mode, else copies on copy_st) and make them
+// members.
+cudaError_t ServeEngine::upload(Group* g, cudaStream_t copy_st)
 {
     cudaError_t e = cudaSuccess;
-    const int64_t L = g->chunk;
     size_t up_bytes = 0;
     for (Req* r : g->incoming) up_bytes += r->bytes;
     unsigned char* up = g->h_up.get(std::max<size_t>(up_bytes, 1), &e);
@@ -357,7 +485,7 @@ cudaError_t ServeEngine::launch(Group* g)
                 f[3 * n + i] = (float)(vd - (double)f[n + i]);
             }
         }
-        e = cudaMemcpyAsync(r->block, dst, state_bytes(sys, r->prec), cudaMemcpyHostToDevice, g->st);
+        e = cudaMemcpyAsync(r->block, dst, state_bytes(sys, r->prec), cudaMemcpyHostToDevice, copy_st);
         off += r->bytes;
         SlotDesc sd{};
         if (sys->path == PATH_SMALL) {
@@ -377,13 +505,29 @@ cudaError_t ServeEngine::launch(Group* g)
         sd.remaining = r->n_steps;
         sd.s = s;
         hd[k] = sd;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_slots.ptr() + r->slot, &hd[k], sizeof(SlotDesc), cudaMemcpyHostToDevice, g->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_status.ptr() + r->slot, 0, sizeof(int32_t), g->st);
+        if (persistent) {
+            // the slot is free: no kernel reads its entry until the host hands it out
+            m_slots.h[r->slot] = sd;
+            ((volatile int32_t*)m_status.h)[r->slot] = 0;
+        } else {
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_slots.ptr() + r->slot, &hd[k], sizeof(SlotDesc), cudaMemcpyHostToDevice, copy_st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_status.ptr() + r->slot, 0, sizeof(int32_t), copy_st);
+        }
     }
     if (e != cudaSuccess) return e;
     g->members.insert(g->members.end(), g->incoming.begin(), g->incoming.end());
     g->incoming.clear();
+    return cudaSuccess;
+}
+
+// Upload the group's new requests, advance every member by one chunk (one launch), and
+// queue the read-back of status words and of the states that finish in this chunk.
+cudaError_t ServeEngine::launch(Group* g)
+{
+    const int64_t L = g->chunk;
+    cudaError_t e = upload(g, g->st);
+    if (e != cudaSuccess) return e;
     g->launched = g->members;
     const size_t n_ids = g->launched.size();
     if (n_ids == 0) return cudaSuccess;
@@ -397,7 +541,7 @@ cudaError_t ServeEngine::launch(Group* g)
     if (e != cudaSuccess) return e;
     const int path = std::get<0>(g->key), size = std::get<1>(g->key), prec = std::get<2>(g->key);
     const bool f64 = fp64_prec(prec);
-    SlotIO io{(int64_t)n_ids, g->d_ids.ptr(), d_slots.ptr(), d_status.ptr(), L};
+    SlotIO io{(int64_t)n_ids, g->d_ids.ptr(), slots_d(), status_d(), L};
     g->max_run = 0;
     for (Req* r : g->launched) g->max_run = std::max(g->max_run, std::min(L, r->remaining));
     if (g->k0) e = cudaEventRecord(g->k0, g->st);
@@ -418,7 +562,7 @@ cudaError_t ServeEngine::launch(Group* g)
             e = launch_rk4_dense_slots(ds, io, f64, g->st);
     }
     if (e == cudaSuccess && g->k1) e = cudaEventRecord(g->k1, g->st);
-    if (e == cudaSuccess) e = launch_gather_status(g->d_ids.ptr(), d_status.ptr(), g->d_st.ptr(), (int64_t)n_ids, g->st);
+    if (e == cudaSuccess) e = launch_gather_status(g->d_ids.ptr(), status_d(), g->d_st.ptr(), (int64_t)n_ids, g->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hst, g->d_st.ptr(), n_ids * sizeof(int32_t), cudaMemcpyDeviceToHost, g->st);
     size_t down_bytes = 0;
@@ -506,9 +650,239 @@ void ServeEngine::retire(Group* g)
     }
 }
 
+// Persistent mode: upload the new members (which may allocate, and so park every resident
+// kernel: first), start the group's resident kernel if it takes no doorbells (within the
+// caps; *fell_back when it does not fit, and the caller relaunches instead), write the
+// generation's slot ids and ring the doorbell.
+cudaError_t ServeEngine::launch_persist(Group* g, bool* fell_back)
+{
+    *fell_back = false;
+    const int path = std::get<0>(g->key), size = std::get<1>(g->key), prec = std::get<2>(g->key);
+    const bool f64 = fp64_prec(prec);
+    const size_t n = g->members.size() + g->incoming.size();
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = upload(g, g->cst);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->cst);     // blocks on the device before the doorbell
+    if (e != cudaSuccess) return e;
+    // a kernel idle for half its doorbell wait may leave before the next ring: replace it
+    if (g->running && (g->ctl.h->status == CHO_ETIMEOUT || now_s() - g->t_last > 0.5)) quit(g);
+    if (!g->running) {
+        const int threads = path == PATH_SMALL ? kSmallThreads : chain_persist_threads(size);
+        const int64_t per_cta = (int64_t)threads * 128;          // registers a CTA may hold
+        const int64_t want = path == PATH_SMALL
+                                 ? ((int64_t)n * small_lanes(size) + kSmallThreads - 1) / kSmallThreads
+                                 : (int64_t)n;
+        // each resident CTA sits on its own SM at most, so capping their number at half the
+        // SMs leaves the other half whole for the launched kernels (a 512-thread dense CTA
+        // needs a full register file)
+        const int64_t room = std::min((persist_cap - persist_regs) / per_cta, persist_cta_cap - persist_ctas);
+        const int64_t most = path == PATH_SMALL ? 2 * (int64_t)ctx->sm_count : (int64_t)ctx->sm_count;
+        const int64_t grid = std::min(std::min(want, most), room);
+        if (grid < 1) {
+            *fell_back = true;
+            return cudaSuccess;
+        }
+        // the group's previous kernel (told to quit, or timed out) has left its stream
+        if (g->resident) {
+            e = cudaStreamSynchronize(g->st);
+            if (e != cudaSuccess) return e;
+            g->resident = false;
+        }
+        PersistCtl* c = g->ctl.h;
+        std::memset((void*)c, 0, sizeof(PersistCtl));
+        g->gen = 0;
+        g->ring_tail = 0;
+        g->grid = (int)grid;
+        g->footprint = grid * per_cta;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        PersistIO pio{g->ctl.d, g->ids.d, m_slots.d, m_status.d, g->ring.d, (uint32_t)g->ring.size()};
+        e = path == PATH_SMALL ? launch_rk4_small_persist(size, pio, f64, g->grid, g->st)
+                               : launch_rk4_chain_persist(size, pio, f64, g->grid, g->st);
+        if (e != cudaSuccess) return e;
+        g->running = true;
+        g->resident = true;
+        g->t_last = now_s();
+        persist_regs += g->footprint;
+        persist_ctas += g->grid;
+    }
+    g->launched = g->members;
+    const int64_t L = g->chunk;
+    g->max_run = 0;
+    for (size_t i = 0; i < g->launched.size(); ++i) {
+        Req* r = g->launched[i];
+        g->ids.h[i] = r->slot;
+        g->max_run = std::max(g->max_run, std::min(L, r->remaining));
+    }
+    PersistCtl* c = g->ctl.h;
+    ((volatile int64_t*)&c->n_items)[0] = (int64_t)g->launched.size();
+    ((volatile int64_t*)&c->chunk)[0] = L;
+    std::atomic_thread_fence(std::memory_order_seq_cst);        // payload before the doorbell
+    ++g->gen;
+    if (!withhold_doorbell) ((volatile uint64_t*)&c->doorbell)[0] = g->gen;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    g->t_ring = now_s();
+    g->busy = true;
+    g->inflight = true;
+    return cudaSuccess;
+}
+
+// Tell the group's resident kernel to leave: it finishes a generation in flight, then
+// leaves at its next doorbell wait.  Its CTAs no longer count against the caps.
+void ServeEngine::quit(Group* g)
+{
+    if (!g->running) return;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    ((volatile int32_t*)&g->ctl.h->quit)[0] = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    g->running = false;
+    persist_regs -= g->footprint;
+    persist_ctas -= g->grid;
+    g->footprint = 0;
+}
+
+void ServeEngine::park()
+{
+    if (withhold_doorbell) return;   // test hook: the withheld kernels are to time out by themselves
+    for (auto& kv : groups) quit(kv.second);
+}
+
+// The resident kernel's doorbell wait ran out (it has left): every request of the
+// generation in flight ends with CHO_ETIMEOUT.  Caller holds mu.
+void ServeEngine::timed_out(Group* g)
+{
+    const double t = now_s();
+    for (Req* r : g->launched) {
+        r->status = CHO_ETIMEOUT;
+        r->state = RQ_DONE;
+        r->t_done = t;
+    }
+    auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
+        if (r->state != RQ_DONE) return false;
+        release(r);
+        return true;
+    });
+    g->members.erase(it, g->members.end());
+    g->launched.clear();
+    g->busy = false;
+    g->inflight = false;
+    quit(g);                        // releases the caps if the kernel still counted
+}
+
+// A generation of the resident kernel is complete: read the completion ring, book the
+// steps, read back finished states (copy stream) and hand them out.  Caller holds mu.
+void ServeEngine::retire_persist(Group* g)
+{
+    const double t = now_s();
+    const int64_t L = g->chunk;
+    PersistCtl* c = g->ctl.h;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    const unsigned long long head = ((volatile unsigned long long*)&c->ring_head)[0];
+    std::vector<char> finished(g->launched.size(), 0);
+    {
+        std::unordered_map<int32_t, size_t> pos;
+        for (size_t i = 0; i < g->launched.size(); ++i) pos[g->launched[i]->slot] = i;
+        for (unsigned long long k = g->ring_tail; k < head; ++k) {
+            const int32_t slot = ((volatile int32_t*)g->ring.h)[k % g->ring.size()];
+            auto it = pos.find(slot);
+            if (it != pos.end()) finished[it->second] = 1;
+        }
+        g->ring_tail = head;
+    }
+    cudaError_t e = cudaSuccess;
+    size_t down_bytes = 0;
+    for (size_t i = 0; i < g->launched.size(); ++i)
+        if (finished[i]) down_bytes += g->launched[i]->bytes;
+    unsigned char* down = g->h_down.get(std::max<size_t>(down_bytes, 1), &e);
+    size_t doff = 0;
+    for (size_t i = 0; i < g->launched.size() && e == cudaSuccess; ++i) {
+        Req* r = g->launched[i];
+        r->remaining -= std::min<int64_t>(L, r->remaining);
+        const int32_t code = ((volatile int32_t*)m_status.h)[r->slot];
+        r->reading_back = finished[i] && code == 0 && r->remaining == 0;
+        if (r->reading_back) {
+            r->readback_off = doff;
+            e = cudaMemcpyAsync(down + doff, r->block, state_bytes(r->sys, r->prec), cudaMemcpyDeviceToHost, g->cst);
+            doff += r->bytes;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->cst);
+    if (e != cudaSuccess) {
+        fail_all(CHO_ECUDA);
+        return;
+    }
+    for (Req* r : g->launched) {
+        const int32_t code = ((volatile int32_t*)m_status.h)[r->slot];
+        if (code != 0) {
+            r->status = (cho_status)code;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        } else if (r->remaining == 0 && r->reading_back) {
+            const cho_system_impl* sys = r->sys;
+            const int nn = sys->path == PATH_SMALL ? sys->S : sys->s;
+            const int sz = sys->s;
+            r->x.resize(sz);
+            r->v.resize(sz);
+            const unsigned char* src = down + r->readback_off;
+            if (fp64_prec(r->prec)) {
+                const double* d = (const double*)src;
+                for (int k = 0; k < sz; ++k) {
+                    r->x[k] = d[k];
+                    r->v[k] = d[nn + k];
+                }
+            } else {
+                const float* f = (const float*)src;
+                for (int k = 0; k < sz; ++k) {           // small and chain families: scaled velocity
+                    r->x[k] = (double)f[k] + (double)f[2 * nn + k];
+                    r->v[k] = unscaled_velocity((double)f[nn + k] + (double)f[3 * nn + k], r->h);
+                }
+            }
+            r->status = CHO_OK;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        } else if (r->remaining == 0) {
+            r->status = CHO_EINTERNAL;                   // finished without a completion entry
+            r->state = RQ_DONE;
+            r->t_done = t;
+        } else if (r->cancel) {
+            r->status = CHO_ECANCELLED;
+            r->state = RQ_DONE;
+            r->t_done = t;
+        }
+    }
+    auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
+        if (r->state != RQ_DONE) return false;
+        release(r);
+        return true;
+    });
+    g->members.erase(it, g->members.end());
+    g->launched.clear();
+    g->busy = false;
+    g->inflight = false;
+    g->t_last = t;
+    // chunk-length tuning from the generation's wall time (doorbell to completion)
+    if (ctx->cfg.chunk_us > 0 && g->max_run > 0) {
+        const double per_step_us = 1e6 * (t - g->t_ring) / (double)g->max_run;
+        if (per_step_us > 0.0) {
+            double target = (double)ctx->cfg.chunk_us / per_step_us;
+            target = std::min(std::max(target, 0.5 * (double)L), 2.0 * (double)L);
+            g->chunk = std::min<int64_t>(std::max<int64_t>(std::llround(target), 16), (int64_t)1 << 22);
+        }
+    }
+}
+
+namespace {
+thread_local ServeEngine* t_serving = nullptr;   // the engine whose serving thread this is
+}
+
+void serving_before_alloc()
+{
+    if (t_serving) t_serving->park();
+}
+
 void ServeEngine::run()
 {
     DeviceGuard dg(ctx->device);
+    t_serving = this;
     std::vector<Group*> to_launch;
     while (true) {
         bool progressed = false;
@@ -520,7 +894,34 @@ void ServeEngine::run()
             // finished launches
             for (auto& kv : groups) {
                 Group* g = kv.second;
-                if (!g->busy) continue;
+                if (!g->inflight) continue;
+                // persistent: the generation is complete when every CTA has counted it
+                volatile PersistCtl* c = g->ctl.h;
+                if (c->status == CHO_ETIMEOUT) {
+                    timed_out(g);
+                    progressed = true;
+                } else if (now_s() - g->t_ring > 10.0 && c->done < (unsigned long long)g->grid * g->gen) {
+                    // host-side deadline: the kernel is told to leave and its stream drained
+                    // before the generation's blocks are given back
+                    quit(g);
+                    if (cudaStreamSynchronize(g->st) != cudaSuccess) {
+                        fail_all(CHO_ECUDA);
+                        return;
+                    }
+                    g->resident = false;
+                    if (c->done >= (unsigned long long)g->grid * g->gen) retire_persist(g);
+                    else timed_out(g);
+                    if (failed) return;
+                    progressed = true;
+                } else if (c->done >= (unsigned long long)g->grid * g->gen) {
+                    retire_persist(g);
+                    if (failed) return;
+                    progressed = true;
+                }
+            }
+            for (auto& kv : groups) {
+                Group* g = kv.second;
+                if (!g->busy || g->inflight) continue;
                 const cudaError_t q = cudaEventQuery(g->ev);
                 if (q == cudaErrorNotReady) continue;
                 if (q != cudaSuccess) {
@@ -586,14 +987,24 @@ void ServeEngine::run()
                 }
                 if (blocked) break;
             }
-            for (auto& kv : groups)
-                if (!kv.second->busy && (!kv.second->members.empty() || !kv.second->incoming.empty()))
-                    to_launch.push_back(kv.second);
+            for (auto& kv : groups) {
+                Group* g = kv.second;
+                if (!g->busy && (!g->members.empty() || !g->incoming.empty())) to_launch.push_back(g);
+                // a resident kernel with nothing left to run leaves its SMs to the others
+                if (!g->busy && g->running && g->members.empty() && g->incoming.empty()) quit(g);
+            }
             if (progressed) cv.notify_all();
         }
         // launches outside the lock (only this thread touches the groups' device side)
         for (Group* g : to_launch) {
-            const cudaError_t e = launch(g);
+            cudaError_t e = cudaSuccess;
+            bool relaunch = !g->persist;
+            if (g->persist) {
+                bool fell_back = false;
+                e = launch_persist(g, &fell_back);
+                relaunch = fell_back;
+            }
+            if (e == cudaSuccess && relaunch) e = launch(g);
             if (e != cudaSuccess) {
                 std::lock_guard<std::mutex> lk(mu);
                 fail_all(CHO_ECUDA);
@@ -618,8 +1029,18 @@ static ServeEngine* engine(cho_ctx* ctx, cho_status* err)
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaSuccess;
     en->slot_cap = ctx->cfg.max_slots;
-    en->d_slots.get((size_t)en->slot_cap, &e);
-    if (e == cudaSuccess) en->d_status.get((size_t)en->slot_cap, &e);
+    en->persistent = ctx->cfg.persistent != 0;
+    if (en->persistent) {
+        e = en->m_slots.alloc((size_t)en->slot_cap);
+        if (e == cudaSuccess) e = en->m_status.alloc((size_t)en->slot_cap);
+        en->persist_cap = (int64_t)(0.6 * (double)ctx->sm_count * 65536.0);
+        en->persist_cta_cap = std::max(1, ctx->sm_count / 2);
+        const char* hook = std::getenv("CHO_TEST_WITHHOLD_DOORBELL");
+        en->withhold_doorbell = hook && hook[0] == '1';
+    } else {
+        en->d_slots.get((size_t)en->slot_cap, &e);
+        if (e == cudaSuccess) en->d_status.get((size_t)en->slot_cap, &e);
+    }
     if (e != cudaSuccess) {
         delete en;
         *err = fail(CHO_ENOMEM, "cho_submit: slot table of %d slots: %s", ctx->cfg.max_slots, cudaGetErrorString(e));
@@ -648,9 +1069,17 @@ void serve_stop(cho_ctx* ctx)
     if (en->worker.joinable()) en->worker.join();
     {
         DeviceGuard g(ctx->device);
+        for (auto& kv : en->groups) en->quit(kv.second);
         for (auto& kv : en->groups) {
             Group* gr = kv.second;
             cudaStreamSynchronize(gr->st);
+            if (gr->cst) {
+                cudaStreamSynchronize(gr->cst);
+                cudaStreamDestroy(gr->cst);
+            }
+            gr->ctl.release();
+            gr->ids.release();
+            gr->ring.release();
             cudaEventDestroy(gr->ev);
             if (gr->k0) cudaEventDestroy(gr->k0);
             if (gr->k1) cudaEventDestroy(gr->k1);
@@ -663,6 +1092,8 @@ void serve_stop(cho_ctx* ctx)
         en->pool.release();
         en->d_slots.release();
         en->d_status.release();
+        en->m_slots.release();
+        en->m_status.release();
     }
     delete en;
 }

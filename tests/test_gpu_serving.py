@@ -418,3 +418,79 @@ def test_dense_requests_with_their_own_k():
         cho.cho_destroy_system(sys_)
     finally:
         cho.cho_shutdown(ctx)
+
+
+# ---- persistent serving -------------------------------------------------------------------
+
+def test_persistent_mode_gives_the_bits_of_the_relaunch_mode():
+    """The same requests served by resident kernels (small and chain groups: doorbell per
+    chunk, completion ring, mapped slot table) and by per-chunk launches: bitwise equal results,
+    alone and inside a mixed stream of 300 others, and equal to the batch API."""
+    ref_ctx = cho.cho_init(0, chunk_steps=512)
+    ref_mix = Mix(ref_ctx, seed=5)
+    probes = [ref_mix.request(k) for k in range(len(ref_mix.systems))]
+    others = [ref_mix.request(k) for k in range(300)]
+    try:
+        t = [ref_mix.submit(r, priority=k % 3) for k, r in enumerate(probes + others)]
+        ref = wait_all(ref_ctx, t, [r["s"] for r in probes + others])
+        ref = [ref[x] for x in t]
+        for r, got in zip(probes, ref[:len(probes)]):
+            b = batch_result(ref_ctx, r)
+            assert np.array_equal(got["x"], b["x"][0]) and np.array_equal(got["v"], b["v"][0]), r["kind"]
+    finally:
+        ref_mix.close()
+        cho.cho_shutdown(ref_ctx)
+    for chunk in (512, 97):
+        ctx = cho.cho_init(0, chunk_steps=chunk, persistent=1)
+        mix = Mix(ctx, seed=5)
+        try:
+            reqs = [dict(r, sys=mix.systems[k % len(mix.systems)][1]) for k, r in enumerate(probes)]
+            reqs += [dict(r, sys=mix.systems[k % len(mix.systems)][1]) for k, r in enumerate(others)]
+            t = [mix.submit(r, priority=k % 3) for k, r in enumerate(reqs)]
+            got = wait_all(ctx, t, [r["s"] for r in reqs])
+            for x, want in zip(t, ref):
+                assert not isinstance(got[x], int), got[x]
+                assert np.array_equal(got[x]["x"], want["x"]) and np.array_equal(got[x]["v"], want["v"]), chunk
+            # the resident kernels leave when their groups empty; a later request starts them again
+            r2 = reqs[0]
+            t2 = mix.submit(r2)
+            again = wait_all(ctx, [t2], [r2["s"]])[t2]
+            assert np.array_equal(again["x"], ref[0]["x"])
+        finally:
+            mix.close()
+            cho.cho_shutdown(ctx)
+
+
+def test_persistent_mode_doorbell_wait_runs_out_cleanly():
+    """Test hook: the serving thread never rings the resident kernels' doorbell, so their
+    bounded waits run out (about a second): the requests end with CHO_ETIMEOUT and nothing
+    hangs; a new context without the hook serves normally."""
+    import os
+
+    os.environ["CHO_TEST_WITHHOLD_DOORBELL"] = "1"
+    try:
+        ctx = cho.cho_init(0, chunk_steps=256, persistent=1)
+        mix = Mix(ctx, seed=6)
+        try:
+            reqs = [mix.request(0, n_steps=300), mix.request(2, n_steps=300)]     # 2-DOF and a 40-mass chain
+            t = [mix.submit(r) for r in reqs]
+            t0 = time.time()
+            got = wait_all(ctx, t, [r["s"] for r in reqs], timeout=30.0)
+            assert all(got[x] == cho.CHO_ETIMEOUT for x in t), got
+            assert time.time() - t0 < 20.0
+        finally:
+            mix.close()
+            cho.cho_shutdown(ctx)
+    finally:
+        del os.environ["CHO_TEST_WITHHOLD_DOORBELL"]
+    ctx = cho.cho_init(0, chunk_steps=256, persistent=1)
+    mix = Mix(ctx, seed=6)
+    try:
+        r = mix.request(0, n_steps=300)
+        t = mix.submit(r)
+        got = wait_all(ctx, [t], [r["s"]])[t]
+        b = batch_result(ctx, r)
+        assert np.array_equal(got["x"], b["x"][0])
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
