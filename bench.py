@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=4000)
+    p.add_argument("--serve-requests", type=int, default=200_000)
     return p.parse_args()
 
 
@@ -214,21 +214,26 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
     return res
 
 
-def run_serving(cho, inputs, device, n_req, load=0.8, stream_seconds=20.0, chunk_us=2000):
-    """Mixed request stream through cho_submit / cho_poll (continuous batching).
+def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_seconds=8.0, load_seconds=6.0,
+                loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000):
+    """The mixed request stream of BASELINE config 5 through cho_submit / cho_poll_any.
 
-    Requests follow the mixed-load recipe of request_stream: Poisson arrivals, s
-    log-uniform over {2..512} (2-DOF, chains, dense groups of 8 sizes), horizons
-    log-uniform 1e3..1e5 steps, three priority classes 20/30/50 %, FP32 + Kahan.
-    A saturated burst of n_req // 10 requests first measures the service rate; the
-    stream then arrives at `load` times that rate.  Returns throughput and the
-    p50/p99 submit-to-done latency per class.  The engine runs on its own context whose
-    kernel groups tune their chunk length to about `chunk_us` of device time each.
-    """
+    Requests follow request_stream: s log-uniform over {2..512} (2-DOF, chains, dense groups
+    of 8 sizes), horizons log-uniform 1e3..1e5 steps, three priority classes 20/30/50 %,
+    FP32 + compensation, 40 GB state budget.  Service rate: the stream submitted with about
+    `outstanding` requests always queued or resident for `sat_seconds` (DOF-steps of the
+    requests that finished after the first second, over that window).  Then Poisson arrivals
+    at each `loads` fraction of that rate for `load_seconds` each: p50/p99 submit-to-done
+    latency per class, queue depth and resident bytes sampled every 20 ms.  At most
+    `max_requests` requests in all (config 5's 200k).  persistent: resident kernels for the
+    small and chain groups (cho_config.persistent)."""
     import time as _t
 
-    ctx = cho.cho_init(device, chunk_us=chunk_us)
-    st = inputs.request_stream(n_req=n_req, rate_per_s=1.0)
+    ctx = cho.cho_init(device, chunk_us=chunk_us, persistent=int(persistent), budget_bytes=40 << 30)
+    st = inputs.request_stream(n_req=max_requests, rate_per_s=1.0)
+    kinds, sizes, steps, prios = st["kind"], st["s"], st["n_steps"], st["priority"]
+    work = sizes.astype(np.float64) * steps
+    mean_work = float(work.mean())
     systems = {}
 
     def system_for(kind, s_):
@@ -246,73 +251,113 @@ def run_serving(cho, inputs, device, n_req, load=0.8, stream_seconds=20.0, chunk
         return systems[key]
 
     rng = np.random.default_rng(inputs.SEED_BASE + 99)
-    reqs = []
-    for i in range(n_req):
-        kind, s_ = int(st["kind"][i]), int(st["s"][i])
+    nxt = [0]
+    open_t = {}                                          # ticket -> request index
+
+    def submit():
+        i = nxt[0]
+        if i >= max_requests:
+            return False
+        nxt[0] += 1
+        kind, s_ = int(kinds[i]), int(sizes[i])
         sys_, hs = system_for(kind, s_)
         k = i % len(hs)
-        # FP32 + compensation throughout: with few requests of one dense system resident at a
-        # time, the few-instance kernels (one instance per CTA or cluster) serve them with a
-        # quarter to a fifth of the tensor-core kernel's time per step
-        prec = "fp32_kahan"
-        reqs.append((sys_, k, rng.uniform(-1, 1, s_), np.zeros(s_), float(hs[k]), int(st["n_steps"][i]),
-                     int(st["priority"][i]), s_, prec))
-    work = np.array([r[7] * r[5] for r in reqs], dtype=np.float64)
+        t = cho.cho_submit(ctx, sys_, rng.uniform(-1, 1, s_), np.zeros(s_), float(hs[k]), int(steps[i]),
+                           "fp32_kahan", int(prios[i]), k)
+        open_t[t] = i
+        return True
 
-    def drive(idx, gaps):
-        tickets = {}
+    def collect(sink):
+        while True:
+            code, t, tm = cho.cho_poll_any(ctx)
+            if code == cho.CHO_PENDING:
+                return
+            i = open_t.pop(t)
+            sink.append((i, code, tm["t_submit"], tm["t_done"]))
+
+    def drain(limit_s=120.0):
+        t_end = _t.perf_counter() + limit_s
+        sink = []
+        while open_t and _t.perf_counter() < t_end:
+            collect(sink)
+            _t.sleep(0.001)
+        for t in list(open_t):
+            cho.cho_cancel(ctx, t)
+        while open_t:
+            collect(sink)
+            _t.sleep(0.001)
+        return sink
+
+    # warm-up: one request of each kind and size (system set-up, kernel attributes)
+    for kind in (0, 1, 2):
+        for s_ in sorted({int(x) for x, kk in zip(sizes[:5000], kinds[:5000]) if kk == kind}):
+            sys_, hs = system_for(kind, s_)
+            t = cho.cho_submit(ctx, sys_, np.zeros(s_), np.zeros(s_), float(hs[0]), 10, "fp32_kahan", 0, 0)
+            open_t[t] = -1
+    drain()
+    # saturation: keep `outstanding` requests in the engine
+    log(f"serving ({'persistent' if persistent else 'relaunch'}): saturation")
+    done = []
+    t0 = _t.perf_counter()
+    while _t.perf_counter() - t0 < sat_seconds and nxt[0] < max_requests:
+        while len(open_t) < outstanding and submit():
+            pass
+        collect(done)
+        _t.sleep(0.0005)
+    # the engine's times are CLOCK_MONOTONIC seconds (time.monotonic)
+    win0 = time.monotonic() - (_t.perf_counter() - t0) + 1.0
+    t_sat_end = time.monotonic()
+    sat_work = sum(work[i] for i, code, _, td in done if code == cho.CHO_OK and td >= win0)
+    rate = sat_work / max(t_sat_end - win0, 1e-9)
+    n_sat = nxt[0]
+    drain()
+    out = {"mode": "persistent" if persistent else "relaunch", "saturated_dof_steps_per_s": rate,
+           "saturation": {"seconds": sat_seconds, "outstanding": outstanding, "requests": n_sat,
+                          "completed": len(done)}, "loads": {}}
+    # Poisson streams at fractions of the service rate
+    for rho in loads:
+        lam = rho * rate / mean_work
+        first = nxt[0]
+        gaps = np.random.default_rng(inputs.SEED_BASE + int(rho * 100)).exponential(1.0 / lam, size=1 << 20)
+        depth, mem, sink = [], [], []
         t0 = _t.perf_counter()
-        next_t = 0.0
-        pending = {}
-        lat = {0: [], 1: [], 2: []}
-        for j, i in enumerate(idx):
-            next_t += gaps[j]
-            while _t.perf_counter() - t0 < next_t:
-                _t.sleep(min(0.0005, max(0.0, next_t - (_t.perf_counter() - t0))))
-            sys_, k, x0, v0, h, n, pr, s_, prec = reqs[i]
-            t = cho.cho_submit(ctx, sys_, x0, v0, h, n, prec, pr, k)
-            pending[t] = (i, pr, s_)
-        deadline = _t.perf_counter() + 300.0
-        while pending and _t.perf_counter() < deadline:
-            for t in list(pending):
-                i, pr, s_ = pending[t]
-                stt, res = cho.cho_poll(ctx, t, s_)
-                if stt == cho.CHO_OK:
-                    lat[pr].append(res["t_done"] - res["t_submit"])
-                    del pending[t]
-            _t.sleep(0.0005)
-        if pending:
-            log(f"serving: {len(pending)} requests unfinished after the deadline; cancelling")
-            for t in list(pending):
-                cho.cho_cancel(ctx, t)
-        return _t.perf_counter() - t0, lat
-
-    # service rate: a burst of n_cal requests submitted at once (its makespan includes the
-    # longest horizon, so this rate is a lower bound and the offered load errs low)
-    n_cal = max(50, n_req // 10)
-    cal = np.arange(n_cal)
-    log(f"serving: burst of {n_cal} requests")
-    t_cal, _ = drive(cal, np.zeros(n_cal))
-    rate_dof = work[cal].sum() / t_cal                      # saturated DOF-steps/s
-    lam = load * rate_dof / work.mean()                      # requests per second at this load
-    # the Poisson stream: at most stream_seconds of arrivals
-    n_stream = int(min(n_req - n_cal, max(20, lam * stream_seconds)))
-    idx = np.arange(n_cal, n_cal + n_stream)
-    gaps = np.random.default_rng(inputs.SEED_BASE + 98).exponential(1.0 / lam, size=len(idx))
-    log(f"serving: burst took {t_cal:.1f} s ({rate_dof:.3e} DOF-steps/s); stream of {n_stream} requests at {lam:.1f}/s")
-    t_run, lat = drive(idx, gaps)
-    log(f"serving: stream took {t_run:.1f} s")
+        next_t, g, last_sample = 0.0, 0, 0.0
+        while True:
+            now = _t.perf_counter() - t0
+            if now >= load_seconds or nxt[0] >= max_requests:
+                break
+            while next_t <= now and nxt[0] < max_requests:
+                submit()
+                next_t += gaps[g]
+                g += 1
+            collect(sink)
+            if now - last_sample >= 0.02:
+                stt = cho.cho_serve_stats(ctx)
+                depth.append(stt["queued"])
+                mem.append(stt["resident_bytes"])
+                last_sample = now
+            _t.sleep(0.0002)
+        offered = nxt[0] - first
+        t_off = _t.perf_counter() - t0
+        sink += drain()
+        lat = {c: [td - ts for i, code, ts, td in sink if code == cho.CHO_OK and i >= first and prios[i] == c]
+               for c in range(3)}
+        out["loads"][f"{rho:.2f}"] = {
+            "arrival_rate_per_s": lam, "offered_requests": offered, "offered_rate_per_s": offered / t_off,
+            "completed_ok": int(sum(len(v) for v in lat.values())),
+            "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99),
+                                        "n": len(lat[c])} for c in range(3)},
+            "queue_depth": {"mean": float(np.mean(depth)) if depth else None, "max": int(max(depth)) if depth else None},
+            "resident_bytes": {"mean": float(np.mean(mem)) if mem else None, "max": int(max(mem)) if mem else None}}
+        log(f"serving load {rho}: {offered} requests at {offered / t_off:.0f}/s "
+            f"(target {lam:.0f}/s), p99 {[out['loads'][f'{rho:.2f}']['latency_s'][f'class{c}']['p99'] for c in range(3)]}")
+    out["requests_total"] = int(nxt[0])
+    out["mix"] = ("config 5: s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5 "
+                  "steps, classes 20/30/50 %, FP32 + compensation, 40 GB budget; each kernel group's chunk tuned to "
+                  f"about {chunk_us} us")
     for sys_, _ in systems.values():
         cho.cho_destroy_system(sys_)
     cho.cho_shutdown(ctx)
-    out = {"requests": int(n_cal + n_stream), "burst_requests": int(n_cal), "saturated_dof_steps_per_s": rate_dof,
-           "chunking": f"each kernel group's chunk length tuned to about {chunk_us} us of device time",
-           "offered_load": load, "arrival_rate_per_s": lam,
-           "stream_dof_steps_per_s": work[idx].sum() / t_run, "stream_seconds": t_run,
-           "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99), "n": len(lat[c])}
-                         for c in range(3)},
-           "mix": "s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5, "
-                  "classes 20/30/50 %, Poisson arrivals; FP32 + compensation"}
     return out
 
 
@@ -382,7 +427,8 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
         k = cfg["x0"].shape[0]
         idx = np.array([0, k - 1][:n_sample]) if n_sample <= 2 else np.linspace(0, k - 1, n_sample).astype(int)
         key = (id(cfg["x0"]), cfg["n_steps"], every, tuple(idx.tolist()))
-        cached = ref_cache.get(key)
+        hit = ref_cache.get(key)
+        cached = hit[1] if hit is not None and hit[0] is cfg["x0"] else None
         x0 = torch.as_tensor(cfg["x0"][idx], device=dev)
         v0 = torch.as_tensor(cfg["v0"][idx], device=dev)
         h = torch.as_tensor(cfg["h"][idx], device=dev)
@@ -405,7 +451,7 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
             cho.cho_destroy_system(s2)
             ref = cached or oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx],
                                              cfg["v0"][idx], cfg["h"][idx], cfg["n_steps"], every, threads=nt)
-        ref_cache[key] = ref
+        ref_cache[key] = (cfg["x0"], ref)       # the array is held, so its id is not reused
         torch.cuda.synchronize()
         e = 0.0
         for key in ("x_traj", "v_traj"):
@@ -923,7 +969,8 @@ def main():
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks,
                                                   alu["fp32_peak_tflops"])
             if args.serve_requests > 0:
-                line["serving"] = run_serving(cho, inputs, local_rank, args.serve_requests)
+                line["serving"] = {"relaunch": run_serving(cho, inputs, local_rank, False, args.serve_requests),
+                                   "persistent": run_serving(cho, inputs, local_rank, True, args.serve_requests)}
                 log("periodic mode")
                 line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:

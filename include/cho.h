@@ -424,6 +424,13 @@ cho_status cho_submit(cho_ctx* ctx, const cho_request* req, uint64_t* ticket);
  * CHO_ENONFINITE, CHO_ECUDA).  CHO_ENOTFOUND for an unknown or released ticket. */
 cho_status cho_poll(cho_ctx* ctx, uint64_t ticket, cho_result* out);
 
+/* The next finished request of any ticket, in the order requests finish: *ticket is set
+ * and its status returned (CHO_OK with out->x, out->v filled when not NULL -- they must
+ * hold s values of that request's system -- or the request's error); the ticket is then
+ * released as by cho_poll.  CHO_PENDING when no finished request is waiting.  A serving
+ * client collects results this way without polling every ticket it holds. */
+cho_status cho_poll_any(cho_ctx* ctx, uint64_t* ticket, cho_result* out);
+
 /* Cancel a queued or running request (it stops at its next chunk boundary). */
 cho_status cho_cancel(cho_ctx* ctx, uint64_t ticket);
 

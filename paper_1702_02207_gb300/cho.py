@@ -43,7 +43,7 @@ EXPORTED = [
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
     "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load", "cho_measure_fma_peak",
-    "cho_integrate_packed",
+    "cho_integrate_packed", "cho_poll_any",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -134,6 +134,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_tune_load": ([V, ctypes.c_char_p, ctypes.POINTER(I32)], I32),
             "cho_measure_fma_peak": ([V, I32, I32, _dp, _dp], I32),
             "cho_integrate_packed": ([V, ctypes.POINTER(cho_batch_desc), I32, V], I32),
+            "cho_poll_any": ([V, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(cho_result)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -452,6 +453,18 @@ def cho_poll(ctx, ticket, s):
         return st, None
     _check(st)
     return st, None
+
+
+def cho_poll_any(ctx):
+    """The next finished request of any ticket: (status, ticket, times) with times a dict of
+    t_submit, t_admit, t_done; (CHO_PENDING, None, None) when none is waiting.  Results of
+    failed requests come back as their status code, not as an exception."""
+    t = ctypes.c_uint64()
+    r = cho_result(None, None, 0.0, 0.0, 0.0)
+    st = load().cho_poll_any(ctx, ctypes.byref(t), ctypes.byref(r))
+    if st == CHO_PENDING:
+        return st, None, None
+    return st, t.value, {"t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
 
 
 def cho_cancel(ctx, ticket):

@@ -361,6 +361,21 @@ struct ServeEngine {
     void park();                    // quit every resident kernel (before an allocation)
     void fail_all(cho_status st_code);
     void release(Req* r);           // caller holds mu
+    // finished requests in the order they finished (cho_poll_any); caller holds mu
+    std::deque<uint64_t> done_fifo;
+    void mark_done(Req* r)
+    {
+        r->state = RQ_DONE;
+        done_fifo.push_back(r->ticket);
+        // tickets collected by cho_poll stay in the queue until cho_poll_any passes them;
+        // drop them when they dominate, so a client that only calls cho_poll holds no memory
+        if (done_fifo.size() > 2 * reqs.size() + 4096) {
+            std::deque<uint64_t> keep;
+            for (uint64_t t : done_fifo)
+                if (reqs.count(t)) keep.push_back(t);
+            done_fifo.swap(keep);
+        }
+    }
 };
 
 void ServeEngine::fail_all(cho_status code)
@@ -373,7 +388,7 @@ void ServeEngine::fail_all(cho_status code)
         quit(g);
         for (auto* list : {&g->members, &g->incoming})
             for (Req* r : *list) {
-                r->state = RQ_DONE;
+                mark_done(r);
                 r->status = code;
                 r->t_done = t;
             }
@@ -383,7 +398,7 @@ void ServeEngine::fail_all(cho_status code)
     }
     for (auto& q : queue) {
         for (Req* r : q) {
-            r->state = RQ_DONE;
+            mark_done(r);
             r->status = code;
             r->t_done = t;
         }
@@ -598,7 +613,7 @@ void ServeEngine::retire(Group* g)
         const int32_t code = hst ? hst[i] : 0;
         if (code != 0) {
             r->status = (cho_status)code;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         } else if (r->remaining == 0 && r->reading_back) {
             const cho_system_impl* sys = r->sys;
@@ -623,11 +638,11 @@ void ServeEngine::retire(Group* g)
                 }
             }
             r->status = CHO_OK;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         } else if (r->cancel) {
             r->status = CHO_ECANCELLED;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         }
     }
@@ -753,7 +768,7 @@ void ServeEngine::timed_out(Group* g)
     const double t = now_s();
     for (Req* r : g->launched) {
         r->status = CHO_ETIMEOUT;
-        r->state = RQ_DONE;
+        mark_done(r);
         r->t_done = t;
     }
     auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
@@ -814,7 +829,7 @@ void ServeEngine::retire_persist(Group* g)
         const int32_t code = ((volatile int32_t*)m_status.h)[r->slot];
         if (code != 0) {
             r->status = (cho_status)code;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         } else if (r->remaining == 0 && r->reading_back) {
             const cho_system_impl* sys = r->sys;
@@ -837,15 +852,15 @@ void ServeEngine::retire_persist(Group* g)
                 }
             }
             r->status = CHO_OK;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         } else if (r->remaining == 0) {
             r->status = CHO_EINTERNAL;                   // finished without a completion entry
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         } else if (r->cancel) {
             r->status = CHO_ECANCELLED;
-            r->state = RQ_DONE;
+            mark_done(r);
             r->t_done = t;
         }
     }
@@ -937,7 +952,7 @@ void ServeEngine::run()
                 if (g->busy) continue;
                 auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
                     if (!r->cancel) return false;
-                    r->state = RQ_DONE;
+                    mark_done(r);
                     r->status = CHO_ECANCELLED;
                     r->t_done = now_s();
                     release(r);
@@ -955,7 +970,7 @@ void ServeEngine::run()
                     if (r->cancel) {
                         queue[p].pop_front();
                         --n_queued;
-                        r->state = RQ_DONE;
+                        mark_done(r);
                         r->status = CHO_ECANCELLED;
                         r->t_done = now_s();
                         ++completed;
@@ -1192,6 +1207,41 @@ extern "C" cho_status cho_poll(cho_ctx* ctx, uint64_t ticket, cho_result* out)
     delete r;
     if (st != CHO_OK) return fail(st, "cho_poll: request %llu ended with status %d", (unsigned long long)ticket, (int)st);
     return CHO_OK;
+}
+
+extern "C" cho_status cho_poll_any(cho_ctx* ctx, uint64_t* ticket, cho_result* out)
+{
+    clear_error();
+    if (!ctx || !ticket) return fail(CHO_EINVAL, "cho_poll_any: NULL argument");
+    ServeEngine* en;
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        en = ctx->serve;
+    }
+    if (!en) return CHO_PENDING;
+    std::lock_guard<std::mutex> lk(en->mu);
+    while (!en->done_fifo.empty()) {
+        const uint64_t t = en->done_fifo.front();
+        en->done_fifo.pop_front();
+        auto it = en->reqs.find(t);
+        if (it == en->reqs.end()) continue;            // already collected by cho_poll
+        Req* r = it->second;
+        const cho_status st = r->status;
+        if (out) {
+            if (st == CHO_OK) {
+                if (out->x) std::memcpy(out->x, r->x.data(), sizeof(double) * r->x.size());
+                if (out->v) std::memcpy(out->v, r->v.data(), sizeof(double) * r->v.size());
+            }
+            out->t_submit = r->t_submit;
+            out->t_admit = r->t_admit;
+            out->t_done = r->t_done;
+        }
+        *ticket = t;
+        en->reqs.erase(it);
+        delete r;
+        return st;
+    }
+    return CHO_PENDING;
 }
 
 extern "C" cho_status cho_cancel(cho_ctx* ctx, uint64_t ticket)

@@ -494,3 +494,29 @@ def test_persistent_mode_doorbell_wait_runs_out_cleanly():
     finally:
         mix.close()
         cho.cho_shutdown(ctx)
+
+
+def test_poll_any_returns_every_finished_request_once():
+    """cho_poll_any hands out finished requests of any ticket, each once, with the timings
+    cho_poll gives; tickets collected by cho_poll are skipped."""
+    ctx = cho.cho_init(0, chunk_steps=300)
+    mix = Mix(ctx, seed=7)
+    try:
+        reqs = [mix.request(k, n_steps=600) for k in range(24)]
+        tickets = [mix.submit(r, priority=k % 3) for k, r in enumerate(reqs)]
+        got = {}
+        by_poll = wait_all(ctx, tickets[:4], [r["s"] for r in reqs[:4]])      # four through cho_poll
+        t0 = time.time()
+        while len(got) < len(tickets) - 4 and time.time() - t0 < 60:
+            code, t, tm = cho.cho_poll_any(ctx)
+            if code == cho.CHO_PENDING:
+                time.sleep(0.002)
+                continue
+            assert code == cho.CHO_OK and t not in got and t not in by_poll
+            assert tm["t_submit"] <= tm["t_admit"] <= tm["t_done"]
+            got[t] = tm
+        assert sorted(got) == sorted(tickets[4:])
+        assert cho.cho_poll_any(ctx)[0] == cho.CHO_PENDING
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
