@@ -148,6 +148,14 @@ typedef struct cho_system_desc {
     const double* springs;
     const double* M;
     const double* K;
+    const double* mass_coupling;   /* TWO_DOF / CHAIN, optional (NULL: diagonal M): (n_sys, s),
+                                      entry i the off-diagonal mass m_{i,i+1} = m_{i+1,i} coupling
+                                      mass i and mass i + 1 (the last entry of each set is unused).
+                                      M is then tridiagonal -- eq. 1 with general m_ij, as a
+                                      consistent mass matrix of a discretised rod has -- and the
+                                      system is built and integrated as a DENSE system of that M and
+                                      the chain's K (s <= 512; cho_system_info reports CHO_DENSE);
+                                      M must be positive definite (CHO_ENOTSPD otherwise). */
 } cho_system_desc;
 
 /* One batch of independent instances of one system.

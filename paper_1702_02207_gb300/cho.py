@@ -64,7 +64,7 @@ class cho_tune_result(ctypes.Structure):
 class cho_system_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("s", ctypes.c_int32), ("n_sys", ctypes.c_int64),
                 ("masses", ctypes.c_void_p), ("springs", ctypes.c_void_p),
-                ("M", ctypes.c_void_p), ("K", ctypes.c_void_p)]
+                ("M", ctypes.c_void_p), ("K", ctypes.c_void_p), ("mass_coupling", ctypes.c_void_p)]
 
 
 class cho_batch_desc(ctypes.Structure):
@@ -211,8 +211,10 @@ def cho_last_error():
 
 # ---- systems -----------------------------------------------------------------------
 
-def cho_create_system(ctx, kind, masses=None, springs=None, M=None, K=None):
-    """Create a system from host arrays: masses/springs (n_sys, s) or M/K (n_sys, s, s)."""
+def cho_create_system(ctx, kind, masses=None, springs=None, M=None, K=None, mass_coupling=None):
+    """Create a system from host arrays: masses/springs (n_sys, s) or M/K (n_sys, s, s).
+    mass_coupling (n_sys, s), spring kinds only: off-diagonal masses m_{i,i+1} (a tridiagonal
+    M; the system is then built as a dense system, see include/cho.h)."""
     kind = KINDS.get(kind, kind)
     keep = []
     if kind == CHO_DENSE:
@@ -228,7 +230,14 @@ def cho_create_system(ctx, kind, masses=None, springs=None, M=None, K=None):
         springs = np.atleast_2d(_host_f64(springs))
         n_sys, s = masses.shape
         keep += [masses, springs]
-        d = cho_system_desc(kind, s, n_sys, masses.ctypes.data, springs.ctypes.data, None, None)
+        mc = None
+        if mass_coupling is not None:
+            mc = np.atleast_2d(_host_f64(mass_coupling))
+            if mc.shape != masses.shape:
+                raise ValueError("mass_coupling must have the shape of masses")
+            keep.append(mc)
+        d = cho_system_desc(kind, s, n_sys, masses.ctypes.data, springs.ctypes.data, None, None,
+                            None if mc is None else mc.ctypes.data)
     out = ctypes.c_void_p()
     _check(load().cho_create_system(ctx, ctypes.byref(d), ctypes.byref(out)))
     del keep

@@ -213,10 +213,47 @@ extern "C" void cho_shutdown(cho_ctx* ctx)
 // systems
 // ------------------------------------------------------------------------------
 
-extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d, cho_system* out)
+extern "C" cho_status cho_create_system(cho_ctx* ctx, const cho_system_desc* d_in, cho_system* out)
 {
     clear_error();
-    if (!ctx || !d || !out) return fail(CHO_EINVAL, "cho_create_system: NULL argument");
+    if (!ctx || !d_in || !out) return fail(CHO_EINVAL, "cho_create_system: NULL argument");
+    // a spring system with coupled masses is eq. 1 with a tridiagonal M: assemble M and K
+    // (K of the chain: K_ii = C_i + C_{i+1}, K_{i,i+1} = -C_{i+1}) and build a dense system
+    cho_system_desc dd = *d_in;
+    const cho_system_desc* d = &dd;
+    std::vector<double> cM, cK;
+    if (d_in->kind != CHO_DENSE && d_in->mass_coupling) {
+        const int s = d_in->s;
+        if (s < 1 || s > 512) return fail(CHO_EINVAL, "cho_create_system: coupled masses need 1 <= s <= 512");
+        if (d_in->n_sys < 1) return fail(CHO_EINVAL, "cho_create_system: n_sys < 1");
+        if (!d_in->masses || !d_in->springs) return fail(CHO_EINVAL, "cho_create_system: masses/springs required");
+        const size_t ss = (size_t)s * s;
+        cM.assign((size_t)d_in->n_sys * ss, 0.0);
+        cK.assign((size_t)d_in->n_sys * ss, 0.0);
+        for (int64_t p = 0; p < d_in->n_sys; ++p) {
+            const double* m = d_in->masses + p * s;
+            const double* c = d_in->springs + p * s;
+            const double* mu = d_in->mass_coupling + p * s;
+            double* M = &cM[(size_t)p * ss];
+            double* K = &cK[(size_t)p * ss];
+            for (int i = 0; i < s; ++i) {
+                if (!std::isfinite(m[i]) || !(m[i] > 0.0) || !std::isfinite(c[i]) || !(c[i] >= 0.0) ||
+                    (i + 1 < s && !std::isfinite(mu[i])))
+                    return fail(CHO_EINVAL, "cho_create_system: set %lld: masses > 0, springs >= 0 and finite "
+                                "couplings required", (long long)p);
+                M[(size_t)i * s + i] = m[i];
+                K[(size_t)i * s + i] = c[i] + (i + 1 < s ? c[i + 1] : 0.0);
+                if (i + 1 < s) {
+                    M[(size_t)i * s + i + 1] = M[(size_t)(i + 1) * s + i] = mu[i];
+                    K[(size_t)i * s + i + 1] = K[(size_t)(i + 1) * s + i] = -c[i + 1];
+                }
+            }
+        }
+        dd.kind = CHO_DENSE;
+        dd.masses = dd.springs = nullptr;
+        dd.M = cM.data();
+        dd.K = cK.data();
+    }
     const int s = d->s;
     const int64_t n_sys = d->n_sys;
     if (s < 1 || s > 8192) return fail(CHO_EINVAL, "cho_create_system: s = %d outside [1, 8192]", s);

@@ -679,20 +679,27 @@ cudaError_t ServeEngine::launch_persist(Group* g, bool* fell_back)
     cudaError_t e = upload(g, g->cst);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->cst);     // blocks on the device before the doorbell
     if (e != cudaSuccess) return e;
-    // a kernel idle for half its doorbell wait may leave before the next ring: replace it
+    const int threads = path == PATH_SMALL ? kSmallThreads : chain_persist_threads(size);
+    const int64_t per_cta = (int64_t)threads * 128;              // registers a CTA may hold
+    const int64_t want = path == PATH_SMALL
+                             ? ((int64_t)n * small_lanes(size) + kSmallThreads - 1) / kSmallThreads
+                             : (int64_t)n;
+    const int64_t most = path == PATH_SMALL ? 2 * (int64_t)ctx->sm_count : (int64_t)ctx->sm_count;
+    // each resident CTA sits on its own SM at most, so capping their number at half the SMs
+    // leaves the other half whole for the launched kernels (a 512-thread dense CTA needs a
+    // full register file)
+    auto room = [&]() {
+        return std::min((persist_cap - persist_regs) / per_cta, persist_cta_cap - persist_ctas);
+    };
+    // a kernel idle for half its doorbell wait may leave before the next ring: replace it;
+    // so is one whose group has outgrown its grid by a quarter when a larger grid fits
     if (g->running && (g->ctl.h->status == CHO_ETIMEOUT || now_s() - g->t_last > 0.5)) quit(g);
+    if (g->running && want > g->grid) {
+        const int64_t bigger = std::min(std::min(want, most), room() + g->grid);
+        if (4 * bigger >= 5 * (int64_t)g->grid) quit(g);
+    }
     if (!g->running) {
-        const int threads = path == PATH_SMALL ? kSmallThreads : chain_persist_threads(size);
-        const int64_t per_cta = (int64_t)threads * 128;          // registers a CTA may hold
-        const int64_t want = path == PATH_SMALL
-                                 ? ((int64_t)n * small_lanes(size) + kSmallThreads - 1) / kSmallThreads
-                                 : (int64_t)n;
-        // each resident CTA sits on its own SM at most, so capping their number at half the
-        // SMs leaves the other half whole for the launched kernels (a 512-thread dense CTA
-        // needs a full register file)
-        const int64_t room = std::min((persist_cap - persist_regs) / per_cta, persist_cta_cap - persist_ctas);
-        const int64_t most = path == PATH_SMALL ? 2 * (int64_t)ctx->sm_count : (int64_t)ctx->sm_count;
-        const int64_t grid = std::min(std::min(want, most), room);
+        const int64_t grid = std::min(std::min(want, most), room());
         if (grid < 1) {
             *fell_back = true;
             return cudaSuccess;

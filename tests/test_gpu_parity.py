@@ -1202,3 +1202,69 @@ def test_fp32x2_is_refused_outside_its_scope():
         cho.cho_destroy_system(sys2)
     finally:
         cho.cho_shutdown(c)
+
+
+# ---- chains with coupled masses (eq. 1 with a tridiagonal M) ------------------------------
+
+def coupled_chain(s, n_inst, seed, per_instance=True, n_steps=1000):
+    """Chains whose mass matrix is tridiagonal: diagonal m_i, off-diagonal m_{i,i+1} =
+    0.2 min(m_i, m_{i+1}) (a consistent-mass-like coupling), springs as in chain_batch; the
+    dense M and K the library assembles, for the oracle."""
+    cfg = inputs.chain_batch(n_inst=n_inst if per_instance else 1, s=s, n_steps=n_steps, seed=seed)
+    m, c = cfg["masses"], cfg["springs"]
+    mu = np.zeros_like(m)
+    mu[:, :-1] = 0.2 * np.minimum(m[:, :-1], m[:, 1:])
+    Ms, Ks = [], []
+    for p in range(m.shape[0]):
+        M = np.diag(m[p]) + np.diag(mu[p, :-1], 1) + np.diag(mu[p, :-1], -1)
+        Ms.append(M)
+        Ks.append(inputs.dense_stiffness_chain(c[p:p + 1])[0])
+    M, K = np.stack(Ms), np.stack(Ks)
+    w = inputs.omega_max_dense(M, K)
+    h = inputs.fp32_exact(2 * math.pi / np.atleast_1d(w) / 100)
+    rng = np.random.default_rng(seed + 1)
+    x0 = rng.normal(0, 0.1, (n_inst, s))
+    h = np.resize(h, n_inst) if per_instance else np.full(n_inst, h[0])
+    return {"kind": "dense", "s": s, "M": M, "K": K, "masses": m, "springs": c, "mu": mu, "x0": x0,
+            "v0": np.zeros((n_inst, s)), "h": h, "n_steps": n_steps}
+
+
+@pytest.mark.parametrize("s", [3, 17, 40, 100, 300])
+@pytest.mark.parametrize("per_instance", [True, False])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("fp32_kahan", TOL_FP32)])
+def test_chain_with_coupled_masses_matches_dense_oracle(ctx, s, per_instance, prec, tol):
+    cfg = coupled_chain(s, 7, 1300 + s, per_instance)
+    sys_ = cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"],
+                                 mass_coupling=cfg["mu"])
+    try:
+        w, s_info, n_sys = cho.cho_system_info(sys_)
+        assert s_info == s and n_sys == cfg["masses"].shape[0]
+        assert np.isclose(w, np.max(inputs.omega_max_dense(cfg["M"], cfg["K"])), rtol=1e-9)
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], cfg["n_steps"], prec, 125,
+                                      trajectory=True, energy=True)
+        E = cho.cho_energy(ctx, sys_, out["x_traj"][:, -1], out["v_traj"][:, -1])
+    finally:
+        cho.cho_destroy_system(sys_)
+    ref = oracle_run(cfg, ckpt_every=125)
+    check(out, ref, tol)
+    import oracle
+
+    M = cfg["M"] if per_instance else np.repeat(cfg["M"], 7, 0)
+    K = cfg["K"] if per_instance else np.repeat(cfg["K"], 7, 0)
+    E_ref = np.array([oracle.energy_dense(M[i], K[i], out["x_traj"][i, -1:], out["v_traj"][i, -1:])[0]
+                      for i in range(7)])
+    assert np.allclose(E, E_ref, rtol=1e-12)
+
+
+def test_chain_with_coupled_masses_rejects_bad_input(ctx):
+    cfg = inputs.chain_batch(n_inst=1, s=6, n_steps=1)
+    mu = np.full_like(cfg["masses"], 0.0)
+    mu[0, 2] = 10.0 * cfg["masses"].max()              # M not positive definite
+    with pytest.raises(cho.ChoError) as ei:
+        cho.cho_create_system(ctx, "chain", masses=cfg["masses"], springs=cfg["springs"], mass_coupling=mu)
+    assert ei.value.status == cho.CHO_ENOTSPD
+    big = inputs.chain_batch(n_inst=1, s=600, n_steps=1)
+    with pytest.raises(cho.ChoError) as ei:
+        cho.cho_create_system(ctx, "chain", masses=big["masses"], springs=big["springs"],
+                              mass_coupling=0.1 * big["masses"])
+    assert ei.value.status == cho.CHO_EINVAL
