@@ -215,7 +215,7 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
 
 
 def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_seconds=8.0, load_seconds=6.0,
-                loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000):
+                loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000, ref_rate=None):
     """The mixed request stream of BASELINE config 5 through cho_submit / cho_poll_any.
 
     Requests follow request_stream: s log-uniform over {2..512} (2-DOF, chains, dense groups
@@ -226,7 +226,8 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
     at each `loads` fraction of that rate for `load_seconds` each: p50/p99 submit-to-done
     latency per class, queue depth and resident bytes sampled every 20 ms.  At most
     `max_requests` requests in all (config 5's 200k).  persistent: resident kernels for the
-    small and chain groups (cho_config.persistent)."""
+    small and chain groups (cho_config.persistent).  ref_rate: offer the loads as fractions of
+    this rate instead of the engine's own (the same arrival rates for both engines)."""
     import time as _t
 
     ctx = cho.cho_init(device, chunk_us=chunk_us, persistent=int(persistent), budget_bytes=40 << 30)
@@ -315,8 +316,10 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
            "saturation": {"seconds": sat_seconds, "outstanding": outstanding, "requests": n_sat,
                           "completed": len(done)}, "loads": {}}
     # Poisson streams at fractions of the service rate
+    base = ref_rate if ref_rate else rate
+    out["loads_relative_to"] = "the relaunch engine's saturated rate" if ref_rate else "this engine's saturated rate"
     for rho in loads:
-        lam = rho * rate / mean_work
+        lam = rho * base / mean_work
         first = nxt[0]
         gaps = np.random.default_rng(inputs.SEED_BASE + int(rho * 100)).exponential(1.0 / lam, size=1 << 20)
         depth, mem, sink = [], [], []
@@ -969,8 +972,10 @@ def main():
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks,
                                                   alu["fp32_peak_tflops"])
             if args.serve_requests > 0:
-                line["serving"] = {"relaunch": run_serving(cho, inputs, local_rank, False, args.serve_requests),
-                                   "persistent": run_serving(cho, inputs, local_rank, True, args.serve_requests)}
+                rel = run_serving(cho, inputs, local_rank, False, args.serve_requests)
+                per = run_serving(cho, inputs, local_rank, True, args.serve_requests,
+                                  ref_rate=rel["saturated_dof_steps_per_s"])
+                line["serving"] = {"relaunch": rel, "persistent": per}
                 log("periodic mode")
                 line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:
