@@ -10,17 +10,22 @@
 //   bf16x3: b0 p0 + b0 p1 + b1 p0                 (operands to 16 bits)
 //   bf16x5: bf16x3 + b1 p1 + b2 p0                (B to 24 bits, Xs to 16)
 //   bf16x6: bf16x5 + b0 p2                        (both to 24 bits; s <= 128)
-// (smallest terms are accumulated first).
+// Grouped issue (grp_a below): one MMA per piece of B covers every piece of Xs that
+// piece pairs with, the Xs pieces laid side by side along N, so bf16x5 issues 3 MMAs
+// per K chunk instead of 5 at the same ~45-cycle cost each, and every accumulator holds
+// the products of each order in its own group of 32 columns.
 //
 // Accumulation.  Summing all K/16 chunk products of a stage into one TMEM
 // accumulator lets the tensor core's accumulation rounding build up a bias that
 // acts like a frequency shift, so the error grew with the horizon (bf16x5 at
-// s = 256: 2.4e-5 after 5e3 steps).  bf16x5 and bf16x6 therefore spread the chunk
-// products over several accumulators and add those on the CUDA cores in FP32
-// round-to-nearest: one per 16-wide K chunk in the 2-CTA clusters (s = 256: 5.9e-6
-// after 5e3 steps), one per two chunks in the one-CTA kernel (s = 128: 6.4e-6
-// against 5.6e-6 with one per chunk, 5.5 % faster); bf16x3, whose truncation
-// error dominates, keeps one.
+// s = 256: 2.4e-5 after 5e3 steps).  bf16x5 and bf16x6 therefore spread the K chunks
+// over several accumulators, and the column groups keep the large order-0 products
+// apart from the small ones: each order is summed over the accumulators and the
+// orders added smallest first, on the CUDA cores in FP32 round-to-nearest.  One CTA
+// (two accumulator sets): two accumulators of 96 columns per set, four K chunks each
+// (s = 128, 5e3 steps: 8.0e-6; one accumulator per set was 7 % faster and reached
+// 1.5e-5 in v); 2-CTA clusters: four accumulators; bf16x3, whose truncation error
+// dominates, keeps one.
 
 // Work split.  s <= 64: one CTA per 64 instances, two tiles of 32 stacked along
 // the 128 rows against the block-diagonal [B 0; 0 B] (the MMA shape is fixed at
@@ -37,10 +42,10 @@
 // thread): about 45 cycles per MMA for N <= 64 whether A comes from shared or
 // tensor memory, 64 at N = 128 and 128 at N = 256 (the full BF16 rate, about
 // 8,150 flop per cycle per SM); the issuing thread is held for about as long as
-// its MMAs run.  A stage here issues 40 MMAs of N = 32 (bf16x5), so the MMAs
-// alone cost about 1,800 cycles a stage at 36 % of the tensor rate, and the
-// epilogue (TMEM loads, FP32 sums, stage update, publishing Xs, barrier) about
-// as much again.  Wider tiles would need the state of 64 instances per SM,
+// its MMAs run.  A stage here issues 24 MMAs (bf16x5, s = 128: 8 K chunks x 3 grouped
+// products of N = 64, 64 and 32), about 1,080 cycles a stage (40 MMAs of N = 32 before
+// the grouping: 1,800), and the epilogue (TMEM loads, FP32 sums, stage update,
+// publishing Xs, barrier) about 1,700 more.  Wider tiles would need the state of 64 instances per SM,
 // which fits neither the register file nor tensor memory beside eight
 // accumulators; a warp that only issues MMAs would leave the others 96 registers
 // (the thread count rounds up to 640 for register allocation).
@@ -195,18 +200,51 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Partial products (piece of B, piece of Xs), smallest first, for bf16x3 / x5 / x6.
-// (compile-time tables: the MMA issue loop is fully unrolled, so every operand
-// offset and accumulate flag is a constant)
-__host__ __device__ constexpr int prod_a(int tbl, int pr)
+// Grouped products.  An MMA of N <= 64 costs about as much as one of
+// N = 32, so the MMA of B piece a covers all the Xs pieces paired with it, laid side by
+// side along N (32 columns per piece), and writes accumulator columns from 32 a on:
+// column group g of an accumulator then collects the products of order g (b0 p0; b0 p1 +
+// b1 p0; b1 p1 + b2 p0 [+ b0 p2]), added smallest first in FP32.  Per K chunk, in an order
+// where every MMA that starts its columns starts all of them:
+//   x3 (PA 2, PB 2): b0.[p0 p1], b1.[p0]            (2 MMAs instead of 3)
+//   x5 (PA 3, PB 2): b0.[p0 p1], b2.[p0], b1.[p0 p1] (3 instead of 5)
+//   x6 (PA 3, PB 3): b0.[p0 p1 p2], b1.[p0 p1], b2.[p0] (3 instead of 6)
+__host__ __device__ constexpr int grp_a(int PA, int PB, int m)       // B piece of the m-th MMA
 {
-    constexpr int t[3][6] = {{1, 0, 0, 0, 0, 0}, {2, 1, 1, 0, 0, 0}, {2, 1, 0, 1, 0, 0}};
-    return t[tbl][pr];
+    return PA == 2 ? m : (PB == 2 ? (m == 0 ? 0 : (m == 1 ? 2 : 1)) : m);
 }
-__host__ __device__ constexpr int prod_b(int tbl, int pr)
+__host__ __device__ constexpr int grp_np(int PA, int PB, int a)      // Xs pieces paired with B piece a
 {
-    constexpr int t[3][6] = {{0, 1, 0, 0, 0, 0}, {0, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
-    return t[tbl][pr];
+    return PA == 2 ? (a == 0 ? 2 : 1) : (PB == 2 ? (a == 2 ? 1 : 2) : 3 - a);
+}
+__host__ __device__ constexpr bool grp_starts(int PA, int PB, int m) // the m-th MMA may start its columns
+{
+    return PA == 2 ? m == 0 : (PB == 2 ? m <= 1 : m == 0);
+}
+constexpr int grp_width(int PA) { return PA == 2 ? 64 : 96; }         // columns of one accumulator
+
+__device__ __forceinline__ uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// Two accumulators' x8 column groups (kNT columns apart) with a single wait.
+__device__ __forceinline__ void tmem_ld8_x2(uint32_t taddr, float (&v)[2][8])
+{
+    uint32_t r[2][8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+          "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+          "=r"(r[1][6]), "=r"(r[1][7])
+        : "r"(taddr), "r"(taddr + (uint32_t)kNT)
+        : "memory");
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[g][i] = __uint_as_float(r[g][i]);
 }
 
 // Batch form: FP64 arrays in and out, shared step count, checkpoints.
@@ -284,8 +322,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     constexpr int NI = kNT;                          // instances per tile
     constexpr int KC = 8 * CS;                       // 16-wide K chunks (K = 128 CS)
     constexpr int A_BYTES = PA * KC * kAChunk;
-    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
-    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(NACC * kNT));
+    constexpr int XCH = PB * kXChunk;                // one K chunk of Xs: its PB pieces side by side
+    constexpr int W = grp_width(PA);                 // columns of one accumulator (grouped products)
+    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(NACC * W));
+    static_assert(NACC * W <= 512, "the accumulators fit tensor memory");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // this CTA's 128 rows of B, PA pieces (shared-memory form)
     unsigned char* sX = smem + A_BYTES;              // Xs, PB pieces
@@ -385,19 +425,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     }
     __syncthreads();
 
-    // Xs addresses of this thread's DOF k in every CTA of the cluster
+    // Xs addresses of this thread's DOF k in every CTA of the cluster (layout of the one-CTA
+    // kernel: the PB pieces side by side along N)
     const int kc = k / 16, kk = k % 16;
-    const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
+    const uint32_t xoff = (uint32_t)(kc * XCH + (kk / 8) * (PB * 512) + (n0 / 8) * 128 + (kk % 8) * 16);
     uint32_t xdst[CS];
 #pragma unroll
     for (int c = 0; c < CS; ++c) xdst[c] = mapa(smem_u32(sX) + xoff, (uint32_t)c);
 
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
     const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
     // operand descriptors of chunk 0; the others add their byte offset / 16
     // (shared-memory addresses stay below 2^18, inside the 14-bit field)
-    const uint64_t bdesc0 = smem_desc(smem_u32(sX), 512, 128);
+    const uint64_t bdesc0 = smem_desc(smem_u32(sX), PB * 512, 128);
     const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
     uint32_t phase = 0;
 
@@ -414,7 +453,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             w.z = pack_bf16(r[4], r[5]);
             w.w = pack_bf16(r[6], r[7]);
 #pragma unroll
-            for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * KC * kXChunk), w);
+            for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * 512), w);
             if (p + 1 < PB) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
@@ -426,22 +465,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         cluster_sync();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0 && !sys.stall_mma) {
-            uint32_t started = 0;                    // accumulators already written this stage
+            // grouped products, B piece by B piece (see grp_a): the MMAs that start columns
+            // of an accumulator come before those that only add to them
 #pragma unroll
-            for (int pr = 0; pr < NPROD; ++pr) {
-                constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
-                const int ia = prod_a(TBL, pr);
-                const int ib = prod_b(TBL, pr);
+            for (int m = 0; m < PA; ++m) {
+                const int a = grp_a(PA, PB, m);
+                const uint32_t idesc = tc_idesc(32 * grp_np(PA, PB, a));
                 // descriptor address fields count 16-byte units; 16 chunks unroll by 4
                 // only: fully unrolled, the offsets held in registers spill
-                uint64_t bd = bdesc0 + (uint64_t)((ib * KC * kXChunk) >> 4);
-                uint64_t ad = adesc0 + (uint64_t)((ia * KC * kAChunk) >> 4);
+                uint64_t bd = bdesc0;
+                uint64_t ad = adesc0 + (uint64_t)((a * KC * kAChunk) >> 4);
 #pragma unroll 4
                 for (int c = 0; c < KC; ++c) {
-                    const int slot = c % NACC;
-                    mma_bf16(tmem + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
-                    started |= 1u << slot;
-                    bd += kXChunk >> 4;
+                    const uint32_t acc = grp_starts(PA, PB, m) ? (c >= NACC ? 1u : 0u) : 1u;
+                    mma_bf16(tmem + (uint32_t)((c % NACC) * W + 32 * a), ad, bd, idesc, acc);
+                    bd += XCH >> 4;
                     ad += kAChunk >> 4;
                 }
             }
@@ -453,20 +491,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
         if (done) {
-            if constexpr (NACC == 1) {
-                tmem_ld8(taddr, acc);
-            } else {
-                static_assert(NACC % 4 == 0, "accumulators are read four at a time");
+            if constexpr (PA == 2) {
+                // accumulators of two column groups: b0 p0 | b0 p1 + b1 p0
+                float big[kCPT], mid[kCPT];
 #pragma unroll
-                for (int g4 = 0; g4 < NACC / 4; ++g4) {
-                    float part[4][kCPT];
-                    tmem_ld8_x4(taddr + (uint32_t)(4 * g4 * kNT), part);
+                for (int sl = 0; sl < NACC; ++sl) {
+                    float g[2][kCPT];
+                    tmem_ld8_x2(taddr + (uint32_t)(sl * W), g);
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-#pragma unroll
-                        for (int j = 0; j < kCPT; ++j) acc[j] = (g4 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
+                    for (int j = 0; j < kCPT; ++j) {
+                        big[j] = sl == 0 ? g[0][j] : __fadd_rn(big[j], g[0][j]);
+                        mid[j] = sl == 0 ? g[1][j] : __fadd_rn(mid[j], g[1][j]);
                     }
                 }
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(big[j], mid[j]);
+            } else {
+                // accumulators of three column groups: each order summed over the
+                // accumulators, the smaller orders then added to the largest
+                float big[kCPT], mid[kCPT], small[kCPT];
+#pragma unroll
+                for (int sl = 0; sl < NACC; ++sl) {
+                    float g[2][kCPT], g2[kCPT];
+                    tmem_ld8_x2(taddr + (uint32_t)(sl * W), g);
+                    tmem_ld8(taddr + (uint32_t)(sl * W + 64), g2);
+#pragma unroll
+                    for (int j = 0; j < kCPT; ++j) {
+                        big[j] = sl == 0 ? g[0][j] : __fadd_rn(big[j], g[0][j]);
+                        mid[j] = sl == 0 ? g[1][j] : __fadd_rn(mid[j], g[1][j]);
+                        small[j] = sl == 0 ? g2[j] : __fadd_rn(small[j], g2[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(big[j], __fadd_rn(mid[j], small[j]));
             }
         }
 #pragma unroll
@@ -574,10 +631,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     constexpr int NI = kNT * PK;                     // instances per CTA
     constexpr int KC = 8;                            // 16-wide K chunks (K = 128)
     constexpr int A_BYTES = PA * KC * kAChunk;
-    constexpr int X_BYTES = PB * KC * kXChunk;       // one Xs buffer set
-    constexpr int NPROD = PA == 2 ? 3 : (PB == 2 ? 5 : 6);
-    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(2 * NACC * kNT));
-    static_assert(2 * NACC * kNT <= 512, "two accumulator sets fit tensor memory");
+    constexpr int XCH = PB * kXChunk;                // one K chunk of Xs: its PB pieces side by side
+    constexpr int X_BYTES = KC * XCH;                // one Xs buffer set
+    constexpr int W = grp_width(PA);                 // columns of one accumulator
+    constexpr uint32_t TCOLS = tc_pow2((uint32_t)(2 * NACC * W));
+    static_assert(2 * NACC * W <= 512, "two accumulator sets fit tensor memory");
+    static_assert((PA == 2 && NACC == 1) || (PA == 3 && (NACC == 1 || NACC == 2)), "accumulators read by collect()");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // B, PA pieces
     unsigned char* sX = smem + A_BYTES;              // two Xs buffer sets of PB pieces
@@ -665,11 +724,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     }
     __syncthreads();
 
+    // Xs chunk layout (MN-major, no swizzle): instance column n of piece p at N index 32 p + n;
+    // the two 8-row K halves LBO = PB * 512 bytes apart, 8-column groups SBO = 128 apart
     const int kc = row / 16, kk = row % 16;
-    const uint32_t xoff = (uint32_t)(kc * kXChunk + (kk / 8) * 512 + (n0 / 8) * 128 + (kk % 8) * 16);
-    const uint32_t xdst = smem_u32(sX) + xoff;      // this thread's cells in buffer set 0
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(kNT >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t xoff = (uint32_t)(kc * XCH + (kk / 8) * (PB * 512) + (n0 / 8) * 128 + (kk % 8) * 16);
+    const uint32_t xdst = smem_u32(sX) + xoff;      // this thread's cells of piece 0 in buffer set 0
     const uint32_t tlane = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)n0;
     const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
     uint32_t phase[2] = {0u, 0u};
@@ -687,7 +746,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             w.y = pack_bf16(r[2], r[3]);
             w.z = pack_bf16(r[4], r[5]);
             w.w = pack_bf16(r[6], r[7]);
-            st_cluster_v4(xdst + (uint32_t)(b * X_BYTES + p * KC * kXChunk), w);
+            st_cluster_v4(xdst + (uint32_t)(b * X_BYTES + p * 512), w);
             if (p + 1 < PB) {
 #pragma unroll
                 for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
@@ -705,22 +764,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     // thread 0: the stage's products from buffer set b into accumulator set b
     auto issue = [&](int b) {
         if (tid == 0 && !sys.stall_mma) {
-            uint32_t started = 0;
-            const uint64_t bdesc0 = smem_desc(smem_u32(sX + b * X_BYTES), 512, 128);
-            const uint32_t dcol = tmem + (uint32_t)(b * NACC * kNT);
+            const uint64_t bdesc0 = smem_desc(smem_u32(sX + b * X_BYTES), PB * 512, 128);
+            const uint32_t dcol = tmem + (uint32_t)(b * NACC * W);
+            // B piece by B piece, K chunk by K chunk: in each accumulator the MMAs that start
+            // columns (m = 0, and for x5 m = 1) come before those that only add to them
 #pragma unroll
-            for (int pr = 0; pr < NPROD; ++pr) {
-                constexpr int TBL = NPROD == 3 ? 0 : NPROD == 5 ? 1 : 2;
-                const int ia = prod_a(TBL, pr);
-                const int ibx = prod_b(TBL, pr);
-                uint64_t bd = bdesc0 + (uint64_t)((ibx * KC * kXChunk) >> 4);
-                uint64_t ad = adesc0 + (uint64_t)((ia * KC * kAChunk) >> 4);
+            for (int m = 0; m < PA; ++m) {
+                const int a = grp_a(PA, PB, m);
+                const uint32_t idesc = tc_idesc(32 * grp_np(PA, PB, a));
+                uint64_t bd = bdesc0;
+                uint64_t ad = adesc0 + (uint64_t)((a * KC * kAChunk) >> 4);
 #pragma unroll
                 for (int c = 0; c < KC; ++c) {
-                    const int slot = c % NACC;
-                    mma_bf16(dcol + (uint32_t)(slot * kNT), ad, bd, idesc, (started >> slot) & 1u);
-                    started |= 1u << slot;
-                    bd += kXChunk >> 4;
+                    const uint32_t acc = grp_starts(PA, PB, m) ? (c >= NACC ? 1u : 0u) : 1u;
+                    mma_bf16(dcol + (uint32_t)((c % NACC) * W + 32 * a), ad, bd, idesc, acc);
+                    bd += XCH >> 4;
                     ad += kAChunk >> 4;
                 }
             }
@@ -738,21 +796,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
         if (done) {
-            const uint32_t taddr = tlane + (uint32_t)(b * NACC * kNT);
-            if constexpr (NACC == 1) {
-                tmem_ld8(taddr, acc);
+            const uint32_t taddr = tlane + (uint32_t)(b * NACC * W);
+            if constexpr (PA == 2) {
+                // one accumulator: b0 p0 | b0 p1 + b1 p0
+                float g[2][kCPT];
+                tmem_ld8_x2(taddr, g);
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(g[0][j], g[1][j]);
+            } else if constexpr (NACC == 1) {
+                // one accumulator of three column groups, the smaller orders first
+                float g[2][kCPT], g2[kCPT];
+                tmem_ld8_x2(taddr, g);
+                tmem_ld8(taddr + 64u, g2);
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(g[0][j], __fadd_rn(g[1][j], g2[j]));
             } else {
-                static_assert(NACC % 4 == 0, "accumulators are read four at a time");
+                // two accumulators of three column groups: each order summed over the two,
+                // then the smaller orders added to the largest
+                float big[kCPT], mid[kCPT], small[kCPT];
+                {
+                    float g[4][kCPT];
+                    tmem_ld8_x4(taddr, g);                      // slot 0: G0 G1 G2; slot 1: G0
 #pragma unroll
-                for (int g4 = 0; g4 < NACC / 4; ++g4) {
-                    float part[4][kCPT];
-                    tmem_ld8_x4(taddr + (uint32_t)(4 * g4 * kNT), part);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-#pragma unroll
-                        for (int j = 0; j < kCPT; ++j) acc[j] = (g4 == 0 && g == 0) ? part[0][j] : __fadd_rn(acc[j], part[g][j]);
+                    for (int j = 0; j < kCPT; ++j) {
+                        big[j] = __fadd_rn(g[0][j], g[3][j]);
+                        mid[j] = g[1][j];
+                        small[j] = g[2][j];
                     }
                 }
+                float h[2][kCPT];
+                tmem_ld8_x2(taddr + (uint32_t)(W + 32), h);      // slot 1: G1 G2
+#pragma unroll
+                for (int j = 0; j < kCPT; ++j)
+                    acc[j] = __fadd_rn(big[j], __fadd_rn(__fadd_rn(mid[j], h[0][j]), __fadd_rn(small[j], h[1][j])));
             }
         }
 #pragma unroll
@@ -881,9 +957,9 @@ template <int PA, int PB, int CS, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
-    // bf16x3: one accumulator; x5/x6: one per K chunk (one per two chunks measured slower
-    // here, 366 against 356 ms at s = 256, and less accurate, 7.5e-6 against 5.9e-6)
-    constexpr int NACC = PA == 2 ? 1 : KC;
+    // grouped products: bf16x3 one accumulator of two column groups; x5 four of three
+    // (each collects four K chunks of every order)
+    constexpr int NACC = PA == 2 ? 1 : 4;
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
     auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -919,10 +995,10 @@ cudaError_t dispatch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, int
             return pack ? launch_tc_pair<2, 2, 1, 2>(sys, src, n_inst, st) : launch_tc_pair<2, 2, 1, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X5:
             if (two) return launch_tc<3, 2, 2>(sys, src, n_inst, st);
-            return pack ? launch_tc_pair<3, 2, 4, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 2, 4, 1>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 2, 2, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 2, 2, 1>(sys, src, n_inst, st);
         case CHO_DENSE_BF16X6:
             if (two) return cudaErrorNotSupported;   // 192 KB of B plus 48 KB of Xs exceed shared memory
-            return pack ? launch_tc_pair<3, 3, 4, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 3, 4, 1>(sys, src, n_inst, st);
+            return pack ? launch_tc_pair<3, 3, 2, 2>(sys, src, n_inst, st) : launch_tc_pair<3, 3, 2, 1>(sys, src, n_inst, st);
         default: return cudaErrorInvalidValue;
     }
 }
