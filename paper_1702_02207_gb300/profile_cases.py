@@ -16,6 +16,10 @@ Cases (each one cho_integrate_batch call, a few MB of device memory):
   dense_split128 s = 128, 608 instances with their own (M, K), 200 steps, fp32_kahan (rk4_dense_split, 1 CTA)
   dense_poly s = 128, 2048 instances, 500 steps, fp32_kahan, k = 25 steps per update (rk4_dense_poly)
   chain_ext 512 damped and forced chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain_ext)
+  small_poly 4096 chains of 17 masses, 2000 steps, fp32_kahan, k = 5 steps per update
+            (small_poly_setup_kernel<32>, rk4_small_poly_kernel<32>)
+  packed    the bench's uneven batches (chains of 33..63 x 400, 5..8 x 4000, 3..4 x 8000), 1000 steps,
+            fp32_kahan, through cho_integrate_packed (one slot-form launch per size class)
 """
 from __future__ import annotations
 
@@ -56,6 +60,25 @@ def run(case: str) -> None:
         elif case == "dense_poly":
             cfg, prec, kind = inputs.dense_group(s=128, n_inst=2048, n_steps=500), "fp32_kahan", "dense"
             poly = 25
+        elif case == "small_poly":
+            cfg, prec, kind = inputs.chain_batch(n_inst=4096, s=17, n_steps=2000, seed=1717), "fp32_kahan", "chain"
+            poly = 5
+        elif case == "packed":
+            cfgs = ([inputs.chain_batch(n_inst=400, s=sv, n_steps=1, seed=9000 + sv) for sv in (33, 40, 47, 55, 63)] +
+                    [inputs.chain_batch(n_inst=4000, s=sv, n_steps=1, seed=9100 + sv) for sv in (5, 6, 7, 8)] +
+                    [inputs.chain_batch(n_inst=8000, s=sv, n_steps=1, seed=9200 + sv) for sv in (3, 4)])
+            systems, batches = [], []
+            for c in cfgs:
+                sy = cho.cho_create_system(ctx, "chain", masses=c["masses"], springs=c["springs"])
+                systems.append(sy)
+                batches.append({"system": sy, "x0": torch.as_tensor(c["x0"], device=dev),
+                                "v0": torch.as_tensor(c["v0"], device=dev), "h": torch.as_tensor(c["h"], device=dev),
+                                "n_steps": 1000, "prec": "fp32_kahan"})
+            cho.cho_integrate_packed(ctx, batches)
+            torch.cuda.synchronize()
+            for sy in systems:
+                cho.cho_destroy_system(sy)
+            return
         elif case == "chain_ext":
             cfg, prec, kind = inputs.chain_batch(n_inst=512, n_steps=2000), "fp32_kahan", "chain"
         else:
