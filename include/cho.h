@@ -39,8 +39,9 @@
  *       read once, at the first such launch of the process);
  *   CHO_TEST_STALL_MMA=1                    the tensor-core dense kernel issues no MMA,
  *       so its bounded wait runs out and the call reports CHO_ETIMEOUT (read per launch);
- *   CHO_TEST_WITHHOLD_HANDOVER=1            the balanced s = 2 kernel publishes no
- *       hand-over flag, so every hand-over wait runs out (CHO_ETIMEOUT, NaN states);
+ *   CHO_TEST_WITHHOLD_HANDOVER=1            the balanced kernels (s = 2, and the
+ *       one-CTA tensor-core kernel for s <= 128) publish no hand-over flag, so every
+ *       hand-over wait runs out (CHO_ETIMEOUT, NaN states; read per launch);
  *   CHO_TEST_WITHHOLD_DOORBELL=1            persistent serving never rings its kernels'
  *       doorbell, so their bounded waits run out (requests end with CHO_ETIMEOUT; read when
  *       a context's serving engine starts).

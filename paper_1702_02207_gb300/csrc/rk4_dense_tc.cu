@@ -72,6 +72,7 @@
 #include "rk4_common.cuh"
 
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -625,8 +626,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 // operations as in rk4_dense_tc_kernel, so both give the same bits.  B's pieces
 // stay in shared memory: two accumulator sets fill the 512 TMEM columns, and an
 // MMA this narrow costs the same with A from shared memory.
+// Balanced schedule of rk4_dense_tc_pair_kernel (batch form, more tiles than SMs).  A
+// launch of one CTA per tile runs ceil(U / SMs) waves (8,192 instances of s = 128: 256
+// tiles on 152 SMs, two waves of which the second is 68 % full).  Instead one CTA per SM
+// takes the tiles' horizons cut in blocks (of ckpt_every steps, or single steps), the
+// U x Tb blocks dealt in order, C = max(Tb, ceil(U Tb / SMs)) to each CTA (McNaughton's
+// wrap-around rule, as for the 2-DOF kernel in rk4_small.cu).  A tile cut between CTAs g
+// and g + 1 runs its first blocks at the start of CTA g + 1, which then publishes the
+// state of all its threads; CTA g runs the remaining blocks at its end, after a bounded
+// wait (a second plus the time it has run) that is normally empty because C >= Tb.
+// The pieces run exactly the operations of the whole-tile launch: the same bits.
+struct TcSched {
+    int64_t units;          // U tiles; 0: one tile per CTA (blockIdx.x), its whole horizon
+    int64_t blocks;         // Tb blocks per tile
+    int64_t block_steps;    // steps per block
+    int64_t cap;            // C blocks per CTA
+    float* xfer;            // [grid][4 kCPT][kTcThreads]: the state of the tile cut at the start of CTA g
+    unsigned* flag;         // [grid], zero before the launch: 1 published, 2 published after a failure
+    int withhold;           // test hook: publish no hand-over, so that every wait runs out
+};
+
 template <int PA, int PB, int NACC, int PK, class Src>
-__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseSys sys, const Src src)
+__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseSys sys, const Src src, const TcSched sc)
 {
     constexpr int NI = kNT * PK;                     // instances per CTA
     constexpr int KC = 8;                            // 16-wide K chunks (K = 128)
@@ -648,11 +669,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     __shared__ long long sh_steps[NI];               // steps of each instance in this launch
     __shared__ long long sh_max_steps;
     __shared__ int sh_bad[NI];
+    __shared__ unsigned sh_in;                       // hand-over flag seen by thread 0
+    __shared__ long long sh_pos;                     // balanced schedule: first block of the next piece
+    __shared__ long long sh_tile;                    // tile of the current piece
+    __shared__ int sh_to_xfer;                       // the current piece hands its state over
+    __shared__ unsigned long long sh_t_start;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const int64_t tile = blockIdx.x;
     const int quad = warp & 3;
     const int colgrp = warp >> 2;
     const int row = 32 * quad + lane;                // row of the 128-row block = K index of the MMA
@@ -668,18 +693,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         mbar_init(&bar_mma[1], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (tid < NI) {
-        const int64_t q = tile * NI + tid;
-        const bool live = q < src.count();
-        const double hd = live ? src.h(q) : 1.0;
-        sh_steps[tid] = live ? (long long)src.steps(q) : 0;
-        sh_bad[tid] = 0;
-        const double h6 = hd / 6.0;
-        sh_h[tid][0] = (float)hd;
-        sh_h[tid][1] = (float)(0.5 * hd);
-        sh_h[tid][2] = (float)h6;
-        sh_h[tid][3] = (float)(h6 - (double)(float)h6);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -705,24 +718,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             bulk_g2s(sA + off, img + off, (uint32_t)n, &bar_load);
         }
     }
-    bool ok = agree(mbar_wait(&bar_load, 0));
-
-    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
-#pragma unroll
-    for (int j = 0; j < kCPT; ++j) {
-        const int64_t q = tile * NI + ib + n0 + j;
-        if (live_row && q < src.count()) {
-            src.load(q, kio, x[j], v[j], cx[j], cv[j]);
-        } else {
-            x[j] = v[j] = cx[j] = cv[j] = 0.f;
-        }
-    }
     if (tid == 0) {
-        long long m = 0;
-        for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
-        sh_max_steps = m;
+        sh_t_start = globaltimer();
+        sh_pos = sc.units > 0 ? (long long)blockIdx.x * sc.cap : -1;
     }
-    __syncthreads();
+    bool ok = agree(mbar_wait(&bar_load, 0));
 
     // Xs chunk layout (MN-major, no swizzle): instance column n of piece p at N index 32 p + n;
     // the two 8-row K halves LBO = PB * 512 bytes apart, 8-column groups SBO = 128 apart
@@ -836,11 +836,103 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         return done;
     };
 
-    const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
-    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
-    int64_t ck = 0, step = 0;
-    for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
-        for (int64_t it = 0; it < every && ok; ++it, ++step) {
+    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+    // the pieces of this CTA: (tile, steps [st0, st1), state from the hand-over of CTA
+    // g + 1 or from the input, state to the hand-over of this CTA or to the output).  The
+    // piece's description is kept in shared memory, not in registers across the steps.
+    for (;;) {
+        const int64_t g = blockIdx.x;
+        const int64_t pos = sh_pos;
+        const int64_t pend = sc.units > 0 ? (g * sc.cap + sc.cap < sc.units * sc.blocks ? g * sc.cap + sc.cap
+                                                                                        : sc.units * sc.blocks)
+                                          : 0;
+        if (sc.units > 0 ? pos >= pend : pos == -2) break;
+        int64_t tile = g, st0 = 0, st1 = -1, next = -2;   // st1 < 0: the tile's largest step count
+        bool from_xfer = false, to_xfer = false;
+        if (sc.units > 0) {
+            const int64_t u = pos / sc.blocks;
+            const int64_t j0 = u * sc.blocks, j1 = j0 + sc.blocks;
+            const int64_t end = j1 < pend ? j1 : pend;
+            tile = u;
+            if (pos > j0) {                         // the first blocks of a tile cut with CTA g - 1
+                st1 = (end - pos) * sc.block_steps;
+                to_xfer = true;
+            } else if (j1 > pend) {                 // the last blocks of a tile cut with CTA g + 1
+                st0 = (sc.blocks - (end - pos)) * sc.block_steps;
+                st1 = sc.blocks * sc.block_steps;
+                from_xfer = true;
+            }
+            next = end;
+        }
+        if (tid < NI) {
+            const int64_t q = tile * NI + tid;
+            const bool live = q < src.count();
+            const double hd = live ? src.h(q) : 1.0;
+            sh_steps[tid] = live ? (long long)src.steps(q) : 0;
+            sh_bad[tid] = 0;
+            const double h6 = hd / 6.0;
+            sh_h[tid][0] = (float)hd;
+            sh_h[tid][1] = (float)(0.5 * hd);
+            sh_h[tid][2] = (float)h6;
+            sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+        }
+        if (tid == 0) {
+            sh_tile = tile;
+            sh_to_xfer = to_xfer ? 1 : 0;
+        }
+        if (from_xfer && tid == 0) {
+            // bounded wait for CTA g + 1's hand-over
+            const unsigned* f = sc.flag + g + 1;
+            const uint64_t t_wait = globaltimer();
+            const uint64_t limit = kWaitNs + (t_wait - sh_t_start);
+            unsigned seen = 0;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(f) : "memory");
+                if (seen) break;
+                if (globaltimer() - t_wait > limit) break;
+                __nanosleep(1024);
+            }
+            __threadfence();
+            sh_in = seen;
+        }
+        __syncthreads();
+        if (tid == 0) sh_pos = next;                // read again after this piece's last barrier
+        bool piece_ok = ok;
+        if (from_xfer) {
+            piece_ok = ok && sh_in == 1u;
+            const float* xf = sc.xfer + (size_t)(g + 1) * (4 * kCPT * kTcThreads) + tid;
+            const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                x[j] = piece_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
+                v[j] = piece_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
+                cx[j] = piece_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
+                cv[j] = piece_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const int64_t q = tile * NI + ib + n0 + j;
+                if (live_row && q < src.count()) {
+                    src.load(q, kio, x[j], v[j], cx[j], cv[j]);
+                } else {
+                    x[j] = v[j] = cx[j] = cv[j] = 0.f;
+                }
+            }
+        }
+        if (tid == 0) {
+            long long m = 0;
+            for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+            sh_max_steps = m;
+        }
+        __syncthreads();
+
+        if (st1 < 0) st1 = ok ? (int64_t)sh_max_steps : 0;
+        const int64_t len = st1 - st0;
+        const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (len > 0 ? len : 1);
+        int64_t ck = src.ckpt_every() > 0 ? st0 / src.ckpt_every() : 0, step = st0;
+        for (int64_t done_steps = st0; done_steps < st1 && ok && piece_ok; done_steps += every) {
+            for (int64_t it = 0; it < every && ok; ++it, ++step) {
             float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vm[kCPT];
             // stages 1 and 2 together: Xs = x and x + h/2 v
 #pragma unroll
@@ -898,45 +990,92 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
                     comp_update(v[j], cv[j], kv[j], h6, h6l);
                 }
             }
-        }
-        if (src.ckpt_every() > 0 && ok) {
-            if (live_row) {
+            }
+            if (src.ckpt_every() > 0 && ok) {
+                if (live_row) {
+                    const int64_t tq = *(volatile long long*)&sh_tile;
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) {
-                    const int64_t q = tile * NI + ib + n0 + j;
-                    if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                    for (int j = 0; j < kCPT; ++j) {
+                        const int64_t q = tq * NI + ib + n0 + j;
+                        if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                    }
+                }
+                ++ck;
+            }
+        }
+        const int64_t tile_out = *(volatile long long*)&sh_tile;
+        if (*(volatile int*)&sh_to_xfer) {
+            // publish the state of every thread for CTA g - 1 (2 after a failure)
+            float* xf = sc.xfer + (size_t)blockIdx.x * (4 * kCPT * kTcThreads) + tid;
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                __stcg(xf + (0 * kCPT + j) * kTcThreads, x[j]);
+                __stcg(xf + (1 * kCPT + j) * kTcThreads, v[j]);
+                __stcg(xf + (2 * kCPT + j) * kTcThreads, cx[j]);
+                __stcg(xf + (3 * kCPT + j) * kTcThreads, cv[j]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0 && !sc.withhold) {
+                const unsigned val = ok ? 1u : 2u;
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sc.flag + blockIdx.x), "r"(val) : "memory");
+            }
+            continue;
+        }
+        if (live_row) {
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const int64_t q = tile_out * NI + ib + n0 + j;
+                if (q < src.count()) {
+                    src.store(q, kio, x[j], v[j], cx[j], cv[j]);
+                    if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
                 }
             }
-            ++ck;
         }
+        __syncthreads();
+        if (tid < NI) {
+            const int64_t q = tile_out * NI + tid;
+            if (q < src.count()) {
+                if (!(ok && piece_ok)) src.flag(q, CHO_ETIMEOUT);
+                else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
+                src.book(q, ok && piece_ok ? (int64_t)sh_steps[tid] : 0);
+            }
+        }
+        if (!piece_ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
+        __syncthreads();                            // sh_* free for the next piece
     }
     // after a failed wait: wait once more (bounded) for what is still in flight
     // before the accumulators are freed
 #pragma unroll
     for (int b = 0; b < 2; ++b)
         if (inflight[b]) (void)mbar_wait(&bar_mma[b], phase[b]);
-    if (live_row) {
-#pragma unroll
-        for (int j = 0; j < kCPT; ++j) {
-            const int64_t q = tile * NI + ib + n0 + j;
-            if (q < src.count()) {
-                src.store(q, kio, x[j], v[j], cx[j], cv[j]);
-                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
-            }
-        }
-    }
     if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid < NI) {
-        const int64_t q = tile * NI + tid;
-        if (q < src.count()) {
-            if (!ok) src.flag(q, CHO_ETIMEOUT);
-            else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
-            src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
-        }
-    }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+}
+
+// The balanced schedule when it helps: batch form, more tiles than SMs and not a whole
+// number of waves, a cooperative launch available (it guarantees that every CTA is
+// resident, so each hand-over wait ends).  The hand-over buffer and flags come from the
+// stream-ordered scratch pool and are freed after the kernel on the same stream.
+template <class Src>
+bool tc_balance(const Src&, int64_t, int64_t, int, TcSched*)
+{
+    return false;
+}
+
+bool tc_balance(const TcBatchSrc& src, int64_t tiles, int64_t sms, int coop, TcSched* sc)
+{
+    const BatchIO& io = src.io;
+    const int64_t g = io.ckpt_every > 0 ? io.ckpt_every : 1;
+    const int64_t Tb = io.n_steps / g;
+    if (!coop || tiles <= sms || tiles % sms == 0 || Tb <= 0 || Tb > ((int64_t)1 << 62) / tiles) return false;
+    sc->units = tiles;
+    sc->blocks = Tb;
+    sc->block_steps = g;
+    sc->cap = std::max(Tb, (tiles * Tb + sms - 1) / sms);
+    return true;
 }
 
 template <int PA, int PB, int NACC, int PK, class Src>
@@ -949,8 +1088,34 @@ cudaError_t launch_tc_pair(const DenseSys& sys, const Src& src, int64_t n_inst, 
     const int64_t tiles = (n_inst + kNT * PK - 1) / (kNT * PK);
     if (tiles <= 0) return cudaSuccess;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    kern<<<(unsigned)tiles, kTcThreads, smem, st>>>(sys, src);
-    return cudaGetLastError();
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    TcSched sc{};
+    if (per_sm < 1 || !tc_balance(src, tiles, (int64_t)sms, coop, &sc)) {
+        kern<<<(unsigned)tiles, kTcThreads, smem, st>>>(sys, src, sc);
+        return cudaGetLastError();
+    }
+    const char* hook = std::getenv("CHO_TEST_WITHHOLD_HANDOVER");
+    sc.withhold = hook && hook[0] == '1' ? 1 : 0;
+    const size_t xfer_bytes = (size_t)sms * 4 * kCPT * kTcThreads * sizeof(float);
+    void* buf = nullptr;
+    e = scratch_alloc(&buf, xfer_bytes + (size_t)sms * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    sc.xfer = (float*)buf;
+    sc.flag = (unsigned*)((char*)buf + xfer_bytes);
+    e = cudaMemsetAsync(sc.flag, 0, (size_t)sms * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        DenseSys a0 = sys;
+        Src a1 = src;
+        void* args[] = {&a0, &a1, &sc};
+        e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)sms), dim3(kTcThreads), args, smem, st);
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 template <int PA, int PB, int CS, class Src>

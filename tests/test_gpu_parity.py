@@ -949,6 +949,70 @@ def test_tensor_core_wait_gives_up_and_reports(ctx):
         cho.cho_destroy_system(sys_)
 
 
+@pytest.mark.parametrize("prec,ckpt", [("bf16x5", 0), ("bf16x3", 50), ("bf16x6", 0)])
+def test_tensor_core_balanced_schedule_gives_the_bits_of_whole_tiles(ctx, prec, ckpt):
+    """s = 128 with 8185 instances: 256 tiles, more than the SMs, run on the balanced schedule
+    (one CTA per SM, tiles cut between CTAs with their state handed over); each half (4096
+    and 4089 instances, 128 tiles, one CTA per tile for the whole horizon) gives the same
+    bits.  With checkpoints the cuts fall on checkpoint blocks and the trajectories agree."""
+    import torch
+
+    n, steps = 8185, 300
+    cfg = inputs.dense_group(s=128, n_inst=n, n_steps=steps)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        x0 = torch.as_tensor(cfg["x0"], device=d)
+        v0 = torch.as_tensor(np.random.default_rng(128).normal(0, 0.1, cfg["x0"].shape), device=d)
+        h = torch.as_tensor(cfg["h"], device=d)
+        full = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, steps, prec, ckpt, trajectory=ckpt > 0)
+        keys = ("x", "v", "x_traj", "v_traj") if ckpt else ("x", "v")
+        for part in (slice(0, 4096), slice(4096, n)):
+            sep = cho.cho_integrate_batch(ctx, sys_, x0[part], v0[part], h[part], steps, prec, ckpt,
+                                          trajectory=ckpt > 0)
+            for key in keys:
+                a, b = full[key][part].cpu().numpy(), sep[key].cpu().numpy()
+                assert np.all(np.isfinite(a)), key
+                assert np.array_equal(a, b), (key, float(np.max(np.abs(a - b))))
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
+def test_tensor_core_handover_wait_gives_up_and_reports(ctx):
+    """Test hook CHO_TEST_WITHHOLD_HANDOVER=1 on the balanced tensor-core schedule: no CTA
+    publishes the state of its first tile, each wait for it runs out (after about a second),
+    those tiles finish as NaN, the call reports CHO_ETIMEOUT and the context stays usable."""
+    import torch
+
+    n, steps = 8192, 200
+    cfg = inputs.dense_group(s=128, n_inst=n, n_steps=steps)
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        os.environ["CHO_TEST_WITHHOLD_HANDOVER"] = "1"
+        try:
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], steps, "bf16x5")
+            assert ei.value.status == cho.CHO_ETIMEOUT
+            o = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                        torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(cfg["h"], device=d),
+                                        steps, "bf16x5")
+            with pytest.raises(cho.ChoError) as ei:
+                cho.cho_system_status(sys_)
+            assert ei.value.status == cho.CHO_ETIMEOUT
+            xo = o["x"].cpu().numpy()
+            assert np.isnan(xo).any() and np.isfinite(xo).any()
+        finally:
+            del os.environ["CHO_TEST_WITHHOLD_HANDOVER"]
+        assert cho.cho_system_status(sys_) == cho.CHO_OK
+        out = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], cfg["h"], steps, "bf16x5")
+        idx = sample_indices(n, 8)
+        ref = oracle_run(cfg, idx=idx)
+        assert rel_err(out["x"][idx][:, None], ref["x"][:, None]).max() < TOL_FP32
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
 # ---- autotuning among kernels that give the same bits ----------------------------------------
 
 def _device_run(ctx, sys_, cfg, prec, n_steps):
