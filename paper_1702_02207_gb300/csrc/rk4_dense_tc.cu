@@ -313,11 +313,32 @@ struct TcSlotSrc {
 
 constexpr uint32_t tc_pow2(uint32_t n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512))); }
 
+// Balanced schedule (batch form, more tiles than CTAs or clusters fit at once).  A launch
+// of one CTA (or cluster) per tile runs ceil(U / P) waves (8,192 instances of s = 128: 256
+// tiles on 152 SMs, two waves of which the second is 68 % full).  Instead P resident units
+// (one CTA per SM, or one cluster per SM pair) take the tiles' horizons cut in blocks (of
+// ckpt_every steps, or single steps), the U x Tb blocks dealt in order, C = max(Tb,
+// ceil(U Tb / P)) to each unit (McNaughton's wrap-around rule, as for the 2-DOF kernel in
+// rk4_small.cu).  A tile cut between units g and g + 1 runs its first blocks at the start
+// of unit g + 1, which then publishes the state of all its threads; unit g runs the
+// remaining blocks at its end, after a bounded wait (a second plus the time it has run)
+// that is normally empty because C >= Tb.  The pieces run exactly the operations of the
+// whole-tile launch: the same bits.
+struct TcSched {
+    int64_t units;          // U tiles; 0: one tile per CTA (blockIdx.x), its whole horizon
+    int64_t blocks;         // Tb blocks per tile
+    int64_t block_steps;    // steps per block
+    int64_t cap;            // C blocks per CTA
+    float* xfer;            // [CTAs][4 kCPT][kTcThreads]: the state of the tile cut at the start of a CTA's unit
+    unsigned* flag;         // [CTAs], zero before the launch: 1 published, 2 published after a failure
+    int withhold;           // test hook: publish no hand-over, so that every wait runs out
+};
+
 // A cluster of CS CTAs per tile (128 < s <= 256): PA pieces of B, PB pieces of Xs,
 // NACC accumulators; one stage at a time (two accumulator sets of 16 would not fit
 // the 512 TMEM columns).
 template <int PA, int PB, int CS, int NACC, class Src>
-__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src)
+__global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sys, const Src src, const TcSched sc)
 {
     static_assert(CS > 1, "one CTA per tile: rk4_dense_tc_pair_kernel");
     constexpr int NI = kNT;                          // instances per tile
@@ -338,12 +359,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     __shared__ long long sh_steps[NI];               // steps of each instance in this launch
     __shared__ long long sh_max_steps;
     __shared__ int sh_bad[NI];
+    __shared__ unsigned sh_in;                       // hand-over flag seen by thread 0
+    __shared__ long long sh_pos;                     // balanced schedule: first block of the next piece
+    __shared__ long long sh_tile;                    // tile of the current piece
+    __shared__ int sh_to_xfer;                       // the current piece hands its state over
+    __shared__ unsigned long long sh_t_start;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const uint32_t rank = cluster_rank();
-    const int64_t tile = blockIdx.x / CS;
     const int quad = warp & 3;
     const int colgrp = warp >> 2;
     const int row = 32 * quad + lane;                // row of this CTA's block
@@ -361,17 +386,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         abort_flag[0] = abort_flag[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < NI) {
-        const int64_t q = tile * NI + tid;
-        const bool live = q < src.count();
-        const double hd = live ? src.h(q) : 1.0;
-        sh_steps[tid] = live ? (long long)src.steps(q) : 0;
-        sh_bad[tid] = 0;
-        const double h6 = hd / 6.0;
-        sh_h[tid][0] = (float)hd;
-        sh_h[tid][1] = (float)(0.5 * hd);
-        sh_h[tid][2] = (float)h6;
-        sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+    if (tid == 0) {
+        sh_t_start = globaltimer();
+        sh_pos = sc.units > 0 ? (long long)(blockIdx.x / CS) * sc.cap : -1;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -407,24 +424,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
         ok = agree(mbar_wait(&bar_load, 0));
     }
-
-    // ---- state of this thread: row k of instances n0 .. n0+7 ----
-    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
-#pragma unroll
-    for (int j = 0; j < kCPT; ++j) {
-        const int64_t q = tile * NI + ib + n0 + j;
-        if (live_row && q < src.count()) {
-            src.load(q, kio, x[j], v[j], cx[j], cv[j]);
-        } else {
-            x[j] = v[j] = cx[j] = cv[j] = 0.f;
-        }
-    }
-    if (tid == 0) {
-        long long m = 0;
-        for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
-        sh_max_steps = m;
-    }
-    __syncthreads();
 
     // Xs addresses of this thread's DOF k in every CTA of the cluster (layout of the one-CTA
     // kernel: the PB pieces side by side along N)
@@ -534,11 +533,105 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         return agree(done);
     };
 
-    const int64_t nsteps = ok ? (int64_t)sh_max_steps : 0;
-    const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (nsteps > 0 ? nsteps : 1);
-    int64_t ck = 0, step = 0;
-    for (int64_t done_steps = 0; done_steps < nsteps && ok; done_steps += every) {
-        for (int64_t it = 0; it < every && ok; ++it, ++step) {
+    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+    // the pieces of this cluster (see TcSched); the piece's description is kept in shared
+    // memory, not in registers across the steps
+    for (;;) {
+        const int64_t g = blockIdx.x / CS;
+        const int64_t pos = sh_pos;
+        const int64_t pend = sc.units > 0 ? (g * sc.cap + sc.cap < sc.units * sc.blocks ? g * sc.cap + sc.cap
+                                                                                        : sc.units * sc.blocks)
+                                          : 0;
+        if (sc.units > 0 ? pos >= pend : pos == -2) break;
+        int64_t tile = g, st0 = 0, st1 = -1, next = -2;   // st1 < 0: the tile's largest step count
+        bool from_xfer = false, to_xfer = false;
+        if (sc.units > 0) {
+            const int64_t u = pos / sc.blocks;
+            const int64_t j0 = u * sc.blocks, j1 = j0 + sc.blocks;
+            const int64_t end = j1 < pend ? j1 : pend;
+            tile = u;
+            if (pos > j0) {                         // the first blocks of a tile cut with cluster g - 1
+                st1 = (end - pos) * sc.block_steps;
+                to_xfer = true;
+            } else if (j1 > pend) {                 // the last blocks of a tile cut with cluster g + 1
+                st0 = (sc.blocks - (end - pos)) * sc.block_steps;
+                st1 = sc.blocks * sc.block_steps;
+                from_xfer = true;
+            }
+            next = end;
+        }
+        if (tid < NI) {
+            const int64_t q = tile * NI + tid;
+            const bool live = q < src.count();
+            const double hd = live ? src.h(q) : 1.0;
+            sh_steps[tid] = live ? (long long)src.steps(q) : 0;
+            sh_bad[tid] = 0;
+            const double h6 = hd / 6.0;
+            sh_h[tid][0] = (float)hd;
+            sh_h[tid][1] = (float)(0.5 * hd);
+            sh_h[tid][2] = (float)h6;
+            sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+        }
+        if (tid == 0) {
+            sh_tile = tile;
+            sh_to_xfer = to_xfer ? 1 : 0;
+            sh_in = 1u;
+        }
+        const int64_t me = g * CS + rank;           // this CTA's hand-over slot
+        if (from_xfer && tid == 0) {
+            // bounded wait for the hand-over of the same rank in cluster g + 1
+            const unsigned* f = sc.flag + me + CS;
+            const uint64_t t_wait = globaltimer();
+            const uint64_t limit = kWaitNs + (t_wait - sh_t_start);
+            unsigned seen = 0;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(f) : "memory");
+                if (seen) break;
+                if (globaltimer() - t_wait > limit) break;
+                __nanosleep(1024);
+            }
+            __threadfence();
+            sh_in = seen;
+        }
+        __syncthreads();
+        if (tid == 0) sh_pos = next;                // read again after this piece's last barrier
+        const bool in_ok = sh_in == 1u;
+        if (from_xfer) {
+            const float* xf = sc.xfer + (size_t)(me + CS) * (4 * kCPT * kTcThreads) + tid;
+            const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                x[j] = in_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
+                v[j] = in_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
+                cx[j] = in_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
+                cv[j] = in_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const int64_t q = tile * NI + ib + n0 + j;
+                if (live_row && q < src.count()) {
+                    src.load(q, kio, x[j], v[j], cx[j], cv[j]);
+                } else {
+                    x[j] = v[j] = cx[j] = cv[j] = 0.f;
+                }
+            }
+        }
+        if (tid == 0) {
+            long long m = 0;
+            for (int j = 0; j < NI; ++j) m = sh_steps[j] > m ? sh_steps[j] : m;
+            sh_max_steps = m;
+        }
+        // both CTAs of the cluster run the piece, or neither (a failed hand-over ends the
+        // cluster's last piece; the abort flags stay set)
+        const bool piece_ok = agree(in_ok);
+
+        if (st1 < 0) st1 = ok ? (int64_t)sh_max_steps : 0;
+        const int64_t len = st1 - st0;
+        const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (len > 0 ? len : 1);
+        int64_t ck = src.ckpt_every() > 0 ? st0 / src.ckpt_every() : 0, step = st0;
+        for (int64_t done_steps = st0; done_steps < st1 && ok && piece_ok; done_steps += every) {
+            for (int64_t it = 0; it < every && ok; ++it, ++step) {
             float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vs[kCPT];
             ok = stage(x, a);
 #pragma unroll
@@ -578,39 +671,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
                     comp_update(v[j], cv[j], kv[j], h6, h6l);
                 }
             }
-        }
-        if (src.ckpt_every() > 0 && ok) {
-            if (live_row) {
+            }
+            if (src.ckpt_every() > 0 && ok) {
+                if (live_row) {
+                    const int64_t tq = *(volatile long long*)&sh_tile;
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) {
-                    const int64_t q = tile * NI + ib + n0 + j;
-                    if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                    for (int j = 0; j < kCPT; ++j) {
+                        const int64_t q = tq * NI + ib + n0 + j;
+                        if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                    }
+                }
+                ++ck;
+            }
+        }
+        const int64_t tile_out = *(volatile long long*)&sh_tile;
+        if (*(volatile int*)&sh_to_xfer) {
+            // publish the state of every thread for cluster g - 1 (2 after a failure)
+            float* xf = sc.xfer + (size_t)(blockIdx.x) * (4 * kCPT * kTcThreads) + tid;
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                __stcg(xf + (0 * kCPT + j) * kTcThreads, x[j]);
+                __stcg(xf + (1 * kCPT + j) * kTcThreads, v[j]);
+                __stcg(xf + (2 * kCPT + j) * kTcThreads, cx[j]);
+                __stcg(xf + (3 * kCPT + j) * kTcThreads, cv[j]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0 && !sc.withhold) {
+                const unsigned val = ok ? 1u : 2u;
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sc.flag + blockIdx.x), "r"(val) : "memory");
+            }
+            continue;
+        }
+        if (live_row) {
+#pragma unroll
+            for (int j = 0; j < kCPT; ++j) {
+                const int64_t q = tile_out * NI + ib + n0 + j;
+                if (q < src.count()) {
+                    src.store(q, kio, x[j], v[j], cx[j], cv[j]);
+                    if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
                 }
             }
-            ++ck;
         }
-    }
-    if (live_row) {
-#pragma unroll
-        for (int j = 0; j < kCPT; ++j) {
-            const int64_t q = tile * NI + ib + n0 + j;
+        __syncthreads();
+        if (tid < NI) {
+            const int64_t q = tile_out * NI + tid;
             if (q < src.count()) {
-                src.store(q, kio, x[j], v[j], cx[j], cv[j]);
-                if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
+                if (!(ok && piece_ok)) src.flag(q, CHO_ETIMEOUT);
+                else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
+                if (rank == 0) src.book(q, ok && piece_ok ? (int64_t)sh_steps[tid] : 0);
             }
         }
+        if (!piece_ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
+        __syncthreads();                            // sh_* free for the next piece
     }
     if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid < NI) {
-        const int64_t q = tile * NI + tid;
-        if (q < src.count()) {
-            if (!ok) src.flag(q, CHO_ETIMEOUT);
-            else if (sh_bad[tid]) src.flag(q, CHO_ENONFINITE);
-            if (rank == 0) src.book(q, ok ? (int64_t)sh_steps[tid] : 0);
-        }
-    }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
     cluster_sync();               // the peer may still write into this CTA's shared memory until here
 }
@@ -626,26 +743,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
 // operations as in rk4_dense_tc_kernel, so both give the same bits.  B's pieces
 // stay in shared memory: two accumulator sets fill the 512 TMEM columns, and an
 // MMA this narrow costs the same with A from shared memory.
-// Balanced schedule of rk4_dense_tc_pair_kernel (batch form, more tiles than SMs).  A
-// launch of one CTA per tile runs ceil(U / SMs) waves (8,192 instances of s = 128: 256
-// tiles on 152 SMs, two waves of which the second is 68 % full).  Instead one CTA per SM
-// takes the tiles' horizons cut in blocks (of ckpt_every steps, or single steps), the
-// U x Tb blocks dealt in order, C = max(Tb, ceil(U Tb / SMs)) to each CTA (McNaughton's
-// wrap-around rule, as for the 2-DOF kernel in rk4_small.cu).  A tile cut between CTAs g
-// and g + 1 runs its first blocks at the start of CTA g + 1, which then publishes the
-// state of all its threads; CTA g runs the remaining blocks at its end, after a bounded
-// wait (a second plus the time it has run) that is normally empty because C >= Tb.
-// The pieces run exactly the operations of the whole-tile launch: the same bits.
-struct TcSched {
-    int64_t units;          // U tiles; 0: one tile per CTA (blockIdx.x), its whole horizon
-    int64_t blocks;         // Tb blocks per tile
-    int64_t block_steps;    // steps per block
-    int64_t cap;            // C blocks per CTA
-    float* xfer;            // [grid][4 kCPT][kTcThreads]: the state of the tile cut at the start of CTA g
-    unsigned* flag;         // [grid], zero before the launch: 1 published, 2 published after a failure
-    int withhold;           // test hook: publish no hand-over, so that every wait runs out
-};
-
 template <int PA, int PB, int NACC, int PK, class Src>
 __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseSys sys, const Src src, const TcSched sc)
 {
@@ -1055,26 +1152,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-// The balanced schedule when it helps: batch form, more tiles than SMs and not a whole
-// number of waves, a cooperative launch available (it guarantees that every CTA is
-// resident, so each hand-over wait ends).  The hand-over buffer and flags come from the
-// stream-ordered scratch pool and are freed after the kernel on the same stream.
+// The balanced schedule when it helps: batch form, more tiles than resident units (CTAs
+// or clusters) and not a whole number of waves, a cooperative launch available (it
+// guarantees that every unit is resident, so each hand-over wait ends).  The hand-over
+// buffer and flags come from the stream-ordered scratch pool and are freed after the
+// kernel on the same stream.
 template <class Src>
 bool tc_balance(const Src&, int64_t, int64_t, int, TcSched*)
 {
     return false;
 }
 
-bool tc_balance(const TcBatchSrc& src, int64_t tiles, int64_t sms, int coop, TcSched* sc)
+bool tc_balance(const TcBatchSrc& src, int64_t tiles, int64_t units, int coop, TcSched* sc)
 {
     const BatchIO& io = src.io;
     const int64_t g = io.ckpt_every > 0 ? io.ckpt_every : 1;
     const int64_t Tb = io.n_steps / g;
-    if (!coop || tiles <= sms || tiles % sms == 0 || Tb <= 0 || Tb > ((int64_t)1 << 62) / tiles) return false;
+    if (!coop || tiles <= units || tiles % units == 0 || Tb <= 0 || Tb > ((int64_t)1 << 62) / tiles) return false;
     sc->units = tiles;
     sc->blocks = Tb;
     sc->block_steps = g;
-    sc->cap = std::max(Tb, (tiles * Tb + sms - 1) / sms);
+    sc->cap = std::max(Tb, (tiles * Tb + units - 1) / units);
     return true;
 }
 
@@ -1118,6 +1216,9 @@ cudaError_t launch_tc_pair(const DenseSys& sys, const Src& src, int64_t n_inst, 
     return e != cudaSuccess ? e : ef;
 }
 
+// Clusters: the balanced schedule needs every cluster resident at once, which a
+// cooperative launch of as many clusters as fit guarantees; where the launch refuses the
+// combination of cooperative launch and clusters, one cluster per tile as before.
 template <int PA, int PB, int CS, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
@@ -1131,19 +1232,52 @@ cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaS
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n_inst + kNT - 1) / kNT;
     if (tiles <= 0) return cudaSuccess;
+    if (tiles * CS > 0x7fffffffLL) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(tiles * CS), 1, 1);
     cfg.blockDim = dim3(kTcThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CS;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, sys, src);
+    TcSched sc{};
+    int dev = 0, coop = 0, clusters = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1 || !tc_balance(src, tiles, (int64_t)clusters, coop, &sc))
+        return cudaLaunchKernelEx(&cfg, kern, sys, src, sc);
+    const char* hook = std::getenv("CHO_TEST_WITHHOLD_HANDOVER");
+    sc.withhold = hook && hook[0] == '1' ? 1 : 0;
+    const int64_t ctas = (int64_t)clusters * CS;
+    const size_t xfer_bytes = (size_t)ctas * 4 * kCPT * kTcThreads * sizeof(float);
+    void* buf = nullptr;
+    e = scratch_alloc(&buf, xfer_bytes + (size_t)ctas * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    sc.xfer = (float*)buf;
+    sc.flag = (unsigned*)((char*)buf + xfer_bytes);
+    e = cudaMemsetAsync(sc.flag, 0, (size_t)ctas * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t bc = cfg;
+        bc.gridDim = dim3((unsigned)ctas, 1, 1);
+        attr[1].id = cudaLaunchAttributeCooperative;
+        attr[1].val.cooperative = 1;
+        bc.numAttrs = 2;
+        e = cudaLaunchKernelEx(&bc, kern, sys, src, sc);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();               // the refusal is not sticky: run one cluster per tile
+            TcSched none{};
+            e = cudaLaunchKernelEx(&cfg, kern, sys, src, none);
+        }
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 template <class Src>

@@ -949,25 +949,29 @@ def test_tensor_core_wait_gives_up_and_reports(ctx):
         cho.cho_destroy_system(sys_)
 
 
-@pytest.mark.parametrize("prec,ckpt", [("bf16x5", 0), ("bf16x3", 50), ("bf16x6", 0)])
-def test_tensor_core_balanced_schedule_gives_the_bits_of_whole_tiles(ctx, prec, ckpt):
-    """s = 128 with 8185 instances: 256 tiles, more than the SMs, run on the balanced schedule
-    (one CTA per SM, tiles cut between CTAs with their state handed over); each half (4096
-    and 4089 instances, 128 tiles, one CTA per tile for the whole horizon) gives the same
-    bits.  With checkpoints the cuts fall on checkpoint blocks and the trajectories agree."""
+@pytest.mark.parametrize("s,prec,ckpt", [(128, "bf16x5", 0), (128, "bf16x3", 50), (128, "bf16x6", 0),
+                                         (256, "bf16x5", 0), (256, "bf16x3", 50)])
+def test_tensor_core_balanced_schedule_gives_the_bits_of_whole_tiles(ctx, s, prec, ckpt):
+    """8185 instances: 256 tiles, more than the CTAs (s = 128) or 2-CTA clusters (s = 256)
+    that fit at once, run on the balanced schedule (tiles cut between CTAs or clusters,
+    their state handed over); parts of 4096 (s = 128: 128 tiles) or 2048 instances (s = 256:
+    64 clusters), the last one ragged, run one CTA or cluster per tile for the whole horizon
+    and give the same bits.  With checkpoints the cuts fall on checkpoint blocks and the
+    trajectories agree."""
     import torch
 
     n, steps = 8185, 300
-    cfg = inputs.dense_group(s=128, n_inst=n, n_steps=steps)
+    part_n = 4096 if s == 128 else 2048
+    cfg = inputs.dense_group(s=s, n_inst=n, n_steps=steps)
     sys_ = make_system(ctx, cfg)
     d = torch.device("cuda:0")
     try:
         x0 = torch.as_tensor(cfg["x0"], device=d)
-        v0 = torch.as_tensor(np.random.default_rng(128).normal(0, 0.1, cfg["x0"].shape), device=d)
+        v0 = torch.as_tensor(np.random.default_rng(s).normal(0, 0.1, cfg["x0"].shape), device=d)
         h = torch.as_tensor(cfg["h"], device=d)
         full = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, steps, prec, ckpt, trajectory=ckpt > 0)
         keys = ("x", "v", "x_traj", "v_traj") if ckpt else ("x", "v")
-        for part in (slice(0, 4096), slice(4096, n)):
+        for part in [slice(i, min(i + part_n, n)) for i in range(0, n, part_n)]:
             sep = cho.cho_integrate_batch(ctx, sys_, x0[part], v0[part], h[part], steps, prec, ckpt,
                                           trajectory=ckpt > 0)
             for key in keys:
@@ -978,14 +982,15 @@ def test_tensor_core_balanced_schedule_gives_the_bits_of_whole_tiles(ctx, prec, 
         cho.cho_destroy_system(sys_)
 
 
-def test_tensor_core_handover_wait_gives_up_and_reports(ctx):
+@pytest.mark.parametrize("s", [128, 256])
+def test_tensor_core_handover_wait_gives_up_and_reports(ctx, s):
     """Test hook CHO_TEST_WITHHOLD_HANDOVER=1 on the balanced tensor-core schedule: no CTA
     publishes the state of its first tile, each wait for it runs out (after about a second),
     those tiles finish as NaN, the call reports CHO_ETIMEOUT and the context stays usable."""
     import torch
 
     n, steps = 8192, 200
-    cfg = inputs.dense_group(s=128, n_inst=n, n_steps=steps)
+    cfg = inputs.dense_group(s=s, n_inst=n, n_steps=steps)
     sys_ = make_system(ctx, cfg)
     d = torch.device("cuda:0")
     try:
