@@ -215,7 +215,8 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
 
 
 def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_seconds=8.0, load_seconds=6.0,
-                loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000, ref_rate=None):
+                loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000, ref_rate=None, active_pct=0,
+                records=None):
     """The mixed request stream of BASELINE config 5 through cho_submit / cho_poll_any.
 
     Requests follow request_stream: s log-uniform over {2..512} (2-DOF, chains, dense groups
@@ -226,11 +227,16 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
     at each `loads` fraction of that rate for `load_seconds` each: p50/p99 submit-to-done
     latency per class, queue depth and resident bytes sampled every 20 ms.  At most
     `max_requests` requests in all (config 5's 200k).  persistent: resident kernels for the
-    small and chain groups (cho_config.persistent).  ref_rate: offer the loads as fractions of
-    this rate instead of the engine's own (the same arrival rates for both engines)."""
+    small and chain groups (cho_config.persistent).  ref_rate: skip the saturation phase and
+    offer the loads as fractions of this rate (the same arrival rates for every engine).
+    active_pct: cho_config.active_pct (0: the library's default active-set cap; -1: none).
+    The service rate is taken without the cap: with it, requests paused at their chunk
+    boundaries hold work that a window of finished requests does not count.
+    records: a list that receives (load, kind, s, steps, class, latency) per finished request."""
     import time as _t
 
-    ctx = cho.cho_init(device, chunk_us=chunk_us, persistent=int(persistent), budget_bytes=40 << 30)
+    ctx = cho.cho_init(device, chunk_us=chunk_us, persistent=int(persistent), budget_bytes=40 << 30,
+                       active_pct=int(active_pct))
     st = inputs.request_stream(n_req=max_requests, rate_per_s=1.0)
     kinds, sizes, steps, prios = st["kind"], st["s"], st["n_steps"], st["priority"]
     work = sizes.astype(np.float64) * steps
@@ -296,28 +302,33 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
             t = cho.cho_submit(ctx, sys_, np.zeros(s_), np.zeros(s_), float(hs[0]), 10, "fp32_kahan", 0, 0)
             open_t[t] = -1
     drain()
-    # saturation: keep `outstanding` requests in the engine
-    log(f"serving ({'persistent' if persistent else 'relaunch'}): saturation")
-    done = []
-    t0 = _t.perf_counter()
-    while _t.perf_counter() - t0 < sat_seconds and nxt[0] < max_requests:
-        while len(open_t) < outstanding and submit():
-            pass
-        collect(done)
-        _t.sleep(0.0005)
-    # the engine's times are CLOCK_MONOTONIC seconds (time.monotonic)
-    win0 = time.monotonic() - (_t.perf_counter() - t0) + 1.0
-    t_sat_end = time.monotonic()
-    sat_work = sum(work[i] for i, code, _, td in done if code == cho.CHO_OK and td >= win0)
-    rate = sat_work / max(t_sat_end - win0, 1e-9)
-    n_sat = nxt[0]
-    drain()
-    out = {"mode": "persistent" if persistent else "relaunch", "saturated_dof_steps_per_s": rate,
-           "saturation": {"seconds": sat_seconds, "outstanding": outstanding, "requests": n_sat,
-                          "completed": len(done)}, "loads": {}}
+    mode = ("persistent" if persistent else "relaunch") + ("" if active_pct >= 0 else ", no active-set cap")
+    out = {"mode": mode, "active_pct": active_pct if active_pct != 0 else 100, "loads": {}}
+    rate = None
+    if not ref_rate:
+        # saturation: keep `outstanding` requests in the engine
+        log(f"serving ({mode}): saturation")
+        done = []
+        t0 = _t.perf_counter()
+        while _t.perf_counter() - t0 < sat_seconds and nxt[0] < max_requests:
+            while len(open_t) < outstanding and submit():
+                pass
+            collect(done)
+            _t.sleep(0.0005)
+        # the engine's times are CLOCK_MONOTONIC seconds (time.monotonic)
+        win0 = time.monotonic() - (_t.perf_counter() - t0) + 1.0
+        t_sat_end = time.monotonic()
+        sat_work = sum(work[i] for i, code, _, td in done if code == cho.CHO_OK and td >= win0)
+        rate = sat_work / max(t_sat_end - win0, 1e-9)
+        n_sat = nxt[0]
+        drain()
+        out["saturated_dof_steps_per_s"] = rate
+        out["saturation"] = {"seconds": sat_seconds, "outstanding": outstanding, "requests": n_sat,
+                             "completed": len(done)}
     # Poisson streams at fractions of the service rate
     base = ref_rate if ref_rate else rate
-    out["loads_relative_to"] = "the relaunch engine's saturated rate" if ref_rate else "this engine's saturated rate"
+    out["loads_relative_to"] = ("the saturated rate of the relaunch engine without the active-set cap"
+                                if ref_rate else "this engine's saturated rate")
     for rho in loads:
         lam = rho * base / mean_work
         first = nxt[0]
@@ -345,6 +356,9 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
         sink += drain()
         lat = {c: [td - ts for i, code, ts, td in sink if code == cho.CHO_OK and i >= first and prios[i] == c]
                for c in range(3)}
+        if records is not None:
+            records += [(rho, int(kinds[i]), int(sizes[i]), int(steps[i]), int(prios[i]), td - ts)
+                        for i, code, ts, td in sink if code == cho.CHO_OK and i >= first]
         out["loads"][f"{rho:.2f}"] = {
             "arrival_rate_per_s": lam, "offered_requests": offered, "offered_rate_per_s": offered / t_off,
             "completed_ok": int(sum(len(v) for v in lat.values())),
@@ -972,10 +986,13 @@ def main():
             line["other_configs"] = other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks,
                                                   alu["fp32_peak_tflops"])
             if args.serve_requests > 0:
-                rel = run_serving(cho, inputs, local_rank, False, args.serve_requests)
-                per = run_serving(cho, inputs, local_rank, True, args.serve_requests,
-                                  ref_rate=rel["saturated_dof_steps_per_s"])
-                line["serving"] = {"relaunch": rel, "persistent": per}
+                # capacity (and processor-sharing latencies) without the active-set cap; then
+                # both engines with it (fixed-priority preemption), offered the same rates
+                base = run_serving(cho, inputs, local_rank, False, args.serve_requests, active_pct=-1)
+                cap = base["saturated_dof_steps_per_s"]
+                rel = run_serving(cho, inputs, local_rank, False, args.serve_requests, ref_rate=cap)
+                per = run_serving(cho, inputs, local_rank, True, args.serve_requests, ref_rate=cap)
+                line["serving"] = {"relaunch_no_cap": base, "relaunch": rel, "persistent": per}
                 log("periodic mode")
                 line["periodic"] = run_periodic_mode(cho, inputs)
         if not args.no_cpu_baseline:

@@ -132,7 +132,14 @@ typedef struct cho_config {
                                resident kernels driven through pinned mapped memory (doorbell per
                                chunk, completion ring; see cho_submit), 0 launches every chunk.
                                Results are bitwise the same. */
-    int32_t reserved[2];
+    int32_t active_pct;     /* serving: the requests advanced by each chunk (the active set) are
+                               chosen in priority order (class, then admission order) up to this
+                               percentage of one wave of the device, each request weighing
+                               1 / (instances its kernel holds resident at once); the others
+                               stay resident and wait at their chunk boundary.  0: 100;
+                               < 0: no cap (every resident request advances every chunk).
+                               Results do not depend on it. */
+    int32_t reserved[1];
 } cho_config;
 
 /* Description of one system kind and size, with n_sys parameter sets.

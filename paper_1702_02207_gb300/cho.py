@@ -52,7 +52,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class cho_config(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("chunk_steps", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("chunk_us", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("active_pct", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class cho_tune_result(ctypes.Structure):
@@ -192,10 +192,11 @@ def _stream_ptr(stream):
 
 # ---- context -----------------------------------------------------------------------
 
-def cho_init(device=0, budget_bytes=0, chunk_steps=0, max_slots=0, chunk_us=0, persistent=0):
+def cho_init(device=0, budget_bytes=0, chunk_steps=0, max_slots=0, chunk_us=0, persistent=0, active_pct=0):
     lib = load()
     ctx = ctypes.c_void_p()
-    cfg = cho_config(int(budget_bytes), int(chunk_steps), int(max_slots), int(chunk_us), int(persistent))
+    cfg = cho_config(int(budget_bytes), int(chunk_steps), int(max_slots), int(chunk_us), int(persistent),
+                     int(active_pct))
     _check(lib.cho_init(ctypes.byref(ctx), int(device), ctypes.byref(cfg)))
     return ctx
 

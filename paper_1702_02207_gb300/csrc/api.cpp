@@ -166,7 +166,9 @@ extern "C" cho_status cho_init(cho_ctx** out, int device, const cho_config* cfg)
         if (cfg->max_slots > 0) c->cfg.max_slots = cfg->max_slots;
         if (cfg->chunk_us > 0) c->cfg.chunk_us = cfg->chunk_us;
         c->cfg.persistent = cfg->persistent != 0 ? 1 : 0;
+        c->cfg.active_pct = cfg->active_pct;
     }
+    if (c->cfg.active_pct == 0) c->cfg.active_pct = 100;
     {
         DeviceGuard g(device);
         if (!g.ok()) {

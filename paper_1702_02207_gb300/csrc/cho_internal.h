@@ -108,6 +108,8 @@ cudaError_t launch_rk4_small(const SmallSys& sys, const BatchIO& io, bool fp64, 
 // Double-FP32 (CHO_FP32X2) for s <= 32 systems (padded S = 2 .. 32), the lanes of rk4_small.
 cudaError_t launch_rk4_small_dw(const SmallSys& sys, const BatchIO& io, cudaStream_t st);
 cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStream_t st);
+// Instances the slot kernel holds resident at once on this device (0: none fits).
+int small_slot_resident(int S, bool fp64);
 
 // ---- rk4_chain ----------------------------------------------------------------
 // Coefficients per parameter set, spring form of eq. 2: g_i = C_i/m_i and
@@ -143,6 +145,7 @@ struct ChainExtSys {
 constexpr int kChainExtMaxS = 1024;
 cudaError_t launch_rk4_chain_ext(const ChainExtSys& sys, const BatchIO& io, bool fp64, cudaStream_t st);
 cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaStream_t st);
+int chain_slot_resident(int s, bool fp64);
 
 // ---- rk4_dense (shared B, s > 32) ------------------------------------------------
 struct DenseSys {
@@ -173,9 +176,11 @@ cudaError_t launch_rk4_dense(const DenseSys& sys, const BatchIO& io, int prec, c
 // the transposed jump blocks [3][s_pad][s_pad] (FP64) or [3][2][s_pad][s_pad] (FP32 pairs).
 cudaError_t launch_rk4_dense_poly(const DenseSys& sys, const void* E, const BatchIO& io, bool fp64, cudaStream_t st);
 cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool fp64, cudaStream_t st);
+int dense_slot_resident(const DenseSys& sys, bool fp64);
 // tensor-core split-BF16 variant (rk4_dense_tc.cu)
 cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec, cudaStream_t st);
 cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int prec, cudaStream_t st);
+int dense_tc_slot_resident(const DenseSys& sys, int prec);
 
 // ---- energy -------------------------------------------------------------------
 struct EnergySys {

@@ -725,6 +725,58 @@ cudaError_t launch_rk4_chain_slots(int s_max, const SlotIO& io, bool fp64, cudaS
     return launch_any<false>(s, io.n_inst, s_max, st);
 }
 
+namespace {
+
+template <int P, bool F64>
+int chain_resident_p(int s)
+{
+    int threads = (s + P - 1) / P;
+    threads = ((threads + 31) / 32) * 32;
+    if (threads > kChainMaxThreads) return 0;
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    using Src = ChainSlotSrc<F64>;
+    bool wide = false;
+    if constexpr (P == 8) {
+        wide = threads > 256;                       // s > 2048: the wide CTAs of launch_p
+        if (wide) {
+            if constexpr (F64)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_chain_kernel<P, F64, kChainMaxThreads, Src>,
+                                                                  threads, 0);
+            else
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_chain_pk_kernel<P, kChainMaxThreads, Src>,
+                                                                  threads, 0);
+        }
+    }
+    if (!wide) {
+        if constexpr (F64 || P < 2)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_chain_kernel<P, F64, 256, Src>, threads, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_chain_pk_kernel<P, 256, Src>, threads, 0);
+    }
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n * sms;
+}
+
+}  // namespace
+
+// Chains of s masses the slot kernel holds resident at once on this device (one per CTA).
+int chain_slot_resident(int s, bool fp64)
+{
+    switch (chain_dofs_per_thread(s)) {
+        case 1: return fp64 ? chain_resident_p<1, true>(s) : chain_resident_p<1, false>(s);
+        case 2: return fp64 ? chain_resident_p<2, true>(s) : chain_resident_p<2, false>(s);
+        case 4: return fp64 ? chain_resident_p<4, true>(s) : chain_resident_p<4, false>(s);
+        default: return fp64 ? chain_resident_p<8, true>(s) : chain_resident_p<8, false>(s);
+    }
+}
+
 int chain_persist_threads(int P) { return P == 8 ? 256 : 64; }
 
 cudaError_t launch_rk4_chain_persist(int P, const PersistIO& pio, bool fp64, int grid, cudaStream_t st)

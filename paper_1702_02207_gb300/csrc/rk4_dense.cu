@@ -1143,6 +1143,77 @@ cudaError_t launch_rk4_dense_slots(const DenseSys& sys, const SlotIO& io, bool f
     });
 }
 
+namespace {
+
+template <class K>
+int blocks_per_sm(K kern, int threads, size_t smem)
+{
+    int n = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int RI, int NT, bool F64, class Src, int NTHR = kDenseThreads>
+int simt_resident()
+{
+    using Real = std::conditional_t<F64, double, float>;
+    constexpr int SP = (NTHR / NT) * RI;
+    constexpr int NB = F64 ? 1 : 2;
+    const size_t smem = sizeof(Real) * (2 * (size_t)SP * NT + 2 * (size_t)NB * kJC * SP);
+    return blocks_per_sm(rk4_dense_simt_kernel<RI, NT, F64, Src, NTHR>, NTHR, smem) * device_sm_count() * NT;
+}
+
+}  // namespace
+
+// Instances the slot kernels of a dense system hold resident at once on this device: the
+// one-instance-per-CTA-or-cluster kernels for FP32 (the choice for up to eight times as
+// many instances), else the streaming kernels.  0 if none fits.
+int dense_slot_resident(const DenseSys& sys, bool fp64)
+{
+    using S32 = DenseSlotSrc<false>;
+    using S64 = DenseSlotSrc<true>;
+    if (!fp64) {
+        int cap = 0;
+        switch (sys.s_pad) {
+            case 64:
+                cap = blocks_per_sm(rk4_dense_own_kernel<S32>, 64, sizeof(float) * ((size_t)64 * 68 + 2 * 64)) *
+                      device_sm_count();
+                break;
+            case 128: cap = split_capacity<128, S32>(); break;
+            case 256: cap = split_capacity<256, S32>(); break;
+            case 512: cap = split_capacity<512, S32>(); break;
+            default: return 0;
+        }
+        if (cap > 0) return cap;
+    }
+#define CHO_RES_OWN(SPV, RI)                                                                         \
+    case SPV: return fp64 ? simt_resident<RI, 1, true, S64, SPV / RI>() : simt_resident<RI, 1, false, S32, SPV / RI>();
+#define CHO_RES(SPV, RI64, NT64, RI32, NT32)                                                         \
+    case SPV: return fp64 ? simt_resident<RI64, NT64, true, S64>() : simt_resident<RI32, NT32, false, S32>();
+    if (sys.per_inst) {
+        switch (sys.s_pad) {
+            CHO_RES_OWN(64, 1)
+            CHO_RES_OWN(128, 2)
+            CHO_RES_OWN(256, 4)
+            CHO_RES_OWN(512, 8)
+            default: return 0;
+        }
+    }
+    switch (sys.s_pad) {
+        CHO_RES(64, 2, 8, 4, 16)
+        CHO_RES(128, 4, 8, 8, 16)
+        CHO_RES(256, 8, 8, 16, 16)
+        CHO_RES(512, 8, 4, 16, 8)
+        default: return 0;
+    }
+#undef CHO_RES
+#undef CHO_RES_OWN
+}
+
 // Device data of a dense system: for each of its n_sys parameter sets B^T padded
 // to s_pad in FP64 and as FP32 pairs (hi block then lo block), back to back; for a
 // single shared set also the BF16 pieces the tensor-core kernel reads.

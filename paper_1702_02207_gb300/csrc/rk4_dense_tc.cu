@@ -1335,6 +1335,70 @@ cudaError_t launch_rk4_dense_tc(const DenseSys& sys, const BatchIO& io, int prec
     return dispatch_tc(d, TcBatchSrc{io, sys.s}, io.n_inst, prec, st);
 }
 
+namespace {
+
+template <int PA, int PB, int NACC, int PK>
+int pair_resident()
+{
+    const size_t smem = (size_t)PA * 8 * kAChunk + 2 * (size_t)PB * 8 * kXChunk;
+    auto kern = rk4_dense_tc_pair_kernel<PA, PB, NACC, PK, TcSlotSrc>;
+    int n = 0, dev = 0, sms = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTcThreads, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n * sms * kNT * PK;
+}
+
+template <int PA, int PB, int CS>
+int cluster_resident()
+{
+    constexpr int KC = 8 * CS;
+    constexpr int NACC = PA == 2 ? 1 : 4;
+    const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
+    auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, TcSlotSrc>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS, 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n * kNT;
+}
+
+}  // namespace
+
+// Instances the tensor-core slot kernels hold resident at once on this device (0: none).
+int dense_tc_slot_resident(const DenseSys& sys, int prec)
+{
+    const bool two = sys.s_tc == 256, pack = sys.s_tc == 64;
+    switch (prec) {
+        case CHO_DENSE_BF16X3:
+            if (two) return cluster_resident<2, 2, 2>();
+            return pack ? pair_resident<2, 2, 1, 2>() : pair_resident<2, 2, 1, 1>();
+        case CHO_DENSE_BF16X5:
+            if (two) return cluster_resident<3, 2, 2>();
+            return pack ? pair_resident<3, 2, 2, 2>() : pair_resident<3, 2, 2, 1>();
+        case CHO_DENSE_BF16X6:
+            if (two) return 0;
+            return pack ? pair_resident<3, 3, 2, 2>() : pair_resident<3, 3, 2, 1>();
+        default: return 0;
+    }
+}
+
 cudaError_t launch_rk4_dense_tc_slots(const DenseSys& sys, const SlotIO& io, int prec, cudaStream_t st)
 {
     DenseSys d = sys;

@@ -1465,6 +1465,38 @@ cudaError_t launch_rk4_small_slots(int S, const SlotIO& io, bool fp64, cudaStrea
     return dispatch<SlotSrc>(S, fp64, io.n_inst, st, [&](auto& s) { s.io = io; });
 }
 
+// Instances of padded size S the slot kernel holds resident at once on this device.
+int small_slot_resident(int S, bool fp64)
+{
+    int n = 0, lanes = 1;
+    cudaError_t e = cudaErrorInvalidValue;
+#define CHO_RES_CASE(SV)                                                                                           \
+    case SV:                                                                                                       \
+        lanes = SV / rows_per_lane(SV);                                                                            \
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_small_kernel<SV, true, SlotSrc<true, SV>>, \
+                                                                  kSmallThreads, 0)                                \
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rk4_small_kernel<SV, false, SlotSrc<false, SV>>, \
+                                                                  kSmallThreads, 0);                               \
+        break;
+    switch (S) {
+        CHO_RES_CASE(2)
+        CHO_RES_CASE(4)
+        CHO_RES_CASE(8)
+        CHO_RES_CASE(16)
+        CHO_RES_CASE(32)
+        default: break;
+    }
+#undef CHO_RES_CASE
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n * sms * (kSmallThreads / lanes);
+}
+
 cudaError_t launch_rk4_small_persist(int S, const PersistIO& pio, bool fp64, int grid, cudaStream_t st)
 {
 #define CHO_PERSIST_CASE(SV)                                                                            \

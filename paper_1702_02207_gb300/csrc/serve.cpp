@@ -6,10 +6,15 @@
 //      first; strict priority, no ageing) while a slot is free and their state
 //      fits the device-memory budget; each admitted request gets a slot in the
 //      device slot table and a resident state block in its kernel's precision;
-//   2. one chunk: every resident request advances min(chunk, remaining) RK4 steps;
-//      requests are grouped by kernel family (rk4_small by padded size,
+//   2. one chunk: every active resident request advances min(chunk, remaining) RK4
+//      steps; requests are grouped by kernel family (rk4_small by padded size,
 //      rk4_chain by threads per CTA, rk4_dense by shared system) and each group
-//      is one kernel launch over a list of slot ids;
+//      is one kernel launch over a list of slot ids.  The active set is chosen in
+//      priority order (class, then admission order) up to about one wave of the device
+//      (cho_config.active_pct of the instances every kernel holds resident at once);
+//      the other resident requests keep their state on the device and wait at their
+//      chunk boundary until there is room (fixed-priority preemption at chunk
+//      granularity);
 //   3. retirement: finished requests are read back, converted to FP64 and
 //      handed to cho_poll; their slots and memory go back to the pool, so the
 //      next chunk admits more work while the others keep running.
@@ -44,6 +49,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -86,6 +92,9 @@ struct Req {
     void* block = nullptr;
     size_t readback_off = 0;
     bool reading_back = false;
+    int64_t weight = 0;             // occupancy weight (ServeEngine::footprint)
+    bool active = false;            // advanced by the next launch of its group
+    std::list<Req*>::iterator res_it;   // place in its class's resident list
 };
 
 bool fp64_prec(int32_t prec) { return prec == CHO_FP64; }
@@ -326,6 +335,10 @@ struct ServeEngine {
     bool stop = false;
     bool failed = false;
     std::deque<Req*> queue[3];
+    std::list<Req*> resident_by_class[3];   // resident requests, admission order per class
+    bool active_dirty = false;              // the active set needs choosing again
+    int64_t active_cap = 0;                 // occupancy weight of the active set; <= 0: no cap
+    std::map<std::tuple<int, int, int, bool>, int64_t> weight_cache;
     std::unordered_map<uint64_t, Req*> reqs;
     int64_t n_resident = 0;
     uint64_t next_ticket = 1;
@@ -361,6 +374,8 @@ struct ServeEngine {
     void park();                    // quit every resident kernel (before an allocation)
     void fail_all(cho_status st_code);
     void release(Req* r);           // caller holds mu
+    void choose_active();           // caller holds mu
+    int64_t footprint(const Req* r);  // caller holds mu
     // finished requests in the order they finished (cho_poll_any); caller holds mu
     std::deque<uint64_t> done_fifo;
     void mark_done(Req* r)
@@ -404,13 +419,61 @@ void ServeEngine::fail_all(cho_status code)
         }
         q.clear();
     }
+    for (auto& l : resident_by_class) l.clear();
     n_queued = 0;
     n_resident = 0;
     cv.notify_all();
 }
 
+// Occupancy weight of a request: its share of the device, D / (instances its slot kernel
+// holds resident at once), with D = SMs x 2048 the unit of the active-set cap; so a cap
+// of 100 % takes about one wave of every kernel family together (a dense s = 512 request
+// on an 8-CTA cluster weighs as much as eight full SMs, a 2-DOF lane next to nothing).
+// Asked once per kernel shape.
+int64_t ServeEngine::footprint(const Req* r)
+{
+    const cho_system_impl* sys = r->sys;
+    const bool f64 = fp64_prec(r->prec);
+    const bool tc = r->prec == CHO_DENSE_BF16X3 || r->prec == CHO_DENSE_BF16X5 || r->prec == CHO_DENSE_BF16X6;
+    const int size = sys->path == PATH_SMALL ? sys->S : (sys->path == PATH_CHAIN ? sys->s : sys->s_pad);
+    const auto key = std::make_tuple((int)sys->path, size, (int)r->prec, sys->path == PATH_DENSE && sys->n_sys != 1);
+    auto it = weight_cache.find(key);
+    if (it != weight_cache.end()) return it->second;
+    int resident = 0;
+    if (sys->path == PATH_SMALL) {
+        resident = small_slot_resident(sys->S, f64);
+    } else if (sys->path == PATH_CHAIN) {
+        resident = chain_slot_resident(sys->s, f64);
+    } else {
+        DenseSys ds{sys->s, sys->s_pad, sys->d_B64, sys->d_B32, sys->d_Bbf, sys->s_tc, sys->d_err, 0,
+                    sys->n_sys != 1 ? 1 : 0};
+        resident = tc ? dense_tc_slot_resident(ds, r->prec) : dense_slot_resident(ds, f64);
+    }
+    const int64_t D = (int64_t)ctx->sm_count * 2048;
+    const int64_t w = resident > 0 ? std::max<int64_t>(1, (D + resident - 1) / resident) : D;
+    weight_cache[key] = w;
+    return w;
+}
+
+// The active set: resident requests in priority order (class 0 first, admission order
+// within a class), each taken while the set's weight stays within the cap (the first one
+// always), so that under load the higher classes run as on a device of their own and the
+// lower ones wait at their chunk boundaries.
+void ServeEngine::choose_active()
+{
+    int64_t used = 0;
+    for (auto& l : resident_by_class)
+        for (Req* r : l) {
+            r->active = active_cap <= 0 || used == 0 || used + r->weight <= active_cap;
+            if (r->active) used += r->weight;
+        }
+    active_dirty = false;
+}
+
 void ServeEngine::release(Req* r)
 {
+    if (r->slot >= 0) resident_by_class[r->priority].erase(r->res_it);
+    active_dirty = true;
     resident_bytes -= (int64_t)r->bytes;
     if (r->block) pool.put(r->bytes, r->block);
     r->block = nullptr;
@@ -543,7 +606,9 @@ cudaError_t ServeEngine::launch(Group* g)
     const int64_t L = g->chunk;
     cudaError_t e = upload(g, g->st);
     if (e != cudaSuccess) return e;
-    g->launched = g->members;
+    g->launched.clear();
+    for (Req* r : g->members)
+        if (r->active) g->launched.push_back(r);
     const size_t n_ids = g->launched.size();
     if (n_ids == 0) return cudaSuccess;
     int32_t* ids = g->h_ids.get(n_ids, &e);
@@ -674,7 +739,9 @@ cudaError_t ServeEngine::launch_persist(Group* g, bool* fell_back)
     *fell_back = false;
     const int path = std::get<0>(g->key), size = std::get<1>(g->key), prec = std::get<2>(g->key);
     const bool f64 = fp64_prec(prec);
-    const size_t n = g->members.size() + g->incoming.size();
+    size_t n = 0;
+    for (auto* list : {&g->members, &g->incoming})
+        for (Req* r : *list) n += r->active ? 1 : 0;
     if (n == 0) return cudaSuccess;
     cudaError_t e = upload(g, g->cst);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->cst);     // blocks on the device before the doorbell
@@ -727,7 +794,9 @@ cudaError_t ServeEngine::launch_persist(Group* g, bool* fell_back)
         persist_regs += g->footprint;
         persist_ctas += g->grid;
     }
-    g->launched = g->members;
+    g->launched.clear();
+    for (Req* r : g->members)
+        if (r->active) g->launched.push_back(r);
     const int64_t L = g->chunk;
     g->max_run = 0;
     for (size_t i = 0; i < g->launched.size(); ++i) {
@@ -1004,16 +1073,25 @@ void ServeEngine::run()
                     r->state = RQ_RESIDENT;
                     r->remaining = r->n_steps;
                     r->t_admit = now_s();
+                    r->weight = footprint(r);
+                    resident_by_class[p].push_back(r);
+                    r->res_it = std::prev(resident_by_class[p].end());
+                    active_dirty = true;
                     g->incoming.push_back(r);
                     progressed = true;
                 }
                 if (blocked) break;
             }
+            if (active_dirty) choose_active();
             for (auto& kv : groups) {
                 Group* g = kv.second;
-                if (!g->busy && (!g->members.empty() || !g->incoming.empty())) to_launch.push_back(g);
-                // a resident kernel with nothing left to run leaves its SMs to the others
-                if (!g->busy && g->running && g->members.empty() && g->incoming.empty()) quit(g);
+                if (g->busy) continue;
+                bool any = false;
+                for (auto* list : {&g->members, &g->incoming})
+                    for (Req* r : *list) any = any || r->active;
+                if (any) to_launch.push_back(g);
+                // a resident kernel with nothing to run leaves its SMs to the others
+                else if (g->running) quit(g);
             }
             if (progressed) cv.notify_all();
         }
@@ -1052,6 +1130,7 @@ static ServeEngine* engine(cho_ctx* ctx, cho_status* err)
     cudaError_t e = cudaSuccess;
     en->slot_cap = ctx->cfg.max_slots;
     en->persistent = ctx->cfg.persistent != 0;
+    en->active_cap = ctx->cfg.active_pct > 0 ? (int64_t)ctx->cfg.active_pct * ctx->sm_count * 2048 / 100 : 0;
     if (en->persistent) {
         e = en->m_slots.alloc((size_t)en->slot_cap);
         if (e == cudaSuccess) e = en->m_status.alloc((size_t)en->slot_cap);

@@ -520,3 +520,41 @@ def test_poll_any_returns_every_finished_request_once():
     finally:
         mix.close()
         cho.cho_shutdown(ctx)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_active_set_preempts_lower_classes(persistent):
+    """Active set capped at 1 % of one wave of the device: of twelve class-2 chains of 2048
+    masses only a few run at a time and the others stay resident, waiting at their chunk
+    boundary; a class-0 request submitted right after them takes the place of a running
+    class-2 request at its next chunk boundary and finishes before the class-2 requests that
+    waited.  Every result is bitwise that of a context without the cap."""
+    rng = np.random.default_rng(9)
+    ch = inputs.chain_batch(n_inst=2, s=2048, n_steps=1, seed=2048)
+    x0s = [rng.uniform(-1, 1, 2048) for _ in range(13)]
+    prios = [2] * 12 + [0]
+
+    def run(ctx):
+        sys_ = cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"])
+        try:
+            tickets = [cho.cho_submit(ctx, sys_, x0s[k], np.zeros(2048), float(ch["h"][k % 2]), 20000,
+                                      "fp32_kahan", prios[k], k % 2) for k in range(13)]
+            res = wait_all(ctx, tickets, [2048] * 13)
+            return [res[tk] for tk in tickets]
+        finally:
+            cho.cho_destroy_system(sys_)
+
+    ctx = cho.cho_init(0, chunk_steps=500, active_pct=1, persistent=persistent)
+    try:
+        got = run(ctx)
+    finally:
+        cho.cho_shutdown(ctx)
+    later = sum(got[k]["t_done"] > got[12]["t_done"] for k in range(12))
+    assert later >= 8, later
+    ctx = cho.cho_init(0, chunk_steps=500, active_pct=-1)
+    try:
+        ref = run(ctx)
+    finally:
+        cho.cho_shutdown(ctx)
+    for k in range(13):
+        assert np.array_equal(got[k]["x"], ref[k]["x"]) and np.array_equal(got[k]["v"], ref[k]["v"]), k
