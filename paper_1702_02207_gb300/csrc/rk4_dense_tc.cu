@@ -439,6 +439,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const uint64_t bdesc0 = smem_desc(smem_u32(sX), PB * 512, 128);
     const uint64_t adesc0 = smem_desc(smem_u32(sA), 128, 256);
     uint32_t phase = 0;
+    bool inflight = false;                           // a commit whose wait ran out (same in every thread)
+    uint32_t inflight_phase = 0;
 
     // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
     auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
@@ -487,6 +489,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
         // the whole warp takes the same branch around the .sync.aligned TMEM load
         const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma, phase));
+        if (!done && !sys.stall_mma) {
+            inflight = true;
+            inflight_phase = phase;
+        }
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc[kCPT];
@@ -725,6 +731,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         if (!piece_ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
         __syncthreads();                            // sh_* free for the next piece
     }
+    // after a failed wait: wait once more (bounded) for the MMAs still in flight before
+    // the accumulators are freed
+    if (inflight) (void)mbar_wait(&bar_mma, inflight_phase);
     if (!ok && tid == 0 && sys.err) atomicExch(sys.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -10,6 +10,9 @@ Cases (each one cho_integrate_batch call, a few MB of device memory):
   dense_tc  s = 128, 2048 instances, 500 steps, bf16x5       (rk4_dense_tc, one CTA per SM)
   dense_tc64 s = 64, 4096 instances, 500 steps, bf16x5      (rk4_dense_tc, two tiles stacked per CTA)
   dense_tc2 s = 256, 2048 instances, 200 steps, bf16x5       (rk4_dense_tc, 2-CTA clusters)
+  dense_tc_bal s = 128, 8192 instances, 200 steps, bf16x5   (rk4_dense_tc_pair on the balanced schedule:
+            one CTA per SM, 256 tiles cut in step blocks)
+  dense_tc2_bal s = 256, 8192 instances, 60 steps, bf16x5   (rk4_dense_tc, balanced over resident clusters)
   dense_simt s = 256, 512 instances, 50 steps, fp32_simt     (rk4_dense_simt)
   dense_own s = 64, 8192 instances with their own (M, K), 100 steps, fp32_kahan (rk4_dense_own, one per CTA)
   dense_split s = 512, 4 instances of one (M, K), 500 steps, fp32_kahan (rk4_dense_split, 8-CTA clusters)
@@ -49,6 +52,10 @@ def run(case: str) -> None:
             cfg, prec, kind = inputs.dense_group(s=64, n_inst=4096, n_steps=500), "bf16x5", "dense"
         elif case == "dense_tc2":
             cfg, prec, kind = inputs.dense_group(s=256, n_inst=2048, n_steps=200), "bf16x5", "dense"
+        elif case == "dense_tc_bal":
+            cfg, prec, kind = inputs.dense_group(s=128, n_inst=8192, n_steps=200), "bf16x5", "dense"
+        elif case == "dense_tc2_bal":
+            cfg, prec, kind = inputs.dense_group(s=256, n_inst=8192, n_steps=60), "bf16x5", "dense"
         elif case == "dense_simt":
             cfg, prec, kind = inputs.dense_group(s=256, n_inst=512, n_steps=50), "fp32_simt", "dense"
         elif case == "dense_own":
