@@ -410,24 +410,31 @@ __device__ __forceinline__ void rk4_chain_pk_body(const Src& src, int64_t q)
     const float has_left = warp > 0 ? 1.f : 0.f;
     const float has_right = warp + 1 < nwarp ? 1.f : 0.f;
     float2 lo1[H];   // lo parts of g and u times the stage-1 extensions (frozen lo)
+    // The extensions and accelerations of the interior pairs use only this thread's
+    // displacements: they are formed before the barrier, while the edge values travel.
     auto accel = [&](const float2 (&xs)[H], float2 (&acc)[H], bool first) {
         const float up = __shfl_up_sync(0xffffffffu, xs[H - 1].y, 1);
         const float dn = __shfl_down_sync(0xffffffffu, xs[0].x, 1);
         edge_last[buf][warp][lane] = xs[H - 1].y;
         edge_first[buf][warp][lane] = xs[0].x;
+        float2 e[H + 1];                     // e[k] = (e_k, e_{k+H}); e[H] = (e_H, e_P)
+#pragma unroll
+        for (int k = 1; k < H; ++k) e[k] = __ffma2_rn(xs[k - 1], m1, xs[k]);
+#pragma unroll
+        for (int k = 1; k + 1 < H; ++k) {
+            if (first) lo1[k] = __ffma2_rn(ul[k], e[k + 1], __fmul2_rn(ngl[k], e[k]));
+            acc[k] = __ffma2_rn(uh[k], e[k + 1], __ffma2_rn(ngh[k], e[k], lo1[k]));
+        }
         __syncthreads();
         const float el = edge_last[buf][wl][31] * has_left;
         const float ef = edge_first[buf][wr][0] * has_right;
         const float left = lane == 0 ? el : up;
         const float right = lane == 31 ? ef : dn;
         buf ^= 1;
-        float2 e[H + 1];                     // e[k] = (e_k, e_{k+H}); e[H] = (e_H, e_P)
         e[0] = __ffma2_rn(make_float2(left, xs[H - 1].x), m1, xs[0]);
-#pragma unroll
-        for (int k = 1; k < H; ++k) e[k] = __ffma2_rn(xs[k - 1], m1, xs[k]);
         e[H] = __ffma2_rn(xs[H - 1], m1, make_float2(xs[0].y, right));
 #pragma unroll
-        for (int k = 0; k < H; ++k) {
+        for (int k = 0; k < H; k += (H > 1 ? H - 1 : 1)) {
             if (first) lo1[k] = __ffma2_rn(ul[k], e[k + 1], __fmul2_rn(ngl[k], e[k]));
             acc[k] = __ffma2_rn(uh[k], e[k + 1], __ffma2_rn(ngh[k], e[k], lo1[k]));
         }
