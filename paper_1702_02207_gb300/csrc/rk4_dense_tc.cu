@@ -248,6 +248,17 @@ __device__ __forceinline__ void tmem_ld8_x2(uint32_t taddr, float (&v)[2][8])
         for (int i = 0; i < 8; ++i) v[g][i] = __uint_as_float(r[g][i]);
 }
 
+// comp_update on packed pairs: each lane rounds as the scalar form in rk4_common.cuh.
+__device__ __forceinline__ void comp_update2(float2& x, float2& e, float2 k, float2 h6, float2 h6lo)
+{
+    float2 y = __ffma2_rn(h6lo, k, e);
+    y = __ffma2_rn(h6, k, y);
+    const float2 t = __fadd2_rn(x, y);
+    const float2 d = __fadd2_rn(t, make_float2(-x.x, -x.y));
+    e = __fadd2_rn(y, make_float2(-d.x, -d.y));
+    x = t;
+}
+
 // Batch form: FP64 arrays in and out, shared step count, checkpoints.
 struct TcBatchSrc {
     BatchIO io;
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag[2];
-    __shared__ float sh_h[NI][4];                    // h, h/2, h/6 hi, h/6 lo of each instance
+    __shared__ __align__(16) float sh_h[4][NI];      // h, h/2, h/6 hi, h/6 lo of each instance
     __shared__ long long sh_steps[NI];               // steps of each instance in this launch
     __shared__ long long sh_max_steps;
     __shared__ int sh_bad[NI];
@@ -378,6 +389,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     const int s = sys.s;
     const bool live_row = kio < s;
     const int n0 = colgrp * kCPT;                    // first instance column of this thread
+    constexpr int kP = kCPT / 2;                     // instance pairs of this thread
+    // (h, h/2, h/6 hi, h/6 lo)[c] of the thread's instance pair j
+    auto hpair = [&](int c, int j) { return *reinterpret_cast<const float2*>(&sh_h[c][ib + n0 + 2 * j]); };
 
     // ---- set-up: barriers, TMEM, B into shared memory ----
     if (tid == 0) {
@@ -443,22 +457,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
     uint32_t inflight_phase = 0;
 
     // One stage: publish Xs pieces, MMA, return a = -(B Xs) for this thread's cells.
-    auto stage = [&](const float (&xs)[kCPT], float (&a)[kCPT]) -> bool {
-        float r[kCPT];
+    auto stage = [&](const float2 (&xs)[kP], float2 (&a)[kP]) -> bool {
+        float2 r[kP];
 #pragma unroll
-        for (int j = 0; j < kCPT; ++j) r[j] = xs[j];
+        for (int j = 0; j < kP; ++j) r[j] = xs[j];
 #pragma unroll
         for (int p = 0; p < PB; ++p) {
+            __nv_bfloat162 q[kP];
+#pragma unroll
+            for (int j = 0; j < kP; ++j) q[j] = __float22bfloat162_rn(r[j]);
             uint4 w;
-            w.x = pack_bf16(r[0], r[1]);
-            w.y = pack_bf16(r[2], r[3]);
-            w.z = pack_bf16(r[4], r[5]);
-            w.w = pack_bf16(r[6], r[7]);
+            w.x = reinterpret_cast<const uint32_t&>(q[0]);
+            w.y = reinterpret_cast<const uint32_t&>(q[1]);
+            w.z = reinterpret_cast<const uint32_t&>(q[2]);
+            w.w = reinterpret_cast<const uint32_t&>(q[3]);
 #pragma unroll
             for (int c = 0; c < CS; ++c) st_cluster_v4(xdst[c] + (uint32_t)(p * 512), w);
             if (p + 1 < PB) {
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
+                for (int j = 0; j < kP; ++j) {
+                    const float2 back = __bfloat1622float2(q[j]);
+                    r[j] = __fadd2_rn(r[j], make_float2(-back.x, -back.y));
+                }
             }
         }
         // the Xs stores (this CTA's and the peer's) visible to the tensor cores (the async proxy)
@@ -495,51 +515,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         }
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc[kCPT];
+        auto pr = [](const float (&g)[kCPT], int j) { return make_float2(g[2 * j], g[2 * j + 1]); };
+        float2 acc[kP];
         if (done) {
             if constexpr (PA == 2) {
                 // accumulators of two column groups: b0 p0 | b0 p1 + b1 p0
-                float big[kCPT], mid[kCPT];
+                float2 big[kP], mid[kP];
 #pragma unroll
                 for (int sl = 0; sl < NACC; ++sl) {
                     float g[2][kCPT];
                     tmem_ld8_x2(taddr + (uint32_t)(sl * W), g);
 #pragma unroll
-                    for (int j = 0; j < kCPT; ++j) {
-                        big[j] = sl == 0 ? g[0][j] : __fadd_rn(big[j], g[0][j]);
-                        mid[j] = sl == 0 ? g[1][j] : __fadd_rn(mid[j], g[1][j]);
+                    for (int j = 0; j < kP; ++j) {
+                        big[j] = sl == 0 ? pr(g[0], j) : __fadd2_rn(big[j], pr(g[0], j));
+                        mid[j] = sl == 0 ? pr(g[1], j) : __fadd2_rn(mid[j], pr(g[1], j));
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(big[j], mid[j]);
+                for (int j = 0; j < kP; ++j) acc[j] = __fadd2_rn(big[j], mid[j]);
             } else {
                 // accumulators of three column groups: each order summed over the
                 // accumulators, the smaller orders then added to the largest
-                float big[kCPT], mid[kCPT], small[kCPT];
+                float2 big[kP], mid[kP], small[kP];
 #pragma unroll
                 for (int sl = 0; sl < NACC; ++sl) {
                     float g[2][kCPT], g2[kCPT];
                     tmem_ld8_x2(taddr + (uint32_t)(sl * W), g);
                     tmem_ld8(taddr + (uint32_t)(sl * W + 64), g2);
 #pragma unroll
-                    for (int j = 0; j < kCPT; ++j) {
-                        big[j] = sl == 0 ? g[0][j] : __fadd_rn(big[j], g[0][j]);
-                        mid[j] = sl == 0 ? g[1][j] : __fadd_rn(mid[j], g[1][j]);
-                        small[j] = sl == 0 ? g2[j] : __fadd_rn(small[j], g2[j]);
+                    for (int j = 0; j < kP; ++j) {
+                        big[j] = sl == 0 ? pr(g[0], j) : __fadd2_rn(big[j], pr(g[0], j));
+                        mid[j] = sl == 0 ? pr(g[1], j) : __fadd2_rn(mid[j], pr(g[1], j));
+                        small[j] = sl == 0 ? pr(g2, j) : __fadd2_rn(small[j], pr(g2, j));
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(big[j], __fadd_rn(mid[j], small[j]));
+                for (int j = 0; j < kP; ++j) acc[j] = __fadd2_rn(big[j], __fadd2_rn(mid[j], small[j]));
             }
         }
 #pragma unroll
-        for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
+        for (int j = 0; j < kP; ++j) a[j] = done ? make_float2(-acc[j].x, -acc[j].y) : make_float2(0.f, 0.f);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         // every CTA has its MMA done (so Xs may be rewritten) and agrees on aborts
         return agree(done);
     };
 
-    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+    float2 x[kP], v[kP], cx[kP], cv[kP];            // instance columns 2j and 2j + 1 of pair j
+    // the value of instance column j of a pair array
+    auto at = [](float2 (&arr)[kP], int j) -> float& { return (j & 1) ? arr[j >> 1].y : arr[j >> 1].x; };
     // the pieces of this cluster (see TcSched); the piece's description is kept in shared
     // memory, not in registers across the steps
     for (;;) {
@@ -573,10 +596,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             sh_steps[tid] = live ? (long long)src.steps(q) : 0;
             sh_bad[tid] = 0;
             const double h6 = hd / 6.0;
-            sh_h[tid][0] = (float)hd;
-            sh_h[tid][1] = (float)(0.5 * hd);
-            sh_h[tid][2] = (float)h6;
-            sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+            sh_h[0][tid] = (float)hd;
+            sh_h[1][tid] = (float)(0.5 * hd);
+            sh_h[2][tid] = (float)h6;
+            sh_h[3][tid] = (float)(h6 - (double)(float)h6);
         }
         if (tid == 0) {
             sh_tile = tile;
@@ -607,19 +630,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                x[j] = in_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
-                v[j] = in_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
-                cx[j] = in_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
-                cv[j] = in_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
+                at(x, j) = in_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
+                at(v, j) = in_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
+                at(cx, j) = in_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
+                at(cv, j) = in_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
                 const int64_t q = tile * NI + ib + n0 + j;
                 if (live_row && q < src.count()) {
-                    src.load(q, kio, x[j], v[j], cx[j], cv[j]);
+                    src.load(q, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
                 } else {
-                    x[j] = v[j] = cx[j] = cv[j] = 0.f;
+                    at(x, j) = at(v, j) = at(cx, j) = at(cv, j) = 0.f;
                 }
             }
         }
@@ -638,53 +661,65 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
         int64_t ck = src.ckpt_every() > 0 ? st0 / src.ckpt_every() : 0, step = st0;
         for (int64_t done_steps = st0; done_steps < st1 && ok && piece_ok; done_steps += every) {
             for (int64_t it = 0; it < every && ok; ++it, ++step) {
-            float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vs[kCPT];
+            float2 a[kP], xs[kP], kx[kP], kv[kP], vs[kP];
+            const float2 two = make_float2(2.f, 2.f);
             ok = stage(x, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[ib + n0 + j][1];
+            for (int j = 0; j < kP; ++j) {
+                const float2 h2 = hpair(1, j);
                 kx[j] = v[j];
                 kv[j] = a[j];
-                xs[j] = __fmaf_rn(h2, v[j], x[j]);
-                vs[j] = __fmaf_rn(h2, a[j], v[j]);
+                xs[j] = __ffma2_rn(h2, v[j], x[j]);
+                vs[j] = __ffma2_rn(h2, a[j], v[j]);
             }
             if (ok) ok = stage(xs, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[ib + n0 + j][1];
-                kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
-                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
-                xs[j] = __fmaf_rn(h2, vs[j], x[j]);
-                vs[j] = __fmaf_rn(h2, a[j], v[j]);
+            for (int j = 0; j < kP; ++j) {
+                const float2 h2 = hpair(1, j);
+                kx[j] = __ffma2_rn(two, vs[j], kx[j]);
+                kv[j] = __ffma2_rn(two, a[j], kv[j]);
+                xs[j] = __ffma2_rn(h2, vs[j], x[j]);
+                vs[j] = __ffma2_rn(h2, a[j], v[j]);
             }
             if (ok) ok = stage(xs, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h = sh_h[ib + n0 + j][0];
-                kx[j] = __fmaf_rn(2.f, vs[j], kx[j]);
-                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
-                xs[j] = __fmaf_rn(h, vs[j], x[j]);
-                vs[j] = __fmaf_rn(h, a[j], v[j]);
+            for (int j = 0; j < kP; ++j) {
+                const float2 h = hpair(0, j);
+                kx[j] = __ffma2_rn(two, vs[j], kx[j]);
+                kv[j] = __ffma2_rn(two, a[j], kv[j]);
+                xs[j] = __ffma2_rn(h, vs[j], x[j]);
+                vs[j] = __ffma2_rn(h, a[j], v[j]);
             }
             if (ok) ok = stage(xs, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                if (step < sh_steps[ib + n0 + j]) {       // instances past their count hold still
-                    const float h6 = sh_h[ib + n0 + j][2], h6l = sh_h[ib + n0 + j][3];
-                    kx[j] = addr(kx[j], vs[j]);
-                    kv[j] = addr(kv[j], a[j]);
-                    comp_update(x[j], cx[j], kx[j], h6, h6l);
-                    comp_update(v[j], cv[j], kv[j], h6, h6l);
+            for (int j = 0; j < kP; ++j) {
+                const float2 h6 = hpair(2, j), h6l = hpair(3, j);
+                kx[j] = __fadd2_rn(kx[j], vs[j]);
+                kv[j] = __fadd2_rn(kv[j], a[j]);
+                float2 nx = x[j], ncx = cx[j], nv = v[j], ncv = cv[j];
+                comp_update2(nx, ncx, kx[j], h6, h6l);
+                comp_update2(nv, ncv, kv[j], h6, h6l);
+                if (step < sh_steps[ib + n0 + 2 * j]) {       // instances past their count hold still
+                    x[j].x = nx.x;
+                    cx[j].x = ncx.x;
+                    v[j].x = nv.x;
+                    cv[j].x = ncv.x;
+                }
+                if (step < sh_steps[ib + n0 + 2 * j + 1]) {
+                    x[j].y = nx.y;
+                    cx[j].y = ncx.y;
+                    v[j].y = nv.y;
+                    cv[j].y = ncv.y;
                 }
             }
-            }
+        }
             if (src.ckpt_every() > 0 && ok) {
                 if (live_row) {
                     const int64_t tq = *(volatile long long*)&sh_tile;
 #pragma unroll
                     for (int j = 0; j < kCPT; ++j) {
                         const int64_t q = tq * NI + ib + n0 + j;
-                        if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                        if (q < src.count()) src.checkpoint(q, ck, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
                     }
                 }
                 ++ck;
@@ -696,10 +731,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             float* xf = sc.xfer + (size_t)(blockIdx.x) * (4 * kCPT * kTcThreads) + tid;
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                __stcg(xf + (0 * kCPT + j) * kTcThreads, x[j]);
-                __stcg(xf + (1 * kCPT + j) * kTcThreads, v[j]);
-                __stcg(xf + (2 * kCPT + j) * kTcThreads, cx[j]);
-                __stcg(xf + (3 * kCPT + j) * kTcThreads, cv[j]);
+                __stcg(xf + (0 * kCPT + j) * kTcThreads, at(x, j));
+                __stcg(xf + (1 * kCPT + j) * kTcThreads, at(v, j));
+                __stcg(xf + (2 * kCPT + j) * kTcThreads, at(cx, j));
+                __stcg(xf + (3 * kCPT + j) * kTcThreads, at(cv, j));
             }
             __threadfence();
             __syncthreads();
@@ -714,8 +749,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             for (int j = 0; j < kCPT; ++j) {
                 const int64_t q = tile_out * NI + ib + n0 + j;
                 if (q < src.count()) {
-                    src.store(q, kio, x[j], v[j], cx[j], cv[j]);
-                    if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
+                    src.store(q, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
+                    if (!(isfinite(at(x, j)) && isfinite(at(v, j)))) sh_bad[ib + n0 + j] = 1;
                 }
             }
         }
@@ -771,7 +806,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     __shared__ __align__(8) uint64_t bar_mma[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    __shared__ float sh_h[NI][4];                    // h, h/2, h/6 hi, h/6 lo of each instance
+    __shared__ __align__(16) float sh_h[4][NI];      // h, h/2, h/6 hi, h/6 lo of each instance
     __shared__ long long sh_steps[NI];               // steps of each instance in this launch
     __shared__ long long sh_max_steps;
     __shared__ int sh_bad[NI];
@@ -792,6 +827,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     const int s = sys.s;
     const bool live_row = kio < s;
     const int n0 = colgrp * kCPT;                    // first instance column of this thread
+    constexpr int kP = kCPT / 2;                     // instance pairs of this thread
+    // (h, h/2, h/6 hi, h/6 lo)[c] of the thread's instance pair j
+    auto hpair = [&](int c, int j) { return *reinterpret_cast<const float2*>(&sh_h[c][ib + n0 + 2 * j]); };
 
     if (tid == 0) {
         mbar_init(&bar_load, 1);
@@ -840,22 +878,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
     uint32_t phase[2] = {0u, 0u};
     bool inflight[2] = {false, false};               // a commit not yet waited for (same in every thread)
 
-    // Xs pieces of xs into buffer set b
-    auto publish = [&](int b, const float (&xs)[kCPT]) {
-        float r[kCPT];
+    // Xs pieces of xs into buffer set b (instance columns in pairs: one conversion
+    // instruction per pair, the residual in packed FP32; the same roundings as per value)
+    auto publish = [&](int b, const float2 (&xs)[kP]) {
+        float2 r[kP];
 #pragma unroll
-        for (int j = 0; j < kCPT; ++j) r[j] = xs[j];
+        for (int j = 0; j < kP; ++j) r[j] = xs[j];
 #pragma unroll
         for (int p = 0; p < PB; ++p) {
+            __nv_bfloat162 q[kP];
+#pragma unroll
+            for (int j = 0; j < kP; ++j) q[j] = __float22bfloat162_rn(r[j]);
             uint4 w;
-            w.x = pack_bf16(r[0], r[1]);
-            w.y = pack_bf16(r[2], r[3]);
-            w.z = pack_bf16(r[4], r[5]);
-            w.w = pack_bf16(r[6], r[7]);
+            w.x = reinterpret_cast<const uint32_t&>(q[0]);
+            w.y = reinterpret_cast<const uint32_t&>(q[1]);
+            w.z = reinterpret_cast<const uint32_t&>(q[2]);
+            w.w = reinterpret_cast<const uint32_t&>(q[3]);
             st_cluster_v4(xdst + (uint32_t)(b * X_BYTES + p * 512), w);
             if (p + 1 < PB) {
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) r[j] -= __bfloat162float(__float2bfloat16_rn(r[j]));
+                for (int j = 0; j < kP; ++j) {
+                    const float2 back = __bfloat1622float2(q[j]);
+                    r[j] = __fadd2_rn(r[j], make_float2(-back.x, -back.y));
+                }
             }
         }
     };
@@ -892,15 +937,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         }
         inflight[b] = !sys.stall_mma;
     };
-    // wait for accumulator set b and return a = -(B Xs) for this thread's cells
-    auto collect = [&](int b, float (&a)[kCPT]) -> bool {
+    // wait for accumulator set b and return a = -(B Xs) for this thread's cells, the column
+    // groups summed in packed FP32 (pairs of instances; each lane rounds as a scalar add)
+    auto collect = [&](int b, float2 (&a)[kP]) -> bool {
         const bool done = __all_sync(0xffffffffu, mbar_wait(&bar_mma[b], phase[b]));
         if (done) {
             phase[b] ^= 1u;
             inflight[b] = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc[kCPT];
+        auto pr = [](const float (&g)[kCPT], int j) { return make_float2(g[2 * j], g[2 * j + 1]); };
+        float2 acc[kP];
         if (done) {
             const uint32_t taddr = tlane + (uint32_t)(b * NACC * W);
             if constexpr (PA == 2) {
@@ -908,41 +955,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
                 float g[2][kCPT];
                 tmem_ld8_x2(taddr, g);
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(g[0][j], g[1][j]);
+                for (int j = 0; j < kP; ++j) acc[j] = __fadd2_rn(pr(g[0], j), pr(g[1], j));
             } else if constexpr (NACC == 1) {
                 // one accumulator of three column groups, the smaller orders first
                 float g[2][kCPT], g2[kCPT];
                 tmem_ld8_x2(taddr, g);
                 tmem_ld8(taddr + 64u, g2);
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j) acc[j] = __fadd_rn(g[0][j], __fadd_rn(g[1][j], g2[j]));
+                for (int j = 0; j < kP; ++j) acc[j] = __fadd2_rn(pr(g[0], j), __fadd2_rn(pr(g[1], j), pr(g2, j)));
             } else {
                 // two accumulators of three column groups: each order summed over the two,
                 // then the smaller orders added to the largest
-                float big[kCPT], mid[kCPT], small[kCPT];
-                {
-                    float g[4][kCPT];
-                    tmem_ld8_x4(taddr, g);                      // slot 0: G0 G1 G2; slot 1: G0
-#pragma unroll
-                    for (int j = 0; j < kCPT; ++j) {
-                        big[j] = __fadd_rn(g[0][j], g[3][j]);
-                        mid[j] = g[1][j];
-                        small[j] = g[2][j];
-                    }
-                }
+                float g[4][kCPT];
+                tmem_ld8_x4(taddr, g);                          // slot 0: G0 G1 G2; slot 1: G0
                 float h[2][kCPT];
                 tmem_ld8_x2(taddr + (uint32_t)(W + 32), h);      // slot 1: G1 G2
 #pragma unroll
-                for (int j = 0; j < kCPT; ++j)
-                    acc[j] = __fadd_rn(big[j], __fadd_rn(__fadd_rn(mid[j], h[0][j]), __fadd_rn(small[j], h[1][j])));
+                for (int j = 0; j < kP; ++j) {
+                    const float2 big = __fadd2_rn(pr(g[0], j), pr(g[3], j));
+                    acc[j] = __fadd2_rn(big, __fadd2_rn(__fadd2_rn(pr(g[1], j), pr(h[0], j)),
+                                                       __fadd2_rn(pr(g[2], j), pr(h[1], j))));
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < kCPT; ++j) a[j] = done ? -acc[j] : 0.f;
+        for (int j = 0; j < kP; ++j) a[j] = done ? make_float2(-acc[j].x, -acc[j].y) : make_float2(0.f, 0.f);
         return done;
     };
 
-    float x[kCPT], v[kCPT], cx[kCPT], cv[kCPT];
+    float2 x[kP], v[kP], cx[kP], cv[kP];            // instance columns 2j and 2j + 1 of pair j
+    // the value of instance column j of a pair array
+    auto at = [](float2 (&arr)[kP], int j) -> float& { return (j & 1) ? arr[j >> 1].y : arr[j >> 1].x; };
     // the pieces of this CTA: (tile, steps [st0, st1), state from the hand-over of CTA
     // g + 1 or from the input, state to the hand-over of this CTA or to the output).  The
     // piece's description is kept in shared memory, not in registers across the steps.
@@ -977,10 +1020,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             sh_steps[tid] = live ? (long long)src.steps(q) : 0;
             sh_bad[tid] = 0;
             const double h6 = hd / 6.0;
-            sh_h[tid][0] = (float)hd;
-            sh_h[tid][1] = (float)(0.5 * hd);
-            sh_h[tid][2] = (float)h6;
-            sh_h[tid][3] = (float)(h6 - (double)(float)h6);
+            sh_h[0][tid] = (float)hd;
+            sh_h[1][tid] = (float)(0.5 * hd);
+            sh_h[2][tid] = (float)h6;
+            sh_h[3][tid] = (float)(h6 - (double)(float)h6);
         }
         if (tid == 0) {
             sh_tile = tile;
@@ -1010,19 +1053,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                x[j] = piece_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
-                v[j] = piece_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
-                cx[j] = piece_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
-                cv[j] = piece_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
+                at(x, j) = piece_ok ? __ldcg(xf + (0 * kCPT + j) * kTcThreads) : nan;
+                at(v, j) = piece_ok ? __ldcg(xf + (1 * kCPT + j) * kTcThreads) : nan;
+                at(cx, j) = piece_ok ? __ldcg(xf + (2 * kCPT + j) * kTcThreads) : nan;
+                at(cv, j) = piece_ok ? __ldcg(xf + (3 * kCPT + j) * kTcThreads) : nan;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
                 const int64_t q = tile * NI + ib + n0 + j;
                 if (live_row && q < src.count()) {
-                    src.load(q, kio, x[j], v[j], cx[j], cv[j]);
+                    src.load(q, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
                 } else {
-                    x[j] = v[j] = cx[j] = cv[j] = 0.f;
+                    at(x, j) = at(v, j) = at(cx, j) = at(cv, j) = 0.f;
                 }
             }
         }
@@ -1039,10 +1082,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         int64_t ck = src.ckpt_every() > 0 ? st0 / src.ckpt_every() : 0, step = st0;
         for (int64_t done_steps = st0; done_steps < st1 && ok && piece_ok; done_steps += every) {
             for (int64_t it = 0; it < every && ok; ++it, ++step) {
-            float a[kCPT], xs[kCPT], kx[kCPT], kv[kCPT], vm[kCPT];
+            float2 a[kP], xs[kP], kx[kP], kv[kP], vm[kP];
+            const float2 two = make_float2(2.f, 2.f);
             // stages 1 and 2 together: Xs = x and x + h/2 v
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) xs[j] = __fmaf_rn(sh_h[ib + n0 + j][1], v[j], x[j]);
+            for (int j = 0; j < kP; ++j) xs[j] = __ffma2_rn(hpair(1, j), v[j], x[j]);
             publish(0, x);
             publish(1, xs);
             if (!(ok = sync(true))) break;
@@ -1051,12 +1095,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             // stage 1 result: a1; stage 3's Xs = x + h/2 v2 with v2 = v + h/2 a1
             bool good = collect(0, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[ib + n0 + j][1];
+            for (int j = 0; j < kP; ++j) {
+                const float2 h2 = hpair(1, j);
                 kx[j] = v[j];
                 kv[j] = a[j];
-                vm[j] = __fmaf_rn(h2, a[j], v[j]);     // v2
-                xs[j] = __fmaf_rn(h2, vm[j], x[j]);    // x3
+                vm[j] = __ffma2_rn(h2, a[j], v[j]);     // v2
+                xs[j] = __ffma2_rn(h2, vm[j], x[j]);    // x3
             }
             publish(0, xs);
             if (!(ok = sync(good))) break;
@@ -1064,12 +1108,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             // stage 2 result: a2; stage 4's Xs = x + h v3 with v3 = v + h/2 a2
             good = collect(1, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h2 = sh_h[ib + n0 + j][1], h = sh_h[ib + n0 + j][0];
-                kx[j] = __fmaf_rn(2.f, vm[j], kx[j]);
-                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
-                vm[j] = __fmaf_rn(h2, a[j], v[j]);     // v3
-                xs[j] = __fmaf_rn(h, vm[j], x[j]);     // x4
+            for (int j = 0; j < kP; ++j) {
+                const float2 h2 = hpair(1, j), h = hpair(0, j);
+                kx[j] = __ffma2_rn(two, vm[j], kx[j]);
+                kv[j] = __ffma2_rn(two, a[j], kv[j]);
+                vm[j] = __ffma2_rn(h2, a[j], v[j]);     // v3
+                xs[j] = __ffma2_rn(h, vm[j], x[j]);     // x4
             }
             publish(1, xs);
             if (!(ok = sync(good))) break;
@@ -1077,33 +1121,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             // stage 3 result: a3; v4 = v + h a3
             good = collect(0, a);
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                const float h = sh_h[ib + n0 + j][0];
-                kx[j] = __fmaf_rn(2.f, vm[j], kx[j]);
-                kv[j] = __fmaf_rn(2.f, a[j], kv[j]);
-                vm[j] = __fmaf_rn(h, a[j], v[j]);      // v4
+            for (int j = 0; j < kP; ++j) {
+                const float2 h = hpair(0, j);
+                kx[j] = __ffma2_rn(two, vm[j], kx[j]);
+                kv[j] = __ffma2_rn(two, a[j], kv[j]);
+                vm[j] = __ffma2_rn(h, a[j], v[j]);      // v4
             }
-            // stage 4 result: a4, then the step's update
+            // stage 4 result: a4, then the step's update (compensated, in packed pairs; an
+            // instance past its step count holds still)
             if (good) good = collect(1, a);
             if (!(ok = agree(good))) break;
 #pragma unroll
-            for (int j = 0; j < kCPT; ++j) {
-                if (step < sh_steps[ib + n0 + j]) {       // instances past their count hold still
-                    const float h6 = sh_h[ib + n0 + j][2], h6l = sh_h[ib + n0 + j][3];
-                    kx[j] = addr(kx[j], vm[j]);
-                    kv[j] = addr(kv[j], a[j]);
-                    comp_update(x[j], cx[j], kx[j], h6, h6l);
-                    comp_update(v[j], cv[j], kv[j], h6, h6l);
+            for (int j = 0; j < kP; ++j) {
+                const float2 h6 = hpair(2, j), h6l = hpair(3, j);
+                kx[j] = __fadd2_rn(kx[j], vm[j]);
+                kv[j] = __fadd2_rn(kv[j], a[j]);
+                float2 nx = x[j], ncx = cx[j], nv = v[j], ncv = cv[j];
+                comp_update2(nx, ncx, kx[j], h6, h6l);
+                comp_update2(nv, ncv, kv[j], h6, h6l);
+                if (step < sh_steps[ib + n0 + 2 * j]) {
+                    x[j].x = nx.x;
+                    cx[j].x = ncx.x;
+                    v[j].x = nv.x;
+                    cv[j].x = ncv.x;
+                }
+                if (step < sh_steps[ib + n0 + 2 * j + 1]) {
+                    x[j].y = nx.y;
+                    cx[j].y = ncx.y;
+                    v[j].y = nv.y;
+                    cv[j].y = ncv.y;
                 }
             }
-            }
+        }
             if (src.ckpt_every() > 0 && ok) {
                 if (live_row) {
                     const int64_t tq = *(volatile long long*)&sh_tile;
 #pragma unroll
                     for (int j = 0; j < kCPT; ++j) {
                         const int64_t q = tq * NI + ib + n0 + j;
-                        if (q < src.count()) src.checkpoint(q, ck, kio, x[j], v[j], cx[j], cv[j]);
+                        if (q < src.count()) src.checkpoint(q, ck, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
                     }
                 }
                 ++ck;
@@ -1115,10 +1171,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             float* xf = sc.xfer + (size_t)blockIdx.x * (4 * kCPT * kTcThreads) + tid;
 #pragma unroll
             for (int j = 0; j < kCPT; ++j) {
-                __stcg(xf + (0 * kCPT + j) * kTcThreads, x[j]);
-                __stcg(xf + (1 * kCPT + j) * kTcThreads, v[j]);
-                __stcg(xf + (2 * kCPT + j) * kTcThreads, cx[j]);
-                __stcg(xf + (3 * kCPT + j) * kTcThreads, cv[j]);
+                __stcg(xf + (0 * kCPT + j) * kTcThreads, at(x, j));
+                __stcg(xf + (1 * kCPT + j) * kTcThreads, at(v, j));
+                __stcg(xf + (2 * kCPT + j) * kTcThreads, at(cx, j));
+                __stcg(xf + (3 * kCPT + j) * kTcThreads, at(cv, j));
             }
             __threadfence();
             __syncthreads();
@@ -1133,8 +1189,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             for (int j = 0; j < kCPT; ++j) {
                 const int64_t q = tile_out * NI + ib + n0 + j;
                 if (q < src.count()) {
-                    src.store(q, kio, x[j], v[j], cx[j], cv[j]);
-                    if (!(isfinite(x[j]) && isfinite(v[j]))) sh_bad[ib + n0 + j] = 1;
+                    src.store(q, kio, at(x, j), at(v, j), at(cx, j), at(cv, j));
+                    if (!(isfinite(at(x, j)) && isfinite(at(v, j)))) sh_bad[ib + n0 + j] = 1;
                 }
             }
         }
