@@ -194,13 +194,6 @@ __device__ __forceinline__ void tmem_ld8_x4(uint32_t taddr, float (&v)[4][8])
         for (int i = 0; i < 8; ++i) v[g][i] = __uint_as_float(r[g][i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    const __nv_bfloat16 a = __float2bfloat16_rn(lo);
-    const __nv_bfloat16 b = __float2bfloat16_rn(hi);
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 // Grouped products.  An MMA of N <= 64 costs about as much as one of
 // N = 32, so the MMA of B piece a covers all the Xs pieces paired with it, laid side by
 // side along N (32 columns per piece), and writes accumulator columns from 32 a on:
