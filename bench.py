@@ -334,6 +334,7 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
         first = nxt[0]
         gaps = np.random.default_rng(inputs.SEED_BASE + int(rho * 100)).exponential(1.0 / lam, size=1 << 20)
         depth, mem, sink = [], [], []
+        tr0 = cho.cho_serve_traffic(ctx)
         t0 = _t.perf_counter()
         next_t, g, last_sample = 0.0, 0, 0.0
         while True:
@@ -354,6 +355,10 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
         offered = nxt[0] - first
         t_off = _t.perf_counter() - t0
         sink += drain()
+        tr1 = cho.cho_serve_traffic(ctx)
+        t_tr = _t.perf_counter() - t0
+        d_bytes = tr1["state_bytes"] - tr0["state_bytes"]
+        d_dof = tr1["dof_steps"] - tr0["dof_steps"]
         lat = {c: [td - ts for i, code, ts, td in sink if code == cho.CHO_OK and i >= first and prios[i] == c]
                for c in range(3)}
         if records is not None:
@@ -365,6 +370,11 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
             "latency_s": {f"class{c}": {"p50": percentile(lat[c], 50), "p99": percentile(lat[c], 99),
                                         "n": len(lat[c])} for c in range(3)},
             "queue_depth": {"mean": float(np.mean(depth)) if depth else None, "max": int(max(depth)) if depth else None},
+            "chunk_boundary_hbm": {"state_bytes": int(d_bytes), "dof_steps": int(d_dof),
+                                   "bytes_per_dof_step": d_bytes / d_dof if d_dof else None,
+                                   "gb_per_s": d_bytes / t_tr / 1e9,
+                                   "note": "resident state read and written back once per chunk by every advanced "
+                                           "request, over the load window and its drain"},
             "resident_bytes": {"mean": float(np.mean(mem)) if mem else None, "max": int(max(mem)) if mem else None}}
         log(f"serving load {rho}: {offered} requests at {offered / t_off:.0f}/s "
             f"(target {lam:.0f}/s), p99 {[out['loads'][f'{rho:.2f}']['latency_s'][f'class{c}']['p99'] for c in range(3)]}")

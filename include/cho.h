@@ -454,6 +454,12 @@ cho_status cho_cancel(cho_ctx* ctx, uint64_t ticket);
 cho_status cho_serve_stats(cho_ctx* ctx, int64_t* queued, int64_t* resident, int64_t* completed,
                            int64_t* resident_bytes);
 
+/* Serving traffic at chunk boundaries (cumulative since the engine started): the resident
+ * state bytes the chunks read and wrote back (each advanced request's state block once each
+ * way per chunk) and the DOF-steps they advanced, so that bytes / DOF-steps is the engine's
+ * memory term per DOF-step (about 2 x 16 B / L for FP32 state and chunks of L steps). */
+cho_status cho_serve_traffic(cho_ctx* ctx, int64_t* state_bytes_moved, int64_t* dof_steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ EXPORTED = [
     "cho_integrate_plain_noalloc",
     "cho_energy", "cho_submit", "cho_poll", "cho_cancel", "cho_serve_stats",
     "cho_autotune", "cho_tune_query", "cho_tune_save", "cho_tune_load", "cho_measure_fma_peak",
-    "cho_integrate_packed", "cho_poll_any",
+    "cho_integrate_packed", "cho_poll_any", "cho_serve_traffic",
 ]
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -128,6 +128,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cho_poll": ([V, ctypes.c_uint64, ctypes.POINTER(cho_result)], I32),
             "cho_cancel": ([V, ctypes.c_uint64], I32),
             "cho_serve_stats": ([V] + [ctypes.POINTER(I64)] * 4, I32),
+            "cho_serve_traffic": ([V] + [ctypes.POINTER(I64)] * 2, I32),
             "cho_autotune": ([V, V, I64, I32, I32, ctypes.POINTER(cho_tune_result)], I32),
             "cho_tune_query": ([V, V, I64, I32, I32, ctypes.POINTER(I32)], I32),
             "cho_tune_save": ([V, ctypes.c_char_p], I32),
@@ -485,6 +486,14 @@ def cho_serve_stats(ctx):
     vals = [ctypes.c_int64() for _ in range(4)]
     _check(load().cho_serve_stats(ctx, *[ctypes.byref(v) for v in vals]))
     return dict(zip(("queued", "resident", "completed", "resident_bytes"), (v.value for v in vals)))
+
+
+def cho_serve_traffic(ctx):
+    """Cumulative chunk-boundary traffic of the serving engine: state bytes read and written
+    back by the chunks and the DOF-steps they advanced (include/cho.h)."""
+    vals = [ctypes.c_int64() for _ in range(2)]
+    _check(load().cho_serve_traffic(ctx, *[ctypes.byref(v) for v in vals]))
+    return {"state_bytes": vals[0].value, "dof_steps": vals[1].value}
 
 
 # ---- autotuning ------------------------------------------------------------------------

@@ -345,6 +345,9 @@ struct ServeEngine {
     int64_t resident_bytes = 0;
     int64_t completed = 0;
     int64_t n_queued = 0;
+    // chunk-boundary traffic: state bytes each chunk reads and writes back (the resident
+    // block of every advanced request, once each way) and the DOF-steps it advances
+    int64_t traffic_bytes = 0, traffic_dof_steps = 0;
     // device side (worker thread only)
     int32_t slot_cap = 0;
     std::vector<int32_t> free_slots;
@@ -674,7 +677,10 @@ void ServeEngine::retire(Group* g)
     const unsigned char* down = g->h_down.ptr();
     for (size_t i = 0; i < g->launched.size(); ++i) {
         Req* r = g->launched[i];
-        r->remaining -= std::min<int64_t>(L, r->remaining);
+        const int64_t ran = std::min<int64_t>(L, r->remaining);
+        traffic_bytes += 2 * (int64_t)state_bytes(r->sys, r->prec);
+        traffic_dof_steps += (int64_t)r->sys->s * ran;
+        r->remaining -= ran;
         const int32_t code = hst ? hst[i] : 0;
         if (code != 0) {
             r->status = (cho_status)code;
@@ -887,7 +893,10 @@ void ServeEngine::retire_persist(Group* g)
     size_t doff = 0;
     for (size_t i = 0; i < g->launched.size() && e == cudaSuccess; ++i) {
         Req* r = g->launched[i];
-        r->remaining -= std::min<int64_t>(L, r->remaining);
+        const int64_t ran = std::min<int64_t>(L, r->remaining);
+        traffic_bytes += 2 * (int64_t)state_bytes(r->sys, r->prec);
+        traffic_dof_steps += (int64_t)r->sys->s * ran;
+        r->remaining -= ran;
         const int32_t code = ((volatile int32_t*)m_status.h)[r->slot];
         r->reading_back = finished[i] && code == 0 && r->remaining == 0;
         if (r->reading_back) {
@@ -1370,5 +1379,25 @@ extern "C" cho_status cho_serve_stats(cho_ctx* ctx, int64_t* queued, int64_t* re
     if (resident) *resident = r;
     if (completed) *completed = c;
     if (resident_bytes) *resident_bytes = b;
+    return CHO_OK;
+}
+
+extern "C" cho_status cho_serve_traffic(cho_ctx* ctx, int64_t* state_bytes_moved, int64_t* dof_steps)
+{
+    clear_error();
+    if (!ctx) return fail(CHO_EINVAL, "cho_serve_traffic: NULL ctx");
+    ServeEngine* en;
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        en = ctx->serve;
+    }
+    int64_t b = 0, d = 0;
+    if (en) {
+        std::lock_guard<std::mutex> lk(en->mu);
+        b = en->traffic_bytes;
+        d = en->traffic_dof_steps;
+    }
+    if (state_bytes_moved) *state_bytes_moved = b;
+    if (dof_steps) *dof_steps = d;
     return CHO_OK;
 }

@@ -558,3 +558,24 @@ def test_active_set_preempts_lower_classes(persistent):
         cho.cho_shutdown(ctx)
     for k in range(13):
         assert np.array_equal(got[k]["x"], ref[k]["x"]) and np.array_equal(got[k]["v"], ref[k]["v"]), k
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_serve_traffic_counts_chunk_boundary_state(persistent):
+    """cho_serve_traffic: with a fixed chunk length L every chain request of s masses and n steps
+    is advanced in ceil(n / L) chunks, each reading and writing back its FP32 state block
+    (x, v and both compensations: 16 s bytes) once, and advances s n DOF-steps in all."""
+    L = 300
+    ctx = cho.cho_init(0, chunk_steps=L, persistent=persistent)
+    mix = Mix(ctx, seed=10)
+    try:
+        reqs = [mix.request(k, n_steps=n) for k, n in zip((2, 3, 2, 3, 2), (900, 1000, 301, 299, 1))]
+        t = [mix.submit(r) for r in reqs]
+        got = wait_all(ctx, t, [r["s"] for r in reqs])
+        assert all(not isinstance(got[x], int) for x in t)
+        tr = cho.cho_serve_traffic(ctx)
+        assert tr["dof_steps"] == sum(r["s"] * r["n"] for r in reqs)
+        assert tr["state_bytes"] == sum(2 * 16 * r["s"] * -(-r["n"] // L) for r in reqs)
+    finally:
+        mix.close()
+        cho.cho_shutdown(ctx)
