@@ -791,9 +791,13 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
             line_ = {"value": dof / t, "unit": UNIT, "ms": 1e3 * t, "n_steps": cfg["n_steps"],
                      "error_vs_oracle": sampled_err(s_, cfg, prec, n_sample=16)}
             if prec.startswith("bf16"):
+                # issued: every split product (x3 / x5 / x6: 3 / 5 / 6), and at s = 64 the zero blocks of
+                # the block-diagonal [B 0; 0 B] the 128-row MMA multiplies
+                issued = ach * {"bf16x3": 3, "bf16x5": 5, "bf16x6": 6}[prec] * (2 if s == 64 else 1)
                 line_["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                                     "frac": ach / bf16_peak,
-                                     "note": "algorithmic flops (8 s per DOF-step) against the sustained BF16 peak"}
+                                     "frac": ach / bf16_peak, "issued": issued, "issued_frac": issued / bf16_peak,
+                                     "note": "algorithmic flops (8 s per DOF-step) against the sustained BF16 peak; "
+                                             "issued = the MMAs' flops (split products, block-diagonal zeros)"}
             elif prec == "fp32_simt":
                 line_["roofline"] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                                      "frac": ach / alu_peak}
