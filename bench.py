@@ -460,31 +460,43 @@ def other_configs(cho, inputs, ctx, dev, stream, sm_count, max_mhz, peaks, alu_p
         v0 = torch.as_tensor(cfg["v0"][idx], device=dev)
         h = torch.as_tensor(cfg["h"][idx], device=dev)
         nt = min(n_sample, host_cores())
+        t_or = 0.0
         if cfg["kind"] == "dense" and cfg["M"].shape[0] > 1:          # one (M, K) per instance
             s2 = cho.cho_create_system(ctx, "dense", M=cfg["M"][idx], K=cfg["K"][idx])
             r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True)
             cho.cho_destroy_system(s2)
+            t_or = time.perf_counter()
             ref = cached or oracle.rk4_dense(cfg["M"][idx], cfg["K"][idx], cfg["x0"][idx], cfg["v0"][idx],
                                              cfg["h"][idx], cfg["n_steps"], every, threads=nt)
+            t_or = time.perf_counter() - t_or
         elif cfg["kind"] == "dense":
             r = cho.cho_integrate_batch(ctx, sys_, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
                                         poly_jump=poly)
+            t_or = time.perf_counter()
             ref = cached or oracle.rk4_dense(cfg["M"][0], cfg["K"][0], cfg["x0"][idx], cfg["v0"][idx],
                                              cfg["h"][idx], cfg["n_steps"], every, threads=nt)
+            t_or = time.perf_counter() - t_or
         else:
             s2 = cho.cho_create_system(ctx, "chain", masses=cfg["masses"][idx], springs=cfg["springs"][idx])
             r = cho.cho_integrate_batch(ctx, s2, x0, v0, h, cfg["n_steps"], prec, every, trajectory=True,
                                         poly_jump=poly)
             cho.cho_destroy_system(s2)
+            t_or = time.perf_counter()
             ref = cached or oracle.rk4_chain(cfg["masses"][idx], cfg["springs"][idx], cfg["x0"][idx],
                                              cfg["v0"][idx], cfg["h"][idx], cfg["n_steps"], every, threads=nt)
+            t_or = time.perf_counter() - t_or
         ref_cache[key] = (cfg["x0"], ref)       # the array is held, so its id is not reused
         torch.cuda.synchronize()
         e = 0.0
         for key in ("x_traj", "v_traj"):
             g = r[key].cpu().numpy()
             e = max(e, float(np.max(np.max(np.abs(g - ref[key]), axis=(1, 2)) / np.max(np.abs(ref[key]), axis=(1, 2)))))
-        return {"max": e, "instances": int(len(idx))}
+        out = {"max": e, "instances": int(len(idx))}
+        if cached is None:
+            # the FP64 oracle on this subset, instances split over nt host threads
+            out["oracle_cpu"] = {"seconds": t_or, "threads": nt,
+                                 "dof_steps_per_s": len(idx) * cfg["x0"].shape[1] * cfg["n_steps"] / t_or}
+        return out
 
     def timed(sys_, cfg, prec, n, poly=0):
         x0 = torch.as_tensor(cfg["x0"], device=dev)

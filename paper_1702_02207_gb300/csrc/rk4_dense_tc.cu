@@ -1074,6 +1074,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
         const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (len > 0 ? len : 1);
         int64_t ck = src.ckpt_every() > 0 ? st0 / src.ckpt_every() : 0, step = st0;
         for (int64_t done_steps = st0; done_steps < st1 && ok && piece_ok; done_steps += every) {
+            // the last product of a step is agreed on at the next step's first barrier (or after
+            // the block, before its results are written): a failure there ends the run
+            bool good_prev = true;
             for (int64_t it = 0; it < every && ok; ++it, ++step) {
             float2 a[kP], xs[kP], kx[kP], kv[kP], vm[kP];
             const float2 two = make_float2(2.f, 2.f);
@@ -1082,7 +1085,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             for (int j = 0; j < kP; ++j) xs[j] = __ffma2_rn(hpair(1, j), v[j], x[j]);
             publish(0, x);
             publish(1, xs);
-            if (!(ok = sync(true))) break;
+            if (!(ok = sync(good_prev))) break;
             issue(0);
             issue(1);
             // stage 1 result: a1; stage 3's Xs = x + h/2 v2 with v2 = v + h/2 a1
@@ -1123,7 +1126,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
             // stage 4 result: a4, then the step's update (compensated, in packed pairs; an
             // instance past its step count holds still)
             if (good) good = collect(1, a);
-            if (!(ok = agree(good))) break;
+            good_prev = good;
 #pragma unroll
             for (int j = 0; j < kP; ++j) {
                 const float2 h6 = hpair(2, j), h6l = hpair(3, j);
@@ -1146,6 +1149,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_pair_kernel(DenseS
                 }
             }
         }
+            if (ok) ok = agree(good_prev);
             if (src.ckpt_every() > 0 && ok) {
                 if (live_row) {
                     const int64_t tq = *(volatile long long*)&sh_tile;
