@@ -431,6 +431,15 @@ cho_status cho_measure_fma_peak(cho_ctx* ctx, int32_t kind, int32_t iters, doubl
  * launched kernels; a group beyond that, and every dense group, is launched per chunk as in
  * the default mode.  A group with no resident request releases its kernel. */
 
+/* Fixed priorities (Section 5's fixed-priority real-time use).  Queued requests are admitted
+ * class 0 first, FIFO within a class, while a slot is free and their state fits the budget.
+ * Each chunk then advances the active set: the resident requests taken in the same order
+ * (class, then admission) while their weights, each the request's share of one wave of the
+ * device (1 / the instances its kernel holds resident at once), stay within
+ * cho_config.active_pct; the other resident requests keep their state on the device and
+ * wait at their chunk boundary, so a higher-class arrival takes the place of lower-class
+ * work at the next boundary.  A request's result does not depend on when it ran. */
+
 /* Queue one request.  Inputs are copied; returns at once with a ticket.
  * Errors: CHO_EINVAL, CHO_EUNSTABLE, CHO_EBUDGET (the request alone exceeds the budget). */
 cho_status cho_submit(cho_ctx* ctx, const cho_request* req, uint64_t* ticket);
