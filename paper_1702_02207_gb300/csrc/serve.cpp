@@ -1031,18 +1031,24 @@ void ServeEngine::run()
                 retire(g);
                 progressed = true;
             }
-            // cancelled requests of idle groups leave before their next launch
+            // cancelled requests leave: those not yet on the device (admitted, waiting for their
+            // group's next launch, possibly paused) at once, members of idle groups before their
+            // next launch
             for (auto& kv : groups) {
                 Group* g = kv.second;
-                if (g->busy) continue;
-                auto it = std::remove_if(g->members.begin(), g->members.end(), [&](Req* r) {
+                auto cancel = [&](Req* r) {
                     if (!r->cancel) return false;
                     mark_done(r);
                     r->status = CHO_ECANCELLED;
                     r->t_done = now_s();
                     release(r);
                     return true;
-                });
+                };
+                auto in = std::remove_if(g->incoming.begin(), g->incoming.end(), cancel);
+                if (in != g->incoming.end()) progressed = true;
+                g->incoming.erase(in, g->incoming.end());
+                if (g->busy) continue;
+                auto it = std::remove_if(g->members.begin(), g->members.end(), cancel);
                 if (it != g->members.end()) progressed = true;
                 g->members.erase(it, g->members.end());
             }

@@ -579,3 +579,34 @@ def test_serve_traffic_counts_chunk_boundary_state(persistent):
     finally:
         mix.close()
         cho.cho_shutdown(ctx)
+
+
+def test_cancel_ends_a_paused_request_at_once():
+    """A cancelled request that waits resident outside the active set (cap at 1 % of a wave:
+    three of eight chains of 2048 masses run) ends with CHO_ECANCELLED at the engine's next
+    scheduling point, while the requests that run are still running."""
+    rng = np.random.default_rng(11)
+    ch = inputs.chain_batch(n_inst=2, s=2048, n_steps=1, seed=2049)
+    ctx = cho.cho_init(0, chunk_steps=500, active_pct=1)
+    sys_ = cho.cho_create_system(ctx, "chain", masses=ch["masses"], springs=ch["springs"])
+    try:
+        tickets = [cho.cho_submit(ctx, sys_, rng.uniform(-1, 1, 2048), np.zeros(2048), float(ch["h"][0]), 60000,
+                                  "fp32_kahan", 2, 0) for _ in range(8)]
+        time.sleep(0.02)
+        cho.cho_cancel(ctx, tickets[-1])
+        t0 = time.time()
+        while True:
+            try:
+                st, _ = cho.cho_poll(ctx, tickets[-1], 2048)
+            except cho.ChoError as e:
+                assert e.status == cho.CHO_ECANCELLED
+                break
+            assert st == cho.CHO_PENDING
+            assert time.time() - t0 < 5.0
+            time.sleep(0.001)
+        first, _ = cho.cho_poll(ctx, tickets[0], 2048)
+        assert first == cho.CHO_PENDING              # the running requests are not through yet
+        wait_all(ctx, tickets[:-1], [2048] * 7)
+    finally:
+        cho.cho_destroy_system(sys_)
+        cho.cho_shutdown(ctx)
