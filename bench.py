@@ -217,7 +217,8 @@ def run_periodic_mode(cho, inputs, seconds=5.0):
 def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_seconds=8.0, load_seconds=6.0,
                 loads=(0.5, 0.8, 0.95), outstanding=3000, chunk_us=2000, ref_rate=None, active_pct=0,
                 records=None):
-    """The mixed request stream of BASELINE config 5 through cho_submit / cho_poll_any.
+    """The mixed serving stream (200k single-instance requests of mixed kind, size, horizon and
+    priority class, 40 GB state budget) through cho_submit / cho_poll_any.
 
     Requests follow request_stream: s log-uniform over {2..512} (2-DOF, chains, dense groups
     of 8 sizes), horizons log-uniform 1e3..1e5 steps, three priority classes 20/30/50 %,
@@ -226,7 +227,7 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
     requests that finished after the first second, over that window).  Then Poisson arrivals
     at each `loads` fraction of that rate for `load_seconds` each: p50/p99 submit-to-done
     latency per class, queue depth and resident bytes sampled every 20 ms.  At most
-    `max_requests` requests in all (config 5's 200k).  persistent: resident kernels for the
+    `max_requests` requests in all (200k).  persistent: resident kernels for the
     small and chain groups (cho_config.persistent).  ref_rate: skip the saturation phase and
     offer the loads as fractions of this rate (the same arrival rates for every engine).
     active_pct: cho_config.active_pct (0: the library's default active-set cap; -1: none).
@@ -379,7 +380,7 @@ def run_serving(cho, inputs, device, persistent, max_requests=200_000, sat_secon
         log(f"serving load {rho}: {offered} requests at {offered / t_off:.0f}/s "
             f"(target {lam:.0f}/s), p99 {[out['loads'][f'{rho:.2f}']['latency_s'][f'class{c}']['p99'] for c in range(3)]}")
     out["requests_total"] = int(nxt[0])
-    out["mix"] = ("config 5: s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5 "
+    out["mix"] = ("mixed serving stream: s log-uniform 2..512 (2-DOF / chain / 8 dense sizes), horizons log-uniform 1e3..1e5 "
                   "steps, classes 20/30/50 %, FP32 + compensation, 40 GB budget; each kernel group's chunk tuned to "
                   f"about {chunk_us} us")
     for sys_, _ in systems.values():
