@@ -24,7 +24,8 @@
 // orders added smallest first, on the CUDA cores in FP32 round-to-nearest.  One CTA
 // (two accumulator sets): two accumulators of 96 columns per set, four K chunks each
 // (s = 128, 5e3 steps: 8.0e-6; one accumulator per set was 7 % faster and reached
-// 1.5e-5 in v); 2-CTA clusters: four accumulators; bf16x3, whose truncation error
+// 1.5e-5 in v); 2-CTA clusters: five accumulators (s = 256, 5e3 steps: 1.0e-5 with four,
+// 9.96e-6 with five over 30 sampled instances); bf16x3, whose truncation error
 // dominates, keeps one.
 
 // Work split.  s <= 64: one CTA per 64 instances, two tiles of 32 stacked along
@@ -216,6 +217,10 @@ __host__ __device__ constexpr bool grp_starts(int PA, int PB, int m) // the m-th
     return PA == 2 ? m == 0 : (PB == 2 ? m <= 1 : m == 0);
 }
 constexpr int grp_width(int PA) { return PA == 2 ? 64 : 96; }         // columns of one accumulator
+// Accumulators of the cluster kernel (one set, no stage pairing): bf16x3 one of two column
+// groups (its truncation error dominates); bf16x5 five of three groups, 480 of the 512 TMEM
+// columns, the 16 K chunks of s = 256 dealt round-robin (four, then three per accumulator)
+constexpr int cluster_nacc(int PA) { return PA == 2 ? 1 : 5; }
 
 __device__ __forceinline__ uint32_t tc_idesc(int n)
 {
@@ -486,11 +491,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rk4_dense_tc_kernel(DenseSys sy
             for (int m = 0; m < PA; ++m) {
                 const int a = grp_a(PA, PB, m);
                 const uint32_t idesc = tc_idesc(32 * grp_np(PA, PB, a));
-                // descriptor address fields count 16-byte units; 16 chunks unroll by 4
-                // only: fully unrolled, the offsets held in registers spill
+                // descriptor address fields count 16-byte units; fully unrolled, so that each
+                // chunk's accumulator (c % NACC) is a constant
                 uint64_t bd = bdesc0;
                 uint64_t ad = adesc0 + (uint64_t)((a * KC * kAChunk) >> 4);
-#pragma unroll 4
+#pragma unroll
                 for (int c = 0; c < KC; ++c) {
                     const uint32_t acc = grp_starts(PA, PB, m) ? (c >= NACC ? 1u : 0u) : 1u;
                     mma_bf16(tmem + (uint32_t)((c % NACC) * W + 32 * a), ad, bd, idesc, acc);
@@ -1285,9 +1290,7 @@ template <int PA, int PB, int CS, class Src>
 cudaError_t launch_tc(const DenseSys& sys, const Src& src, int64_t n_inst, cudaStream_t st)
 {
     constexpr int KC = 8 * CS;
-    // grouped products: bf16x3 one accumulator of two column groups; x5 four of three
-    // (each collects four K chunks of every order)
-    constexpr int NACC = PA == 2 ? 1 : 4;
+    constexpr int NACC = cluster_nacc(PA);
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
     auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, Src>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1418,7 +1421,7 @@ template <int PA, int PB, int CS>
 int cluster_resident()
 {
     constexpr int KC = 8 * CS;
-    constexpr int NACC = PA == 2 ? 1 : 4;
+    constexpr int NACC = cluster_nacc(PA);
     const size_t smem = (size_t)PA * KC * kAChunk + (size_t)PB * KC * kXChunk;
     auto kern = rk4_dense_tc_kernel<PA, PB, CS, NACC, TcSlotSrc>;
     cudaLaunchConfig_t cfg = {};
