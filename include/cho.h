@@ -299,7 +299,9 @@ void cho_destroy_system(cho_system sys);
  * CHAIN/TWO_DOF s > 32 -> rk4_chain; DENSE s > 32 with one shared parameter set ->
  * rk4_dense.  Errors: CHO_EINVAL, CHO_EUNSTABLE (omega_max * h > 2 sqrt 2 for some
  * instance; checked on host values only, i.e. for CHO_MEM_HOST or h_per_inst == 0),
- * CHO_ECUDA, CHO_ENOMEM.  CHO_MEM_DEVICE: asynchronous on `stream`. */
+ * CHO_ECUDA, CHO_ENOMEM.  CHO_MEM_DEVICE: asynchronous on `stream`.  CHO_MEM_HOST: the arrays
+ * are staged through the context's device workspace on `stream` (NULL: the legacy default
+ * stream) and the call returns once the results are in host memory. */
 cho_status cho_integrate_batch(cho_ctx* ctx, const cho_batch_desc* batch, void* stream);
 
 /* CUDA graphs.  With device arrays and h_per_inst = 1 (and not the dense polynomial form,

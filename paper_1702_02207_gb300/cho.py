@@ -342,7 +342,8 @@ def _batch(fn_name, ctx, system, x0, v0, h, n_steps, prec=CHO_FP64, ckpt_every=0
     b.x_out, b.v_out = _ptr(res["x"]), _ptr(res["v"])
     b.x_traj, b.v_traj = _ptr(res.get("x_traj")), _ptr(res.get("v_traj"))
     b.energy = _ptr(res.get("energy"))
-    st = _stream_ptr(stream) if device else None
+    # host arrays are staged on the caller's stream when one is given (NULL: the default stream)
+    st = _stream_ptr(stream) if (device or stream is not None) else None
     _check(getattr(load(), fn_name)(ctx, ctypes.byref(b), st))
     return res
 

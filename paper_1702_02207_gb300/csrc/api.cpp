@@ -651,12 +651,22 @@ static cho_status check_batch(const cho_batch_desc* b, const char* who, bool pla
             const bool per_set = sys->n_sys != 1 && b->h_per_inst;   // one h: check the largest omega
             const double w0 = b->h_per_inst ? sys->omegas[0] : sys->omega_max;
             const double* w = sys->omegas.data();
-            bool bad = false;
-            for (int64_t i = 0; i < nh; ++i) {
-                const double hv = b->h[i];
-                const double wv = per_set ? w[i] : w0;
-                bad |= !(hv > 0.0) | !(hv < INFINITY) | (wv * hv > lim);
+            const double* hp = b->h;
+            // count the step sizes out of range (a NaN fails every comparison), one plain loop
+            // per case so that each vectorises
+            int64_t nbad = 0;
+            if (per_set) {
+                for (int64_t i = 0; i < nh; ++i) {
+                    const double hv = hp[i];
+                    nbad += (int64_t)((hv > 0.0) & (hv < INFINITY) & (w[i] * hv <= lim)) ^ 1;
+                }
+            } else {
+                for (int64_t i = 0; i < nh; ++i) {
+                    const double hv = hp[i];
+                    nbad += (int64_t)((hv > 0.0) & (hv < INFINITY) & (w0 * hv <= lim)) ^ 1;
+                }
             }
+            const bool bad = nbad != 0;
             if (bad) {
                 for (int64_t i = 0; i < nh; ++i) {
                     const double hv = b->h[i];
