@@ -113,6 +113,47 @@ def test_host_and_device_memory_agree(ctx):
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v_traj"], b["v_traj"])
 
 
+@pytest.mark.parametrize("case", ["two_dof", "chain", "dense_tc", "dense_simt"])
+def test_pinned_and_pageable_host_arrays_agree_with_device_arrays(ctx, case):
+    """Host arrays, page-locked (as the benchmark's end-to-end call passes them) or pageable,
+    are staged through the context's workspace: the results, trajectories and energies are
+    bitwise those of device arrays, for every kernel family."""
+    import torch
+
+    if case == "two_dof":
+        cfg, prec = inputs.two_dof_batch(n_inst=5000, n_steps=400), "fp32_kahan"
+    elif case == "chain":
+        cfg, prec = inputs.chain_batch(n_inst=9, s=300, n_steps=400, seed=301), "fp32_kahan"
+    elif case == "dense_tc":
+        cfg, prec = inputs.dense_group(s=128, n_inst=70, n_steps=400, seed=128), "bf16x5"
+    else:
+        cfg, prec = inputs.dense_group(s=100, n_inst=20, n_steps=400, seed=100), "fp32_simt"
+    sys_ = make_system(ctx, cfg)
+    d = torch.device("cuda:0")
+    try:
+        n, s = cfg["x0"].shape
+        h = np.asarray(cfg["h"], dtype=np.float64).reshape(-1)
+        energy = case != "dense_tc"
+        ref = cho.cho_integrate_batch(ctx, sys_, torch.as_tensor(cfg["x0"], device=d),
+                                      torch.as_tensor(cfg["v0"], device=d), torch.as_tensor(h, device=d), 400, prec,
+                                      100, trajectory=True, energy=energy)
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        out = {"x": pin(np.zeros((n, s))), "v": pin(np.zeros((n, s))), "x_traj": pin(np.zeros((n, 4, s))),
+               "v_traj": pin(np.zeros((n, 4, s)))}
+        if energy:
+            out["energy"] = pin(np.zeros((n, 4)))
+        got = cho.cho_integrate_batch(ctx, sys_, pin(cfg["x0"]), pin(cfg["v0"]), pin(h), 400, prec, 100,
+                                      trajectory=True, energy=energy, out=out)
+        staged = cho.cho_integrate_batch(ctx, sys_, cfg["x0"], cfg["v0"], h, 400, prec, 100, trajectory=True,
+                                         energy=energy)
+        for key in ("x", "v", "x_traj", "v_traj") + (("energy",) if energy else ()):
+            r = ref[key].cpu().numpy()
+            assert np.array_equal(np.asarray(got[key]), r), key
+            assert np.array_equal(np.asarray(staged[key]), r), key
+    finally:
+        cho.cho_destroy_system(sys_)
+
+
 # ---- small systems (rk4_small) ----------------------------------------------------------
 
 @pytest.mark.parametrize("s", [1, 3, 4, 5, 8, 9, 16, 17, 31, 32])
