@@ -46,10 +46,12 @@
 // its MMAs run.  A stage here issues 24 MMAs (bf16x5, s = 128: 8 K chunks x 3 grouped
 // products of N = 64, 64 and 32), about 1,080 cycles a stage (40 MMAs of N = 32 before
 // the grouping: 1,800), and the epilogue (TMEM loads, FP32 sums, stage update,
-// publishing Xs, barrier) about 1,700 more.  Wider tiles would need the state of 64 instances per SM,
-// which fits neither the register file nor tensor memory beside eight
-// accumulators; a warp that only issues MMAs would leave the others 96 registers
-// (the thread count rounds up to 640 for register allocation).
+// publishing Xs, barrier) runs on packed pairs of instances (FADD2 / FFMA2).  Wider tiles
+// would need the state of 64 instances per SM, which fits neither the register file nor
+// tensor memory beside the accumulators.  A warp that only issues MMAs was measured slower
+// in both forms tried: with setmaxnreg (the epilogue then spilled) and with 17 warps and
+// the state in tensor memory (the mbarrier hand-over and the state traffic cost more than
+// the issuing thread's wait).
 //
 // Per CTA: 16 warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of its
 // 128-row block) and columns 8 (w / 4) .. +7 (instances); each thread keeps the
