@@ -27,6 +27,8 @@
 namespace cho {
 namespace {
 
+constexpr int kChainUnroll = 2;   // steps per pass of the packed kernel's step loop
+
 // Batch form: coefficient set per instance or shared; FP64 in and out.
 template <bool F64>
 struct ChainBatchSrc {
@@ -167,21 +169,25 @@ struct ChainSlotSrc {
 
 // One instance per CTA: the work of instance q (the kernel's CTA blockIdx.x, or an item
 // of a persistent kernel's generation).
-template <int P, bool F64, class Src>
+template <int P, bool F64, int MAXT, class Src>
 __device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
 {
     using Real = std::conditional_t<F64, double, float>;
-    __shared__ Real edge_last[2][32][32];   // last DOF of every thread, [buffer][warp][lane]
-    __shared__ Real edge_first[2][32][32];  // first DOF of every thread
+    // edge displacements, [buffer][slot]: thread t stores its last DOF in edge_last[.][t + 1]
+    // and its first in edge_first[.][t]; edge_last[.][0] (the wall) and
+    // edge_first[.][blockDim.x] (past the free end) stay zero
+    __shared__ Real edge_last[2][MAXT + 1];
+    __shared__ Real edge_first[2][MAXT + 1];
     __shared__ int any_bad;
 
     const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int warp = t >> 5;
-    const int nwarp = blockDim.x >> 5;
     const int s = src.s(q);
     const int i0 = t * P;
-    if (t == 0) any_bad = 0;
+    if (t == 0) {
+        any_bad = 0;
+        edge_last[0][0] = edge_last[1][0] = (Real)0;
+        edge_first[0][blockDim.x] = edge_first[1][blockDim.x] = (Real)0;
+    }
     __syncthreads();
 
     // coefficients of DOFs i0 .. i0+P-1 (zero beyond s: padded DOFs stay at rest)
@@ -225,26 +231,17 @@ __device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
     }
 
     int buf = 0;
-    // neighbours across warp edges come from shared memory: every lane stores its
-    // edge values (no lane-dependent branch), then reads its neighbour warp's edge
-    // lane as a broadcast and selects
-    const int wl = warp > 0 ? warp - 1 : 0;
-    const int wr = warp + 1 < nwarp ? warp + 1 : warp;
-    const Real has_left = warp > 0 ? (Real)1 : (Real)0;
-    const Real has_right = warp + 1 < nwarp ? (Real)1 : (Real)0;
     // FP32: the lo parts of g and u multiply the stage-1 extensions and the sum is
     // reused by stages 2-4 (frozen lo, as in rk4_small.cu).
     float lo1[P];
+    // the neighbours' edge displacements come through shared memory: one store and one
+    // load per side and stage, the zero slots standing in for the wall and the free end
     auto accel = [&](const Real (&xs)[P], Real (&acc)[P], bool first) {
-        const Real up = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
-        const Real dn = __shfl_down_sync(0xffffffffu, xs[0], 1);
-        edge_last[buf][warp][lane] = xs[P - 1];
-        edge_first[buf][warp][lane] = xs[0];
+        edge_last[buf][t + 1] = xs[P - 1];
+        edge_first[buf][t] = xs[0];
         __syncthreads();
-        const Real el = edge_last[buf][wl][31] * has_left;
-        const Real ef = edge_first[buf][wr][0] * has_right;
-        const Real left = lane == 0 ? el : up;
-        const Real right = lane == 31 ? ef : dn;
+        const Real left = edge_last[buf][t];
+        const Real right = edge_first[buf][t + 1];
         buf ^= 1;
         Real e[P + 1];                       // spring extensions e_{i0} .. e_{i0+P}
         e[0] = xs[0] - left;
@@ -273,7 +270,8 @@ __device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
             accel(x, a, true);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                kx[p] = v[p];
+                if constexpr (F64) kx[p] = v[p];
+                else kx[p] = fmar((Real)2, v[p], cx[p]);   // FP32: the x sum starts on its compensation
                 kv[p] = a[p];
                 xs[p] = fmar(c_half, v[p], x[p]);
                 vs[p] = fmar(c_half, a[p], v[p]);
@@ -292,18 +290,21 @@ __device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
                 kx[p] = fmar((Real)2, vs[p], kx[p]);
                 kv[p] = fmar((Real)2, a[p], kv[p]);
                 xs[p] = fmar(c_full, vs[p], x[p]);
-                vs[p] = fmar(c_full, a[p], v[p]);
+                // FP32: the stage-4 velocity v + 6 a3 enters only the x sum, which takes 2v + 6 a3
+                if constexpr (F64) vs[p] = fmar(c_full, a[p], v[p]);
+                else kx[p] = fmar(c_full, a[p], kx[p]);
             }
             accel(xs, a, false);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                kx[p] = addr(kx[p], vs[p]);
-                kv[p] = addr(kv[p], a[p]);
                 if constexpr (F64) {
+                    kx[p] = addr(kx[p], vs[p]);
+                    kv[p] = addr(kv[p], a[p]);
                     state_update<true>(x[p], cx[p], kx[p], hs);
                     state_update<true>(v[p], cv[p], kv[p], hs);
                 } else {
-                    comp_add(x[p], cx[p], kx[p]);
+                    kv[p] = addr(kv[p], a[p]);
+                    comp_add_folded(x[p], cx[p], kx[p]);
                     comp_add(v[p], cv[p], kv[p]);
                 }
             }
@@ -331,7 +332,7 @@ __device__ __forceinline__ void rk4_chain_body(const Src& src, int64_t q)
 template <int P, bool F64, int MAXT, class Src>
 __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
 {
-    rk4_chain_body<P, F64>(src, blockIdx.x);
+    rk4_chain_body<P, F64, MAXT>(src, blockIdx.x);
 }
 
 // FP32 with P >= 2 DOFs per thread in packed FP32x2 arithmetic: the step of
@@ -341,22 +342,37 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_kernel(const Src src)
 // E_k = (e_k, e_{k+P/2}) = X_k - X_{k-1}, and leaves two pairs per stage to assemble
 // from scalars: (left neighbour, x_{P/2-1}) for E_0 and (x_{P/2}, right neighbour)
 // for E_{P/2}.  Packing halves the FP32 instructions the stage issues.
-template <int P, class Src>
+//
+// PAIR: the four stage accelerations are formed two at a time.  For x'' = -B x the
+// stage-2 displacement x + (h/2) v does not depend on a1, nor the stage-4
+// displacement x + h (v + (h/2) a2) on a3, so {a1, a2} and then {a3, a4} are
+// independent pairs: one neighbour exchange and one barrier serve two stages, and
+// each thread has twice the independent work between barriers.  Every value keeps
+// its operations and their order, so the bits are those of the stage-by-stage form.
+// The paired form needs about 2P more registers; CTAs wider than 256 threads (64
+// registers a thread) run stage by stage.
+template <int P, bool PAIR, int MAXT, class Src>
 __device__ __forceinline__ void rk4_chain_pk_body(const Src& src, int64_t q)
 {
     static_assert(P >= 2 && P % 2 == 0, "pairs of DOFs");
     constexpr int H = P / 2;
-    __shared__ float edge_last[2][32][32];   // last DOF of every thread, [buffer][warp][lane]
-    __shared__ float edge_first[2][32][32];  // first DOF of every thread
+    constexpr int NS = PAIR ? 2 : 1;          // stages evaluated per exchange
+    using Edge = std::conditional_t<PAIR, float2, float>;   // one value per stage in flight
+    // edge displacements, [buffer][slot]: thread t stores its last DOF in edge_last[.][t + 1]
+    // and its first in edge_first[.][t]; edge_last[.][0] (the wall) and
+    // edge_first[.][blockDim.x] (past the free end) stay zero
+    __shared__ Edge edge_last[2][MAXT + 1];
+    __shared__ Edge edge_first[2][MAXT + 1];
     __shared__ int any_bad;
 
     const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int warp = t >> 5;
-    const int nwarp = blockDim.x >> 5;
     const int s = src.s(q);
     const int i0 = t * P;
-    if (t == 0) any_bad = 0;
+    if (t == 0) {
+        any_bad = 0;
+        edge_last[0][0] = edge_last[1][0] = Edge{};
+        edge_first[0][blockDim.x] = edge_first[1][blockDim.x] = Edge{};
+    }
     __syncthreads();
 
     // coefficients, negated g (zero beyond s: padded DOFs stay at rest)
@@ -405,85 +421,138 @@ __device__ __forceinline__ void rk4_chain_pk_body(const Src& src, int64_t q)
     }
 
     int buf = 0;
-    const int wl = warp > 0 ? warp - 1 : 0;
-    const int wr = warp + 1 < nwarp ? warp + 1 : warp;
-    const float has_left = warp > 0 ? 1.f : 0.f;
-    const float has_right = warp + 1 < nwarp ? 1.f : 0.f;
     float2 lo1[H];   // lo parts of g and u times the stage-1 extensions (frozen lo)
-    // The extensions and accelerations of the interior pairs use only this thread's
-    // displacements: they are formed before the barrier, while the edge values travel.
-    auto accel = [&](const float2 (&xs)[H], float2 (&acc)[H], bool first) {
-        const float up = __shfl_up_sync(0xffffffffu, xs[H - 1].y, 1);
-        const float dn = __shfl_down_sync(0xffffffffu, xs[0].x, 1);
-        edge_last[buf][warp][lane] = xs[H - 1].y;
-        edge_first[buf][warp][lane] = xs[0].x;
-        float2 e[H + 1];                     // e[k] = (e_k, e_{k+H}); e[H] = (e_H, e_P)
+    auto edge_of = [](const Edge& v, int j) -> float {
+        if constexpr (PAIR) return j == 0 ? v.x : v.y;
+        else return v;
+    };
+    // Accelerations of NS stages, xs[j] their displacements (xs[0] = x when first).
+    // The neighbours' edge displacements come through shared memory (one store and one
+    // load per side for the NS stages).  The extensions and accelerations of the interior
+    // pairs use only this thread's displacements: they are formed before the barrier.
+    auto accel = [&](const float2 (&xs)[NS][H], float2 (&acc)[NS][H], bool first) {
+        if constexpr (PAIR) {
+            edge_last[buf][t + 1] = make_float2(xs[0][H - 1].y, xs[1][H - 1].y);
+            edge_first[buf][t] = make_float2(xs[0][0].x, xs[1][0].x);
+        } else {
+            edge_last[buf][t + 1] = xs[0][H - 1].y;
+            edge_first[buf][t] = xs[0][0].x;
+        }
+        float2 e[NS][H + 1];                 // e[j][k] = (e_k, e_{k+H}); e[j][H] = (e_H, e_P)
 #pragma unroll
-        for (int k = 1; k < H; ++k) e[k] = __ffma2_rn(xs[k - 1], m1, xs[k]);
+        for (int j = 0; j < NS; ++j)
+#pragma unroll
+            for (int k = 1; k < H; ++k) e[j][k] = __ffma2_rn(xs[j][k - 1], m1, xs[j][k]);
 #pragma unroll
         for (int k = 1; k + 1 < H; ++k) {
-            if (first) lo1[k] = __ffma2_rn(ul[k], e[k + 1], __fmul2_rn(ngl[k], e[k]));
-            acc[k] = __ffma2_rn(uh[k], e[k + 1], __ffma2_rn(ngh[k], e[k], lo1[k]));
+            if (first) lo1[k] = __ffma2_rn(ul[k], e[0][k + 1], __fmul2_rn(ngl[k], e[0][k]));
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                acc[j][k] = __ffma2_rn(uh[k], e[j][k + 1], __ffma2_rn(ngh[k], e[j][k], lo1[k]));
         }
         __syncthreads();
-        const float el = edge_last[buf][wl][31] * has_left;
-        const float ef = edge_first[buf][wr][0] * has_right;
-        const float left = lane == 0 ? el : up;
-        const float right = lane == 31 ? ef : dn;
+        const Edge l = edge_last[buf][t];          // thread t - 1's last DOF (zero at the wall)
+        const Edge r = edge_first[buf][t + 1];     // thread t + 1's first DOF
         buf ^= 1;
-        e[0] = __ffma2_rn(make_float2(left, xs[H - 1].x), m1, xs[0]);
-        e[H] = __ffma2_rn(xs[H - 1], m1, make_float2(xs[0].y, right));
+        // the two boundary pairs (e_0, e_H) and (e_H, e_P) from scalar differences (the
+        // values of the packed lanes; no pair of operands to assemble)
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const float e0 = __fsub_rn(xs[j][0].x, edge_of(l, j));
+            const float eH = __fsub_rn(xs[j][0].y, xs[j][H - 1].x);
+            const float eP = __fsub_rn(edge_of(r, j), xs[j][H - 1].y);
+            e[j][0] = make_float2(e0, eH);
+            e[j][H] = make_float2(eH, eP);
+        }
 #pragma unroll
         for (int k = 0; k < H; k += (H > 1 ? H - 1 : 1)) {
-            if (first) lo1[k] = __ffma2_rn(ul[k], e[k + 1], __fmul2_rn(ngl[k], e[k]));
-            acc[k] = __ffma2_rn(uh[k], e[k + 1], __ffma2_rn(ngh[k], e[k], lo1[k]));
+            if (first) lo1[k] = __ffma2_rn(ul[k], e[0][k + 1], __fmul2_rn(ngl[k], e[0][k]));
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                acc[j][k] = __ffma2_rn(uh[k], e[j][k + 1], __ffma2_rn(ngh[k], e[j][k], lo1[k]));
         }
     };
-    // compensated x += k
-    auto comp_add2 = [&](float2& xx, float2& ee, float2 kk) {
-        const float2 y = __fadd2_rn(kk, ee);
+    // compensated x += y, y already holding the compensation (comp_add_folded)
+    auto comp_add2_folded = [&](float2& xx, float2& ee, float2 y) {
         const float2 tt = __fadd2_rn(xx, y);
         ee = __ffma2_rn(__ffma2_rn(xx, m1, tt), m1, y);     // y - (t - x)
         xx = tt;
     };
+    // compensated x += k (comp_add)
+    auto comp_add2 = [&](float2& xx, float2& ee, float2 kk) { comp_add2_folded(xx, ee, __fadd2_rn(kk, ee)); };
 
     const int64_t n = src.steps(q);
     const int64_t every = src.ckpt_every() > 0 ? src.ckpt_every() : (n > 0 ? n : 1);
     int64_t ck = 0;
     for (int64_t done = 0; done < n; done += every) {
-        repeat_steps(every, [&]() {
-            float2 a[H], xs[H], kx[H], kv[H], vs[H];
-            accel(x, a, true);
+        // The x sum starts on its compensation and takes the stage-4 velocity v + 6 a3 as
+        // 2v + 6 a3 (the stage-4 velocity enters nothing else): kx = 2v + cx + 2 vs2 + 2 vs3
+        // + 6 a3, and the update adds it to x without a further sum (comp_add_folded).
+        repeat_steps<kChainUnroll>(every, [&]() {
+            float2 xs[NS][H], a[NS][H], kx[H], kv[H];
+            if constexpr (PAIR) {
+                // stages 1 and 2: a1 = A(x), a2 = A(x + 3v)
 #pragma unroll
-            for (int k = 0; k < H; ++k) {
-                kx[k] = v[k];
-                kv[k] = a[k];
-                xs[k] = __ffma2_rn(three, v[k], x[k]);
-                vs[k] = __ffma2_rn(three, a[k], v[k]);
-            }
-            accel(xs, a, false);
+                for (int k = 0; k < H; ++k) {
+                    xs[0][k] = x[k];
+                    xs[1][k] = __ffma2_rn(three, v[k], x[k]);
+                }
+                accel(xs, a, true);
+                // stages 3 and 4: a3 = A(x + 3 vs2), a4 = A(x + 6 vs3)
 #pragma unroll
-            for (int k = 0; k < H; ++k) {
-                kx[k] = __ffma2_rn(two, vs[k], kx[k]);
-                kv[k] = __ffma2_rn(two, a[k], kv[k]);
-                xs[k] = __ffma2_rn(three, vs[k], x[k]);
-                vs[k] = __ffma2_rn(three, a[k], v[k]);
-            }
-            accel(xs, a, false);
+                for (int k = 0; k < H; ++k) {
+                    const float2 vs2 = __ffma2_rn(three, a[0][k], v[k]);
+                    const float2 vs3 = __ffma2_rn(three, a[1][k], v[k]);
+                    kx[k] = __ffma2_rn(two, vs2, __ffma2_rn(two, v[k], cx[k]));
+                    kv[k] = __ffma2_rn(two, a[1][k], a[0][k]);
+                    kx[k] = __ffma2_rn(two, vs3, kx[k]);
+                    xs[0][k] = __ffma2_rn(three, vs2, x[k]);
+                    xs[1][k] = __ffma2_rn(six, vs3, x[k]);
+                }
+                accel(xs, a, false);
 #pragma unroll
-            for (int k = 0; k < H; ++k) {
-                kx[k] = __ffma2_rn(two, vs[k], kx[k]);
-                kv[k] = __ffma2_rn(two, a[k], kv[k]);
-                xs[k] = __ffma2_rn(six, vs[k], x[k]);
-                vs[k] = __ffma2_rn(six, a[k], v[k]);
-            }
-            accel(xs, a, false);
+                for (int k = 0; k < H; ++k) {
+                    kx[k] = __ffma2_rn(six, a[0][k], kx[k]);
+                    kv[k] = __ffma2_rn(two, a[0][k], kv[k]);
+                    kv[k] = __fadd2_rn(kv[k], a[1][k]);
+                    comp_add2_folded(x[k], cx[k], kx[k]);
+                    comp_add2(v[k], cv[k], kv[k]);
+                }
+            } else {
+                float2 vs[H];
 #pragma unroll
-            for (int k = 0; k < H; ++k) {
-                kx[k] = __fadd2_rn(kx[k], vs[k]);
-                kv[k] = __fadd2_rn(kv[k], a[k]);
-                comp_add2(x[k], cx[k], kx[k]);
-                comp_add2(v[k], cv[k], kv[k]);
+                for (int k = 0; k < H; ++k) xs[0][k] = x[k];
+                accel(xs, a, true);
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    kx[k] = __ffma2_rn(two, v[k], cx[k]);
+                    kv[k] = a[0][k];
+                    xs[0][k] = __ffma2_rn(three, v[k], x[k]);
+                    vs[k] = __ffma2_rn(three, a[0][k], v[k]);
+                }
+                accel(xs, a, false);
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    kx[k] = __ffma2_rn(two, vs[k], kx[k]);
+                    kv[k] = __ffma2_rn(two, a[0][k], kv[k]);
+                    xs[0][k] = __ffma2_rn(three, vs[k], x[k]);
+                    vs[k] = __ffma2_rn(three, a[0][k], v[k]);
+                }
+                accel(xs, a, false);
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    kx[k] = __ffma2_rn(two, vs[k], kx[k]);
+                    kv[k] = __ffma2_rn(two, a[0][k], kv[k]);
+                    xs[0][k] = __ffma2_rn(six, vs[k], x[k]);
+                    kx[k] = __ffma2_rn(six, a[0][k], kx[k]);
+                }
+                accel(xs, a, false);
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    kv[k] = __fadd2_rn(kv[k], a[0][k]);
+                    comp_add2_folded(x[k], cx[k], kx[k]);
+                    comp_add2(v[k], cv[k], kv[k]);
+                }
             }
         });
         if (src.ckpt_every() > 0) {
@@ -512,10 +581,12 @@ __device__ __forceinline__ void rk4_chain_pk_body(const Src& src, int64_t q)
     if (t == 0) src.finish(q, n, any_bad != 0);
 }
 
+// At most 128 registers a thread for CTAs of up to 256 threads: the paired body keeps
+// four 128-thread CTAs (16 warps) on an SM without spilling.
 template <int P, int MAXT, class Src>
-__global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1) rk4_chain_pk_kernel(const Src src)
 {
-    rk4_chain_pk_body<P>(src, blockIdx.x);
+    rk4_chain_pk_body<P, (MAXT <= 256), MAXT>(src, blockIdx.x);
 }
 
 // Persistent form for the serving engine: the generation loop of persist.cuh around the
@@ -523,15 +594,15 @@ __global__ void __launch_bounds__(MAXT) rk4_chain_pk_kernel(const Src src)
 // one generation item per CTA in turn.  The CTA has the thread count of the size class
 // (64 threads for P = 1, 2, 4: s < 256; 256 for P = 8: s <= 2048).
 template <int P, bool F64, int MAXT>
-__global__ void __launch_bounds__(MAXT) rk4_chain_persist_kernel(const PersistIO pio)
+__global__ void __launch_bounds__(MAXT, (!F64 && P >= 2) ? 2 : 1) rk4_chain_persist_kernel(const PersistIO pio)
 {
     persist_loop(pio, [&](int64_t n, int64_t chunk) {
         ChainSlotSrc<F64, true> src;
         src.io = SlotIO{n, pio.slot_ids, pio.slots, pio.status, chunk};
         src.pio = &pio;
         for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
-            if constexpr (!F64 && P >= 2) rk4_chain_pk_body<P>(src, q);
-            else rk4_chain_body<P, F64>(src, q);
+            if constexpr (!F64 && P >= 2) rk4_chain_pk_body<P, true, MAXT>(src, q);
+            else rk4_chain_body<P, F64, MAXT>(src, q);
         }
     });
 }

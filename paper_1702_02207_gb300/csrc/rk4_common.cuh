@@ -31,6 +31,15 @@ __device__ __forceinline__ void comp_add(float& x, float& e, float k)
     x = t;
 }
 
+// Compensated x += y in FP32 where y already holds the compensation e (the increment
+// was summed onto e): the last two steps of comp_add.
+__device__ __forceinline__ void comp_add_folded(float& x, float& e, float y)
+{
+    const float t = __fadd_rn(x, y);
+    e = __fsub_rn(y, __fsub_rn(t, x));
+    x = t;
+}
+
 // FP32 small systems integrate the scaled velocity u = (h/6) v (scaled_velocity,
 // cho_internal.h) with the scaled iteration matrix B'' = (h^2/36) B, an FP32 pair
 // formed from B's pair in FP64: then h/2 v = 3 u and h v = 6 u, and the state update
@@ -220,12 +229,13 @@ __device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t ba
 }
 
 // Run f() n times with a 32-bit inner counter (64-bit compares cost extra
-// instructions and a branch every step).
-template <class F>
+// instructions and a branch every step), the inner loop unrolled U times.
+template <int U = 1, class F>
 __device__ __forceinline__ void repeat_steps(int64_t n, F&& f)
 {
     for (int64_t base = 0; base < n; base += 0x40000000LL) {
         const int32_t m = (int32_t)(n - base < 0x40000000LL ? n - base : 0x40000000LL);
+#pragma unroll U
         for (int32_t i = 0; i < m; ++i) f();
     }
 }

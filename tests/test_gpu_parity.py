@@ -1072,7 +1072,8 @@ def _device_run(ctx, sys_, cfg, prec, n_steps):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("case", ["two_dof", "chain_fp32", "chain_fp32_s40", "chain_fp64", "dense_fp32"])
+@pytest.mark.parametrize("case", ["two_dof", "chain_fp32", "chain_fp32_s40", "chain_fp32_s200", "chain_fp64",
+                                  "dense_fp32"])
 def test_autotune_chooses_among_same_bit_kernels(tmp_path, case):
     """cho_autotune times every candidate kernel of the shape; all give the bits of the first,
     the fastest is recorded, later batches of the shape use it (same bits as an untuned
@@ -1082,6 +1083,11 @@ def test_autotune_chooses_among_same_bit_kernels(tmp_path, case):
     elif case == "chain_fp32_s40":
         # 1 DOF per thread (the default, scalar FP32) against 2, 4 and 8 (packed FP32x2 pairs)
         cfg, prec, n_cand = inputs.chain_batch(n_inst=64, s=40, n_steps=200), "fp32_kahan", 4
+    elif case == "chain_fp32_s200":
+        # 4 DOFs per thread (the default: 2 warps) against the scalar kernel on 7 warps and the
+        # packed kernel at 2 (4 warps) and 8 (1 warp): the packed kernels evaluate two stages per
+        # neighbour exchange, the scalar kernel one, and the warp-edge exchange differs in each
+        cfg, prec, n_cand = inputs.chain_batch(n_inst=64, s=200, n_steps=200), "fp32_kahan", 4
     elif case.startswith("chain"):
         cfg = inputs.chain_batch(n_inst=64, s=300, n_steps=200)
         prec, n_cand = ("fp32_kahan" if case == "chain_fp32" else "fp64"), 3     # 8 (default), 2, 4 DOFs per thread
