@@ -301,7 +301,8 @@ __device__ __forceinline__ void rk4_small_body(const Src& src, int64_t cta)
             accel(x, a, true);                             // stage 1
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                kx[r] = v[r];
+                if constexpr (F64) kx[r] = v[r];
+                else kx[r] = fmar((Real)2, v[r], cx[r]);   // FP32: the x sum starts on its compensation
                 kv[r] = a[r];
                 xs[r] = fmar(c_half, v[r], x[r]);
                 vs[r] = fmar(c_half, a[r], v[r]);
@@ -320,18 +321,21 @@ __device__ __forceinline__ void rk4_small_body(const Src& src, int64_t cta)
                 kx[r] = fmar((Real)2, vs[r], kx[r]);
                 kv[r] = fmar((Real)2, a[r], kv[r]);
                 xs[r] = fmar(c_full, vs[r], x[r]);
-                vs[r] = fmar(c_full, a[r], v[r]);
+                // FP32: the stage-4 velocity v + 6 a3 enters only the x sum, which takes 2v + 6 a3
+                if constexpr (F64) vs[r] = fmar(c_full, a[r], v[r]);
+                else kx[r] = fmar(c_full, a[r], kx[r]);
             }
             accel(xs, a, false);                           // stage 4
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                kx[r] = addr(kx[r], vs[r]);
-                kv[r] = addr(kv[r], a[r]);
                 if constexpr (F64) {
+                    kx[r] = addr(kx[r], vs[r]);
+                    kv[r] = addr(kv[r], a[r]);
                     state_update<true>(x[r], cx[r], kx[r], hs);
                     state_update<true>(v[r], cv[r], kv[r], hs);
                 } else {
-                    comp_add(x[r], cx[r], kx[r]);          // the scaled sums are the increments
+                    kv[r] = addr(kv[r], a[r]);
+                    comp_add_folded(x[r], cx[r], kx[r]);   // the scaled sums are the increments
                     comp_add(v[r], cv[r], kv[r]);
                 }
             }
@@ -415,15 +419,17 @@ constexpr int kPairThreads = 32;
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Compensated x += k (the increment without a step-size factor).
-__device__ __forceinline__ void pair_add(float2& x, float2& e, float2 k)
+// x += y with y already holding the compensation (comp_add_folded on both lanes).
+__device__ __forceinline__ void pair_add_folded(float2& x, float2& e, float2 y)
 {
     const float2 m1 = f2(-1.f, -1.f);
-    const float2 y = __fadd2_rn(k, e);
     const float2 t = __fadd2_rn(x, y);
     const float2 d = __ffma2_rn(x, m1, t);       // t - x
     e = __ffma2_rn(d, m1, y);                    // y - (t - x)
     x = t;
 }
+
+__device__ __forceinline__ void pair_add(float2& x, float2& e, float2 k) { pair_add_folded(x, e, __fadd2_rn(k, e)); }
 
 // State of two 2-DOF instances held by one thread (lanes .x and .y of every
 // float2): x, v and their compensations, FP32.  An odd instance count repeats
@@ -563,40 +569,38 @@ struct Pair2 : Pair2State {
             a[r] = __ffma2_rn(nbh[r][1 - r], xs[1 - r], acc);
         }
     }
+    // The stage accelerations two at a time: stage 2's displacement x + 3u does not
+    // depend on a1, nor stage 4's x + 6 (u + 3 a2) on a3, so {a1, a2} and {a3, a4} are
+    // independent pairs (twice the independent work for the one warp of the
+    // sub-partition).  Every value keeps its operations and their order.  The x sum
+    // starts on its compensation and takes the stage-4 velocity u + 6 a3 as 2u + 6 a3
+    // (as rk4_small_kernel in FP32).
     __device__ __forceinline__ void step()
     {
         const float2 two = f2(2.f, 2.f), three = f2(3.f, 3.f), six = f2(6.f, 6.f);
-        float2 a[2], xs[2], kx[2], kv[2], vs[2], lo[2];
-        accel(x, a, lo, true);
+        float2 a1[2], a2[2], xs[2], xt[2], kx[2], kv[2], lo[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) xs[r] = __ffma2_rn(three, v[r], x[r]);
+        accel(x, a1, lo, true);
+        accel(xs, a2, lo, false);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            kx[r] = v[r];
-            kv[r] = a[r];
-            xs[r] = __ffma2_rn(three, v[r], x[r]);
-            vs[r] = __ffma2_rn(three, a[r], v[r]);
+            const float2 vs2 = __ffma2_rn(three, a1[r], v[r]);
+            const float2 vs3 = __ffma2_rn(three, a2[r], v[r]);
+            kx[r] = __ffma2_rn(two, vs2, __ffma2_rn(two, v[r], ex[r]));
+            kv[r] = __ffma2_rn(two, a2[r], a1[r]);
+            kx[r] = __ffma2_rn(two, vs3, kx[r]);
+            xs[r] = __ffma2_rn(three, vs2, x[r]);
+            xt[r] = __ffma2_rn(six, vs3, x[r]);
         }
-        accel(xs, a, lo, false);
+        accel(xs, a1, lo, false);                // a3
+        accel(xt, a2, lo, false);                // a4
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            kx[r] = __ffma2_rn(two, vs[r], kx[r]);
-            kv[r] = __ffma2_rn(two, a[r], kv[r]);
-            xs[r] = __ffma2_rn(three, vs[r], x[r]);
-            vs[r] = __ffma2_rn(three, a[r], v[r]);
-        }
-        accel(xs, a, lo, false);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            kx[r] = __ffma2_rn(two, vs[r], kx[r]);
-            kv[r] = __ffma2_rn(two, a[r], kv[r]);
-            xs[r] = __ffma2_rn(six, vs[r], x[r]);
-            vs[r] = __ffma2_rn(six, a[r], v[r]);
-        }
-        accel(xs, a, lo, false);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            kx[r] = __fadd2_rn(kx[r], vs[r]);
-            kv[r] = __fadd2_rn(kv[r], a[r]);
-            pair_add(x[r], ex[r], kx[r]);
+            kx[r] = __ffma2_rn(six, a1[r], kx[r]);
+            kv[r] = __ffma2_rn(two, a1[r], kv[r]);
+            kv[r] = __fadd2_rn(kv[r], a2[r]);
+            pair_add_folded(x[r], ex[r], kx[r]);
             pair_add(v[r], ev[r], kv[r]);
         }
     }
