@@ -4,9 +4,9 @@
 //     m_i x_i'' = -C_i e_i + C_{i+1} e_{i+1} - c_i e_i' + c_{i+1} e_{i+1}' + F_i cos(omega t + phase),
 // e_i = x_i - x_{i-1} (e_0 = x_0, the wall), e_i' = v_i - v_{i-1}, nothing to the
 // right of the last mass.  The layout is rk4_chain's (one CTA per instance, P
-// consecutive DOFs per thread, neighbours by shuffle inside a warp and through a
-// double-buffered shared-memory edge array across warps); here each stage also
-// exchanges the stage velocities, and takes the force at its own time
+// consecutive DOFs per thread, the neighbours' edge values through a
+// double-buffered shared-memory slot array with one barrier per stage); here each
+// stage also exchanges the stage velocities, and takes the force at its own time
 // t, t + h/2, t + h/2, t + h.
 //
 // FP32: coefficients as FP32 pairs with the lo products of springs and dashpots
@@ -36,14 +36,13 @@ struct Phase32 {
         split_ff(c, hi, lo);
         split_ff(omega * h / two_pi, dhi, dlo);
     }
-    // cos(2 pi (phase + frac * step)) for frac = 0, 1/2, 1
-    __device__ __forceinline__ void cosines(float& f0, float& f1, float& f2) const
+    // cos(2 pi (phase + frac * step)) for frac = 0, 1/2, 1 (j = 0, 1, 2)
+    __device__ __forceinline__ float cosine(int j) const
     {
         const float r0 = __fadd_rn(hi, lo);
         const float d = __fadd_rn(dhi, dlo);
-        f0 = cospif(2.f * r0);
-        f1 = cospif(2.f * __fmaf_rn(0.5f, d, r0));
-        f2 = cospif(2.f * __fadd_rn(r0, d));
+        const float r = j == 0 ? r0 : (j == 1 ? __fmaf_rn(0.5f, d, r0) : __fadd_rn(r0, d));
+        return cospif(2.f * r);
     }
     __device__ __forceinline__ void advance()
     {
@@ -62,16 +61,22 @@ template <int P, bool F64>
 __global__ void __launch_bounds__(kExtThreads) rk4_chain_ext_kernel(const ChainExtSys sys, const BatchIO io)
 {
     using Real = std::conditional_t<F64, double, float>;
-    constexpr int NW = kExtThreads / 32;
-    __shared__ Real edge_xl[2][NW][32], edge_xf[2][NW][32];   // last / first stage displacement per thread
-    __shared__ Real edge_vl[2][NW][32], edge_vf[2][NW][32];   // last / first stage velocity per thread
+    struct XV {
+        Real x, v;
+    };
+    // stage displacement and velocity at the edges, [buffer][slot]: thread t stores its
+    // last DOF's in edge_l[.][t + 1] and its first DOF's in edge_f[.][t]; edge_l[.][0]
+    // (the wall) and edge_f[.][blockDim.x] (past the free end) stay zero
+    __shared__ XV edge_l[2][kExtThreads + 1], edge_f[2][kExtThreads + 1];
 
     const int64_t q = blockIdx.x;
     const int t = threadIdx.x;
     const int lane = t & 31;
-    const int warp = t >> 5;
-    const int nwarp = blockDim.x >> 5;
     const int s = sys.s;
+    if (t == 0) {
+        edge_l[0][0] = edge_l[1][0] = XV{0, 0};
+        edge_f[0][blockDim.x] = edge_f[1][blockDim.x] = XV{0, 0};
+    }
     const int i0 = t * P;
     const int64_t set = sys.per_inst_sys ? q : 0;
 
@@ -131,25 +136,16 @@ __global__ void __launch_bounds__(kExtThreads) rk4_chain_ext_kernel(const ChainE
     }
 
     int buf = 0;
-    const int wl_ = warp > 0 ? warp - 1 : 0;
-    const int wr_ = warp + 1 < nwarp ? warp + 1 : warp;
-    const Real has_left = warp > 0 ? (Real)1 : (Real)0;
-    const Real has_right = warp + 1 < nwarp ? (Real)1 : (Real)0;
     float lo1[P];
+    // the neighbours' edge values come through shared memory: one store and one load per
+    // side and stage, the zero slots standing in for the wall and the free end
     auto accel = [&](const Real (&xs)[P], const Real (&vs)[P], Real fst, Real (&acc)[P], bool first) {
-        const Real xup = __shfl_up_sync(0xffffffffu, xs[P - 1], 1);
-        const Real xdn = __shfl_down_sync(0xffffffffu, xs[0], 1);
-        const Real vup = __shfl_up_sync(0xffffffffu, vs[P - 1], 1);
-        const Real vdn = __shfl_down_sync(0xffffffffu, vs[0], 1);
-        edge_xl[buf][warp][lane] = xs[P - 1];
-        edge_xf[buf][warp][lane] = xs[0];
-        edge_vl[buf][warp][lane] = vs[P - 1];
-        edge_vf[buf][warp][lane] = vs[0];
+        edge_l[buf][t + 1] = XV{xs[P - 1], vs[P - 1]};
+        edge_f[buf][t] = XV{xs[0], vs[0]};
         __syncthreads();
-        const Real xleft = lane == 0 ? edge_xl[buf][wl_][31] * has_left : xup;
-        const Real xright = lane == 31 ? edge_xf[buf][wr_][0] * has_right : xdn;
-        const Real vleft = lane == 0 ? edge_vl[buf][wl_][31] * has_left : vup;
-        const Real vright = lane == 31 ? edge_vf[buf][wr_][0] * has_right : vdn;
+        const XV l = edge_l[buf][t];
+        const XV r_ = edge_f[buf][t + 1];
+        const Real xleft = l.x, vleft = l.v, xright = r_.x, vright = r_.v;
         buf ^= 1;
         Real e[P + 1], r[P + 1];                 // extensions and their rates
         e[0] = xs[0] - xleft;
@@ -188,19 +184,26 @@ __global__ void __launch_bounds__(kExtThreads) rk4_chain_ext_kernel(const ChainE
     const int64_t every = io.ckpt_every > 0 ? io.ckpt_every : (n > 0 ? n : 1);
     int64_t ck = 0;
     int64_t step = 0;
+    // the step's three force cosines: lane j of every warp evaluates cosine j, then all
+    // lanes take the three by shuffle (the same values as three evaluations per thread)
+    const int jc = lane < 3 ? lane : 0;
     for (int64_t done = 0; done < n; done += every) {
+#pragma unroll 2
         for (int64_t it = 0; it < every; ++it, ++step) {
             Real f0 = 0, f1 = 0, f2 = 0;
             if (forced) {
+                Real c;
                 if constexpr (F64) {
                     const double tn = (double)step * hd;
-                    f0 = cos(omega * tn + phase0);
-                    f1 = cos(omega * (tn + hd / 2.0) + phase0);
-                    f2 = cos(omega * (tn + hd) + phase0);
+                    const double tj = jc == 0 ? tn : (jc == 1 ? tn + hd / 2.0 : tn + hd);
+                    c = cos(omega * tj + phase0);
                 } else {
-                    ph32.cosines(f0, f1, f2);
+                    c = ph32.cosine(jc);
                     ph32.advance();
                 }
+                f0 = __shfl_sync(0xffffffffu, c, 0);
+                f1 = __shfl_sync(0xffffffffu, c, 1);
+                f2 = __shfl_sync(0xffffffffu, c, 2);
             }
             Real a[P], xs[P], kx[P], kv[P], vs[P];
             accel(x, v, f0, a, true);
