@@ -12,9 +12,11 @@
 // One CTA integrates one instance for the whole horizon.  Thread t owns P
 // consecutive DOFs [tP, tP + P) with their coefficients and state in
 // registers.  Per stage it needs one displacement from each neighbouring
-// thread: inside a warp these come by shuffle, across warps through a
-// double-buffered shared-memory edge array, so each stage costs a single
-// __syncthreads.  Stage order and the state update are those of rk4_small.cu.
+// thread: every thread stores its first and last displacement in a
+// double-buffered shared-memory slot array and, after the stage's single
+// __syncthreads, loads its neighbours' slots (zero slots stand for the wall
+// and for the space past the free end).  Stage order and the state update are
+// those of rk4_small.cu.
 //
 // Kernels: rk4_chain_kernel (FP64 at every P; FP32 at P = 1), rk4_chain_pk_kernel
 // (FP32 at P >= 2: the same operations on packed pairs of DOFs, the same bits) and
@@ -764,7 +766,7 @@ cudaError_t launch_any(const Src& src, int64_t n_inst, int s_max, cudaStream_t s
 }  // namespace
 
 // DOFs per thread: the most (up to 8) that still leaves a full warp, so that the
-// per-stage exchange (two shuffles, two shared-memory edge values, one barrier)
+// per-stage exchange (two shared-memory stores and loads, one barrier)
 // is shared by as many DOFs as possible.  s = 1024: 8 DOFs on 128 threads ran
 // 55.2 ms against 64.4 ms with 4 on 256 (4096 chains, 1e4 steps).  Up to s =
 // 2048 at most 256 threads; above, 8 DOFs per thread on up to 1024 threads.

@@ -5,7 +5,7 @@
 Cases (each one cho_integrate_batch call, a few MB of device memory):
   pair      65,536 two-DOF systems, 1e4 steps, fp32_kahan   (rk4_pair2_balanced, the benchmark launch)
   pair_dw   65,536 two-DOF systems, 2000 steps, fp32x2      (rk4_dw_small<2>, double-FP32)
-  chain     512 chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain<8>)
+  chain     512 chains of 1024 masses, 2000 steps, fp32_kahan (rk4_chain_pk<8>)
   chain_dw  512 chains of 1024 masses, 500 steps, fp32x2    (rk4_chain_dw<4>, double-FP32)
   dense_tc  s = 128, 2048 instances, 500 steps, bf16x5       (rk4_dense_tc, one CTA per SM)
   dense_tc64 s = 64, 4096 instances, 500 steps, bf16x5      (rk4_dense_tc, two tiles stacked per CTA)
